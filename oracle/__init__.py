@@ -1,0 +1,174 @@
+"""FP64 CPU oracle for the GMRT software backend's FX correlator and beamformer.
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package; the product path (``paper_0910_1517_gb300``) never does.  The
+arithmetic lives in ``fx_oracle.c`` (plain C, double precision, direct DFT);
+this module only builds it with gcc and marshals numpy arrays through ctypes.
+
+Functions and the passage each follows (Roy et al., arXiv:0910.1517):
+  fengine   -- integer delay, real DFT, FSTC + fringe phasor (Sec. 2.1, Eq. 2)
+  xengine   -- MAC over N(N+1)/2 baselines x n_pol^2 products (Sec. 2.1)
+  beams     -- incoherent and coherent array beams (Sec. 2.2, 4.3)
+  requant   -- 8-bit requantisation of spectra (precision form; Sec. 4.1 analogue)
+  xint      -- exact integer MAC on requantised spectra (Sec. 4.1)
+  mad_flag  -- median-absolute-deviation flagger (Sec. 5, Eq. 3-4)
+All of them are pinned by the ``-m "not gpu"`` tests in tests/test_oracle_*.py.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fx_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile fx_oracle.c into liboracle.so with gcc + OpenMP (no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call([
+            "gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+            "-std=c11", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        i32, i64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        L.oracle_fengine.argtypes = [i32, i32, i32, i32, P, i64, i64, P, P, P, i64, P, i32, P]
+        L.oracle_xengine.argtypes = [i32, i32, i32, i32, P, P]
+        L.oracle_beams.argtypes = [i32, i32, i32, i32, i32, P, P, P, P, P, P, i32, P]
+        L.oracle_requant.argtypes = [i32, i32, i32, P, P, P]
+        L.oracle_xint.argtypes = [i32, i32, i32, i32, P, P, P, P]
+        L.oracle_mad_flag.argtypes = [i32, P, f64, P, P, P]
+        L.oracle_threads.argtypes = []
+        L.oracle_n_baselines.argtypes = [i32]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed with code {rc}")
+
+
+def n_baselines(n_ant: int) -> int:
+    return n_ant * (n_ant + 1) // 2
+
+
+def threads() -> int:
+    return int(lib().oracle_threads())
+
+
+def fengine(x, n_ant, n_pol, n_fft, n_frames, delay, phi0, rate, g0=0, chans=None):
+    """Spectra Y[i][t][c] (complex128) after integer delay, DFT and the Eq. 2 phasor.
+
+    x: int8 [n_in][n_avail] (rows may be strided); delay/phi0/rate: per antenna.
+    """
+    x = np.asarray(x)
+    assert x.dtype == np.int8 and x.ndim == 2 and x.shape[0] == n_ant * n_pol
+    if x.strides[1] != 1:
+        x = np.ascontiguousarray(x)
+    d = np.ascontiguousarray(delay, dtype=np.float64)
+    f0 = np.ascontiguousarray(phi0, dtype=np.float64)
+    w = np.ascontiguousarray(rate, dtype=np.float64)
+    assert d.shape == f0.shape == w.shape == (n_ant,)
+    if chans is None:
+        ch, nch, chp = None, n_fft // 2, None
+    else:
+        ch = np.ascontiguousarray(chans, dtype=np.int32)
+        nch, chp = len(ch), _p(ch)
+    Y = np.zeros((n_ant * n_pol, n_frames, nch, 2), dtype=np.float64)
+    rc = lib().oracle_fengine(n_ant, n_pol, n_fft, n_frames, _p(x), x.strides[0], x.shape[1],
+                              _p(d), _p(f0), _p(w), int(g0), chp, nch, _p(Y))
+    _check(rc, "fengine")
+    return Y[..., 0] + 1j * Y[..., 1]
+
+
+def _as_ri(Y):
+    Y = np.asarray(Y)
+    out = np.empty(Y.shape + (2,), dtype=np.float64)
+    out[..., 0] = Y.real
+    out[..., 1] = Y.imag
+    return out
+
+
+def xengine(Y, n_ant, n_pol):
+    """Visibilities V[c][b][p*n_pol+q] (complex128), baselines a <= a' row-major."""
+    n_in, n_frames, nch = Y.shape
+    assert n_in == n_ant * n_pol
+    Yr = _as_ri(Y)
+    V = np.zeros((nch, n_baselines(n_ant), n_pol * n_pol, 2), dtype=np.float64)
+    _check(lib().oracle_xengine(n_ant, n_pol, nch, n_frames, _p(Yr), _p(V)), "xengine")
+    return V[..., 0] + 1j * V[..., 1]
+
+
+def beams(Y, n_ant, n_pol, n_fft, gain=None, theta=None, inc_mask=None, coh_mask=None,
+          beam_avg=1, chans=None):
+    """(B_inc, B_coh), each [n_frames/beam_avg][n_chans] float64."""
+    n_in, n_frames, nch = Y.shape
+    Yr = _as_ri(Y)
+    g = np.ones(n_ant) if gain is None else np.ascontiguousarray(gain, dtype=np.float64)
+    th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float64)
+    if th is not None:
+        assert th.shape == (n_ant, n_fft // 2)
+    im = np.ones(n_ant, np.uint8) if inc_mask is None else np.ascontiguousarray(inc_mask, dtype=np.uint8)
+    cm = np.ones(n_ant, np.uint8) if coh_mask is None else np.ascontiguousarray(coh_mask, dtype=np.uint8)
+    ch = None if chans is None else np.ascontiguousarray(chans, dtype=np.int32)
+    n_out = n_frames // beam_avg
+    B = np.zeros((2, n_out, nch), dtype=np.float64)
+    rc = lib().oracle_beams(n_ant, n_pol, n_fft, nch, n_frames, _p(Yr),
+                            None if ch is None else _p(ch), _p(g),
+                            None if th is None else _p(th), _p(im), _p(cm), beam_avg, _p(B))
+    _check(rc, "beams")
+    return B[0], B[1]
+
+
+def requant(Y, scale):
+    """q[i][t][c][2] int8 = clamp(rint(Y * s[i][c]), +-127) per real component."""
+    n_in, n_frames, nch = Y.shape
+    Yr = _as_ri(Y)
+    s = np.ascontiguousarray(scale, dtype=np.float64)
+    assert s.shape == (n_in, nch)
+    q = np.zeros(Yr.shape, dtype=np.int8)
+    _check(lib().oracle_requant(n_in, n_frames, nch, _p(Yr), _p(s), _p(q)), "requant")
+    return q
+
+
+def xint(q, scale, n_ant, n_pol):
+    """Exact integer visibilities (int64 [c][b][pp][2]) and their descaled FP64 values."""
+    q = np.ascontiguousarray(q, dtype=np.int8)
+    n_in, n_frames, nch, two = q.shape
+    assert two == 2 and n_in == n_ant * n_pol
+    s = np.ascontiguousarray(scale, dtype=np.float64)
+    nbl, npp = n_baselines(n_ant), n_pol * n_pol
+    Vi = np.zeros((nch, nbl, npp, 2), dtype=np.int64)
+    V = np.zeros((nch, nbl, npp, 2), dtype=np.float64)
+    _check(lib().oracle_xint(n_ant, n_pol, nch, n_frames, _p(q), _p(s), _p(Vi), _p(V)), "xint")
+    return Vi, V[..., 0] + 1j * V[..., 1]
+
+
+def mad_flag(x, M):
+    """(flags uint8 [n], median, MAD) per Eq. 3 and Eq. 4."""
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    f = np.zeros(x.size, dtype=np.uint8)
+    med, mad = ctypes.c_double(), ctypes.c_double()
+    rc = lib().oracle_mad_flag(x.size, _p(x), float(M), _p(f), ctypes.byref(med), ctypes.byref(mad))
+    _check(rc, "mad_flag")
+    return f, med.value, mad.value
