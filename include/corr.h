@@ -1,0 +1,159 @@
+/*
+ * corr.h -- C ABI of a GB300-native FX correlator and beamformer.
+ *
+ * The operation is the real-time FX correlator + array beamformer of Roy et
+ * al., "A real-time software backend for the GMRT" (arXiv:0910.1517):
+ *   F-engine (Sec. 2.1, 2.3.2): per input (antenna a, polarisation p) the real
+ *     8-bit stream is read with an integer-sample delay offset, channelised by
+ *     an N-point real FFT (N/2 channels, DC kept, Nyquist dropped), and each
+ *     channel is multiplied by the post-FFT phasor of Eq. 2:
+ *       Y[k] = X[k] * exp(i (2 pi k tau_f / N - phi_a(g))),
+ *       phi_a(g) = phi0_a + omega_a * g,  g = global frame index since create.
+ *   Beams (Sec. 2.2): incoherent B_inc = sum_{a in inc} g_a^2 sum_p |Y_ap|^2 and
+ *     coherent B_coh = sum_p |sum_{a in coh} g_a exp(i theta_ak) Y_ap|^2 at the raw
+ *     FFT time resolution (optionally averaged over beam_avg frames).
+ *   X-engine (Sec. 2.1): for every channel k, baseline a <= a' (N(N+1)/2 of them,
+ *     autocorrelations included) and product pq in RR*, RL*, LR*, LL*:
+ *       V[k][b][p*n_pol+q] = sum_t Y_{a,p}[t][k] conj(Y_{a',q}[t][k]) over n_int frames.
+ *
+ * Indexing: input i = a * n_pol + p (p = 0 is R); baselines b row-major over
+ * a <= a': (0,0),(0,1)..(0,n_ant-1),(1,1),...; channels k = 0..n_fft/2-1.
+ *
+ * Precision modes (corr_set_mode): CORR_FP32 computes everything in FP32 on
+ * CUDA cores.  CORR_I8 requantises the FP32 spectra to int8 with per-(input,
+ * channel) scales, q = clamp(rint(Y*s), +-127), and accumulates q_i conj(q_j)
+ * exactly (integer result, bit-exact), then divides by s_i s_j.  CORR_F16
+ * rounds Y*s to FP16 and accumulates in FP32.  Both run the X-engine on the
+ * tcgen05 tensor cores.  Beams are always formed from the FP32 spectra.
+ *
+ * Ownership: the library allocates and owns every device buffer and one CUDA
+ * stream per handle; callers own every host buffer and any device buffer they
+ * pass in.  All entry points return CORR_OK (0) or a negative CORR_E_* code;
+ * corr_last_error() then describes the failure (per calling thread).  A
+ * handle is not thread-safe: one thread at a time may use it.
+ */
+#ifndef GB300_CORR_H
+#define GB300_CORR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
+typedef struct corr corr_t;
+
+enum {
+    CORR_OK = 0,
+    CORR_E_INVAL = -1,     /* bad argument (size, null pointer, alignment) */
+    CORR_E_RANGE = -2,     /* delay outside [0, max_delay] or buffer too short */
+    CORR_E_AGAIN = -3,     /* non-blocking read: no completed integration yet */
+    CORR_E_DATALOSS = -4,  /* sequence gap in pushed samples; integration dropped */
+    CORR_E_CUDA = -5,      /* CUDA runtime error */
+    CORR_E_NOMEM = -6,     /* device or pinned allocation failed */
+    CORR_E_STATE = -7,     /* call not valid in the current state */
+    CORR_E_TIMEOUT = -8    /* a kernel's bounded wait ran out; results invalid */
+};
+
+enum { CORR_FP32 = 0, CORR_I8 = 1, CORR_F16 = 2 };  /* X-engine precision */
+
+/* Create a correlator for n_ant antennas x n_pol (1 or 2) polarisations
+ * (n_in = n_ant * n_pol <= 128), an n_fft-point real FFT (power of two,
+ * 64..4096) and n_int frames per integration (multiple of 16).  Defaults:
+ * CORR_FP32, beam_avg 1, max_delay 2048 samples, zero delays and fringes,
+ * unit gains, all antennas in both beams, no scales.  *out receives the handle.
+ * The tensor-core modes (CORR_I8, CORR_F16) need n_in <= 64, and CORR_I8
+ * needs n_int <= 66571 so that 2 * 127^2 * n_int fits in int32. */
+int corr_create(corr_t** out, int n_ant, int n_pol, int n_fft, int n_int);
+int corr_destroy(corr_t* h);
+
+/* Message for the most recent failing call on this thread ("" if none). */
+const char* corr_last_error(void);
+
+/* Precision mode, polarisation products and beam time averaging.
+ * xmode: CORR_FP32 | CORR_I8 | CORR_F16.  polmode must be 0 (all n_pol^2
+ * products are produced).  beam_avg >= 1 must divide n_int. */
+int corr_set_mode(corr_t* h, int xmode, int polmode, int beam_avg);
+
+/* Largest integer delay (samples) the streaming ring supports; only before the
+ * first push.  Sec. 2.3.2 keeps an overlap of this many samples between time
+ * slices so the delay correction is seamless. */
+int corr_set_max_delay(corr_t* h, int max_delay);
+
+/* Per-antenna total delay tau_a in samples (Sec. 2.1; 0 <= tau_a, and
+ * floor(tau_a + 1/2) <= max_delay), fringe phase phi0_a (rad) at global frame
+ * 0 and fringe rate omega_a (rad/frame), all host arrays of n_ant doubles.
+ * The integer part D_a = floor(tau_a + 1/2) offsets the read pointer; tau_f =
+ * tau_a - D_a enters the Eq. 2 phasor.  Takes effect at the next integration. */
+int corr_set_delays(corr_t* h, const double* delay, const double* phi0, const double* rate);
+
+/* Beam weights (Sec. 2.2, 4.3): gain g_a [n_ant] (NULL = 1), phase
+ * calibration theta [n_ant][n_fft/2] radians (NULL = 0), and antenna masks
+ * inc_mask, coh_mask [n_ant] (nonzero = in the beam; NULL = all). */
+int corr_set_beam_weights(corr_t* h, const float* gain, const float* theta,
+                          const uint8_t* inc_mask, const uint8_t* coh_mask);
+
+/* Requantisation scales s [n_in][n_fft/2] for CORR_I8 / CORR_F16.  NULL
+ * derives them from the last completed integration's autocorrelations as
+ * s = 127 / (4 sigma), sigma^2 = V_ii[k] / (2 n_int). */
+int corr_set_scales(corr_t* h, const float* scale);
+
+/* Streaming ingest of host samples x [n_in][n] (planar int8, row i holds n
+ * samples of input i).  seq is the stream index of the first sample; it must
+ * continue the previous push, else the partial integration is dropped, the
+ * stream restarts at seq and CORR_E_DATALOSS is returned.  Whenever
+ * n_int * n_fft + max_delay samples are buffered an integration is launched
+ * asynchronously on the handle's stream.  x is copied before return. */
+int corr_push_samples(corr_t* h, const int8_t* x, int64_t n, int64_t seq);
+
+/* As corr_push_samples with x in device memory (row stride n); the copies are
+ * ordered after work already on `stream` (a cudaStream_t, NULL = legacy). */
+int corr_push_samples_device(corr_t* h, const int8_t* x, int64_t n, int64_t seq, void* stream);
+
+/* One whole integration straight from device memory, no copy of the input:
+ * row i of input starts at x + i*ld (x and ld 16-byte aligned), holds n_avail
+ * readable samples, and n_avail >= n_int*n_fft + max_a D_a.  Frames are global
+ * frames g0 .. g0+n_int-1 (fringe phase index).  Runs on `stream` (NULL =
+ * the handle's stream); returns once the work is queued. */
+int corr_integrate_device(corr_t* h, const int8_t* x, int64_t ld, int64_t n_avail,
+                          int64_t g0, void* stream);
+
+/* Results of the last completed integration, copied to host memory.
+ * Visibilities: out [n_fft/2][n_bl][n_pol^2] complex64 as (re, im) float pairs.
+ * Beams: out [2][n_int/beam_avg][n_fft/2] float32 (0 = incoherent, 1 = coherent).
+ * blocking = 1 waits for an integration in flight; 0 returns CORR_E_AGAIN if
+ * none has completed since create. */
+int corr_read_visibilities(corr_t* h, float* out, int blocking);
+int corr_read_beams(corr_t* h, float* out, int blocking);
+
+/* Exact integer visibilities of the last CORR_I8 integration,
+ * out [n_fft/2][n_bl][n_pol^2][2] int32 (re, im) = sum_t q_i conj(q_j). */
+int corr_read_vis_int(corr_t* h, int32_t* out, int blocking);
+
+/* Requantised spectra of the last CORR_I8 integration for channels k0..k0+nk-1,
+ * q [n_in][n_int][nk][2] int8, and the scales used, scale [n_in][n_fft/2]
+ * (either may be NULL). */
+int corr_read_requant(corr_t* h, int k0, int nk, int8_t* q, float* scale);
+
+/* FP32 spectra Y of the last CORR_FP32 integration for channels k0..k0+nk-1,
+ * out [n_in][n_int][nk] complex64 (re, im pairs). */
+int corr_read_spectra(corr_t* h, int k0, int nk, float* out);
+
+/* Device pointers of the result buffers of handle h (valid until destroy):
+ * visibilities (float2), beams (float), and the stream results are written on. */
+int corr_device_outputs(corr_t* h, void** vis, void** beams, void** stream);
+
+/* Sizes: n_in, n_bl, n_chan, n_prod, beam frames per integration, and the
+ * number of completed integrations. */
+int corr_info(corr_t* h, int64_t* out6);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+#ifdef __cplusplus
+}
+#endif
+#endif

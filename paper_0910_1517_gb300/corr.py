@@ -1,0 +1,209 @@
+"""Thin Python binding of the C ABI in include/corr.h (argument marshalling only).
+
+Every function below has the name of the C entry point it calls and does no
+arithmetic of its own: numpy arrays and torch tensors are turned into raw
+pointers, shapes are computed from the handle's sizes, and a negative return
+code becomes a ``CorrError`` carrying ``corr_last_error()``.  The library is
+the in-tree ``libgb300corr.so``; there is no fallback if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgb300corr.so")
+
+CORR_FP32, CORR_I8, CORR_F16 = 0, 1, 2
+CODES = {0: "CORR_OK", -1: "CORR_E_INVAL", -2: "CORR_E_RANGE", -3: "CORR_E_AGAIN", -4: "CORR_E_DATALOSS",
+         -5: "CORR_E_CUDA", -6: "CORR_E_NOMEM", -7: "CORR_E_STATE", -8: "CORR_E_TIMEOUT"}
+
+# every symbol include/corr.h declares, with its ctypes signature
+_P, _I, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+SIGNATURES = {
+    "corr_create": ([ctypes.POINTER(ctypes.c_void_p), _I, _I, _I, _I], _I),
+    "corr_destroy": ([_P], _I),
+    "corr_last_error": ([], ctypes.c_char_p),
+    "corr_set_mode": ([_P, _I, _I, _I], _I),
+    "corr_set_max_delay": ([_P, _I], _I),
+    "corr_set_delays": ([_P, _P, _P, _P], _I),
+    "corr_set_beam_weights": ([_P, _P, _P, _P, _P], _I),
+    "corr_set_scales": ([_P, _P], _I),
+    "corr_push_samples": ([_P, _P, _L, _L], _I),
+    "corr_push_samples_device": ([_P, _P, _L, _L, _P], _I),
+    "corr_integrate_device": ([_P, _P, _L, _L, _L, _P], _I),
+    "corr_read_visibilities": ([_P, _P, _I], _I),
+    "corr_read_beams": ([_P, _P, _I], _I),
+    "corr_read_vis_int": ([_P, _P, _I], _I),
+    "corr_read_requant": ([_P, _I, _I, _P, _P], _I),
+    "corr_read_spectra": ([_P, _I, _I, _P], _I),
+    "corr_device_outputs": ([_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                             ctypes.POINTER(ctypes.c_void_p)], _I),
+    "corr_info": ([_P, _P], _I),
+}
+
+_lib = None
+
+
+class CorrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load():
+    """Load libgb300corr.so (built by paper_0910_1517_gb300.build); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_0910_1517_gb300.build.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _ok(rc: int, allow=()):
+    if rc != 0 and rc not in allow:
+        raise CorrError(rc, load().corr_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    """Raw data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return ctypes.c_void_p(s)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def corr_create(n_ant: int, n_pol: int, n_fft: int, n_int: int):
+    h = ctypes.c_void_p()
+    _ok(load().corr_create(ctypes.byref(h), n_ant, n_pol, n_fft, n_int))
+    return h
+
+
+def corr_destroy(h):
+    return _ok(load().corr_destroy(h))
+
+
+def corr_last_error() -> str:
+    return load().corr_last_error().decode()
+
+
+def corr_set_mode(h, xmode: int, polmode: int = 0, beam_avg: int = 1):
+    return _ok(load().corr_set_mode(h, xmode, polmode, beam_avg))
+
+
+def corr_set_max_delay(h, max_delay: int):
+    return _ok(load().corr_set_max_delay(h, max_delay))
+
+
+def corr_set_delays(h, delay, phi0, rate):
+    d = np.ascontiguousarray(delay, dtype=np.float64)
+    f = np.ascontiguousarray(phi0, dtype=np.float64)
+    w = np.ascontiguousarray(rate, dtype=np.float64)
+    return _ok(load().corr_set_delays(h, _ptr(d), _ptr(f), _ptr(w)))
+
+
+def corr_set_beam_weights(h, gain=None, theta=None, inc_mask=None, coh_mask=None):
+    g = None if gain is None else np.ascontiguousarray(gain, dtype=np.float32)
+    t = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
+    im = None if inc_mask is None else np.ascontiguousarray(inc_mask, dtype=np.uint8)
+    cm = None if coh_mask is None else np.ascontiguousarray(coh_mask, dtype=np.uint8)
+    return _ok(load().corr_set_beam_weights(h, _ptr(g), _ptr(t), _ptr(im), _ptr(cm)))
+
+
+def corr_set_scales(h, scale=None):
+    s = None if scale is None else np.ascontiguousarray(scale, dtype=np.float32)
+    return _ok(load().corr_set_scales(h, _ptr(s)))
+
+
+def corr_push_samples(h, x, seq: int, allow_dataloss: bool = False):
+    """x: host int8 [n_in][n] (numpy array or pinned CPU tensor), rows contiguous."""
+    n = x.shape[1]
+    allow = (-4,) if allow_dataloss else ()
+    return _ok(load().corr_push_samples(h, _ptr(x), n, seq), allow)
+
+
+def corr_push_samples_device(h, x, seq: int, stream=None):
+    return _ok(load().corr_push_samples_device(h, _ptr(x), x.shape[1], seq, _stream(stream)))
+
+
+def corr_integrate_device(h, x, n_avail=None, g0: int = 0, stream=None, ld=None):
+    """x: device int8 tensor [n_in][ld]; ld (bytes) defaults to the row stride."""
+    if ld is None:
+        ld = x.stride(0)
+    if n_avail is None:
+        n_avail = x.shape[1]
+    return _ok(load().corr_integrate_device(h, _ptr(x), ld, n_avail, g0, _stream(stream)))
+
+
+def _info(h):
+    out = np.zeros(6, dtype=np.int64)
+    _ok(load().corr_info(h, _ptr(out)))
+    return out
+
+
+def corr_info(h) -> dict:
+    v = _info(h)
+    return dict(n_in=int(v[0]), n_bl=int(v[1]), n_chan=int(v[2]), n_prod=int(v[3]), n_beam=int(v[4]),
+                completed=int(v[5]))
+
+
+def corr_read_visibilities(h, out=None, blocking: int = 1):
+    i = corr_info(h)
+    if out is None:
+        out = np.empty((i["n_chan"], i["n_bl"], i["n_prod"]), dtype=np.complex64)
+    _ok(load().corr_read_visibilities(h, _ptr(out), blocking))
+    return out
+
+
+def corr_read_beams(h, out=None, blocking: int = 1):
+    i = corr_info(h)
+    if out is None:
+        out = np.empty((2, i["n_beam"], i["n_chan"]), dtype=np.float32)
+    _ok(load().corr_read_beams(h, _ptr(out), blocking))
+    return out
+
+
+def corr_read_vis_int(h, blocking: int = 1):
+    i = corr_info(h)
+    out = np.empty((i["n_chan"], i["n_bl"], i["n_prod"], 2), dtype=np.int32)
+    _ok(load().corr_read_vis_int(h, _ptr(out), blocking))
+    return out
+
+
+def corr_read_requant(h, k0: int, nk: int, n_int: int):
+    i = corr_info(h)
+    q = np.empty((i["n_in"], n_int, nk, 2), dtype=np.int8)
+    s = np.empty((i["n_in"], i["n_chan"]), dtype=np.float32)
+    _ok(load().corr_read_requant(h, k0, nk, _ptr(q), _ptr(s)))
+    return q, s
+
+
+def corr_read_spectra(h, k0: int, nk: int, n_int: int):
+    i = corr_info(h)
+    out = np.empty((i["n_in"], n_int, nk), dtype=np.complex64)
+    _ok(load().corr_read_spectra(h, k0, nk, _ptr(out)))
+    return out
+
+
+def corr_device_outputs(h):
+    v, b, s = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _ok(load().corr_device_outputs(h, ctypes.byref(v), ctypes.byref(b), ctypes.byref(s)))
+    return v.value, b.value, s.value

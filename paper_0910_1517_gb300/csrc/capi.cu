@@ -1,0 +1,562 @@
+// capi.cu -- the C ABI declared in include/corr.h: handle state, the streaming
+// ring with its delay overlap (Sec. 2.3.2), sequencing of the per-integration
+// kernels, and result read-back.  All compute happens in the kernels of
+// fengine.cu, xengine_fp32.cu and xengine_tc.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/corr.h"
+#include "fengine.cuh"
+#include "xengine.cuh"
+
+using namespace gbx;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(CORR_E_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                                 \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+    return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T));
+}
+
+}  // namespace
+
+struct corr {
+    int n_ant = 0, n_pol = 0, n_in = 0, n_fft = 0, n_chan = 0, n_int = 0, n_bl = 0, npp = 0;
+    int xmode = CORR_FP32, beam_avg = 1, max_delay = 2048;
+    int dev = 0, n_sm = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_done = nullptr, ev_aux = nullptr;
+    // host-side model
+    std::vector<double> tau, phi0, rate;
+    bool scales_set = false;
+    // streaming ring
+    int8_t* d_ring = nullptr;
+    int64_t ring_ld = 0, fill = 0, seq_next = -1, seq_origin = -1, g_next = 0;
+    bool ring_started = false;
+    // device tables and outputs
+    double* d_model = nullptr;          // tau | phi0 | rate, 3 * n_ant
+    double* h_model = nullptr;          // pinned staging of the same
+    float2* d_pf = nullptr;
+    float2* d_ff = nullptr;
+    int* d_D = nullptr;
+    float2* d_wcoh = nullptr;
+    float* d_ginc = nullptr;
+    float* d_scale = nullptr;
+    float2* d_tw = nullptr;
+    void* d_spec = nullptr;
+    float* d_beams_raw = nullptr;
+    float* d_beams = nullptr;
+    float2* d_vis = nullptr;
+    int2* d_vis_int = nullptr;
+    unsigned* d_err = nullptr;
+    // bookkeeping
+    int64_t launched = 0, completed = 0;
+    int last_mode = -1;
+};
+
+namespace {
+
+int64_t ring_need(const corr* h) { return static_cast<int64_t>(h->n_int) * h->n_fft + h->max_delay; }
+
+int alloc_ring(corr* h) {
+    if (h->d_ring) cudaFree(h->d_ring);
+    h->d_ring = nullptr;
+    h->ring_ld = ((ring_need(h) + 64 + 255) / 256) * 256;
+    CU(dalloc(&h->d_ring, static_cast<size_t>(h->ring_ld) * h->n_in));
+    CU(cudaMemset(h->d_ring, 0, static_cast<size_t>(h->ring_ld) * h->n_in));
+    return CORR_OK;
+}
+
+int upload_beam_weights(corr* h, const float* gain, const float* theta, const uint8_t* inc, const uint8_t* coh) {
+    std::vector<float2> w(static_cast<size_t>(h->n_ant) * h->n_chan);
+    std::vector<float> g2(h->n_ant);
+    for (int a = 0; a < h->n_ant; ++a) {
+        const double g = gain ? gain[a] : 1.0;
+        const bool in_inc = inc ? inc[a] != 0 : true;
+        const bool in_coh = coh ? coh[a] != 0 : true;
+        g2[a] = in_inc ? static_cast<float>(g * g) : 0.0f;
+        for (int k = 0; k < h->n_chan; ++k) {
+            const double th = theta ? theta[static_cast<size_t>(a) * h->n_chan + k] : 0.0;
+            w[static_cast<size_t>(a) * h->n_chan + k] =
+                in_coh ? make_float2(static_cast<float>(g * std::cos(th)), static_cast<float>(g * std::sin(th)))
+                       : make_float2(0.f, 0.f);
+        }
+    }
+    CU(cudaMemcpy(h->d_wcoh, w.data(), w.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->d_ginc, g2.data(), g2.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return CORR_OK;
+}
+
+int max_int_delay(const corr* h) {
+    int m = 0;
+    for (double t : h->tau) m = std::max(m, static_cast<int>(std::floor(t + 0.5)));
+    return m;
+}
+
+// Queue one integration (phasors, F-engine, X-engine, beam averaging) on stream s.
+int run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, int64_t g0, cudaStream_t s) {
+    if (h->xmode != CORR_FP32 && !h->scales_set)
+        return fail(CORR_E_STATE, "CORR_I8 / CORR_F16 need requantisation scales (corr_set_scales)");
+    const int nd = h->n_ant;
+    std::memcpy(h->h_model, h->tau.data(), nd * sizeof(double));
+    std::memcpy(h->h_model + nd, h->phi0.data(), nd * sizeof(double));
+    std::memcpy(h->h_model + 2 * nd, h->rate.data(), nd * sizeof(double));
+    CU(cudaMemcpyAsync(h->d_model, h->h_model, 3 * nd * sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(launch_phasor_setup(h->n_ant, h->n_chan, h->n_fft, h->n_int, g0, h->d_model, h->d_model + nd,
+                           h->d_model + 2 * nd, h->d_pf, h->d_ff, h->d_D, s));
+    FeParams fp{};
+    fp.x = x;
+    fp.ld = ld;
+    fp.n_avail = n_avail;
+    fp.n_ant = h->n_ant;
+    fp.n_pol = h->n_pol;
+    fp.n_in = h->n_in;
+    fp.n_fft = h->n_fft;
+    fp.n_chan = h->n_chan;
+    fp.n_int = h->n_int;
+    fp.D = h->d_D;
+    fp.pf = h->d_pf;
+    fp.ff = h->d_ff;
+    fp.wcoh = h->d_wcoh;
+    fp.ginc = h->d_ginc;
+    fp.scale = h->d_scale;
+    fp.spec = h->d_spec;
+    fp.beams = h->d_beams_raw;
+    fp.tw = h->d_tw;
+    fp.err = h->d_err;
+    const int fmode = h->xmode == CORR_FP32 ? OUT_FP32 : (h->xmode == CORR_I8 ? OUT_I8 : OUT_F16);
+    CU(launch_fengine(fp, fmode, s));
+    XParams xp{};
+    xp.spec = h->d_spec;
+    xp.n_ant = h->n_ant;
+    xp.n_pol = h->n_pol;
+    xp.n_in = h->n_in;
+    xp.n_chan = h->n_chan;
+    xp.n_int = h->n_int;
+    xp.scale = h->d_scale;
+    xp.vis = h->d_vis;
+    xp.vis_int = h->xmode == CORR_I8 ? h->d_vis_int : nullptr;
+    xp.err = h->d_err;
+    xp.exact = h->xmode == CORR_I8 ? 1 : 0;
+    if (h->xmode == CORR_FP32)
+        CU(launch_xengine_fp32(xp, h->n_sm, s));
+    else
+        CU(launch_xengine_tc(xp, h->n_sm, s));
+    if (h->beam_avg > 1) CU(launch_beam_average(h->d_beams_raw, h->d_beams, h->n_int, h->n_chan, h->beam_avg, s));
+    CU(cudaEventRecord(h->ev_done, s));
+    h->launched += 1;
+    h->last_mode = h->xmode;
+    return CORR_OK;
+}
+
+// Wait for (or poll) the last launched integration; check the device error word.
+int settle(corr* h, int blocking) {
+    if (h->launched == 0) return fail(CORR_E_AGAIN, "no integration has been launched");
+    if (h->completed < h->launched) {
+        if (blocking) {
+            CU(cudaEventSynchronize(h->ev_done));
+        } else {
+            cudaError_t q = cudaEventQuery(h->ev_done);
+            if (q == cudaErrorNotReady) return fail(CORR_E_AGAIN, "integration still in flight");
+            if (q != cudaSuccess) return fail(CORR_E_CUDA, "integration failed: %s", cudaGetErrorString(q));
+        }
+        h->completed = h->launched;
+    }
+    unsigned err = 0;
+    CU(cudaMemcpy(&err, h->d_err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) return fail(CORR_E_TIMEOUT, "a kernel wait timed out (error bits 0x%x); results invalid", err);
+    return CORR_OK;
+}
+
+int check_handle(corr* h) {
+    if (!h) return fail(CORR_E_INVAL, "null handle");
+    cudaError_t e = cudaSetDevice(h->dev);
+    if (e != cudaSuccess) return fail(CORR_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return CORR_OK;
+}
+
+// Append n samples per input (host or device rows of pitch spitch) to the ring,
+// launching integrations as it fills.  kind is the cudaMemcpyKind of the copy.
+int ingest(corr* h, const int8_t* x, int64_t spitch, int64_t n, int64_t seq, cudaMemcpyKind kind, bool sync_copy) {
+    int rc = CORR_OK;
+    if (!h->ring_started) {
+        h->ring_started = true;
+        h->seq_origin = seq;
+        h->seq_next = seq;
+        h->g_next = 0;
+        h->fill = 0;
+    } else if (seq != h->seq_next) {
+        // gap or overlap: drop the partial integration, restart the ring at seq
+        const int64_t gap = seq - h->seq_next;
+        h->fill = 0;
+        h->seq_next = seq;
+        h->g_next = (seq - h->seq_origin) >= 0 ? (seq - h->seq_origin) / h->n_fft : 0;
+        fail(CORR_E_DATALOSS, "sequence gap of %lld samples: partial integration dropped", (long long)gap);
+        rc = CORR_E_DATALOSS;
+    }
+    const int64_t need = ring_need(h);
+    int64_t done = 0;
+    while (done < n) {
+        const int64_t take = std::min(n - done, need - h->fill);
+        CU(cudaMemcpy2DAsync(h->d_ring + h->fill, h->ring_ld, x + done, spitch, take, h->n_in, kind, h->stream));
+        h->fill += take;
+        done += take;
+        if (h->fill == need) {
+            if (max_int_delay(h) > h->max_delay)
+                return fail(CORR_E_RANGE, "a delay exceeds max_delay = %d", h->max_delay);
+            int r = run_integration(h, h->d_ring, h->ring_ld, need, h->g_next, h->stream);
+            if (r != CORR_OK) return r;
+            // keep the last max_delay samples: they begin the next integration (overlap, Sec. 2.3.2)
+            const int64_t body = static_cast<int64_t>(h->n_int) * h->n_fft;
+            if (h->max_delay > 0)
+                CU(cudaMemcpy2DAsync(h->d_ring, h->ring_ld, h->d_ring + body, h->ring_ld, h->max_delay, h->n_in,
+                                     cudaMemcpyDeviceToDevice, h->stream));
+            h->fill = h->max_delay;
+            h->g_next += h->n_int;
+        }
+    }
+    h->seq_next += n;
+    if (sync_copy) {
+        CU(cudaEventRecord(h->ev_aux, h->stream));
+        CU(cudaEventSynchronize(h->ev_aux));
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* corr_last_error(void) { return g_err.c_str(); }
+
+int corr_create(corr_t** out, int n_ant, int n_pol, int n_fft, int n_int) {
+    g_err.clear();
+    if (!out) return fail(CORR_E_INVAL, "out is null");
+    *out = nullptr;
+    if (n_ant < 1 || (n_pol != 1 && n_pol != 2) || n_ant * n_pol > 128)
+        return fail(CORR_E_INVAL, "need 1 <= n_ant * n_pol <= 128 and n_pol in {1, 2}");
+    if (n_fft < 64 || n_fft > 4096 || (n_fft & (n_fft - 1)))
+        return fail(CORR_E_INVAL, "n_fft must be a power of two in [64, 4096]");
+    if (n_int < 16 || n_int % 16) return fail(CORR_E_INVAL, "n_int must be a positive multiple of 16");
+    corr* h = new corr();
+    h->n_ant = n_ant;
+    h->n_pol = n_pol;
+    h->n_in = n_ant * n_pol;
+    h->n_fft = n_fft;
+    h->n_chan = n_fft / 2;
+    h->n_int = n_int;
+    h->n_bl = n_ant * (n_ant + 1) / 2;
+    h->npp = n_pol * n_pol;
+    h->tau.assign(n_ant, 0.0);
+    h->phi0.assign(n_ant, 0.0);
+    h->rate.assign(n_ant, 0.0);
+    auto bail = [&](int rc) {
+        corr_destroy(h);
+        return rc;
+    };
+#define CUB(call)                                                                                \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return bail(fail(CORR_E_NOMEM, "%s: %s", #call, cudaGetErrorString(e_))); \
+    } while (0)
+    CUB(cudaGetDevice(&h->dev));
+    CUB(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->dev));
+    CUB(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CUB(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
+    CUB(cudaEventCreateWithFlags(&h->ev_aux, cudaEventDisableTiming));
+    const size_t nch = h->n_chan, na = n_ant, ni = h->n_in;
+    CUB(dalloc(&h->d_model, 3 * na));
+    CUB(cudaMallocHost(reinterpret_cast<void**>(&h->h_model), 3 * na * sizeof(double)));
+    CUB(dalloc(&h->d_pf, na * nch));
+    CUB(dalloc(&h->d_ff, na * static_cast<size_t>(n_int)));
+    CUB(dalloc(&h->d_D, na));
+    CUB(dalloc(&h->d_wcoh, na * nch));
+    CUB(dalloc(&h->d_ginc, na));
+    CUB(dalloc(&h->d_scale, ni * nch));
+    CUB(dalloc(&h->d_tw, nch + nch / 2 + 1));
+    const size_t spec_bytes = nch * static_cast<size_t>(n_int) * 2 * ni * sizeof(float);
+    CUB(cudaMalloc(&h->d_spec, spec_bytes));
+    CUB(dalloc(&h->d_beams_raw, 2 * static_cast<size_t>(n_int) * nch));
+    h->d_beams = h->d_beams_raw;
+    const size_t nvis = nch * h->n_bl * h->npp;
+    CUB(dalloc(&h->d_vis, nvis));
+    CUB(dalloc(&h->d_vis_int, nvis));
+    CUB(dalloc(&h->d_err, 1));
+    CUB(cudaMemset(h->d_err, 0, sizeof(unsigned)));
+    CUB(cudaMemset(h->d_vis, 0, nvis * sizeof(float2)));
+    CUB(cudaMemset(h->d_vis_int, 0, nvis * sizeof(int2)));
+    CUB(cudaMemset(h->d_scale, 0, ni * nch * sizeof(float)));
+    // FFT twiddles in FP64, rounded once: exp(-2 pi i m / M) and exp(-2 pi i k / N)
+    {
+        std::vector<float2> tw(nch + nch / 2 + 1);
+        const double two_pi = 6.283185307179586476925286766559;
+        for (size_t m = 0; m < nch; ++m)
+            tw[m] = make_float2(static_cast<float>(std::cos(two_pi * m / nch)),
+                                static_cast<float>(-std::sin(two_pi * m / nch)));
+        for (size_t k = 0; k <= nch / 2; ++k)
+            tw[nch + k] = make_float2(static_cast<float>(std::cos(two_pi * k / n_fft)),
+                                      static_cast<float>(-std::sin(two_pi * k / n_fft)));
+        CUB(cudaMemcpy(h->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    }
+#undef CUB
+    int rc = upload_beam_weights(h, nullptr, nullptr, nullptr, nullptr);
+    if (rc != CORR_OK) return bail(rc);
+    *out = h;
+    return CORR_OK;
+}
+
+int corr_destroy(corr_t* h) {
+    if (!h) return CORR_OK;
+    cudaSetDevice(h->dev);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    void* bufs[] = {h->d_ring, h->d_model, h->d_pf, h->d_ff, h->d_D, h->d_wcoh, h->d_ginc, h->d_scale,
+                    h->d_tw, h->d_spec, h->d_beams_raw, h->d_vis, h->d_vis_int, h->d_err};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (h->d_beams && h->d_beams != h->d_beams_raw) cudaFree(h->d_beams);
+    if (h->h_model) cudaFreeHost(h->h_model);
+    if (h->ev_done) cudaEventDestroy(h->ev_done);
+    if (h->ev_aux) cudaEventDestroy(h->ev_aux);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return CORR_OK;
+}
+
+int corr_set_mode(corr_t* h, int xmode, int polmode, int beam_avg) {
+    if (int rc = check_handle(h)) return rc;
+    if (xmode != CORR_FP32 && xmode != CORR_I8 && xmode != CORR_F16) return fail(CORR_E_INVAL, "unknown xmode");
+    if (polmode != 0) return fail(CORR_E_INVAL, "only polmode 0 (all products) is supported");
+    if (beam_avg < 1 || h->n_int % beam_avg) return fail(CORR_E_INVAL, "beam_avg must divide n_int");
+    if (xmode != CORR_FP32 && !xengine_tc_supported(h->n_in))
+        return fail(CORR_E_INVAL, "tensor-core modes need n_in <= 64");
+    if (xmode == CORR_I8 && h->n_int > 66571) return fail(CORR_E_INVAL, "CORR_I8 needs n_int <= 66571");
+    CU(cudaStreamSynchronize(h->stream));
+    if (beam_avg != h->beam_avg) {
+        if (h->d_beams != h->d_beams_raw) cudaFree(h->d_beams);
+        h->d_beams = h->d_beams_raw;
+        if (beam_avg > 1) CU(dalloc(&h->d_beams, 2 * static_cast<size_t>(h->n_int / beam_avg) * h->n_chan));
+    }
+    h->xmode = xmode;
+    h->beam_avg = beam_avg;
+    return CORR_OK;
+}
+
+int corr_set_max_delay(corr_t* h, int max_delay) {
+    if (int rc = check_handle(h)) return rc;
+    if (h->ring_started) return fail(CORR_E_STATE, "max_delay is fixed once samples have been pushed");
+    if (max_delay < 0 || max_delay > (1 << 24)) return fail(CORR_E_INVAL, "max_delay out of range");
+    h->max_delay = max_delay;
+    if (h->d_ring) return alloc_ring(h);
+    return CORR_OK;
+}
+
+int corr_set_delays(corr_t* h, const double* delay, const double* phi0, const double* rate) {
+    if (int rc = check_handle(h)) return rc;
+    for (int a = 0; a < h->n_ant; ++a) {
+        const double t = delay ? delay[a] : 0.0;
+        if (!std::isfinite(t) || t < 0.0 || std::floor(t + 0.5) > 2.0e9)
+            return fail(CORR_E_RANGE, "delay[%d] = %g must be finite and >= 0", a, t);
+        if ((phi0 && !std::isfinite(phi0[a])) || (rate && !std::isfinite(rate[a])))
+            return fail(CORR_E_INVAL, "fringe model of antenna %d is not finite", a);
+    }
+    for (int a = 0; a < h->n_ant; ++a) {
+        h->tau[a] = delay ? delay[a] : 0.0;
+        h->phi0[a] = phi0 ? phi0[a] : 0.0;
+        h->rate[a] = rate ? rate[a] : 0.0;
+    }
+    return CORR_OK;
+}
+
+int corr_set_beam_weights(corr_t* h, const float* gain, const float* theta, const uint8_t* inc_mask,
+                          const uint8_t* coh_mask) {
+    if (int rc = check_handle(h)) return rc;
+    CU(cudaStreamSynchronize(h->stream));
+    return upload_beam_weights(h, gain, theta, inc_mask, coh_mask);
+}
+
+int corr_set_scales(corr_t* h, const float* scale) {
+    if (int rc = check_handle(h)) return rc;
+    const size_t n = static_cast<size_t>(h->n_in) * h->n_chan;
+    std::vector<float> s(n);
+    if (scale) {
+        for (size_t q = 0; q < n; ++q) {
+            if (!(scale[q] > 0.0f) || !std::isfinite(scale[q]))
+                return fail(CORR_E_INVAL, "scale[%zu] must be finite and > 0", q);
+            s[q] = scale[q];
+        }
+    } else {
+        if (int rc = settle(h, 1)) return rc;
+        std::vector<float2> v(static_cast<size_t>(h->n_chan) * h->n_bl * h->npp);
+        CU(cudaMemcpy(v.data(), h->d_vis, v.size() * sizeof(float2), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < h->n_in; ++i) {
+            const int a = i / h->n_pol, p = i % h->n_pol;
+            const int bl = a * h->n_ant - a * (a - 1) / 2;
+            for (int k = 0; k < h->n_chan; ++k) {
+                const double auto_p = v[(static_cast<size_t>(k) * h->n_bl + bl) * h->npp + p * h->n_pol + p].x;
+                const double sigma = std::sqrt(std::max(auto_p, 0.0) / (2.0 * h->n_int));
+                s[static_cast<size_t>(i) * h->n_chan + k] = sigma > 0 ? static_cast<float>(127.0 / (4.0 * sigma)) : 1.0f;
+            }
+        }
+    }
+    CU(cudaStreamSynchronize(h->stream));
+    CU(cudaMemcpy(h->d_scale, s.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    h->scales_set = true;
+    return CORR_OK;
+}
+
+int corr_push_samples(corr_t* h, const int8_t* x, int64_t n, int64_t seq) {
+    if (int rc = check_handle(h)) return rc;
+    if (!x || n < 0) return fail(CORR_E_INVAL, "bad sample buffer");
+    if (n == 0) return CORR_OK;
+    if (!h->d_ring)
+        if (int rc = alloc_ring(h)) return rc;
+    return ingest(h, x, n, n, seq, cudaMemcpyHostToDevice, true);
+}
+
+int corr_push_samples_device(corr_t* h, const int8_t* x, int64_t n, int64_t seq, void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (!x || n < 0) return fail(CORR_E_INVAL, "bad sample buffer");
+    if (n == 0) return CORR_OK;
+    if (!h->d_ring)
+        if (int rc = alloc_ring(h)) return rc;
+    // order the copy after the caller's producer work
+    CU(cudaEventRecord(h->ev_aux, static_cast<cudaStream_t>(stream)));
+    CU(cudaStreamWaitEvent(h->stream, h->ev_aux, 0));
+    return ingest(h, x, n, n, seq, cudaMemcpyDeviceToDevice, false);
+}
+
+int corr_integrate_device(corr_t* h, const int8_t* x, int64_t ld, int64_t n_avail, int64_t g0, void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (!x || (reinterpret_cast<uintptr_t>(x) & 15) || (ld & 15) || ld < n_avail)
+        return fail(CORR_E_INVAL, "x and ld must be 16-byte aligned and ld >= n_avail");
+    const int64_t need = static_cast<int64_t>(h->n_int) * h->n_fft + max_int_delay(h);
+    if (n_avail < need)
+        return fail(CORR_E_RANGE, "n_avail = %lld < n_int * n_fft + max delay = %lld", (long long)n_avail,
+                    (long long)need);
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : h->stream;
+    return run_integration(h, x, ld, n_avail, g0, s);
+}
+
+int corr_read_visibilities(corr_t* h, float* out, int blocking) {
+    if (int rc = check_handle(h)) return rc;
+    if (!out) return fail(CORR_E_INVAL, "out is null");
+    if (int rc = settle(h, blocking)) return rc;
+    CU(cudaMemcpy(out, h->d_vis, static_cast<size_t>(h->n_chan) * h->n_bl * h->npp * sizeof(float2),
+                  cudaMemcpyDeviceToHost));
+    return CORR_OK;
+}
+
+int corr_read_beams(corr_t* h, float* out, int blocking) {
+    if (int rc = check_handle(h)) return rc;
+    if (!out) return fail(CORR_E_INVAL, "out is null");
+    if (int rc = settle(h, blocking)) return rc;
+    CU(cudaMemcpy(out, h->d_beams, 2 * static_cast<size_t>(h->n_int / h->beam_avg) * h->n_chan * sizeof(float),
+                  cudaMemcpyDeviceToHost));
+    return CORR_OK;
+}
+
+int corr_read_vis_int(corr_t* h, int32_t* out, int blocking) {
+    if (int rc = check_handle(h)) return rc;
+    if (!out) return fail(CORR_E_INVAL, "out is null");
+    if (int rc = settle(h, blocking)) return rc;
+    if (h->last_mode != CORR_I8) return fail(CORR_E_STATE, "last integration was not CORR_I8");
+    CU(cudaMemcpy(out, h->d_vis_int, static_cast<size_t>(h->n_chan) * h->n_bl * h->npp * sizeof(int2),
+                  cudaMemcpyDeviceToHost));
+    return CORR_OK;
+}
+
+int corr_read_requant(corr_t* h, int k0, int nk, int8_t* q, float* scale) {
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = settle(h, 1)) return rc;
+    if (h->last_mode != CORR_I8) return fail(CORR_E_STATE, "last integration was not CORR_I8");
+    if (k0 < 0 || nk < 0 || k0 + nk > h->n_chan) return fail(CORR_E_INVAL, "channel range");
+    if (scale)
+        CU(cudaMemcpy(scale, h->d_scale, static_cast<size_t>(h->n_in) * h->n_chan * sizeof(float),
+                      cudaMemcpyDeviceToHost));
+    if (q && nk > 0) {
+        const int R = 2 * h->n_in, ntb = h->n_int / kTbHalf;
+        const size_t per_ch = static_cast<size_t>(ntb) * R * kTbHalf;
+        std::vector<__half> buf(per_ch * nk);
+        CU(cudaMemcpy(buf.data(), static_cast<const __half*>(h->d_spec) + per_ch * k0, buf.size() * sizeof(__half),
+                      cudaMemcpyDeviceToHost));
+        for (int c = 0; c < nk; ++c)
+            for (int kb = 0; kb < ntb; ++kb)
+                for (int r = 0; r < R; ++r)
+                    for (int e = 0; e < kTbHalf; ++e) {
+                        const float v = __half2float(buf[((static_cast<size_t>(c) * ntb + kb) * R + r) * kTbHalf + e]);
+                        const int i = r / 2, cc = r % 2, t = kb * kTbHalf + e;
+                        q[((static_cast<size_t>(i) * h->n_int + t) * nk + c) * 2 + cc] = static_cast<int8_t>(v);
+                    }
+    }
+    return CORR_OK;
+}
+
+int corr_read_spectra(corr_t* h, int k0, int nk, float* out) {
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = settle(h, 1)) return rc;
+    if (h->last_mode != CORR_FP32) return fail(CORR_E_STATE, "last integration was not CORR_FP32");
+    if (!out || k0 < 0 || nk < 0 || k0 + nk > h->n_chan) return fail(CORR_E_INVAL, "channel range");
+    const int R = 2 * h->n_in, ntb = h->n_int / kTbFp32;
+    const size_t per_ch = static_cast<size_t>(ntb) * R * kTbFp32;
+    std::vector<float> buf(per_ch * nk);
+    CU(cudaMemcpy(buf.data(), static_cast<const float*>(h->d_spec) + per_ch * k0, buf.size() * sizeof(float),
+                  cudaMemcpyDeviceToHost));
+    for (int c = 0; c < nk; ++c)
+        for (int kb = 0; kb < ntb; ++kb)
+            for (int r = 0; r < R; ++r)
+                for (int e = 0; e < kTbFp32; ++e) {
+                    const int i = r / 2, cc = r % 2, t = kb * kTbFp32 + e;
+                    out[((static_cast<size_t>(i) * h->n_int + t) * nk + c) * 2 + cc] =
+                        buf[((static_cast<size_t>(c) * ntb + kb) * R + r) * kTbFp32 + e];
+                }
+    return CORR_OK;
+}
+
+int corr_device_outputs(corr_t* h, void** vis, void** beams, void** stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (vis) *vis = h->d_vis;
+    if (beams) *beams = h->d_beams;
+    if (stream) *stream = h->stream;
+    return CORR_OK;
+}
+
+int corr_info(corr_t* h, int64_t* out6) {
+    if (!h || !out6) return fail(CORR_E_INVAL, "null argument");
+    out6[0] = h->n_in;
+    out6[1] = h->n_bl;
+    out6[2] = h->n_chan;
+    out6[3] = h->npp;
+    out6[4] = h->n_int / h->beam_avg;
+    out6[5] = h->completed;
+    return CORR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,486 @@
+// fengine.cu -- F-engine of the FX correlator for sm_103a.
+//
+// One CTA owns a block of F consecutive frames (F * n_chan = 8192 complex
+// channel-frames) and walks over every input (antenna x polarisation) in turn:
+//   1. the F frames of input i, offset by its integer delay D_a (Sec. 2.1,
+//      Sec. 2.3.2: the read pointer is moved, no data is shifted), arrive in
+//      shared memory through one TMA-engine bulk copy, double-buffered so the
+//      next input streams in while this one is transformed;
+//   2. each frame is an n_fft-point real FFT computed as an M = n_fft/2-point
+//      complex FFT of (x[2n] + i x[2n+1]) -- Stockham radix-16/16/R passes, 16
+//      points per thread in registers, shared memory between passes -- followed
+//      by the even/odd real split; channels 0..M-1 are kept (Nyquist dropped);
+//   3. every channel is multiplied by the post-FFT phasor of Eq. 2, the FSTC
+//      term exp(+2 pi i k tau_f / N) times the fringe term exp(-i phi_a(g));
+//   4. the incoherent beam (sum of g_a^2 |Y|^2) and the coherent voltage sum
+//      (sum of g_a e^{i theta} Y, detected once per polarisation) accumulate
+//      in shared memory, since this CTA sees every antenna of its frames
+//      (Sec. 2.2) -- no atomics, no second pass over the spectra;
+//   5. the spectra are transposed in shared memory and written in the K-block
+//      layout the X-engines read (FP32, or requantised int8-valued / FP16
+//      values for the tensor-core X-engine), 32-byte runs per (channel, input).
+#include "common.cuh"
+#include "fengine.cuh"
+
+namespace gbx {
+
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kE = 16;                      // complex points per thread per FFT
+constexpr int kChanFrames = 8192;           // F * M per CTA
+
+template <int M>
+struct Plan {
+    static constexpr int T = M / kE;                           // threads per FFT
+    static constexpr int F = kThreads / T;                     // frames per CTA
+    static constexpr int N = 2 * M;                            // real FFT size
+    static constexpr int R1 = 16;
+    static constexpr int R2 = (M / 16 >= 16) ? 16 : M / 16;
+    static constexpr int R3 = M / (R1 * R2);                   // 1 when two passes suffice
+    static constexpr int PADM = M + M / 32;                    // padded frame length (float2)
+    static constexpr int STAGE = F * N + 32;                   // staging bytes per buffer
+    static_assert(F * M == kChanFrames, "CTA covers 8192 channel-frames");
+};
+
+__host__ __device__ constexpr int pad32(int i) { return i + (i >> 5); }
+
+// cos / sin of 2 pi m / 16
+__device__ __forceinline__ constexpr float c16(int m) {
+    return m == 0 ? 1.0f : m == 1 ? 0.92387953251128674f : m == 2 ? 0.70710678118654752f
+         : m == 3 ? 0.38268343236508977f : m == 4 ? 0.0f : m == 5 ? -0.38268343236508977f
+         : m == 6 ? -0.70710678118654752f : m == 7 ? -0.92387953251128674f : -1.0f;
+}
+
+// o * exp(-2 pi i k / R) with the trivial cases spelled out
+template <int R, int K>
+__device__ __forceinline__ float2 twiddle_const(float2 o) {
+    constexpr int m = K * (16 / R);              // position on the 16-point circle, 0..7
+    if constexpr (m == 0) {
+        return o;
+    } else if constexpr (m == 4) {               // -i
+        return make_float2(o.y, -o.x);
+    } else if constexpr (m == 2) {               // (1 - i) / sqrt2
+        constexpr float h = 0.70710678118654752f;
+        return make_float2(h * (o.x + o.y), h * (o.y - o.x));
+    } else if constexpr (m == 6) {               // (-1 - i) / sqrt2
+        constexpr float h = 0.70710678118654752f;
+        return make_float2(h * (o.y - o.x), -h * (o.x + o.y));
+    } else {
+        constexpr float c = c16(m);
+        constexpr float s = (m <= 4) ? c16(4 - m) : c16(m - 4);  // sin(2 pi m / 16), m = 1..7
+        // w = c - i s
+        return make_float2(c * o.x + s * o.y, c * o.y - s * o.x);
+    }
+}
+
+// In-register forward DFT of R points (radix-2 recursion, natural-order output).
+template <int R>
+struct Dft {
+    template <int S>
+    __device__ __forceinline__ static void run(float2* v) {
+        // v[0], v[S], v[2S], ... hold the R inputs; transform in place
+        Dft<R / 2>::template run<2 * S>(v);      // evens
+        Dft<R / 2>::template run<2 * S>(v + S);  // odds
+        float2 out[R];
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            out[k] = v[2 * S * k];
+            out[k + R / 2] = v[2 * S * k + S];
+        }
+        apply<0>(out);
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[S * k] = out[k];
+    }
+    template <int K>
+    __device__ __forceinline__ static void apply(float2* out) {
+        if constexpr (K < R / 2) {
+            const float2 e = out[K];
+            const float2 t = twiddle_const<R, K>(out[K + R / 2]);
+            out[K] = cadd(e, t);
+            out[K + R / 2] = csub(e, t);
+            apply<K + 1>(out);
+        }
+    }
+};
+template <>
+struct Dft<1> {
+    template <int S>
+    __device__ __forceinline__ static void run(float2*) {}
+};
+
+// Stockham pass of radix R over span Ns for one frame: read X[b + r*M/R], twiddle,
+// DFT, write X[(b/Ns)*Ns*R + b%Ns + r*Ns].  Reads come from `src` (padded frame).
+template <int M, int R, int Ns>
+__device__ __forceinline__ void pass_load(const float2* __restrict__ src, const float2* __restrict__ twM, int t,
+                                          float2 (&v)[kE]) {
+    constexpr int T = M / kE, NB = M / R, PER = kE / R;
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int b = t + m * T;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[m * R + r] = src[pad32(b + r * NB)];
+        if constexpr (Ns > 1) {
+            const int j = b % Ns;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[m * R + r] = cmul(twM[(j * r) * (M / (Ns * R))], v[m * R + r]);
+        }
+        Dft<R>::template run<1>(v + m * R);
+    }
+}
+
+template <int M, int R, int Ns>
+__device__ __forceinline__ void pass_store(float2* __restrict__ dst, int t, const float2 (&v)[kE]) {
+    constexpr int T = M / kE, PER = kE / R;
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int b = t + m * T;
+        const int base = (b / Ns) * Ns * R + (b % Ns);
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[pad32(base + r * Ns)] = v[m * R + r];
+    }
+}
+
+// swizzle of the transposed [channel][frame] buffer: spreads a warp's same-frame stores over banks
+template <int F>
+__device__ __forceinline__ int tswz(int ch) {
+    constexpr int rows_per_line = (16 / F) > 1 ? (16 / F) : 1;
+    return (ch / rows_per_line) & (F - 1);
+}
+
+template <int M, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) fengine_kernel(const FeParams p) {
+    using P = Plan<M>;
+    constexpr int T = P::T, F = P::F, N = P::N;
+    constexpr int TB = (MODE == OUT_FP32) ? kTbFp32 : kTbHalf;
+    constexpr int L = (F < TB) ? F : TB;                 // frames per output run
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* stage0 = smem;
+    float2* X = reinterpret_cast<float2*>(smem + 2 * P::STAGE);           // F * PADM
+    float* inc = reinterpret_cast<float*>(X + F * P::PADM);                // F * M
+    float2* coh = reinterpret_cast<float2*>(inc + F * M);                  // F * M
+    float2* twM = coh + F * M;                                             // M
+    float2* twN = twM + M;                                                 // M/2 + 1
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    const int f = tid / T;            // frame within the CTA owned by this thread's FFT group
+    const int t = tid % T;            // thread within the group
+    const int t0 = blockIdx.x * F;
+    const int n_fr = min(F, p.n_int - t0);
+    const bool live = f < n_fr;
+    const int R = 2 * p.n_in;
+
+    for (int m = tid; m < M + M / 2 + 1; m += kThreads) (m < M ? twM[m] : twN[m - M]) = p.tw[m];
+    for (int m = tid; m < F * M; m += kThreads) inc[m] = 0.0f;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+
+    const int n_iter = p.n_in;  // pol-major order: it = p * n_ant + a
+    auto issue = [&](int it) {
+        const int pol = it / p.n_ant, a = it % p.n_ant;
+        const int i = a * p.n_pol + pol;
+        unsigned char* dst = stage0 + (it & 1) * P::STAGE;
+        const int64_t s0 = static_cast<int64_t>(t0) * N + p.D[a];
+        const int64_t aligned = s0 & ~static_cast<int64_t>(15);
+        const int64_t end = s0 + static_cast<int64_t>(n_fr) * N;
+        const uint32_t bulk = static_cast<uint32_t>((end - aligned) & ~static_cast<int64_t>(15));
+        const int8_t* row = p.x + static_cast<int64_t>(i) * p.ld;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar[it & 1], bulk);
+        bulk_g2s(dst, row + aligned, bulk, &bar[it & 1]);
+        for (int64_t q = aligned + bulk; q < end; ++q) dst[q - aligned] = static_cast<unsigned char>(row[q]);
+    };
+    if (tid == 0) issue(0);
+    __syncthreads();
+
+    for (int it = 0; it < n_iter; ++it) {
+        const int pol = it / p.n_ant, a = it % p.n_ant;
+        const int i = a * p.n_pol + pol;
+        if (tid == 0 && it + 1 < n_iter) issue(it + 1);
+        if (!mbar_wait(&bar[it & 1], (it >> 1) & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) break;
+        const int64_t s0 = static_cast<int64_t>(t0) * N + p.D[a];
+        const unsigned char* st = stage0 + (it & 1) * P::STAGE + (s0 & 15) + f * N;
+        float2* Xf = X + f * P::PADM;
+
+        // ---- pass 1: radix-16 straight from the int8 staging buffer
+        float2 v[kE];
+        {
+            constexpr int NB = M / P::R1;
+#pragma unroll
+            for (int r = 0; r < kE; ++r) {
+                const int n = t + r * NB;
+                const signed char lo = static_cast<signed char>(st[2 * n]);
+                const signed char hi = static_cast<signed char>(st[2 * n + 1]);
+                v[r] = make_float2(static_cast<float>(lo), static_cast<float>(hi));
+            }
+            Dft<16>::template run<1>(v);
+        }
+        __syncthreads();  // previous iteration's readers of X are done
+        pass_store<M, P::R1, 1>(Xf, t, v);
+        __syncthreads();
+        // ---- pass 2
+        pass_load<M, P::R2, P::R1>(Xf, twM, t, v);
+        __syncthreads();
+        pass_store<M, P::R2, P::R1>(Xf, t, v);
+        __syncthreads();
+        // ---- pass 3
+        if constexpr (P::R3 > 1) {
+            pass_load<M, P::R3, P::R1 * P::R2>(Xf, twM, t, v);
+            __syncthreads();
+            pass_store<M, P::R3, P::R1 * P::R2>(Xf, t, v);
+            __syncthreads();
+        }
+
+        // ---- real split, Eq. 2 phasor, beams
+        const float2 fr = p.ff[static_cast<int64_t>(a) * p.n_int + min(t0 + f, p.n_int - 1)];
+        const float g2 = p.ginc[a];
+        const float2* pfa = p.pf + static_cast<int64_t>(a) * M;
+        const float2* wa = p.wcoh + static_cast<int64_t>(a) * M;
+        float2 y[kE];
+        int ch[kE];
+#pragma unroll
+        for (int m = 0; m < kE / 2; ++m) {
+            const int k = t + m * T;                       // 0 .. M/2 - 1
+            const float2 zk = Xf[pad32(k)];
+            float2 xk, xmk;
+            int kk;
+            if (k == 0) {
+                const float2 zh = Xf[pad32(M / 2)];
+                xk = make_float2(zk.x + zk.y, 0.0f);       // DC
+                xmk = make_float2(zh.x, -zh.y);            // channel M/2
+                kk = M / 2;
+            } else {
+                const float2 zm = Xf[pad32(M - k)];
+                const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+                const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+                const float2 wo = cmul(twN[k], o);
+                xk = cadd(e, wo);
+                const float2 d = csub(e, wo);
+                xmk = make_float2(d.x, -d.y);
+                kk = M - k;
+            }
+            ch[2 * m] = k;
+            ch[2 * m + 1] = kk;
+            y[2 * m] = cmul(xk, cmul(pfa[k], fr));
+            y[2 * m + 1] = cmul(xmk, cmul(pfa[kk], fr));
+        }
+        if (live) {
+            if (a == 0) {
+#pragma unroll
+                for (int e = 0; e < kE; ++e) coh[f * M + ch[e]] = make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int e = 0; e < kE; ++e) {
+                const int o = f * M + ch[e];
+                inc[o] += g2 * (y[e].x * y[e].x + y[e].y * y[e].y);
+                coh[o] = cadd(coh[o], cmul(wa[ch[e]], y[e]));
+            }
+            if (a == p.n_ant - 1) {  // this polarisation's coherent sum is complete: detect
+                float* bc = p.beams + (static_cast<int64_t>(p.n_int) + t0 + f) * M;
+#pragma unroll
+                for (int e = 0; e < kE; ++e) {
+                    const float2 c = coh[f * M + ch[e]];
+                    const float pw = c.x * c.x + c.y * c.y;
+                    bc[ch[e]] = (pol == 0) ? pw : bc[ch[e]] + pw;
+                }
+            }
+        }
+
+        // ---- transpose through shared memory and write the K-block layout
+        __syncthreads();  // all reads of X are done
+        float2* Tb = X;   // [M][F], swizzled
+#pragma unroll
+        for (int e = 0; e < kE; ++e) Tb[ch[e] * F + (f ^ tswz<F>(ch[e]))] = y[e];
+        __syncthreads();
+        {
+            constexpr int RUNS = F / L;                    // output runs per channel
+            const float* sc = p.scale + static_cast<int64_t>(i) * M;
+            for (int item = tid; item < M * RUNS; item += kThreads) {
+                const int k = item / RUNS, run = item % RUNS;
+                const int fl0 = run * L;
+                if (fl0 >= n_fr) continue;
+                const int tg = t0 + fl0;                   // global frame of the run start
+                const int kb = tg / TB, off = tg % TB;
+                float2 val[L];
+#pragma unroll
+                for (int l = 0; l < L; ++l) val[l] = Tb[k * F + ((fl0 + l) ^ tswz<F>(k))];
+                const int64_t ntb = p.n_int / TB;
+                const int64_t rowbase = ((static_cast<int64_t>(k) * ntb + kb) * R + 2 * i) * TB + off;
+                if constexpr (MODE == OUT_FP32) {
+                    float* o = static_cast<float*>(p.spec) + rowbase;
+                    float re[L], im[L];
+#pragma unroll
+                    for (int l = 0; l < L; ++l) { re[l] = val[l].x; im[l] = val[l].y; }
+                    if constexpr (L == 4) {
+                        *reinterpret_cast<float4*>(o) = make_float4(re[0], re[1], re[2], re[3]);
+                        *reinterpret_cast<float4*>(o + TB) = make_float4(im[0], im[1], im[2], im[3]);
+                    } else {
+#pragma unroll
+                        for (int l = 0; l < L; ++l) { o[l] = re[l]; o[TB + l] = im[l]; }
+                    }
+                } else {
+                    const float s = sc[k];
+                    __half re[L], im[L];
+#pragma unroll
+                    for (int l = 0; l < L; ++l) {
+                        const float xr = val[l].x * s, xi = val[l].y * s;
+                        if constexpr (MODE == OUT_I8) {
+                            const int qr = max(-127, min(127, __float2int_rn(xr)));
+                            const int qi = max(-127, min(127, __float2int_rn(xi)));
+                            re[l] = __int2half_rn(qr);
+                            im[l] = __int2half_rn(qi);
+                        } else {
+                            re[l] = __float2half_rn(xr);
+                            im[l] = __float2half_rn(xi);
+                        }
+                    }
+                    __half* o = static_cast<__half*>(p.spec) + rowbase;
+                    if constexpr (L == 8) {
+                        uint4 ur, ui;
+                        memcpy(&ur, re, 16);
+                        memcpy(&ui, im, 16);
+                        *reinterpret_cast<uint4*>(o) = ur;
+                        *reinterpret_cast<uint4*>(o + TB) = ui;
+                    } else if constexpr (L == 4) {
+                        uint2 ur, ui;
+                        memcpy(&ur, re, 8);
+                        memcpy(&ui, im, 8);
+                        *reinterpret_cast<uint2*>(o) = ur;
+                        *reinterpret_cast<uint2*>(o + TB) = ui;
+                    } else {
+#pragma unroll
+                        for (int l = 0; l < L; ++l) { o[l] = re[l]; o[TB + l] = im[l]; }
+                    }
+                }
+            }
+        }
+    }
+
+    // incoherent beam of this CTA's frames
+    __syncthreads();
+    if (!abort_flag) {
+        for (int m = tid; m < n_fr * M; m += kThreads) p.beams[static_cast<int64_t>(t0) * M + m] = inc[m];
+    }
+}
+
+template <int M, int MODE>
+cudaError_t launch_t(const FeParams& p, cudaStream_t s) {
+    using P = Plan<M>;
+    const size_t smem = 2 * P::STAGE + sizeof(float2) * (P::F * P::PADM + P::F * M + M + M / 2 + 1) +
+                        sizeof(float) * P::F * M;
+    cudaError_t e = cudaFuncSetAttribute(fengine_kernel<M, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int grid = (p.n_int + P::F - 1) / P::F;
+    fengine_kernel<M, MODE><<<grid, kThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_mode(const FeParams& p, cudaStream_t s) {
+    switch (p.n_chan) {
+        case 32: return launch_t<32, MODE>(p, s);
+        case 64: return launch_t<64, MODE>(p, s);
+        case 128: return launch_t<128, MODE>(p, s);
+        case 256: return launch_t<256, MODE>(p, s);
+        case 512: return launch_t<512, MODE>(p, s);
+        case 1024: return launch_t<1024, MODE>(p, s);
+        case 2048: return launch_t<2048, MODE>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+__global__ void phasor_setup_kernel(int n_ant, int n_chan, int n_fft, int n_int, int64_t g0,
+                                    const double* __restrict__ tau, const double* __restrict__ phi0,
+                                    const double* __restrict__ rate, float2* __restrict__ pf,
+                                    float2* __restrict__ ff, int* __restrict__ D) {
+    const int64_t n1 = static_cast<int64_t>(n_ant) * n_chan, n2 = static_cast<int64_t>(n_ant) * n_int;
+    for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < n1 + n2 + n_ant;
+         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (q < n1) {
+            const int a = static_cast<int>(q / n_chan), k = static_cast<int>(q % n_chan);
+            const double Da = floor(tau[a] + 0.5), tf = tau[a] - Da;
+            double sn, cs;
+            sincospi(2.0 * k * tf / n_fft, &sn, &cs);   // exp(+2 pi i k tau_f / N)
+            pf[q] = make_float2(static_cast<float>(cs), static_cast<float>(sn));
+        } else if (q < n1 + n2) {
+            const int64_t r = q - n1;
+            const int a = static_cast<int>(r / n_int), t = static_cast<int>(r % n_int);
+            const double twopi = 6.283185307179586476925286766559;
+            double ph = phi0[a] + rate[a] * static_cast<double>(g0 + t);   // FP64 over the global frame counter
+            ph -= twopi * rint(ph / twopi);
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            ff[r] = make_float2(static_cast<float>(cs), static_cast<float>(-sn));  // exp(-i phi)
+        } else {
+            const int a = static_cast<int>(q - n1 - n2);
+            D[a] = static_cast<int>(floor(tau[a] + 0.5));
+        }
+    }
+}
+
+__global__ void beam_average_kernel(const float* __restrict__ raw, float* __restrict__ out, int n_int, int n_chan,
+                                    int beam_avg) {
+    const int n_out = n_int / beam_avg;
+    const int64_t total = 2LL * n_out * n_chan;
+    const float inv = 1.0f / beam_avg;
+    for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
+         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int k = static_cast<int>(q % n_chan);
+        const int64_t bt = q / n_chan;
+        const int b = static_cast<int>(bt / n_out), to = static_cast<int>(bt % n_out);
+        const float* src = raw + (static_cast<int64_t>(b) * n_int + static_cast<int64_t>(to) * beam_avg) * n_chan + k;
+        float acc = 0.0f;
+        for (int j = 0; j < beam_avg; ++j) acc += src[static_cast<int64_t>(j) * n_chan];
+        out[q] = acc * inv;
+    }
+}
+
+}  // namespace
+
+size_t fengine_smem_bytes(int n_fft) {
+    const int M = n_fft / 2;
+    const int F = kChanFrames / M;
+    return 2 * (static_cast<size_t>(F) * n_fft + 32) +
+           sizeof(float2) * (F * (M + M / 32) + F * M + M + M / 2 + 1) + sizeof(float) * F * M;
+}
+
+int fengine_frames_per_cta(int n_fft) { return kChanFrames / (n_fft / 2); }
+
+cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s) {
+    if (p.n_chan * 2 != p.n_fft) return cudaErrorInvalidValue;
+    switch (mode) {
+        case OUT_FP32: return launch_mode<OUT_FP32>(p, s);
+        case OUT_I8: return launch_mode<OUT_I8>(p, s);
+        case OUT_F16: return launch_mode<OUT_F16>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_phasor_setup(int n_ant, int n_chan, int n_fft, int n_int, int64_t g0, const double* tau,
+                                const double* phi0, const double* rate, float2* pf, float2* ff, int* D,
+                                cudaStream_t s) {
+    const int64_t total = static_cast<int64_t>(n_ant) * (n_chan + n_int) + n_ant;
+    const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4096));
+    phasor_setup_kernel<<<grid, 256, 0, s>>>(n_ant, n_chan, n_fft, n_int, g0, tau, phi0, rate, pf, ff, D);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_beam_average(const float* raw, float* out, int n_int, int n_chan, int beam_avg,
+                                cudaStream_t s) {
+    const int64_t total = 2LL * (n_int / beam_avg) * n_chan;
+    const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, 8192));
+    beam_average_kernel<<<grid, 256, 0, s>>>(raw, out, n_int, n_chan, beam_avg);
+    return cudaGetLastError();
+}
+
+}  // namespace gbx

@@ -1,0 +1,49 @@
+// fengine.cuh -- launch interface of the F-engine (integer delay, real FFT,
+// Eq. 2 phasor, beams, requantisation) and of the per-integration phasor set-up.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace gbx {
+
+enum OutMode : int { OUT_FP32 = 0, OUT_I8 = 1, OUT_F16 = 2 };
+
+// Spectra hand-off layout ("K-block layout"), shared by every X-engine:
+//   S[k][kb][r][TB]   k channel, kb = t / TB, r = 2*i + c (c = 0 re, 1 im), TB = t % TB
+// with TB = 4 (fp32) or 8 (fp16).  One (k, kb) block is R = 2*n_in rows of 16 bytes,
+// i.e. exactly the no-swizzle K-major canonical layout of a tcgen05 operand tile.
+constexpr int kTbFp32 = 4;
+constexpr int kTbHalf = 8;
+
+struct FeParams {
+    const int8_t* x;       // input rows, row i at x + i*ld
+    int64_t ld;            // row stride in bytes (multiple of 16)
+    int64_t n_avail;       // readable samples per row
+    int n_ant, n_pol, n_in, n_fft, n_chan, n_int;
+    const int* D;          // [n_ant] integer delays
+    const float2* pf;      // [n_ant][n_chan] fractional-delay phasor exp(+2 pi i k tau_f / N)
+    const float2* ff;      // [n_ant][n_int] fringe phasor exp(-i phi_a(g0 + t))
+    const float2* wcoh;    // [n_ant][n_chan] coherent-beam weight g_a exp(i theta_ak), 0 if unselected
+    const float* ginc;     // [n_ant] incoherent weight g_a^2, 0 if unselected
+    const float* scale;    // [n_in][n_chan] requantisation scales (I8 / F16)
+    void* spec;            // spectra in the K-block layout
+    float* beams;          // [2][n_int][n_chan] raw-resolution beams (0 inc, 1 coh)
+    const float2* tw;      // [n_chan] exp(-2 pi i m / n_chan), then [n_chan/2 + 1] exp(-2 pi i k / n_fft)
+    unsigned* err;
+};
+
+// Dynamic shared memory needed by the F-engine for a given FFT size.
+size_t fengine_smem_bytes(int n_fft);
+int fengine_frames_per_cta(int n_fft);
+cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s);
+
+// pf, ff and D for one integration from the FP64 delay / fringe model.
+cudaError_t launch_phasor_setup(int n_ant, int n_chan, int n_fft, int n_int, int64_t g0, const double* tau,
+                                const double* phi0, const double* rate, float2* pf, float2* ff, int* D,
+                                cudaStream_t s);
+
+// beams_out[b][to][k] = mean over beam_avg frames of beams_raw[b][to*beam_avg + j][k]
+cudaError_t launch_beam_average(const float* raw, float* out, int n_int, int n_chan, int beam_avg,
+                                cudaStream_t s);
+
+}  // namespace gbx

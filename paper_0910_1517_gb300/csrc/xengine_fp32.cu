@@ -1,0 +1,172 @@
+// xengine_fp32.cu -- the plain FP32 X-engine on CUDA cores (Sec. 2.1 MAC).
+//
+// A persistent CTA takes one channel at a time.  Its threads tile the upper
+// triangle of the n_in x n_in complex visibility matrix into 4x4 input blocks
+// (I <= J); each thread keeps its 16 complex sums in registers and walks over
+// the frames.  Frames stream into shared memory as K-blocks of 4 frames x
+// 2 n_in rows (the layout the F-engine writes), by TMA-engine bulk copies,
+// double-buffered.  Sums are kept per 256-frame chunk and added into a second
+// set of FP32 registers, which bounds the rounding error of long integrations.
+#include "common.cuh"
+#include "fengine.cuh"
+#include "xengine.cuh"
+
+namespace gbx {
+namespace {
+
+constexpr int kKbPerStage = 16;             // 64 frames per stage
+constexpr int kChunkKb = 64;                // 256 frames per FP32 partial sum
+constexpr int kSlack = 8 * 16;              // rows read past R by the last 4-input block
+
+__device__ __forceinline__ void decode_tri(int idx, int nb, int& I, int& J) {
+    I = 0;
+    int rem = idx;
+    while (rem >= nb - I) {
+        rem -= nb - I;
+        ++I;
+    }
+    J = I + rem;
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int abort_flag;
+    const int R = 2 * p.n_in;
+    const int stage_bytes = kKbPerStage * R * 16 + kSlack;
+    const int nb = (p.n_in + 3) / 4;
+    const int n_work = nb * (nb + 1) / 2;
+    const int tid = threadIdx.x;
+    const bool active = tid < n_work;
+    int I = 0, J = 0;
+    if (active) decode_tri(tid, nb, I, J);
+    const int ntb = p.n_int / kTbFp32;
+    const int n_stage_ch = (ntb + kKbPerStage - 1) / kKbPerStage;  // stages per channel
+    const int n_ch_mine = (p.n_chan - static_cast<int>(blockIdx.x) + gridDim.x - 1) / gridDim.x;
+    const int total = n_ch_mine * n_stage_ch;
+    const float* spec = static_cast<const float*>(p.spec);
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int w) {
+        const int k = blockIdx.x + (w / n_stage_ch) * gridDim.x;
+        const int kb0 = (w % n_stage_ch) * kKbPerStage;
+        const int nkb = min(kKbPerStage, ntb - kb0);
+        const uint32_t bytes = static_cast<uint32_t>(nkb) * R * 16;
+        const float* src = spec + (static_cast<int64_t>(k) * ntb + kb0) * R * kTbFp32;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar[w & 1], bytes);
+        bulk_g2s(smem + (w & 1) * stage_bytes, src, bytes, &bar[w & 1]);
+    };
+    if (tid == 0 && total > 0) issue(0);
+
+    float2 acc[4][4], tot[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = tot[a][b] = make_float2(0.f, 0.f);
+    int kb_in_chunk = 0;
+
+    for (int w = 0; w < total; ++w) {
+        if (tid == 0 && w + 1 < total) issue(w + 1);
+        if (!mbar_wait(&bar[w & 1], (w >> 1) & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) break;
+        const int kb0 = (w % n_stage_ch) * kKbPerStage;
+        const int nkb = min(kKbPerStage, ntb - kb0);
+        const float4* st = reinterpret_cast<const float4*>(smem + (w & 1) * stage_bytes);
+        if (active) {
+            for (int kb = 0; kb < nkb; ++kb) {
+                const float4* blk = st + kb * R;
+                float4 ar[4], ai[4];
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii) {
+                    ar[ii] = blk[8 * I + 2 * ii];
+                    ai[ii] = blk[8 * I + 2 * ii + 1];
+                }
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const float4 br = blk[8 * J + 2 * jj];
+                    const float4 bi = blk[8 * J + 2 * jj + 1];
+#pragma unroll
+                    for (int ii = 0; ii < 4; ++ii) {
+                        float2 c = acc[ii][jj];
+                        // Y_i conj(Y_j) = (ar + i ai)(br - i bi)
+                        c.x = fmaf(ar[ii].x, br.x, c.x); c.x = fmaf(ai[ii].x, bi.x, c.x);
+                        c.y = fmaf(ai[ii].x, br.x, c.y); c.y = fmaf(-ar[ii].x, bi.x, c.y);
+                        c.x = fmaf(ar[ii].y, br.y, c.x); c.x = fmaf(ai[ii].y, bi.y, c.x);
+                        c.y = fmaf(ai[ii].y, br.y, c.y); c.y = fmaf(-ar[ii].y, bi.y, c.y);
+                        c.x = fmaf(ar[ii].z, br.z, c.x); c.x = fmaf(ai[ii].z, bi.z, c.x);
+                        c.y = fmaf(ai[ii].z, br.z, c.y); c.y = fmaf(-ar[ii].z, bi.z, c.y);
+                        c.x = fmaf(ar[ii].w, br.w, c.x); c.x = fmaf(ai[ii].w, bi.w, c.x);
+                        c.y = fmaf(ai[ii].w, br.w, c.y); c.y = fmaf(-ar[ii].w, bi.w, c.y);
+                        acc[ii][jj] = c;
+                    }
+                }
+                if (++kb_in_chunk == kChunkKb) {
+                    kb_in_chunk = 0;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            tot[a][b] = cadd(tot[a][b], acc[a][b]);
+                            acc[a][b] = make_float2(0.f, 0.f);
+                        }
+                }
+            }
+        }
+        const bool ch_done = (w % n_stage_ch) == n_stage_ch - 1;
+        if (ch_done && active) {
+            const int k = blockIdx.x + (w / n_stage_ch) * gridDim.x;
+            const int n_bl = p.n_ant * (p.n_ant + 1) / 2, npp = p.n_pol * p.n_pol;
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int i = 4 * I + ii, j = 4 * J + jj;
+                    const float2 v = cadd(tot[ii][jj], acc[ii][jj]);
+                    tot[ii][jj] = acc[ii][jj] = make_float2(0.f, 0.f);
+                    if (i >= p.n_in || j >= p.n_in) continue;
+                    const int a = i / p.n_pol, pp = i % p.n_pol, a2 = j / p.n_pol, qq = j % p.n_pol;
+                    if (a > a2) continue;
+                    const int bl = a * p.n_ant - a * (a - 1) / 2 + (a2 - a);
+                    p.vis[(static_cast<int64_t>(k) * n_bl + bl) * npp + pp * p.n_pol + qq] = v;
+                }
+            kb_in_chunk = 0;
+        }
+        __syncthreads();  // buffer (w & 1) free for the copy issued at w + 2
+    }
+    if (abort_flag && tid == 0) {
+        // a copy may still be in flight into the other buffer: let it land before exit
+        mbar_wait(&bar[0], 0, nullptr, 0);
+        mbar_wait(&bar[1], 0, nullptr, 0);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_xengine_fp32(const XParams& p, int n_sm, cudaStream_t s) {
+    const int nb = (p.n_in + 3) / 4;
+    const int n_work = nb * (nb + 1) / 2;
+    const int threads = ((n_work + 31) / 32) * 32;
+    if (threads > 544) return cudaErrorInvalidValue;
+    const size_t smem = 2 * (static_cast<size_t>(kKbPerStage) * 2 * p.n_in * 16 + kSlack);
+    auto go = [&](auto kern) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        int per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+        const int grid = std::max(1, std::min(p.n_chan, n_sm * std::max(per_sm, 1)));
+        kern<<<grid, threads, smem, s>>>(p);
+        return cudaGetLastError();
+    };
+    return threads <= 256 ? go(xengine_fp32_kernel<256>) : go(xengine_fp32_kernel<544>);
+}
+
+}  // namespace gbx

@@ -1,0 +1,70 @@
+"""CPU-side checks of the boundary: the library builds and loads, exports every
+symbol include/corr.h declares, the binding covers exactly those, and the
+argument validation that runs before any CUDA call rejects bad sizes."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "corr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"\b(corr_[a-z_0-9]+)\s*\(", src))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0910_1517_gb300 import build, corr
+    build.build()
+    return corr.load()
+
+
+def test_header_declares_the_north_star_calls():
+    d = _declared()
+    for name in ("corr_create", "corr_set_delays", "corr_push_samples", "corr_read_visibilities",
+                 "corr_read_beams"):
+        assert name in d
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_0910_1517_gb300 import corr
+    out = subprocess.run(["nm", "-D", "--defined-only", corr.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (corr_[a-z_0-9]+)$", out, flags=re.M))
+    assert _declared() <= exported, _declared() - exported
+    assert set(corr.SIGNATURES) == _declared()
+    for name in _declared():
+        assert hasattr(lib, name)
+
+
+def test_binding_has_no_fallback(tmp_path, monkeypatch):
+    from paper_0910_1517_gb300 import corr
+    monkeypatch.setattr(corr, "_lib", None)
+    monkeypatch.setattr(corr, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        corr.load()
+
+
+@pytest.mark.parametrize("args", [
+    (0, 2, 512, 64),       # no antennas
+    (4, 3, 512, 64),       # bad polarisation count
+    (4, 2, 500, 64),       # n_fft not a power of two
+    (4, 2, 8192, 64),      # n_fft above the supported range
+    (4, 2, 512, 60),       # n_int not a multiple of 16
+    (65, 2, 512, 64),      # more than 128 inputs
+])
+def test_create_rejects_bad_sizes_before_touching_cuda(lib, args):
+    from paper_0910_1517_gb300 import corr
+    with pytest.raises(corr.CorrError) as ei:
+        corr.corr_create(*args)
+    assert ei.value.code == -1
+    assert corr.corr_last_error()
+
+
+def test_null_handle_is_rejected(lib):
+    from paper_0910_1517_gb300 import corr
+    with pytest.raises(corr.CorrError):
+        corr.corr_set_mode(None, 0, 0, 1)
