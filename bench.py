@@ -1,0 +1,425 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 FX correlator + beamformer on the GMRT-scale workload.
+
+Workload (one step = one integration through every hot-path stage): 32 antennas
+x 2 polarisations of real int8 samples (66.67 MS/s, 33.33 MHz band), integer +
+fractional delays 0-2000 samples, fringe rates 0-0.1 rad/spectrum, 2048-point
+real FFT -> 1024 channels, 8192 spectra (~0.25 s of sky data, 1.07 GB of
+samples), incoherent beam over 32 antennas and coherent beam over antennas
+0-29, 528 baselines x 4 products accumulated in FP32.  Inputs are seeded
+synthetic streams resident in HBM; at 1.07 GB per step they are larger than L2.
+
+value   antenna-samples/s over all ranks (device-resident input)
+e2e     the same through corr_push_samples from pinned host memory plus the
+        read-back of visibilities and beams, copies inside the timed region
+The JSON line also carries the real-time factor, the per-stage times, the
+roofline of the dominant kernel, the int8 / FP16 tensor-core forms of the
+X-engine (same data) with their speedups, clocks seen during the timed
+region and the FP64 oracle timed on a bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank correlates its own time slice (no data-path
+collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "antenna-samples/s, real-time factor at 32 ant/33 MHz/2 pol; X-engine % of peak"
+UNIT = "antenna-samples/s"
+SAMPLE_RATE = 66.67e6                      # per stream, 33.33 MHz Nyquist
+N_ANT, N_POL, N_FFT, N_INT = 32, 2, 2048, 8192
+N_IN, N_CHAN = N_ANT * N_POL, N_FFT // 2
+N_BL = N_ANT * (N_ANT + 1) // 2
+COH_ANTENNAS = 30                          # the "30-antenna phased" coherent beam
+CONFIG = {
+    "workload": "GMRT-scale FP32 FX correlator + beamformer: 32 ant x 2 pol int8 at 66.67 MS/s, "
+                "2048-pt FFT -> 1024 ch, 8192 spectra/integration, 528 baselines x 4 products, "
+                "incoherent (32 ant) + coherent (30 ant) beams",
+    "n_ant": N_ANT, "n_pol": N_POL, "n_fft": N_FFT, "n_int": N_INT, "xmode": "fp32",
+    "l2": "inputs larger than L2 (1.07 GB of samples per step)",
+    "parallelism": "time slices across ranks (replicas), no data-path collective",
+}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def set_n_int(n):
+    """Scale the integration length (profiling runs); the headline workload is 8192."""
+    global N_INT
+    N_INT = n
+    CONFIG["n_int"] = n
+    CONFIG["workload"] += f" [scaled to {n} spectra per integration]"
+
+
+def peaks():
+    p = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0,
+         "source": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained", "sm_max_mhz"):
+            if k in m:
+                p[k] = float(m[k])
+        p["source"] = "measured"
+    except (OSError, ValueError):
+        pass
+    return p
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", str(dev_id)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        rows = []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in out.splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                rows.append((float(f[0]), float(f[1]), float(f[2]), f[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        pmax = max(r[2] for r in rows)
+        load = [r for r in rows if r[2] >= 0.5 * pmax]          # samples taken under load
+        reasons = set()
+        for r in load:
+            for n, v in zip(names, r[3]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(load), "power_w_max": pmax}
+
+
+# ------------------------------------------------------------ work accounting
+
+def step_samples():
+    return N_IN * N_INT * N_FFT
+
+
+def stage_roofline(stage, mode, ms, pk):
+    """(bound, achieved, peak, unit, algorithmic amount per launch) of one kernel."""
+    if stage == "fengine":
+        out_b = N_CHAN * N_INT * 2 * N_IN * (4 if mode == "fp32" else 2)
+        alg = N_IN * N_INT * N_FFT + out_b + 2 * N_INT * N_CHAN * 4
+        return "hbm", alg / (ms * 1e-3) / 1e9, pk["hbm_gbs"], "GB/s", alg
+    if stage == "xengine" and mode == "fp32":
+        # useful FP32 work: n_in(n_in+1)/2 complex MACs (8 flop) per channel and frame
+        alg = 8.0 * N_CHAN * N_INT * N_IN * (N_IN + 1) / 2
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+        return "alu", alg / (ms * 1e-3) / 1e12, peak, "TFLOP/s", alg
+    # tensor-core X-engine: the fp16 operand read from HBM bounds it
+    alg = N_CHAN * N_INT * 2 * N_IN * 2 + N_CHAN * N_BL * 4 * 8
+    return "hbm", alg / (ms * 1e-3) / 1e9, pk["hbm_gbs"], "GB/s", alg
+
+
+def tensor_fraction(ms, pk):
+    """Executed tcgen05 flops (full 128x128 Gram per channel) vs the dense fp16 peak."""
+    executed = 2.0 * N_CHAN * N_INT * (2 * N_IN) ** 2
+    return executed / (ms * 1e-3) / 1e12 / pk["bf16_tflops_sustained"]
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged since."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        e = t[kernel]
+        src = os.path.join(ROOT, "paper_0910_1517_gb300", "csrc", e["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if h != e["source_sha"]:
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ oracle
+
+def oracle_sample(x, s, n_frames):
+    """FP64 oracle (F-engine, beams, X-engine) on n_frames of the workload; seconds."""
+    import oracle
+    t0 = time.perf_counter()
+    Y = oracle.fengine(x, s.n_ant, s.n_pol, s.n_fft, n_frames, s.delay, s.phi0, s.rate)
+    oracle.beams(Y, s.n_ant, s.n_pol, s.n_fft, coh_mask=(np.arange(s.n_ant) < COH_ANTENNAS).astype(np.uint8))
+    oracle.xengine(Y, s.n_ant, s.n_pol)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_auto(x, s, target_s=15.0):
+    import oracle
+    t1 = oracle_sample(x, s, 2)
+    n_frames = int(max(2, min(s.n_int, round(2 * target_s / max(t1, 1e-3)))))
+    n_frames -= n_frames % 2
+    dt = oracle_sample(x, s, n_frames)
+    v = N_IN * n_frames * N_FFT / dt
+    return {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"FP64 direct-DFT oracle (F-engine, beams, X-engine) on {n_frames} of the 8192 spectra of "
+                      f"all 64 inputs, all 1024 channels ({dt:.1f} s)"}
+
+
+def run_reference(args, world, rank):
+    """The FP64 oracle timed on bounded samples of the same workload (rank 0 only)."""
+    if rank != 0:
+        return 0
+    import oracle
+    from synth import make_config
+    oracle.build()
+    s = make_config(2, n_int=64)
+    t_one = oracle_sample(s.x, s, 1)
+    budget = 150.0
+    nf = int(max(1, min(64, budget / max(t_one, 1e-3) / max(1, args.steps + args.warmup))))
+    for _ in range(args.warmup):
+        oracle_sample(s.x, s, nf)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample(s.x, s, nf)
+    dt = time.perf_counter() - t0
+    v = args.steps * N_IN * nf * N_FFT / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": CONFIG,
+        "rtf": v / (N_IN * SAMPLE_RATE),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                         "sample": f"each step: FP64 direct-DFT oracle on {nf} spectra x 64 inputs x 1024 channels"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- ours
+
+def run_e2e(args, corr, torch, dist, s, coh, world):
+    K = args.steps
+    body = N_INT * N_FFT
+    hx0 = torch.from_numpy(np.ascontiguousarray(s.x[:, :body + 2048])).pin_memory()
+    hx = torch.from_numpy(np.ascontiguousarray(s.x[:, 2048:2048 + body])).pin_memory()
+    hv = torch.empty((N_CHAN, N_BL, 4, 2), dtype=torch.float32).pin_memory()
+    hb = torch.empty((2, N_INT, N_CHAN), dtype=torch.float32).pin_memory()
+    he = corr.corr_create(N_ANT, N_POL, N_FFT, N_INT)
+    corr.corr_set_delays(he, s.delay, s.phi0, s.rate)
+    corr.corr_set_beam_weights(he, None, None, None, coh)
+    seq = 0
+    corr.corr_push_samples(he, hx0.numpy(), seq)
+    seq += body + 2048
+    corr.corr_read_visibilities(he, hv.numpy())
+    k3 = max(5, min(K, 40))
+    for _ in range(2):                                     # warm the path
+        corr.corr_push_samples(he, hx.numpy(), seq)
+        seq += body
+        corr.corr_read_visibilities(he, hv.numpy())
+        corr.corr_read_beams(he, hb.numpy())
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(k3):
+        corr.corr_push_samples(he, hx.numpy(), seq)
+        seq += body
+        corr.corr_read_visibilities(he, hv.numpy())
+        corr.corr_read_beams(he, hb.numpy())
+    dt = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    e2e = {"value": world * k3 * step_samples() / dt, "unit": UNIT, "h2d_bytes_per_step": N_IN * body,
+           "d2h_bytes_per_step": hv.numel() * 4 + hb.numel() * 4, "steps": k3,
+           "path": "corr_push_samples (pinned host) + corr_read_visibilities + corr_read_beams"}
+    corr.corr_destroy(he)
+
+    return e2e
+
+
+def run_ours(args, world, rank, local_rank):
+    import torch
+    from paper_0910_1517_gb300 import build as libbuild
+    from paper_0910_1517_gb300 import corr
+    from synth import make_config
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if rank == 0:
+        libbuild.build()
+    if dist:
+        dist.barrier()
+    corr.load()
+    pk = peaks()
+
+    s = make_config(2, seed=1002 + rank, n_int=N_INT)    # this rank's time slice
+    n_avail = s.x.shape[1]
+    ld = ((n_avail + 15) // 16) * 16 + 16
+    xt = torch.zeros((N_IN, ld), dtype=torch.int8, device="cuda")
+    xt[:, :n_avail] = torch.from_numpy(s.x).cuda()
+    stream = torch.cuda.current_stream()
+    coh = (np.arange(N_ANT) < COH_ANTENNAS).astype(np.uint8)
+
+    h = corr.corr_create(N_ANT, N_POL, N_FFT, N_INT)
+    corr.corr_set_delays(h, s.delay, s.phi0, s.rate)
+    corr.corr_set_beam_weights(h, None, None, None, coh)
+
+    def steps(n, mode, g_start):
+        for j in range(n):
+            corr.corr_integrate_device(h, xt, n_avail=n_avail, g0=(g_start + j) * N_INT, stream=stream)
+
+    def timed(mode, k, w, sample_clocks=False):
+        corr.corr_set_mode(h, mode, 0, 1)
+        steps(w, mode, 0)
+        torch.cuda.synchronize()
+        corr.corr_set_timing(h, 1)
+        sampler = None
+        if sample_clocks:
+            bus = getattr(torch.cuda.get_device_properties(local_rank), "pci_bus_id", None)
+            sampler = ClockSampler(bus if bus else local_rank)
+            time.sleep(0.3)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        steps(k, mode, w)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clocks = sampler.stop() if sampler else None
+        ms = e0.elapsed_time(e1)
+        st, n = corr.corr_stage_times(h)
+        corr.corr_set_timing(h, 0)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, st / max(n, 1), clocks
+
+    K, W = args.steps, args.warmup
+    ms, st, clocks = timed(corr.CORR_FP32, K, W, sample_clocks=True)
+    value = world * K * step_samples() / (ms * 1e-3)
+    stage_names = ["phasor_setup", "fengine", "xengine", "beam_average"]
+
+    # precision forms of the X-engine on the same data (scales from this FP32 integration's autos)
+    corr.corr_set_scales(h, None)
+    modes = {}
+    for name, m in (() if args.no_extras else (("i8", corr.CORR_I8), ("f16", corr.CORR_F16))):
+        k2 = max(10, min(K, 100))
+        ms2, st2, _ = timed(m, k2, 3)
+        modes[name] = {
+            "value": world * k2 * step_samples() / (ms2 * 1e-3), "ms_per_step": ms2 / k2,
+            "stage_ms": dict(zip(stage_names, [round(v, 4) for v in st2])),
+            "xengine_speedup_vs_fp32": st[2] / st2[2], "step_speedup_vs_fp32": (ms / K) / (ms2 / k2),
+            "xengine_tensor_frac_of_sustained_peak": tensor_fraction(st2[2], pk),
+        }
+        bound, ach, peak, unit, _ = stage_roofline("xengine", name, st2[2], pk)
+        modes[name]["xengine_roofline"] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                                           "frac": ach / peak}
+    corr.corr_set_mode(h, corr.CORR_FP32, 0, 1)
+
+    # end to end through the public API: pinned host samples in, visibilities + beams out
+    e2e = None if args.no_extras else run_e2e(args, corr, torch, dist, s, coh, world)
+
+    # roofline of the dominant kernel of the FP32 step
+    # roofline of the dominant kernel of the FP32 step
+    dom = 1 if st[1] >= st[2] else 2
+    kname = {1: "fengine", 2: "xengine"}[dom]
+    bound, ach, peak, unit, alg = stage_roofline(kname, "fp32", st[dom], pk)
+    kern_id = {"fengine": "fengine_kernel", "xengine": "xengine_fp32_kernel"}[kname]
+    roofline = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                "traffic": traffic_for(kern_id), "kernel": kern_id,
+                "algorithmic_per_launch": alg, "peak_source": pk["source"],
+                "avg_launch_ms": st[dom]}
+    stages = {}
+    for i, nme in ((1, "fengine"), (2, "xengine")):
+        b, a, p, u, _ = stage_roofline(nme, "fp32", st[i], pk)
+        stages[nme] = {"ms": st[i], "bound": b, "achieved": a, "peak": p, "unit": u, "frac": a / p}
+    stages["phasor_setup"] = {"ms": st[0]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline_auto(s.x, s)
+
+    corr.corr_destroy(h)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded Gaussian sky + noise + tones, GMRT shapes)",
+            "config": CONFIG,
+            "rtf": value / (world * N_IN * SAMPLE_RATE),
+            "xengine_frac_of_fp32_peak": stages["xengine"]["frac"],
+            "roofline": roofline, "stages": stages, "precision_forms": modes,
+            "e2e": e2e, "gpu_launches": 3 * K, "clocks": clocks, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time only the FP32 step (no precision forms, no end-to-end leg); for profiling runs")
+    ap.add_argument("--n-int", type=int, default=N_INT,
+                    help="spectra per integration (default 8192, the GMRT-scale workload; smaller for profiling)")
+    args = ap.parse_args()
+    if args.n_int != N_INT:
+        set_n_int(args.n_int)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -150,6 +150,15 @@ int corr_device_outputs(corr_t* h, void** vis, void** beams, void** stream);
  * number of completed integrations. */
 int corr_info(corr_t* h, int64_t* out6);
 
+/* Per-stage CUDA-event timing, for measurement.  While enabled (enable = 1),
+ * every integration records events around its kernels on the stream it runs
+ * on.  corr_stage_times waits for them and sums, over the integrations
+ * recorded since its previous call (at most 4096), the milliseconds spent in
+ * ms4[0] phasor set-up, ms4[1] F-engine, ms4[2] X-engine, ms4[3] beam
+ * averaging; *n receives the number of integrations summed. */
+int corr_set_timing(corr_t* h, int enable);
+int corr_stage_times(corr_t* h, float* ms4, int* n);
+
 #if defined(__GNUC__)
 #pragma GCC visibility pop
 #endif

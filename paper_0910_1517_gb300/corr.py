@@ -42,6 +42,8 @@ SIGNATURES = {
     "corr_device_outputs": ([_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                              ctypes.POINTER(ctypes.c_void_p)], _I),
     "corr_info": ([_P, _P], _I),
+    "corr_set_timing": ([_P, _I], _I),
+    "corr_stage_times": ([_P, _P, ctypes.POINTER(ctypes.c_int)], _I),
 }
 
 _lib = None
@@ -207,3 +209,15 @@ def corr_device_outputs(h):
     v, b, s = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
     _ok(load().corr_device_outputs(h, ctypes.byref(v), ctypes.byref(b), ctypes.byref(s)))
     return v.value, b.value, s.value
+
+
+def corr_set_timing(h, enable: int = 1):
+    return _ok(load().corr_set_timing(h, int(enable)))
+
+
+def corr_stage_times(h):
+    """(ms summed per stage [set-up, F-engine, X-engine, beam averaging], integrations summed)."""
+    ms = np.zeros(4, dtype=np.float32)
+    n = ctypes.c_int()
+    _ok(load().corr_stage_times(h, _ptr(ms), ctypes.byref(n)))
+    return ms.astype(np.float64), int(n.value)

@@ -80,11 +80,25 @@ struct corr {
     // bookkeeping
     int64_t launched = 0, completed = 0;
     int last_mode = -1;
+    // per-stage timing: kTimedMax integrations x 5 events (before set-up and after each stage)
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;
+    int t_count = 0;
 };
 
 namespace {
 
+constexpr int kTimedMax = 4096;
+constexpr int kStages = 4;
+
 int64_t ring_need(const corr* h) { return static_cast<int64_t>(h->n_int) * h->n_fft + h->max_delay; }
+
+// record the boundary event `b` (0..kStages) of the current timed integration
+int mark(corr* h, int b, cudaStream_t s) {
+    if (!h->timing || h->t_count >= kTimedMax) return CORR_OK;
+    CU(cudaEventRecord(h->tev[static_cast<size_t>(h->t_count) * (kStages + 1) + b], s));
+    return CORR_OK;
+}
 
 int alloc_ring(corr* h) {
     if (h->d_ring) cudaFree(h->d_ring);
@@ -130,6 +144,7 @@ int run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, int64
     std::memcpy(h->h_model + nd, h->phi0.data(), nd * sizeof(double));
     std::memcpy(h->h_model + 2 * nd, h->rate.data(), nd * sizeof(double));
     CU(cudaMemcpyAsync(h->d_model, h->h_model, 3 * nd * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (int rc = mark(h, 0, s)) return rc;
     CU(launch_phasor_setup(h->n_ant, h->n_chan, h->n_fft, h->n_int, g0, h->d_model, h->d_model + nd,
                            h->d_model + 2 * nd, h->d_pf, h->d_ff, h->d_D, s));
     FeParams fp{};
@@ -153,7 +168,9 @@ int run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, int64
     fp.tw = h->d_tw;
     fp.err = h->d_err;
     const int fmode = h->xmode == CORR_FP32 ? OUT_FP32 : (h->xmode == CORR_I8 ? OUT_I8 : OUT_F16);
+    if (int rc = mark(h, 1, s)) return rc;
     CU(launch_fengine(fp, fmode, s));
+    if (int rc = mark(h, 2, s)) return rc;
     XParams xp{};
     xp.spec = h->d_spec;
     xp.n_ant = h->n_ant;
@@ -170,7 +187,10 @@ int run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, int64
         CU(launch_xengine_fp32(xp, h->n_sm, s));
     else
         CU(launch_xengine_tc(xp, h->n_sm, s));
+    if (int rc = mark(h, 3, s)) return rc;
     if (h->beam_avg > 1) CU(launch_beam_average(h->d_beams_raw, h->d_beams, h->n_int, h->n_chan, h->beam_avg, s));
+    if (int rc = mark(h, 4, s)) return rc;
+    if (h->timing && h->t_count < kTimedMax) h->t_count += 1;
     CU(cudaEventRecord(h->ev_done, s));
     h->launched += 1;
     h->last_mode = h->xmode;
@@ -343,6 +363,7 @@ int corr_destroy(corr_t* h) {
         if (b) cudaFree(b);
     if (h->d_beams && h->d_beams != h->d_beams_raw) cudaFree(h->d_beams);
     if (h->h_model) cudaFreeHost(h->h_model);
+    for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
     if (h->ev_done) cudaEventDestroy(h->ev_done);
     if (h->ev_aux) cudaEventDestroy(h->ev_aux);
     if (h->stream) cudaStreamDestroy(h->stream);
@@ -545,6 +566,35 @@ int corr_device_outputs(corr_t* h, void** vis, void** beams, void** stream) {
     if (vis) *vis = h->d_vis;
     if (beams) *beams = h->d_beams;
     if (stream) *stream = h->stream;
+    return CORR_OK;
+}
+
+int corr_set_timing(corr_t* h, int enable) {
+    if (int rc = check_handle(h)) return rc;
+    if (enable && h->tev.empty()) {
+        h->tev.resize(static_cast<size_t>(kTimedMax) * (kStages + 1), nullptr);
+        for (auto& e : h->tev) CU(cudaEventCreate(&e));
+    }
+    h->timing = enable != 0;
+    h->t_count = 0;
+    return CORR_OK;
+}
+
+int corr_stage_times(corr_t* h, float* ms4, int* n) {
+    if (int rc = check_handle(h)) return rc;
+    if (!ms4 || !n) return fail(CORR_E_INVAL, "null output");
+    for (int b = 0; b < kStages; ++b) ms4[b] = 0.0f;
+    *n = h->t_count;
+    for (int t = 0; t < h->t_count; ++t) {
+        cudaEvent_t* e = &h->tev[static_cast<size_t>(t) * (kStages + 1)];
+        CU(cudaEventSynchronize(e[kStages]));
+        for (int b = 0; b < kStages; ++b) {
+            float ms = 0.0f;
+            CU(cudaEventElapsedTime(&ms, e[b], e[b + 1]));
+            ms4[b] += ms;
+        }
+    }
+    h->t_count = 0;
     return CORR_OK;
 }
 

@@ -155,10 +155,13 @@ def test_i8_bit_exact_on_requantised_spectra(env):
     qo = orc.requant(Y, sc[:, chans].astype(np.float64))
     mism = np.abs(qg[:, :, chans].astype(int) - qo.astype(int))
     frac = float((mism > 0).mean())
-    e_v = vis_norm_error(r["V"][chans], V, s.n_ant, s.n_pol)
-    print(f"i8: requant mismatch fraction {frac:.2e} (max {mism.max()}), vis error vs FP64 {e_v:.2e}")
+    e_ch = [vis_norm_error(r["V"][c:c + 1], V[j:j + 1], s.n_ant, s.n_pol) for j, c in enumerate(chans)]
+    print(f"i8: requant mismatch fraction {frac:.2e} (max {mism.max()}), vis error vs FP64 per channel "
+          + " ".join(f"{c}:{e:.1e}" for c, e in zip(chans, e_ch)))
     assert mism.max() <= 1 and frac <= 1e-3
-    assert e_v <= 5e-2
+    # quantisation noise of a 4-sigma / 127 step: ~3e-3 at circular channels; the DC bin of a real
+    # signal is real before the fringe rotation, so its 4-sigma scale clips and it carries more
+    assert e_ch[0] <= 6e-2 and max(e_ch[1:]) <= 2e-2
     corr.corr_destroy(h)
 
 
