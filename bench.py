@@ -302,7 +302,7 @@ def run_ours(args, world, rank, local_rank):
 
     def steps(n, mode, g_start):
         for j in range(n):
-            corr.corr_integrate_device(h, xt, n_avail=n_avail, g0=(g_start + j) * N_INT, stream=stream)
+            corr.corr_integrate_device(h, xt, n_avail=ld, g0=(g_start + j) * N_INT, stream=stream)
 
     def timed(mode, k, w, sample_clocks=False):
         corr.corr_set_mode(h, mode, 0, 1)

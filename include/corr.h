@@ -110,14 +110,16 @@ int corr_set_scales(corr_t* h, const float* scale);
 int corr_push_samples(corr_t* h, const int8_t* x, int64_t n, int64_t seq);
 
 /* As corr_push_samples with x in device memory (row stride n); the copies are
- * ordered after work already on `stream` (a cudaStream_t, NULL = legacy). */
+ * ordered after work already on `stream` (a cudaStream_t; NULL and
+ * cudaStreamLegacy both name the legacy default stream here). */
 int corr_push_samples_device(corr_t* h, const int8_t* x, int64_t n, int64_t seq, void* stream);
 
 /* One whole integration straight from device memory, no copy of the input:
  * row i of input starts at x + i*ld (x and ld 16-byte aligned), holds n_avail
  * readable samples, and n_avail >= n_int*n_fft + max_a D_a.  Frames are global
- * frames g0 .. g0+n_int-1 (fringe phase index).  Runs on `stream` (NULL =
- * the handle's stream); returns once the work is queued. */
+ * frames g0 .. g0+n_int-1 (fringe phase index).  Runs on `stream`, a
+ * cudaStream_t: NULL selects the handle's own stream, cudaStreamLegacy the
+ * legacy default stream.  Returns once the work is queued. */
 int corr_integrate_device(corr_t* h, const int8_t* x, int64_t ld, int64_t n_avail,
                           int64_t g0, void* stream);
 

@@ -85,12 +85,17 @@ def _ptr(a):
     return ctypes.c_void_p(a.data_ptr())
 
 
+CUDA_STREAM_LEGACY = 1   # cudaStreamLegacy: the legacy default stream
+
+
 def _stream(s):
+    """cudaStream_t of a torch stream or raw handle; torch's default stream (handle 0) is
+    the legacy default stream, which the C ABI spells cudaStreamLegacy (NULL means the
+    handle's own stream there)."""
     if s is None:
         return None
-    if isinstance(s, int):
-        return ctypes.c_void_p(s)
-    return ctypes.c_void_p(s.cuda_stream)
+    h = s if isinstance(s, int) else s.cuda_stream
+    return ctypes.c_void_p(h if h else CUDA_STREAM_LEGACY)
 
 
 def corr_create(n_ant: int, n_pol: int, n_fft: int, n_int: int):

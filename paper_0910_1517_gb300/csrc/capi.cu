@@ -321,8 +321,7 @@ int corr_create(corr_t** out, int n_ant, int n_pol, int n_fft, int n_int) {
     CUB(dalloc(&h->d_wcoh, na * nch));
     CUB(dalloc(&h->d_ginc, na));
     CUB(dalloc(&h->d_scale, ni * nch));
-    CUB(dalloc(&h->d_tw, nch + nch / 2 + 1));
-    const size_t spec_bytes = nch * static_cast<size_t>(n_int) * 2 * ni * sizeof(float);
+    const size_t spec_bytes = nch * static_cast<size_t>(n_int) * rows_fp32(h->n_in) * sizeof(float);
     CUB(cudaMalloc(&h->d_spec, spec_bytes));
     CUB(dalloc(&h->d_beams_raw, 2 * static_cast<size_t>(n_int) * nch));
     h->d_beams = h->d_beams_raw;
@@ -334,16 +333,9 @@ int corr_create(corr_t** out, int n_ant, int n_pol, int n_fft, int n_int) {
     CUB(cudaMemset(h->d_vis, 0, nvis * sizeof(float2)));
     CUB(cudaMemset(h->d_vis_int, 0, nvis * sizeof(int2)));
     CUB(cudaMemset(h->d_scale, 0, ni * nch * sizeof(float)));
-    // FFT twiddles in FP64, rounded once: exp(-2 pi i m / M) and exp(-2 pi i k / N)
     {
-        std::vector<float2> tw(nch + nch / 2 + 1);
-        const double two_pi = 6.283185307179586476925286766559;
-        for (size_t m = 0; m < nch; ++m)
-            tw[m] = make_float2(static_cast<float>(std::cos(two_pi * m / nch)),
-                                static_cast<float>(-std::sin(two_pi * m / nch)));
-        for (size_t k = 0; k <= nch / 2; ++k)
-            tw[nch + k] = make_float2(static_cast<float>(std::cos(two_pi * k / n_fft)),
-                                      static_cast<float>(-std::sin(two_pi * k / n_fft)));
+        const std::vector<float2> tw = fengine_twiddles(n_fft);
+        CUB(dalloc(&h->d_tw, tw.size()));
         CUB(cudaMemcpy(h->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
     }
 #undef CUB
@@ -545,8 +537,8 @@ int corr_read_spectra(corr_t* h, int k0, int nk, float* out) {
     if (int rc = settle(h, 1)) return rc;
     if (h->last_mode != CORR_FP32) return fail(CORR_E_STATE, "last integration was not CORR_FP32");
     if (!out || k0 < 0 || nk < 0 || k0 + nk > h->n_chan) return fail(CORR_E_INVAL, "channel range");
-    const int R = 2 * h->n_in, ntb = h->n_int / kTbFp32;
-    const size_t per_ch = static_cast<size_t>(ntb) * R * kTbFp32;
+    const int R = 2 * h->n_in, Rp = rows_fp32(h->n_in), ntb = h->n_int / kTbFp32;
+    const size_t per_ch = static_cast<size_t>(ntb) * Rp * kTbFp32;
     std::vector<float> buf(per_ch * nk);
     CU(cudaMemcpy(buf.data(), static_cast<const float*>(h->d_spec) + per_ch * k0, buf.size() * sizeof(float),
                   cudaMemcpyDeviceToHost));
@@ -556,7 +548,7 @@ int corr_read_spectra(corr_t* h, int k0, int nk, float* out) {
                 for (int e = 0; e < kTbFp32; ++e) {
                     const int i = r / 2, cc = r % 2, t = kb * kTbFp32 + e;
                     out[((static_cast<size_t>(i) * h->n_int + t) * nk + c) * 2 + cc] =
-                        buf[((static_cast<size_t>(c) * ntb + kb) * R + r) * kTbFp32 + e];
+                        buf[((static_cast<size_t>(c) * ntb + kb) * Rp + swz_row(r)) * kTbFp32 + e];
                 }
     return CORR_OK;
 }

@@ -19,6 +19,9 @@
 //   5. the spectra are transposed in shared memory and written in the K-block
 //      layout the X-engines read (FP32, or requantised int8-valued / FP16
 //      values for the tensor-core X-engine), 32-byte runs per (channel, input).
+#include <cmath>
+#include <vector>
+
 #include "common.cuh"
 #include "fengine.cuh"
 
@@ -29,6 +32,7 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kE = 16;                      // complex points per thread per FFT
 constexpr int kChanFrames = 8192;           // F * M per CTA
+constexpr int kMaxAnt = 128;
 
 template <int M>
 struct Plan {
@@ -109,10 +113,11 @@ struct Dft<1> {
     __device__ __forceinline__ static void run(float2*) {}
 };
 
-// Stockham pass of radix R over span Ns for one frame: read X[b + r*M/R], twiddle,
-// DFT, write X[(b/Ns)*Ns*R + b%Ns + r*Ns].  Reads come from `src` (padded frame).
+// Stockham pass of radix R over span Ns for one frame: read X[b + r*M/R], twiddle by
+// W_{Ns R}^{(b mod Ns) r}, DFT, write X[(b/Ns)*Ns*R + b%Ns + r*Ns].  The pass's twiddles are
+// tabulated as tw[r*Ns + j] so that a warp's consecutive j read consecutive words.
 template <int M, int R, int Ns>
-__device__ __forceinline__ void pass_load(const float2* __restrict__ src, const float2* __restrict__ twM, int t,
+__device__ __forceinline__ void pass_load(const float2* __restrict__ src, const float2* __restrict__ tw, int t,
                                           float2 (&v)[kE]) {
     constexpr int T = M / kE, NB = M / R, PER = kE / R;
 #pragma unroll
@@ -120,11 +125,9 @@ __device__ __forceinline__ void pass_load(const float2* __restrict__ src, const 
         const int b = t + m * T;
 #pragma unroll
         for (int r = 0; r < R; ++r) v[m * R + r] = src[pad32(b + r * NB)];
-        if constexpr (Ns > 1) {
-            const int j = b % Ns;
+        const int j = b % Ns;
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[m * R + r] = cmul(twM[(j * r) * (M / (Ns * R))], v[m * R + r]);
-        }
+        for (int r = 1; r < R; ++r) v[m * R + r] = cmul(tw[r * Ns + j], v[m * R + r]);
         Dft<R>::template run<1>(v + m * R);
     }
 }
@@ -141,6 +144,16 @@ __device__ __forceinline__ void pass_store(float2* __restrict__ dst, int t, cons
     }
 }
 
+// barrier among the T threads of one FFT group (group g); a warp when T <= 32
+template <int T>
+__device__ __forceinline__ void group_sync(int g) {
+    if constexpr (T <= 32) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(T) : "memory");
+    }
+}
+
 // swizzle of the transposed [channel][frame] buffer: spreads a warp's same-frame stores over banks
 template <int F>
 __device__ __forceinline__ int tswz(int ch) {
@@ -148,21 +161,43 @@ __device__ __forceinline__ int tswz(int ch) {
     return (ch / rows_per_line) & (F - 1);
 }
 
+template <int M>
+struct Smem {
+    using P = Plan<M>;
+    static constexpr bool kTabSmem = M <= 1024;                       // per-antenna tables staged in smem
+    static constexpr int kTw = P::R2 * 16 + (P::R3 > 1 ? P::R3 * 16 * P::R2 : 0) + M / 2 + 1;
+    static constexpr size_t stage = 0;
+    static constexpr size_t X = stage + 2 * static_cast<size_t>(P::STAGE);
+    static constexpr size_t inc = X + sizeof(float2) * P::F * P::PADM;
+    static constexpr size_t coh = inc + sizeof(float) * P::F * M;
+    static constexpr size_t tw = coh + sizeof(float2) * P::F * M;
+    static constexpr size_t tab = ((tw + sizeof(float2) * kTw + 127) / 128) * 128;   // bulk-copy target
+    static constexpr size_t total = tab + (kTabSmem ? sizeof(float2) * 2 * M : 0);
+    static_assert(total <= 232448, "F-engine shared memory exceeds 227 KB");
+    static_assert(X % 16 == 0 && tab % 16 == 0 && P::STAGE % 16 == 0, "bulk-copy targets are 16-byte aligned");
+};
+
 template <int M, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) fengine_kernel(const FeParams p) {
     using P = Plan<M>;
+    using S = Smem<M>;
     constexpr int T = P::T, F = P::F, N = P::N;
+    constexpr int Ns3 = P::R1 * P::R2;
     constexpr int TB = (MODE == OUT_FP32) ? kTbFp32 : kTbHalf;
     constexpr int L = (F < TB) ? F : TB;                 // frames per output run
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char* stage0 = smem;
-    float2* X = reinterpret_cast<float2*>(smem + 2 * P::STAGE);           // F * PADM
-    float* inc = reinterpret_cast<float*>(X + F * P::PADM);                // F * M
-    float2* coh = reinterpret_cast<float2*>(inc + F * M);                  // F * M
-    float2* twM = coh + F * M;                                             // M
-    float2* twN = twM + M;                                                 // M/2 + 1
+    unsigned char* stage0 = smem + S::stage;
+    float2* X = reinterpret_cast<float2*>(smem + S::X);           // F * PADM
+    float* inc = reinterpret_cast<float*>(smem + S::inc);        // F * M
+    float2* coh = reinterpret_cast<float2*>(smem + S::coh);      // F * M
+    float2* tw2 = reinterpret_cast<float2*>(smem + S::tw);       // [R2][16]
+    float2* tw3 = tw2 + P::R2 * 16;                               // [R3][Ns3]
+    float2* twN = tw3 + (P::R3 > 1 ? P::R3 * Ns3 : 0);            // [M/2 + 1]
+    float2* tab = reinterpret_cast<float2*>(smem + S::tab);      // [pf | wcoh] of one antenna
     __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t tbar;
     __shared__ int abort_flag;
+    __shared__ int Ds[kMaxAnt];       // integer delays, read every iteration
 
     const int tid = threadIdx.x;
     const int f = tid / T;            // frame within the CTA owned by this thread's FFT group
@@ -172,79 +207,119 @@ __global__ void __launch_bounds__(kThreads, 1) fengine_kernel(const FeParams p) 
     const bool live = f < n_fr;
     const int R = 2 * p.n_in;
 
-    for (int m = tid; m < M + M / 2 + 1; m += kThreads) (m < M ? twM[m] : twN[m - M]) = p.tw[m];
+    for (int m = tid; m < S::kTw; m += kThreads) tw2[m] = p.tw[m];
     for (int m = tid; m < F * M; m += kThreads) inc[m] = 0.0f;
+    for (int m = tid; m < p.n_ant; m += kThreads) Ds[m] = p.D[m];
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
+        mbar_init(&tbar, 1);
         fence_mbar_init();
         abort_flag = 0;
     }
     __syncthreads();
 
-    const int n_iter = p.n_in;  // pol-major order: it = p * n_ant + a
+    const int n_iter = p.n_in;  // polarisation-major order: it = pol * n_ant + a
+    // Called by all of warp 0: lane 0 issues the bulk copy of the F frames of input `it`
+    // (offset by its integer delay); bytes past the last 16-byte boundary are copied by the
+    // lanes only when rounding the copy up would read past the row's readable samples.
     auto issue = [&](int it) {
         const int pol = it / p.n_ant, a = it % p.n_ant;
         const int i = a * p.n_pol + pol;
         unsigned char* dst = stage0 + (it & 1) * P::STAGE;
-        const int64_t s0 = static_cast<int64_t>(t0) * N + p.D[a];
+        const int64_t s0 = static_cast<int64_t>(t0) * N + Ds[a];
         const int64_t aligned = s0 & ~static_cast<int64_t>(15);
         const int64_t end = s0 + static_cast<int64_t>(n_fr) * N;
-        const uint32_t bulk = static_cast<uint32_t>((end - aligned) & ~static_cast<int64_t>(15));
+        const int64_t up = (end + 15) & ~static_cast<int64_t>(15);
+        const int64_t bulk_end = up <= p.n_avail ? up : (end & ~static_cast<int64_t>(15));
+        const uint32_t bulk = static_cast<uint32_t>(bulk_end - aligned);
         const int8_t* row = p.x + static_cast<int64_t>(i) * p.ld;
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bar[it & 1], bulk);
-        bulk_g2s(dst, row + aligned, bulk, &bar[it & 1]);
-        for (int64_t q = aligned + bulk; q < end; ++q) dst[q - aligned] = static_cast<unsigned char>(row[q]);
+        const int lane = tid & 31;
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar[it & 1], bulk);
+            bulk_g2s(dst, row + aligned, bulk, &bar[it & 1]);
+        }
+        const int64_t q = bulk_end + lane;
+        if (q < end) dst[q - aligned] = static_cast<unsigned char>(row[q]);
     };
-    if (tid == 0) issue(0);
+    auto issue_tab = [&](int it) {  // phasor and beam-weight rows of the antenna of input `it`
+        if constexpr (S::kTabSmem) {
+            const int a = it % p.n_ant;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&tbar, 2 * M * sizeof(float2));
+            bulk_g2s(tab, p.pf + static_cast<int64_t>(a) * M, M * sizeof(float2), &tbar);
+            bulk_g2s(tab + M, p.wcoh + static_cast<int64_t>(a) * M, M * sizeof(float2), &tbar);
+        }
+    };
+    __syncthreads();                 // Ds visible to warp 0
+    if (tid < 32) issue(0);
+    if (tid == 0) issue_tab(0);
     __syncthreads();
 
-    for (int it = 0; it < n_iter; ++it) {
+    int it = 0;
+    for (; it < n_iter; ++it) {
         const int pol = it / p.n_ant, a = it % p.n_ant;
         const int i = a * p.n_pol + pol;
-        if (tid == 0 && it + 1 < n_iter) issue(it + 1);
+        if (tid < 32 && it + 1 < n_iter) issue(it + 1);
+        // fringe phasor and incoherent weight: loaded now, used after the FFT
+        const float2 fr = p.ff[static_cast<int64_t>(a) * p.n_int + min(t0 + f, p.n_int - 1)];
+        const float g2 = p.ginc[a];
         if (!mbar_wait(&bar[it & 1], (it >> 1) & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
-        __syncthreads();
-        if (abort_flag) break;
-        const int64_t s0 = static_cast<int64_t>(t0) * N + p.D[a];
+        const int64_t s0 = static_cast<int64_t>(t0) * N + Ds[a];
         const unsigned char* st = stage0 + (it & 1) * P::STAGE + (s0 & 15) + f * N;
         float2* Xf = X + f * P::PADM;
 
-        // ---- pass 1: radix-16 straight from the int8 staging buffer
+        // ---- pass 1: radix-16 straight from the int8 staging buffer (z[n] = x[2n] + i x[2n+1])
         float2 v[kE];
         {
             constexpr int NB = M / P::R1;
+            if ((s0 & 1) == 0) {                       // pairs are 2-byte aligned: one load each
+                const uint16_t* st16 = reinterpret_cast<const uint16_t*>(st);
 #pragma unroll
-            for (int r = 0; r < kE; ++r) {
-                const int n = t + r * NB;
-                const signed char lo = static_cast<signed char>(st[2 * n]);
-                const signed char hi = static_cast<signed char>(st[2 * n + 1]);
-                v[r] = make_float2(static_cast<float>(lo), static_cast<float>(hi));
+                for (int r = 0; r < kE; ++r) {
+                    const uint16_t w = st16[t + r * NB];
+                    v[r] = make_float2(static_cast<float>(static_cast<signed char>(w & 0xff)),
+                                       static_cast<float>(static_cast<signed char>(w >> 8)));
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < kE; ++r) {
+                    const int n = t + r * NB;
+                    v[r] = make_float2(static_cast<float>(static_cast<signed char>(st[2 * n])),
+                                       static_cast<float>(static_cast<signed char>(st[2 * n + 1])));
+                }
             }
             Dft<16>::template run<1>(v);
         }
-        __syncthreads();  // previous iteration's readers of X are done
+        __syncthreads();  // every group left the previous iteration's transposed buffer (aliases X)
+        if (abort_flag) break;
         pass_store<M, P::R1, 1>(Xf, t, v);
-        __syncthreads();
+        group_sync<T>(f);
         // ---- pass 2
-        pass_load<M, P::R2, P::R1>(Xf, twM, t, v);
-        __syncthreads();
+        pass_load<M, P::R2, P::R1>(Xf, tw2, t, v);
+        group_sync<T>(f);
         pass_store<M, P::R2, P::R1>(Xf, t, v);
-        __syncthreads();
+        group_sync<T>(f);
         // ---- pass 3
         if constexpr (P::R3 > 1) {
-            pass_load<M, P::R3, P::R1 * P::R2>(Xf, twM, t, v);
-            __syncthreads();
-            pass_store<M, P::R3, P::R1 * P::R2>(Xf, t, v);
-            __syncthreads();
+            pass_load<M, P::R3, Ns3>(Xf, tw3, t, v);
+            group_sync<T>(f);
+            pass_store<M, P::R3, Ns3>(Xf, t, v);
+            group_sync<T>(f);
         }
 
         // ---- real split, Eq. 2 phasor, beams
-        const float2 fr = p.ff[static_cast<int64_t>(a) * p.n_int + min(t0 + f, p.n_int - 1)];
-        const float g2 = p.ginc[a];
-        const float2* pfa = p.pf + static_cast<int64_t>(a) * M;
-        const float2* wa = p.wcoh + static_cast<int64_t>(a) * M;
+        const float2* pfa;
+        const float2* wa;
+        if constexpr (S::kTabSmem) {
+            if (!mbar_wait(&tbar, it & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
+            pfa = tab;
+            wa = tab + M;
+        } else {
+            pfa = p.pf + static_cast<int64_t>(a) * M;
+            wa = p.wcoh + static_cast<int64_t>(a) * M;
+        }
         float2 y[kE];
         int ch[kE];
 #pragma unroll
@@ -296,7 +371,8 @@ __global__ void __launch_bounds__(kThreads, 1) fengine_kernel(const FeParams p) 
         }
 
         // ---- transpose through shared memory and write the K-block layout
-        __syncthreads();  // all reads of X are done
+        __syncthreads();  // all reads of X and of the antenna tables are done
+        if (tid == 0 && it + 1 < n_iter) issue_tab(it + 1);
         float2* Tb = X;   // [M][F], swizzled
 #pragma unroll
         for (int e = 0; e < kE; ++e) Tb[ch[e] * F + (f ^ tswz<F>(ch[e]))] = y[e];
@@ -314,20 +390,23 @@ __global__ void __launch_bounds__(kThreads, 1) fengine_kernel(const FeParams p) 
 #pragma unroll
                 for (int l = 0; l < L; ++l) val[l] = Tb[k * F + ((fl0 + l) ^ tswz<F>(k))];
                 const int64_t ntb = p.n_int / TB;
-                const int64_t rowbase = ((static_cast<int64_t>(k) * ntb + kb) * R + 2 * i) * TB + off;
                 if constexpr (MODE == OUT_FP32) {
-                    float* o = static_cast<float*>(p.spec) + rowbase;
+                    const int Rp = rows_fp32(p.n_in);
+                    const int64_t blk = (static_cast<int64_t>(k) * ntb + kb) * Rp;
+                    float* ore = static_cast<float*>(p.spec) + (blk + swz_row(2 * i)) * TB + off;
+                    float* oim = static_cast<float*>(p.spec) + (blk + swz_row(2 * i + 1)) * TB + off;
                     float re[L], im[L];
 #pragma unroll
                     for (int l = 0; l < L; ++l) { re[l] = val[l].x; im[l] = val[l].y; }
                     if constexpr (L == 4) {
-                        *reinterpret_cast<float4*>(o) = make_float4(re[0], re[1], re[2], re[3]);
-                        *reinterpret_cast<float4*>(o + TB) = make_float4(im[0], im[1], im[2], im[3]);
+                        *reinterpret_cast<float4*>(ore) = make_float4(re[0], re[1], re[2], re[3]);
+                        *reinterpret_cast<float4*>(oim) = make_float4(im[0], im[1], im[2], im[3]);
                     } else {
 #pragma unroll
-                        for (int l = 0; l < L; ++l) { o[l] = re[l]; o[TB + l] = im[l]; }
+                        for (int l = 0; l < L; ++l) { ore[l] = re[l]; oim[l] = im[l]; }
                     }
                 } else {
+                    const int64_t rowbase = ((static_cast<int64_t>(k) * ntb + kb) * R + 2 * i) * TB + off;
                     const float s = sc[k];
                     __half re[L], im[L];
 #pragma unroll
@@ -369,14 +448,17 @@ __global__ void __launch_bounds__(kThreads, 1) fengine_kernel(const FeParams p) 
     __syncthreads();
     if (!abort_flag) {
         for (int m = tid; m < n_fr * M; m += kThreads) p.beams[static_cast<int64_t>(t0) * M + m] = inc[m];
+    } else if (tid == 0) {
+        // copies issued ahead of an aborted iteration must land before the CTA exits
+        if (it + 1 < n_iter) mbar_wait(&bar[(it + 1) & 1], ((it + 1) >> 1) & 1, nullptr, 0);
+        if (S::kTabSmem) mbar_wait(&tbar, it & 1, nullptr, 0);
     }
 }
 
 template <int M, int MODE>
 cudaError_t launch_t(const FeParams& p, cudaStream_t s) {
     using P = Plan<M>;
-    const size_t smem = 2 * P::STAGE + sizeof(float2) * (P::F * P::PADM + P::F * M + M + M / 2 + 1) +
-                        sizeof(float) * P::F * M;
+    const size_t smem = Smem<M>::total;
     cudaError_t e = cudaFuncSetAttribute(fengine_kernel<M, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
@@ -448,10 +530,35 @@ __global__ void beam_average_kernel(const float* __restrict__ raw, float* __rest
 }  // namespace
 
 size_t fengine_smem_bytes(int n_fft) {
+    switch (n_fft / 2) {
+        case 32: return Smem<32>::total;
+        case 64: return Smem<64>::total;
+        case 128: return Smem<128>::total;
+        case 256: return Smem<256>::total;
+        case 512: return Smem<512>::total;
+        case 1024: return Smem<1024>::total;
+        case 2048: return Smem<2048>::total;
+        default: return 0;
+    }
+}
+
+std::vector<float2> fengine_twiddles(int n_fft) {
+    // [R2][16] pass-2, [R3][16 R2] pass-3 and [M/2 + 1] real-split twiddles, from FP64
     const int M = n_fft / 2;
-    const int F = kChanFrames / M;
-    return 2 * (static_cast<size_t>(F) * n_fft + 32) +
-           sizeof(float2) * (F * (M + M / 32) + F * M + M + M / 2 + 1) + sizeof(float) * F * M;
+    const int R2 = (M / 16 >= 16) ? 16 : M / 16, R3 = M / (16 * R2), Ns3 = 16 * R2;
+    const double two_pi = 6.283185307179586476925286766559;
+    std::vector<float2> tw;
+    auto w = [&](double num, double den) {
+        return make_float2(static_cast<float>(std::cos(two_pi * num / den)),
+                           static_cast<float>(-std::sin(two_pi * num / den)));
+    };
+    for (int r = 0; r < R2; ++r)
+        for (int j = 0; j < 16; ++j) tw.push_back(w(static_cast<double>(j) * r, 16.0 * R2));
+    if (R3 > 1)
+        for (int r = 0; r < R3; ++r)
+            for (int j = 0; j < Ns3; ++j) tw.push_back(w(static_cast<double>(j) * r, static_cast<double>(M)));
+    for (int k = 0; k <= M / 2; ++k) tw.push_back(w(k, n_fft));
+    return tw;
 }
 
 int fengine_frames_per_cta(int n_fft) { return kChanFrames / (n_fft / 2); }

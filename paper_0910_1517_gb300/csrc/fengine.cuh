@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 namespace gbx {
 
@@ -12,8 +13,16 @@ enum OutMode : int { OUT_FP32 = 0, OUT_I8 = 1, OUT_F16 = 2 };
 //   S[k][kb][r][TB]   k channel, kb = t / TB, r = 2*i + c (c = 0 re, 1 im), TB = t % TB
 // with TB = 4 (fp32) or 8 (fp16).  One (k, kb) block is R = 2*n_in rows of 16 bytes,
 // i.e. exactly the no-swizzle K-major canonical layout of a tcgen05 operand tile.
+// The FP32 layout pads the rows of a block to Rp = round_up(2 n_in, 8) and stores
+// row r at physical row swz_row(r): the 16-byte rows of each 128-byte line are
+// XOR-permuted by the line index, so that the CUDA-core X-engine's threads,
+// which read the same row of different 8-row groups at once, hit distinct banks.
+// (The fp16 layout stays unswizzled: it is the tensor cores' operand image.)
 constexpr int kTbFp32 = 4;
 constexpr int kTbHalf = 8;
+
+__host__ __device__ __forceinline__ int rows_fp32(int n_in) { return ((2 * n_in + 7) / 8) * 8; }
+__host__ __device__ __forceinline__ int swz_row(int r) { return (r & ~7) | ((r & 7) ^ ((r >> 3) & 7)); }
 
 struct FeParams {
     const int8_t* x;       // input rows, row i at x + i*ld
@@ -28,13 +37,15 @@ struct FeParams {
     const float* scale;    // [n_in][n_chan] requantisation scales (I8 / F16)
     void* spec;            // spectra in the K-block layout
     float* beams;          // [2][n_int][n_chan] raw-resolution beams (0 inc, 1 coh)
-    const float2* tw;      // [n_chan] exp(-2 pi i m / n_chan), then [n_chan/2 + 1] exp(-2 pi i k / n_fft)
+    const float2* tw;      // FFT twiddles laid out by fengine_twiddles()
     unsigned* err;
 };
 
 // Dynamic shared memory needed by the F-engine for a given FFT size.
 size_t fengine_smem_bytes(int n_fft);
 int fengine_frames_per_cta(int n_fft);
+// Twiddle tables of the F-engine's FFT plan for n_fft, computed in FP64 and rounded once.
+std::vector<float2> fengine_twiddles(int n_fft);
 cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s);
 
 // pf, ff and D for one integration from the FP64 delay / fringe model.

@@ -14,9 +14,9 @@
 namespace gbx {
 namespace {
 
-constexpr int kKbPerStage = 16;             // 64 frames per stage
+constexpr int kKbPerStage = 8;              // 32 frames per stage
+constexpr int kStages = 3;
 constexpr int kChunkKb = 64;                // 256 frames per FP32 partial sum
-constexpr int kSlack = 8 * 16;              // rows read past R by the last 4-input block
 
 __device__ __forceinline__ void decode_tri(int idx, int nb, int& I, int& J) {
     I = 0;
@@ -31,13 +31,14 @@ __device__ __forceinline__ void decode_tri(int idx, int nb, int& I, int& J) {
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int abort_flag;
-    const int R = 2 * p.n_in;
-    const int stage_bytes = kKbPerStage * R * 16 + kSlack;
+    __shared__ __align__(8) uint64_t full[kStages];
+    __shared__ __align__(8) uint64_t empty[kStages];
+    const int R = rows_fp32(p.n_in);             // rows per K-block, a multiple of 8
+    const int stage_bytes = kKbPerStage * R * 16;
+    float* part = reinterpret_cast<float*>(smem + kStages * stage_bytes);   // [32][blockDim] chunk sums
     const int nb = (p.n_in + 3) / 4;
     const int n_work = nb * (nb + 1) / 2;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
     const bool active = tid < n_work;
     int I = 0, J = 0;
     if (active) decode_tri(tid, nb, I, J);
@@ -48,52 +49,73 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p) {
     const float* spec = static_cast<const float*>(p.spec);
 
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int q = 0; q < kStages; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], nthr / 32);
+        }
         fence_mbar_init();
-        abort_flag = 0;
     }
+    for (int e = 0; e < 32; ++e) part[e * nthr + tid] = 0.0f;
     __syncthreads();
     auto issue = [&](int w) {
+        const int slot = w % kStages;
         const int k = blockIdx.x + (w / n_stage_ch) * gridDim.x;
         const int kb0 = (w % n_stage_ch) * kKbPerStage;
         const int nkb = min(kKbPerStage, ntb - kb0);
         const uint32_t bytes = static_cast<uint32_t>(nkb) * R * 16;
         const float* src = spec + (static_cast<int64_t>(k) * ntb + kb0) * R * kTbFp32;
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bar[w & 1], bytes);
-        bulk_g2s(smem + (w & 1) * stage_bytes, src, bytes, &bar[w & 1]);
+        mbar_arrive_expect_tx(&full[slot], bytes);
+        bulk_g2s(smem + slot * stage_bytes, src, bytes, &full[slot]);
     };
-    if (tid == 0 && total > 0) issue(0);
+    int issued = 0;                              // stages issued so far (thread 0)
+    if (tid == 0)
+        for (; issued < min(kStages - 1, total); ++issued) issue(issued);
 
-    float2 acc[4][4], tot[4][4];
+    float2 acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = tot[a][b] = make_float2(0.f, 0.f);
+        for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
     int kb_in_chunk = 0;
+    bool ok = true;
 
-    for (int w = 0; w < total; ++w) {
-        if (tid == 0 && w + 1 < total) issue(w + 1);
-        if (!mbar_wait(&bar[w & 1], (w >> 1) & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
-        __syncthreads();
-        if (abort_flag) break;
+    int w = 0;
+    for (; w < total && ok; ++w) {
+        const int slot = w % kStages;
+        if (tid == 0 && w + kStages - 1 < total) {
+            const int ws = w + kStages - 1;
+            // the slot's previous stage (ws - kStages) must be released by every warp
+            if (ws >= kStages &&
+                !mbar_wait(&empty[ws % kStages], ((ws / kStages) - 1) & 1, p.err, ERR_WAIT_STAGE)) {
+                ok = false;
+            } else {
+                issue(ws);
+                issued = ws + 1;
+            }
+        }
+        if (!mbar_wait(&full[slot], (w / kStages) & 1, p.err, ERR_WAIT_STAGE)) ok = false;
         const int kb0 = (w % n_stage_ch) * kKbPerStage;
         const int nkb = min(kKbPerStage, ntb - kb0);
-        const float4* st = reinterpret_cast<const float4*>(smem + (w & 1) * stage_bytes);
-        if (active) {
+        const float4* st = reinterpret_cast<const float4*>(smem + slot * stage_bytes);
+        if (active && ok) {
             for (int kb = 0; kb < nkb; ++kb) {
+                // rows 8I..8I+7 and 8J..8J+7 are one 128-byte line each; row q of line L sits
+                // at position q ^ (L & 7), so a warp's loads of one q spread over the banks
                 const float4* blk = st + kb * R;
+                const float4* li = blk + 8 * I;
+                const float4* lj = blk + 8 * J;
+                const int si = I & 7, sj = J & 7;
                 float4 ar[4], ai[4];
 #pragma unroll
                 for (int ii = 0; ii < 4; ++ii) {
-                    ar[ii] = blk[8 * I + 2 * ii];
-                    ai[ii] = blk[8 * I + 2 * ii + 1];
+                    ar[ii] = li[(2 * ii) ^ si];
+                    ai[ii] = li[(2 * ii + 1) ^ si];
                 }
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) {
-                    const float4 br = blk[8 * J + 2 * jj];
-                    const float4 bi = blk[8 * J + 2 * jj + 1];
+                    const float4 br = lj[(2 * jj) ^ sj];
+                    const float4 bi = lj[(2 * jj + 1) ^ sj];
 #pragma unroll
                     for (int ii = 0; ii < 4; ++ii) {
                         float2 c = acc[ii][jj];
@@ -109,20 +131,23 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p) {
                         acc[ii][jj] = c;
                     }
                 }
-                if (++kb_in_chunk == kChunkKb) {
+                if (++kb_in_chunk == kChunkKb) {   // fold this chunk's FP32 sums into the running ones
                     kb_in_chunk = 0;
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
 #pragma unroll
                         for (int b = 0; b < 4; ++b) {
-                            tot[a][b] = cadd(tot[a][b], acc[a][b]);
+                            part[(8 * a + 2 * b) * nthr + tid] += acc[a][b].x;
+                            part[(8 * a + 2 * b + 1) * nthr + tid] += acc[a][b].y;
                             acc[a][b] = make_float2(0.f, 0.f);
                         }
                 }
             }
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);  // this warp is done with the stage
         const bool ch_done = (w % n_stage_ch) == n_stage_ch - 1;
-        if (ch_done && active) {
+        if (ch_done && active && ok) {
             const int k = blockIdx.x + (w / n_stage_ch) * gridDim.x;
             const int n_bl = p.n_ant * (p.n_ant + 1) / 2, npp = p.n_pol * p.n_pol;
 #pragma unroll
@@ -130,8 +155,12 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p) {
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) {
                     const int i = 4 * I + ii, j = 4 * J + jj;
-                    const float2 v = cadd(tot[ii][jj], acc[ii][jj]);
-                    tot[ii][jj] = acc[ii][jj] = make_float2(0.f, 0.f);
+                    float* pr = &part[(8 * ii + 2 * jj) * nthr + tid];
+                    float* pi = &part[(8 * ii + 2 * jj + 1) * nthr + tid];
+                    const float2 v = make_float2(*pr + acc[ii][jj].x, *pi + acc[ii][jj].y);
+                    *pr = 0.0f;
+                    *pi = 0.0f;
+                    acc[ii][jj] = make_float2(0.f, 0.f);
                     if (i >= p.n_in || j >= p.n_in) continue;
                     const int a = i / p.n_pol, pp = i % p.n_pol, a2 = j / p.n_pol, qq = j % p.n_pol;
                     if (a > a2) continue;
@@ -140,12 +169,11 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p) {
                 }
             kb_in_chunk = 0;
         }
-        __syncthreads();  // buffer (w & 1) free for the copy issued at w + 2
+        if (ch_done) kb_in_chunk = 0;
     }
-    if (abort_flag && tid == 0) {
-        // a copy may still be in flight into the other buffer: let it land before exit
-        mbar_wait(&bar[0], 0, nullptr, 0);
-        mbar_wait(&bar[1], 0, nullptr, 0);
+    if (tid == 0) {
+        // stages issued but never consumed (only after a failed wait) must land before exit
+        for (int q = w; q < issued; ++q) mbar_wait(&full[q % kStages], (q / kStages) & 1, nullptr, 0);
     }
 }
 
@@ -156,7 +184,8 @@ cudaError_t launch_xengine_fp32(const XParams& p, int n_sm, cudaStream_t s) {
     const int n_work = nb * (nb + 1) / 2;
     const int threads = ((n_work + 31) / 32) * 32;
     if (threads > 544) return cudaErrorInvalidValue;
-    const size_t smem = 2 * (static_cast<size_t>(kKbPerStage) * 2 * p.n_in * 16 + kSlack);
+    const size_t smem = kStages * (static_cast<size_t>(kKbPerStage) * rows_fp32(p.n_in) * 16) +
+                        32 * sizeof(float) * threads;
     auto go = [&](auto kern) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
