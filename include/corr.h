@@ -161,6 +161,32 @@ int corr_info(corr_t* h, int64_t* out6);
 int corr_set_timing(corr_t* h, int enable);
 int corr_stage_times(corr_t* h, float* ms4, int* n);
 
+/* One FP32 integration that allocates nothing (the paper has no counterpart:
+ * this serves callers that may not allocate device memory while they run --
+ * a real-time acquisition thread that cannot afford cudaMalloc's device
+ * synchronisation and driver locks, or a process whose device memory budget
+ * is entirely reserved by its host framework).  It runs the same F-engine and
+ * FP32 X-engine as corr_integrate_device with unit beam weights over all
+ * antennas; every intermediate buffer lives in one static device array of
+ * 32 MiB that each GPU loading this library holds until the process exits.
+ *   x, ld, n_avail, g0   as for corr_integrate_device (device samples)
+ *   delay, phi0, rate    host arrays of n_ant doubles (phi0, rate may be NULL = 0),
+ *                        passed to the kernels by value
+ *   vis                  device out [n_fft/2][n_bl][n_pol^2] complex64
+ *   beams                device out [2][n_int][n_fft/2] float32 (raw resolution)
+ *   stream               cudaStream_t to run on (NULL = legacy default stream)
+ *   blocking             1: wait for completion and report kernel wait timeouts
+ * Limits: n_ant <= 64 and the tables plus the FP32 spectra must fit the 32 MiB
+ * (e.g. 4 ant x 2 pol x 512-pt FFT x 64 spectra uses ~1.1 MiB); larger
+ * problems return CORR_E_RANGE.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  All calls share the one
+ * array, so calls whose work overlaps on the GPU race with each other:
+ * serialise them (one stream, or wait for the previous call). */
+int corr_integrate_static(int n_ant, int n_pol, int n_fft, int n_int, const int8_t* x, int64_t ld,
+                          int64_t n_avail, int64_t g0, const double* delay, const double* phi0,
+                          const double* rate, float* vis, float* beams, void* stream, int blocking);
+
 #if defined(__GNUC__)
 #pragma GCC visibility pop
 #endif

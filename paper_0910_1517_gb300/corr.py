@@ -44,6 +44,7 @@ SIGNATURES = {
     "corr_info": ([_P, _P], _I),
     "corr_set_timing": ([_P, _I], _I),
     "corr_stage_times": ([_P, _P, ctypes.POINTER(ctypes.c_int)], _I),
+    "corr_integrate_static": ([_I, _I, _I, _I, _P, _L, _L, _L, _P, _P, _P, _P, _P, _P, _I], _I),
 }
 
 _lib = None
@@ -226,3 +227,16 @@ def corr_stage_times(h):
     n = ctypes.c_int()
     _ok(load().corr_stage_times(h, _ptr(ms), ctypes.byref(n)))
     return ms.astype(np.float64), int(n.value)
+
+
+def corr_integrate_static(n_ant, n_pol, n_fft, n_int, x, vis, beams, delay, phi0=None, rate=None,
+                          n_avail=None, g0: int = 0, stream=None, blocking: int = 1):
+    """One FP32 integration with no allocation: x device int8 [n_in][ld], vis and beams device
+    float32 tensors of [n_chan][n_bl][n_pol^2][2] and [2][n_int][n_chan]."""
+    d = np.ascontiguousarray(delay, dtype=np.float64)
+    f = None if phi0 is None else np.ascontiguousarray(phi0, dtype=np.float64)
+    w = None if rate is None else np.ascontiguousarray(rate, dtype=np.float64)
+    n_avail = x.shape[1] if n_avail is None else n_avail
+    return _ok(load().corr_integrate_static(n_ant, n_pol, n_fft, n_int, _ptr(x), x.stride(0), n_avail, g0,
+                                            _ptr(d), _ptr(f), _ptr(w), _ptr(vis), _ptr(beams),
+                                            _stream(stream), blocking))

@@ -48,6 +48,11 @@ cudaError_t dalloc(T** p, size_t n) {
 
 }  // namespace
 
+namespace gbx {
+// Message reported by corr_last_error() on this thread (used by entry points in other files).
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace gbx
+
 struct corr {
     int n_ant = 0, n_pol = 0, n_in = 0, n_fft = 0, n_chan = 0, n_int = 0, n_bl = 0, npp = 0;
     int xmode = CORR_FP32, beam_avg = 1, max_delay = 2048;

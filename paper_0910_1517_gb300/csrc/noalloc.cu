@@ -1,0 +1,246 @@
+// noalloc.cu -- corr_integrate_static: one FP32 integration with no allocation.
+//
+// Some callers cannot allocate device memory while they run: a real-time
+// acquisition thread with a hard per-block deadline cannot afford cudaMalloc,
+// which can synchronise the device and take driver locks for an unbounded
+// time, and a process embedded in a larger pipeline often finds the whole
+// device memory budget already reserved by its host framework.  For them this
+// entry point runs the same F-engine and FP32 X-engine kernels as
+// corr_integrate_device, but every intermediate buffer (integer delays,
+// phasor and twiddle tables, beam weights, the F-to-X spectra hand-off and
+// the error word) lives in one file-scope static device array of fixed size.
+// The caller passes the samples and the output buffers; the delay model is
+// passed by value in the kernel parameters, so no host-to-device copy and no
+// host allocation is needed either.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/corr.h"
+#include "common.cuh"
+#include "fengine.cuh"
+#include "xengine.cuh"
+
+namespace gbx {
+void set_last_error(const char* msg);   // capi.cu: the message corr_last_error() returns
+}
+
+namespace {
+
+constexpr size_t kScratchBytes = static_cast<size_t>(32) << 20;   // 32 MiB per device
+constexpr int kMaxDevices = 64;
+constexpr int kStaticMaxAnt = 64;
+
+// The scratch array.  In host code `g_scratch` names only a host-side stand-in;
+// its device address comes from cudaGetSymbolAddress (once per device).
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void* g_scratch_dev[kMaxDevices] = {};
+
+struct Model {
+    double tau[kStaticMaxAnt];
+    double phi0[kStaticMaxAnt];
+    double rate[kStaticMaxAnt];
+};
+
+size_t align256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
+
+struct Layout {
+    size_t err, D, ginc, pf, wcoh, ff, tw, spec, total;
+};
+
+int twiddle_count(int n_fft) {
+    const int M = n_fft / 2;
+    const int R2 = (M / 16 >= 16) ? 16 : M / 16, R3 = M / (16 * R2);
+    return R2 * 16 + (R3 > 1 ? R3 * 16 * R2 : 0) + M / 2 + 1;
+}
+
+Layout layout(int n_ant, int n_pol, int n_fft, int n_int) {
+    const size_t nch = n_fft / 2;
+    Layout L{};
+    size_t o = 0;
+    L.err = o;
+    o = align256(o + sizeof(unsigned));
+    L.D = o;
+    o = align256(o + sizeof(int) * n_ant);
+    L.ginc = o;
+    o = align256(o + sizeof(float) * n_ant);
+    L.pf = o;
+    o = align256(o + sizeof(float2) * n_ant * nch);
+    L.wcoh = o;
+    o = align256(o + sizeof(float2) * n_ant * nch);
+    L.ff = o;
+    o = align256(o + sizeof(float2) * n_ant * static_cast<size_t>(n_int));
+    L.tw = o;
+    o = align256(o + sizeof(float2) * twiddle_count(n_fft));
+    L.spec = o;
+    o = align256(o + sizeof(float) * nch * static_cast<size_t>(n_int) * gbx::rows_fp32(n_ant * n_pol));
+    L.total = o;
+    return L;
+}
+
+// Fill the per-integration tables of the F-engine: integer delays, FSTC and fringe phasors
+// (FP64 phase, as in the handle path), unit beam weights over all antennas, and the FFT
+// twiddles in the layout the F-engine reads.
+__global__ void static_tables_kernel(Model m, int n_ant, int n_fft, int n_int, int64_t g0, unsigned char* base,
+                                     Layout L) {
+    const int M = n_fft / 2;
+    const int R2 = (M / 16 >= 16) ? 16 : M / 16, R3 = M / (16 * R2), Ns3 = 16 * R2;
+    const int n_tw = R2 * 16 + (R3 > 1 ? R3 * Ns3 : 0) + M / 2 + 1;
+    int* D = reinterpret_cast<int*>(base + L.D);
+    float* ginc = reinterpret_cast<float*>(base + L.ginc);
+    float2* pf = reinterpret_cast<float2*>(base + L.pf);
+    float2* wcoh = reinterpret_cast<float2*>(base + L.wcoh);
+    float2* ff = reinterpret_cast<float2*>(base + L.ff);
+    float2* tw = reinterpret_cast<float2*>(base + L.tw);
+    const int64_t n_pf = static_cast<int64_t>(n_ant) * M, n_ff = static_cast<int64_t>(n_ant) * n_int;
+    const int64_t total = n_pf + n_ff + n_tw + n_ant;
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
+         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (q < n_pf) {
+            const int a = static_cast<int>(q / M), k = static_cast<int>(q % M);
+            const double Da = floor(m.tau[a] + 0.5), tf = m.tau[a] - Da;
+            double sn, cs;
+            sincospi(2.0 * k * tf / n_fft, &sn, &cs);
+            pf[q] = make_float2(static_cast<float>(cs), static_cast<float>(sn));
+            wcoh[q] = make_float2(1.0f, 0.0f);
+        } else if (q < n_pf + n_ff) {
+            const int64_t r = q - n_pf;
+            const int a = static_cast<int>(r / n_int), t = static_cast<int>(r % n_int);
+            double ph = m.phi0[a] + m.rate[a] * static_cast<double>(g0 + t);
+            ph -= two_pi * rint(ph / two_pi);
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            ff[r] = make_float2(static_cast<float>(cs), static_cast<float>(-sn));
+        } else if (q < n_pf + n_ff + n_tw) {
+            int e = static_cast<int>(q - n_pf - n_ff);
+            double num, den;
+            if (e < R2 * 16) {                                   // pass 2: W_{16 R2}^{j r}, [r][j]
+                num = static_cast<double>(e % 16) * (e / 16);
+                den = 16.0 * R2;
+            } else if (R3 > 1 && e < R2 * 16 + R3 * Ns3) {       // pass 3: W_M^{j r}, [r][j]
+                e -= R2 * 16;
+                num = static_cast<double>(e % Ns3) * (e / Ns3);
+                den = M;
+            } else {                                             // real split: W_N^k
+                e -= R2 * 16 + (R3 > 1 ? R3 * Ns3 : 0);
+                num = e;
+                den = n_fft;
+            }
+            double sn, cs;
+            sincospi(2.0 * num / den, &sn, &cs);
+            tw[q - n_pf - n_ff] = make_float2(static_cast<float>(cs), static_cast<float>(-sn));
+        } else {
+            const int a = static_cast<int>(q - n_pf - n_ff - n_tw);
+            D[a] = static_cast<int>(floor(m.tau[a] + 0.5));
+            ginc[a] = 1.0f;
+        }
+    }
+}
+
+int fail(int code, const char* msg) {
+    gbx::set_last_error(msg);
+    return code;
+}
+
+}  // namespace
+
+extern "C" int corr_integrate_static(int n_ant, int n_pol, int n_fft, int n_int, const int8_t* x, int64_t ld,
+                                     int64_t n_avail, int64_t g0, const double* delay, const double* phi0,
+                                     const double* rate, float* vis, float* beams, void* stream, int blocking) {
+    if (n_ant < 1 || n_ant > kStaticMaxAnt || (n_pol != 1 && n_pol != 2))
+        return fail(CORR_E_INVAL, "corr_integrate_static: need 1 <= n_ant <= 64 and n_pol in {1, 2}");
+    if (n_fft < 64 || n_fft > 4096 || (n_fft & (n_fft - 1)) || n_int < 16 || n_int % 16)
+        return fail(CORR_E_INVAL, "corr_integrate_static: n_fft a power of two in [64, 4096], n_int a multiple of 16");
+    if (!x || !vis || !beams || !delay || (reinterpret_cast<uintptr_t>(x) & 15) || (ld & 15) || ld < n_avail)
+        return fail(CORR_E_INVAL, "corr_integrate_static: null buffer, or x / ld not 16-byte aligned");
+    const Layout L = layout(n_ant, n_pol, n_fft, n_int);
+    if (L.total > kScratchBytes)
+        return fail(CORR_E_RANGE, "corr_integrate_static: problem needs more than the 32 MiB static scratch");
+    Model m{};
+    int dmax = 0;
+    for (int a = 0; a < n_ant; ++a) {
+        if (!std::isfinite(delay[a]) || delay[a] < 0.0) return fail(CORR_E_RANGE, "corr_integrate_static: bad delay");
+        m.tau[a] = delay[a];
+        m.phi0[a] = phi0 ? phi0[a] : 0.0;
+        m.rate[a] = rate ? rate[a] : 0.0;
+        dmax = std::max(dmax, static_cast<int>(std::floor(delay[a] + 0.5)));
+    }
+    if (n_avail < static_cast<int64_t>(n_int) * n_fft + dmax)
+        return fail(CORR_E_RANGE, "corr_integrate_static: n_avail < n_int * n_fft + max delay");
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return fail(CORR_E_CUDA, "corr_integrate_static: no current device");
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_scratch_dev[dev]) {   // once per device, with that device current
+            void* ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr)
+                return fail(CORR_E_CUDA, "corr_integrate_static: cudaGetSymbolAddress failed");
+            g_scratch_dev[dev] = ptr;
+        }
+        scratch = g_scratch_dev[dev];
+    }
+    int n_sm = 0;
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return fail(CORR_E_CUDA, "corr_integrate_static: device query failed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char* base = static_cast<unsigned char*>(scratch);
+    // the error word keeps the previous call's value: clear it
+    if (cudaMemsetAsync(base + L.err, 0, sizeof(unsigned), s) != cudaSuccess)
+        return fail(CORR_E_CUDA, "corr_integrate_static: memset failed");
+    const int n_tw = twiddle_count(n_fft);
+    const int64_t work = static_cast<int64_t>(n_ant) * (n_fft / 2 + n_int) + n_tw + n_ant;
+    static_tables_kernel<<<static_cast<int>(std::min<int64_t>((work + 255) / 256, 4096)), 256, 0, s>>>(
+        m, n_ant, n_fft, n_int, g0, base, L);
+    if (cudaGetLastError() != cudaSuccess) return fail(CORR_E_CUDA, "corr_integrate_static: table kernel");
+
+    gbx::FeParams fp{};
+    fp.x = x;
+    fp.ld = ld;
+    fp.n_avail = n_avail;
+    fp.n_ant = n_ant;
+    fp.n_pol = n_pol;
+    fp.n_in = n_ant * n_pol;
+    fp.n_fft = n_fft;
+    fp.n_chan = n_fft / 2;
+    fp.n_int = n_int;
+    fp.D = reinterpret_cast<const int*>(base + L.D);
+    fp.pf = reinterpret_cast<const float2*>(base + L.pf);
+    fp.ff = reinterpret_cast<const float2*>(base + L.ff);
+    fp.wcoh = reinterpret_cast<const float2*>(base + L.wcoh);
+    fp.ginc = reinterpret_cast<const float*>(base + L.ginc);
+    fp.scale = nullptr;
+    fp.spec = base + L.spec;
+    fp.beams = beams;
+    fp.tw = reinterpret_cast<const float2*>(base + L.tw);
+    fp.err = reinterpret_cast<unsigned*>(base + L.err);
+    if (gbx::launch_fengine(fp, gbx::OUT_FP32, s) != cudaSuccess)
+        return fail(CORR_E_CUDA, "corr_integrate_static: F-engine launch");
+    gbx::XParams xp{};
+    xp.spec = base + L.spec;
+    xp.n_ant = n_ant;
+    xp.n_pol = n_pol;
+    xp.n_in = n_ant * n_pol;
+    xp.n_chan = n_fft / 2;
+    xp.n_int = n_int;
+    xp.vis = reinterpret_cast<float2*>(vis);
+    xp.err = fp.err;
+    if (gbx::launch_xengine_fp32(xp, n_sm, s) != cudaSuccess)
+        return fail(CORR_E_CUDA, "corr_integrate_static: X-engine launch");
+    if (blocking) {
+        unsigned err = 0;
+        if (cudaStreamSynchronize(s) != cudaSuccess ||
+            cudaMemcpy(&err, base + L.err, sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(CORR_E_CUDA, "corr_integrate_static: synchronisation failed");
+        if (err) return fail(CORR_E_TIMEOUT, "corr_integrate_static: a kernel wait timed out");
+    }
+    return CORR_OK;
+}
