@@ -13,6 +13,9 @@ Functions and the passage each follows (Roy et al., arXiv:0910.1517):
   requant   -- 8-bit requantisation of spectra (precision form; Sec. 4.1 analogue)
   xint      -- exact integer MAC on requantised spectra (Sec. 4.1)
   mad_flag  -- median-absolute-deviation flagger (Sec. 5, Eq. 3-4)
+  power_dumps, patch_stats, rfi_forward, rfi_loss_grad (rfi_oracle.c) -- the RFI
+            stage: 1 ms auto-power dumps, per-patch Eq. 3-4 statistics and flags,
+            and the learned flagger's forward pass, BCE loss and exact gradient
 All of them are pinned by the ``-m "not gpu"`` tests in tests/test_oracle_*.py.
 """
 from __future__ import annotations
@@ -24,18 +27,19 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "fx_oracle.c")
+_SRCS = [os.path.join(_HERE, "fx_oracle.c"), os.path.join(_HERE, "rfi_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 
 def build(force: bool = False) -> str:
     """Compile fx_oracle.c into liboracle.so with gcc + OpenMP (no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(f) for f in _SRCS)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call([
             "gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-            "-std=c11", _SRC, "-o", tmp, "-lm"])
+            "-std=c11"] + _SRCS + ["-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -55,6 +59,11 @@ def lib():
         L.oracle_mad_flag.argtypes = [i32, P, f64, P, P, P]
         L.oracle_threads.argtypes = []
         L.oracle_n_baselines.argtypes = [i32]
+        L.oracle_rfi_n_params.argtypes = []
+        L.oracle_power_dumps.argtypes = [i32, i32, i32, i32, P, P]
+        L.oracle_patch_stats.argtypes = [i32, i32, P, f64, P, P, P, P]
+        L.oracle_rfi_forward.argtypes = [i32, i32, i32, P, P, P]
+        L.oracle_rfi_loss_grad.argtypes = [i32, i32, i32, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -172,3 +181,53 @@ def mad_flag(x, M):
     rc = lib().oracle_mad_flag(x.size, _p(x), float(M), _p(f), ctypes.byref(med), ctypes.byref(mad))
     _check(rc, "mad_flag")
     return f, med.value, mad.value
+
+
+# ------------------------------------------------------------------ RFI stage
+
+def rfi_n_params() -> int:
+    return int(lib().oracle_rfi_n_params())
+
+
+def power_dumps(Y, dump):
+    """P[i][d][k] = sum over each dump of `dump` frames of |Y|^2 (float64)."""
+    n_in, n_frames, nch = Y.shape
+    Yr = _as_ri(Y)
+    P = np.zeros((n_in, n_frames // dump, nch), dtype=np.float64)
+    _check(lib().oracle_power_dumps(n_in, n_frames, nch, dump, _p(Yr), _p(P)), "power_dumps")
+    return P
+
+
+def patch_stats(x, M=5.0):
+    """Per patch (leading axis): median, MAD, Eq. 4 flags and log-compressed network input."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    B = x.shape[0]
+    n = int(np.prod(x.shape[1:]))
+    med, mad = np.zeros(B), np.zeros(B)
+    flags = np.zeros(x.shape, dtype=np.uint8)
+    z = np.zeros(x.shape, dtype=np.float64)
+    _check(lib().oracle_patch_stats(B, n, _p(x), float(M), _p(med), _p(mad), _p(flags), _p(z)), "patch_stats")
+    return med, mad, flags, z
+
+
+def rfi_forward(params, x):
+    """Logits [B][H][W] of the 1->16->32->16->1 network for inputs x [B][H][W]."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    assert p.size == rfi_n_params()
+    B, H, W = x.shape
+    out = np.zeros((B, H, W), dtype=np.float64)
+    _check(lib().oracle_rfi_forward(B, H, W, _p(p), _p(x), _p(out)), "rfi_forward")
+    return out
+
+
+def rfi_loss_grad(params, x, mask):
+    """(mean BCE loss, d loss / d params) of the network on inputs x and masks."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    B, H, W = x.shape
+    g = np.zeros(p.size, dtype=np.float64)
+    loss = ctypes.c_double()
+    _check(lib().oracle_rfi_loss_grad(B, H, W, _p(p), _p(x), _p(m), ctypes.byref(loss), _p(g)), "rfi_loss_grad")
+    return loss.value, g
