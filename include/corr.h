@@ -152,6 +152,15 @@ int corr_device_outputs(corr_t* h, void** vis, void** beams, void** stream);
  * number of completed integrations. */
 int corr_info(corr_t* h, int64_t* out6);
 
+/* Auto-power dumps for the RFI stage (include/rfi.h): with dump > 0 every CORR_FP32
+ * integration also produces P [n_in][n_int/dump][n_fft/2] float32,
+ * P[i][d][k] = sum over the dump's frames of |Y_i[t][k]|^2 (the paper studies
+ * RFI on such 1 ms total-intensity samples, Sec. 5).  dump: 0 (off) or a
+ * multiple of 4 dividing n_int.  corr_read_power copies the last integration's
+ * dumps to host memory `out` (may be NULL) and/or returns their device address. */
+int corr_set_power_dump(corr_t* h, int dump);
+int corr_read_power(corr_t* h, float* out, void** device_ptr);
+
 /* Per-stage CUDA-event timing, for measurement.  While enabled (enable = 1),
  * every integration records events around its kernels on the stream it runs
  * on.  corr_stage_times waits for them and sums, over the integrations

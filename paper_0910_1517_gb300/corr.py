@@ -45,6 +45,18 @@ SIGNATURES = {
     "corr_set_timing": ([_P, _I], _I),
     "corr_stage_times": ([_P, _P, ctypes.POINTER(ctypes.c_int)], _I),
     "corr_integrate_static": ([_I, _I, _I, _I, _P, _L, _L, _L, _P, _P, _P, _P, _P, _P, _I], _I),
+    "corr_set_power_dump": ([_P, _I], _I),
+    "corr_read_power": ([_P, _P, ctypes.POINTER(ctypes.c_void_p)], _I),
+    # include/rfi.h
+    "rfi_n_params": ([], _I),
+    "rfi_create": ([ctypes.POINTER(ctypes.c_void_p), _I], _I),
+    "rfi_destroy": ([_P], _I),
+    "rfi_set_params": ([_P, _P], _I),
+    "rfi_get_params": ([_P, _P], _I),
+    "rfi_loss_grad": ([_P, _P, _P, _I, ctypes.POINTER(ctypes.c_float), _P, _P], _I),
+    "rfi_train_step": ([_P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(ctypes.c_float), _P], _I),
+    "rfi_infer": ([_P, _P, _I, _P, _P], _I),
+    "rfi_patches": ([_P, _I, _I, _I, ctypes.c_float, _P, _P, _P, _P], _I),
 }
 
 _lib = None
@@ -78,11 +90,13 @@ def _ok(rc: int, allow=()):
 
 
 def _ptr(a):
-    """Raw data pointer of a numpy array or torch tensor (None -> NULL)."""
+    """Raw data pointer of a numpy array, torch tensor or integer address (None -> NULL)."""
     if a is None:
         return None
     if isinstance(a, np.ndarray):
         return a.ctypes.data_as(ctypes.c_void_p)
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
     return ctypes.c_void_p(a.data_ptr())
 
 
@@ -240,3 +254,73 @@ def corr_integrate_static(n_ant, n_pol, n_fft, n_int, x, vis, beams, delay, phi0
     return _ok(load().corr_integrate_static(n_ant, n_pol, n_fft, n_int, _ptr(x), x.stride(0), n_avail, g0,
                                             _ptr(d), _ptr(f), _ptr(w), _ptr(vis), _ptr(beams),
                                             _stream(stream), blocking))
+
+
+def corr_set_power_dump(h, dump: int):
+    return _ok(load().corr_set_power_dump(h, dump))
+
+
+def corr_power_device(h):
+    """Device address of the power-dump buffer [n_in][n_dump][n_chan] float32."""
+    dev = ctypes.c_void_p()
+    _ok(load().corr_read_power(h, None, ctypes.byref(dev)))
+    return dev.value
+
+
+def corr_read_power_host(h, n_dump: int):
+    i = corr_info(h)
+    out = np.empty((i["n_in"], n_dump, i["n_chan"]), dtype=np.float32)
+    _ok(load().corr_read_power(h, _ptr(out), None))
+    return out
+
+
+# ------------------------------------------------------------------ rfi.h
+
+def rfi_n_params() -> int:
+    return int(load().rfi_n_params())
+
+
+def rfi_create(max_batch: int):
+    n = ctypes.c_void_p()
+    _ok(load().rfi_create(ctypes.byref(n), max_batch))
+    return n
+
+
+def rfi_destroy(net):
+    return _ok(load().rfi_destroy(net))
+
+
+def rfi_set_params(net, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == rfi_n_params()
+    return _ok(load().rfi_set_params(net, _ptr(p)))
+
+
+def rfi_get_params(net):
+    p = np.empty(rfi_n_params(), dtype=np.float32)
+    _ok(load().rfi_get_params(net, _ptr(p)))
+    return p
+
+
+def rfi_loss_grad(net, x, mask, B: int, stream=None):
+    """(loss, grad float32 [n_params]) of a batch; x fp16 and mask uint8 device tensors."""
+    loss = ctypes.c_float()
+    g = np.empty(rfi_n_params(), dtype=np.float32)
+    _ok(load().rfi_loss_grad(net, _ptr(x), _ptr(mask), B, ctypes.byref(loss), _ptr(g), _stream(stream)))
+    return float(loss.value), g
+
+
+def rfi_train_step(net, x, mask, B: int, lr: float, want_loss: bool = False, stream=None):
+    loss = ctypes.c_float()
+    _ok(load().rfi_train_step(net, _ptr(x), _ptr(mask), B, lr, ctypes.byref(loss) if want_loss else None,
+                              _stream(stream)))
+    return float(loss.value) if want_loss else None
+
+
+def rfi_infer(net, x, B: int, prob, stream=None):
+    return _ok(load().rfi_infer(net, _ptr(x), B, _ptr(prob), _stream(stream)))
+
+
+def rfi_patches(power, n_in: int, n_dump: int, n_chan: int, M: float, x=None, flags=None, stats=None, stream=None):
+    return _ok(load().rfi_patches(_ptr(power), n_in, n_dump, n_chan, M, _ptr(x), _ptr(flags), _ptr(stats),
+                                  _stream(stream)))

@@ -85,6 +85,9 @@ struct corr {
     // bookkeeping
     int64_t launched = 0, completed = 0;
     int last_mode = -1;
+    // auto-power dumps for the RFI stage (0 = off)
+    int dump = 0;
+    float* d_power = nullptr;
     // per-stage timing: kTimedMax integrations x 5 events (before set-up and after each stage)
     bool timing = false;
     std::vector<cudaEvent_t> tev;
@@ -192,6 +195,11 @@ int run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, int64
         CU(launch_xengine_fp32(xp, h->n_sm, s));
     else
         CU(launch_xengine_tc(xp, h->n_sm, s));
+    if (h->dump > 0) {
+        if (h->xmode != CORR_FP32) return fail(CORR_E_STATE, "power dumps need the CORR_FP32 spectra");
+        CU(launch_power_dumps(static_cast<const float*>(h->d_spec), h->n_in, h->n_chan, h->n_int, h->dump,
+                              h->d_power, s));
+    }
     if (int rc = mark(h, 3, s)) return rc;
     if (h->beam_avg > 1) CU(launch_beam_average(h->d_beams_raw, h->d_beams, h->n_int, h->n_chan, h->beam_avg, s));
     if (int rc = mark(h, 4, s)) return rc;
@@ -354,6 +362,7 @@ int corr_destroy(corr_t* h) {
     if (!h) return CORR_OK;
     cudaSetDevice(h->dev);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->d_power) cudaFree(h->d_power);
     void* bufs[] = {h->d_ring, h->d_model, h->d_pf, h->d_ff, h->d_D, h->d_wcoh, h->d_ginc, h->d_scale,
                     h->d_tw, h->d_spec, h->d_beams_raw, h->d_vis, h->d_vis_int, h->d_err};
     for (void* b : bufs)
@@ -563,6 +572,33 @@ int corr_device_outputs(corr_t* h, void** vis, void** beams, void** stream) {
     if (vis) *vis = h->d_vis;
     if (beams) *beams = h->d_beams;
     if (stream) *stream = h->stream;
+    return CORR_OK;
+}
+
+int corr_set_power_dump(corr_t* h, int dump) {
+    if (int rc = check_handle(h)) return rc;
+    if (dump < 0 || (dump > 0 && (dump % kTbFp32 || h->n_int % dump)))
+        return fail(CORR_E_INVAL, "dump must be 0 or a multiple of 4 dividing n_int");
+    CU(cudaStreamSynchronize(h->stream));
+    if (h->d_power) cudaFree(h->d_power);
+    h->d_power = nullptr;
+    h->dump = dump;
+    if (dump > 0) {
+        CU(dalloc(&h->d_power, static_cast<size_t>(h->n_in) * (h->n_int / dump) * h->n_chan));
+        CU(cudaMemset(h->d_power, 0, sizeof(float) * h->n_in * (h->n_int / dump) * h->n_chan));
+    }
+    return CORR_OK;
+}
+
+int corr_read_power(corr_t* h, float* out, void** device_ptr) {
+    if (int rc = check_handle(h)) return rc;
+    if (h->dump == 0) return fail(CORR_E_STATE, "power dumps are off (corr_set_power_dump)");
+    if (device_ptr) *device_ptr = h->d_power;
+    if (out) {
+        if (int rc = settle(h, 1)) return rc;
+        CU(cudaMemcpy(out, h->d_power, sizeof(float) * h->n_in * (h->n_int / h->dump) * h->n_chan,
+                      cudaMemcpyDeviceToHost));
+    }
     return CORR_OK;
 }
 

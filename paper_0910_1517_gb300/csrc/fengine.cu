@@ -510,6 +510,26 @@ __global__ void phasor_setup_kernel(int n_ant, int n_chan, int n_fft, int n_int,
     }
 }
 
+// grid.x: dumps, grid.y: 32-channel groups; lane = channel, warp rows step over inputs
+__global__ void power_dump_kernel(const float* __restrict__ spec, int n_in, int n_chan, int n_int, int dump,
+                                  float* __restrict__ P) {
+    const int d = blockIdx.x, k = blockIdx.y * 32 + threadIdx.x;
+    if (k >= n_chan) return;
+    const int Rp = rows_fp32(n_in), ntb = n_int / kTbFp32, n_dump = n_int / dump;
+    const int kb0 = d * dump / kTbFp32, nkb = dump / kTbFp32;
+    for (int i = threadIdx.y; i < n_in; i += blockDim.y) {
+        float acc = 0.0f;
+        for (int kb = kb0; kb < kb0 + nkb; ++kb) {
+            const float* blk = spec + (static_cast<int64_t>(k) * ntb + kb) * Rp * kTbFp32;
+            const float4 re = *reinterpret_cast<const float4*>(blk + swz_row(2 * i) * kTbFp32);
+            const float4 im = *reinterpret_cast<const float4*>(blk + swz_row(2 * i + 1) * kTbFp32);
+            acc += re.x * re.x + re.y * re.y + re.z * re.z + re.w * re.w;
+            acc += im.x * im.x + im.y * im.y + im.z * im.z + im.w * im.w;
+        }
+        P[(static_cast<int64_t>(i) * n_dump + d) * n_chan + k] = acc;
+    }
+}
+
 __global__ void beam_average_kernel(const float* __restrict__ raw, float* __restrict__ out, int n_int, int n_chan,
                                     int beam_avg) {
     const int n_out = n_int / beam_avg;
@@ -579,6 +599,14 @@ cudaError_t launch_phasor_setup(int n_ant, int n_chan, int n_fft, int n_int, int
     const int64_t total = static_cast<int64_t>(n_ant) * (n_chan + n_int) + n_ant;
     const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4096));
     phasor_setup_kernel<<<grid, 256, 0, s>>>(n_ant, n_chan, n_fft, n_int, g0, tau, phi0, rate, pf, ff, D);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_power_dumps(const float* spec, int n_in, int n_chan, int n_int, int dump, float* P,
+                               cudaStream_t s) {
+    if (dump < kTbFp32 || dump % kTbFp32 || n_int % dump) return cudaErrorInvalidValue;
+    const dim3 grid(n_int / dump, (n_chan + 31) / 32), block(32, 8);
+    power_dump_kernel<<<grid, block, 0, s>>>(spec, n_in, n_chan, n_int, dump, P);
     return cudaGetLastError();
 }
 

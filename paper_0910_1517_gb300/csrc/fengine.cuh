@@ -53,6 +53,11 @@ cudaError_t launch_phasor_setup(int n_ant, int n_chan, int n_fft, int n_int, int
                                 const double* phi0, const double* rate, float2* pf, float2* ff, int* D,
                                 cudaStream_t s);
 
+// Auto-power dumps from the FP32 K-block spectra: P[i][d][k] = sum of |Y_i[t][k]|^2 over the
+// `dump` frames of dump d (dump a multiple of 4 dividing n_int).
+cudaError_t launch_power_dumps(const float* spec, int n_in, int n_chan, int n_int, int dump, float* P,
+                               cudaStream_t s);
+
 // beams_out[b][to][k] = mean over beam_avg frames of beams_raw[b][to*beam_avg + j][k]
 cudaError_t launch_beam_average(const float* raw, float* out, int n_int, int n_chan, int beam_avg,
                                 cudaStream_t s);

@@ -11,9 +11,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "corr.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return set(re.findall(r"\b(corr_[a-z_0-9]+)\s*\(", src))
+    names = set()
+    for hdr in ("corr.h", "rfi.h"):
+        src = open(os.path.join(ROOT, "include", hdr)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b((?:corr|rfi)_[a-z_0-9]+)\s*\(", src))
+    return names
 
 
 @pytest.fixture(scope="module")
@@ -33,7 +36,7 @@ def test_header_declares_the_north_star_calls():
 def test_library_exports_every_declared_symbol(lib):
     from paper_0910_1517_gb300 import corr
     out = subprocess.run(["nm", "-D", "--defined-only", corr.LIB_PATH], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\bT (corr_[a-z_0-9]+)$", out, flags=re.M))
+    exported = set(re.findall(r"\bT ((?:corr|rfi)_[a-z_0-9]+)$", out, flags=re.M))
     assert _declared() <= exported, _declared() - exported
     assert set(corr.SIGNATURES) == _declared()
     for name in _declared():
