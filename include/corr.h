@@ -65,8 +65,7 @@ enum { CORR_FP32 = 0, CORR_I8 = 1, CORR_F16 = 2 };  /* X-engine precision */
  * 64..4096) and n_int frames per integration (multiple of 16).  Defaults:
  * CORR_FP32, beam_avg 1, max_delay 2048 samples, zero delays and fringes,
  * unit gains, all antennas in both beams, no scales.  *out receives the handle.
- * The tensor-core modes (CORR_I8, CORR_F16) need n_in <= 64, and CORR_I8
- * needs n_int <= 66571 so that 2 * 127^2 * n_int fits in int32. */
+ * CORR_I8 needs n_int <= 66571 so that 2 * 127^2 * n_int fits in int32. */
 int corr_create(corr_t** out, int n_ant, int n_pol, int n_fft, int n_int);
 int corr_destroy(corr_t* h);
 
@@ -95,6 +94,11 @@ int corr_set_delays(corr_t* h, const double* delay, const double* phi0, const do
  * inc_mask, coh_mask [n_ant] (nonzero = in the beam; NULL = all). */
 int corr_set_beam_weights(corr_t* h, const float* gain, const float* theta,
                           const uint8_t* inc_mask, const uint8_t* coh_mask);
+
+/* Frames per operand stage of the tensor-core X-engine (a tile-shape choice, normally
+ * made by corr_batch_tune): 0 = the largest that fits, else a power of two in
+ * [16, 512] with (ks / 8) * 2 n_in * 16 <= 32768 bytes. */
+int corr_set_xengine_stage(corr_t* h, int ks);
 
 /* Requantisation scales s [n_in][n_fft/2] for CORR_I8 / CORR_F16.  NULL
  * derives them from the last completed integration's autocorrelations as
@@ -169,6 +173,29 @@ int corr_read_power(corr_t* h, float* out, void** device_ptr);
  * averaging; *n receives the number of integrations summed. */
 int corr_set_timing(corr_t* h, int enable);
 int corr_stage_times(corr_t* h, float* ms4, int* n);
+
+/* ---- Several sub-arrays in one launch ----------------------------------------
+ * A batch runs one integration of each of up to 8 handles (sub-arrays of uneven
+ * antenna counts and FFT sizes, all in the same precision mode) as a single CUDA
+ * graph: one phasor set-up per sub-array, one F-engine launch whose CTAs cover
+ * the frame blocks of every sub-array, and one persistent X-engine launch whose
+ * CTAs walk the (sub-array, channel) work of all of them (tensor-core modes; in
+ * CORR_FP32 the X stage is one launch per sub-array).  The paper runs its
+ * functional pipeline over several time slices concurrently (Sec. 2.3.2); here
+ * the concurrency is across independent observations.  Results are read per
+ * handle with the functions above.  The handles stay owned by the caller and
+ * must outlive the batch.  corr_batch_integrate_device takes per-sub-array
+ * device sample pointers, row strides, readable samples and first global
+ * frames (arrays of n_sub); the graph is captured on the first call.
+ * corr_batch_tune times every allowed X-engine stage size per sub-array on the
+ * spectra of the last batch integration, keeps the fastest (ks_out, ms_out per
+ * sub-array, either may be NULL) and rebuilds the graph. */
+typedef struct corr_batch corr_batch_t;
+int corr_batch_create(corr_batch_t** out, int n_sub, corr_t* const* subs);
+int corr_batch_destroy(corr_batch_t* b);
+int corr_batch_integrate_device(corr_batch_t* b, const int8_t* const* x, const int64_t* ld,
+                                const int64_t* n_avail, const int64_t* g0, void* stream);
+int corr_batch_tune(corr_batch_t* b, int* ks_out, float* ms_out);
 
 /* One FP32 integration that allocates nothing (the paper has no counterpart:
  * this serves callers that may not allocate device memory while they run --

@@ -46,6 +46,11 @@ SIGNATURES = {
     "corr_stage_times": ([_P, _P, ctypes.POINTER(ctypes.c_int)], _I),
     "corr_integrate_static": ([_I, _I, _I, _I, _P, _L, _L, _L, _P, _P, _P, _P, _P, _P, _I], _I),
     "corr_set_power_dump": ([_P, _I], _I),
+    "corr_set_xengine_stage": ([_P, _I], _I),
+    "corr_batch_create": ([ctypes.POINTER(ctypes.c_void_p), _I, _P], _I),
+    "corr_batch_destroy": ([_P], _I),
+    "corr_batch_integrate_device": ([_P, _P, _P, _P, _P, _P], _I),
+    "corr_batch_tune": ([_P, _P, _P], _I),
     "corr_read_power": ([_P, _P, ctypes.POINTER(ctypes.c_void_p)], _I),
     # include/rfi.h
     "rfi_n_params": ([], _I),
@@ -324,3 +329,36 @@ def rfi_infer(net, x, B: int, prob, stream=None):
 def rfi_patches(power, n_in: int, n_dump: int, n_chan: int, M: float, x=None, flags=None, stats=None, stream=None):
     return _ok(load().rfi_patches(_ptr(power), n_in, n_dump, n_chan, M, _ptr(x), _ptr(flags), _ptr(stats),
                                   _stream(stream)))
+
+
+def corr_set_xengine_stage(h, ks: int):
+    return _ok(load().corr_set_xengine_stage(h, ks))
+
+
+def corr_batch_create(handles):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    b = ctypes.c_void_p()
+    _ok(load().corr_batch_create(ctypes.byref(b), len(handles), arr))
+    return b
+
+
+def corr_batch_destroy(b):
+    return _ok(load().corr_batch_destroy(b))
+
+
+def corr_batch_integrate_device(b, xs, n_avail=None, g0=None, stream=None):
+    """xs: device int8 tensors [n_in_s][ld_s], one per sub-array."""
+    n = len(xs)
+    ptrs = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    lds = np.ascontiguousarray([x.stride(0) for x in xs], dtype=np.int64)
+    na = np.ascontiguousarray(n_avail if n_avail is not None else [x.shape[1] for x in xs], dtype=np.int64)
+    g = None if g0 is None else np.ascontiguousarray(g0, dtype=np.int64)
+    return _ok(load().corr_batch_integrate_device(b, ptrs, _ptr(lds), _ptr(na), _ptr(g), _stream(stream)))
+
+
+def corr_batch_tune(b, n_sub: int):
+    """(chosen frames-per-stage, their X-engine ms) per sub-array."""
+    ks = np.zeros(n_sub, dtype=np.int32)
+    ms = np.zeros(n_sub, dtype=np.float32)
+    _ok(load().corr_batch_tune(b, _ptr(ks), _ptr(ms)))
+    return ks, ms

@@ -14,6 +14,7 @@
 
 #include "../../include/corr.h"
 #include "fengine.cuh"
+#include "handle.cuh"
 #include "xengine.cuh"
 
 using namespace gbx;
@@ -53,46 +54,7 @@ namespace gbx {
 void set_last_error(const char* msg) { g_err = msg; }
 }  // namespace gbx
 
-struct corr {
-    int n_ant = 0, n_pol = 0, n_in = 0, n_fft = 0, n_chan = 0, n_int = 0, n_bl = 0, npp = 0;
-    int xmode = CORR_FP32, beam_avg = 1, max_delay = 2048;
-    int dev = 0, n_sm = 0;
-    cudaStream_t stream = nullptr;
-    cudaEvent_t ev_done = nullptr, ev_aux = nullptr;
-    // host-side model
-    std::vector<double> tau, phi0, rate;
-    bool scales_set = false;
-    // streaming ring
-    int8_t* d_ring = nullptr;
-    int64_t ring_ld = 0, fill = 0, seq_next = -1, seq_origin = -1, g_next = 0;
-    bool ring_started = false;
-    // device tables and outputs
-    double* d_model = nullptr;          // tau | phi0 | rate, 3 * n_ant
-    double* h_model = nullptr;          // pinned staging of the same
-    float2* d_pf = nullptr;
-    float2* d_ff = nullptr;
-    int* d_D = nullptr;
-    float2* d_wcoh = nullptr;
-    float* d_ginc = nullptr;
-    float* d_scale = nullptr;
-    float2* d_tw = nullptr;
-    void* d_spec = nullptr;
-    float* d_beams_raw = nullptr;
-    float* d_beams = nullptr;
-    float2* d_vis = nullptr;
-    int2* d_vis_int = nullptr;
-    unsigned* d_err = nullptr;
-    // bookkeeping
-    int64_t launched = 0, completed = 0;
-    int last_mode = -1;
-    // auto-power dumps for the RFI stage (0 = off)
-    int dump = 0;
-    float* d_power = nullptr;
-    // per-stage timing: kTimedMax integrations x 5 events (before set-up and after each stage)
-    bool timing = false;
-    std::vector<cudaEvent_t> tev;
-    int t_count = 0;
-};
+#include "handle.cuh"
 
 namespace {
 
@@ -143,8 +105,10 @@ int max_int_delay(const corr* h) {
     return m;
 }
 
+}  // namespace
+
 // Queue one integration (phasors, F-engine, X-engine, beam averaging) on stream s.
-int run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, int64_t g0, cudaStream_t s) {
+int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, int64_t g0, cudaStream_t s) {
     if (h->xmode != CORR_FP32 && !h->scales_set)
         return fail(CORR_E_STATE, "CORR_I8 / CORR_F16 need requantisation scales (corr_set_scales)");
     const int nd = h->n_ant;
@@ -194,7 +158,7 @@ int run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, int64
     if (h->xmode == CORR_FP32)
         CU(launch_xengine_fp32(xp, h->n_sm, s));
     else
-        CU(launch_xengine_tc(xp, h->n_sm, s));
+        CU(launch_xengine_tc_table(h->d_xtab, h->n_items, h->n_sm, s));
     if (h->dump > 0) {
         if (h->xmode != CORR_FP32) return fail(CORR_E_STATE, "power dumps need the CORR_FP32 spectra");
         CU(launch_power_dumps(static_cast<const float*>(h->d_spec), h->n_in, h->n_chan, h->n_int, h->dump,
@@ -207,6 +171,40 @@ int run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, int64
     CU(cudaEventRecord(h->ev_done, s));
     h->launched += 1;
     h->last_mode = h->xmode;
+    return CORR_OK;
+}
+
+gbx::XtSub gbx::xt_sub_of(const corr* h) {
+    XtSub x{};
+    x.spec = static_cast<const __half*>(h->d_spec);
+    x.n_ant = h->n_ant;
+    x.n_pol = h->n_pol;
+    x.n_in = h->n_in;
+    x.n_chan = h->n_chan;
+    x.n_int = h->n_int;
+    x.scale = h->d_scale;
+    x.vis = h->d_vis;
+    x.vis_int = h->xmode == CORR_I8 ? h->d_vis_int : nullptr;
+    x.exact = h->xmode == CORR_I8 ? 1 : 0;
+    x.ks = h->ks > 0 ? h->ks : xengine_tc_max_ks(h->n_in);
+    return x;
+}
+
+int gbx::fail_code(int code, const char* msg) { return fail(code, "%s", msg); }
+
+namespace {
+
+// Rewrite the handle's one-entry tensor-core table (after a mode or stage-size change).
+int upload_xtab(corr* h) {
+    if (!h->d_xtab) return CORR_OK;
+    XtBatch t{};
+    t.n_sub = 1;
+    t.sub[0] = xt_sub_of(h);
+    t.n_items = h->n_items;
+    t.items = h->d_items;
+    t.err = h->d_err;
+    CU(cudaDeviceSynchronize());
+    CU(cudaMemcpy(h->d_xtab, &t, sizeof t, cudaMemcpyHostToDevice));
     return CORR_OK;
 }
 
@@ -352,7 +350,19 @@ int corr_create(corr_t** out, int n_ant, int n_pol, int n_fft, int n_int) {
         CUB(cudaMemcpy(h->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
     }
 #undef CUB
+    if (xengine_tc_supported(h->n_in)) {
+        const int rb = 2 * h->n_in > 128 ? 2 : 1;
+        std::vector<int4> items;
+        for (int k = 0; k < h->n_chan; ++k)
+            for (int r = 0; r < rb; ++r) items.push_back(make_int4(0, k, r, 0));
+        h->n_items = static_cast<int>(items.size());
+        if (cudaMalloc(&h->d_xtab, sizeof(XtBatch)) != cudaSuccess ||
+            cudaMalloc(&h->d_items, sizeof(int4) * items.size()) != cudaSuccess ||
+            cudaMemcpy(h->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(CORR_E_NOMEM, "tensor-core tables"));
+    }
     int rc = upload_beam_weights(h, nullptr, nullptr, nullptr, nullptr);
+    if (rc == CORR_OK) rc = upload_xtab(h);
     if (rc != CORR_OK) return bail(rc);
     *out = h;
     return CORR_OK;
@@ -363,6 +373,8 @@ int corr_destroy(corr_t* h) {
     cudaSetDevice(h->dev);
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->d_power) cudaFree(h->d_power);
+    if (h->d_xtab) cudaFree(h->d_xtab);
+    if (h->d_items) cudaFree(h->d_items);
     void* bufs[] = {h->d_ring, h->d_model, h->d_pf, h->d_ff, h->d_D, h->d_wcoh, h->d_ginc, h->d_scale,
                     h->d_tw, h->d_spec, h->d_beams_raw, h->d_vis, h->d_vis_int, h->d_err};
     for (void* b : bufs)
@@ -383,7 +395,7 @@ int corr_set_mode(corr_t* h, int xmode, int polmode, int beam_avg) {
     if (polmode != 0) return fail(CORR_E_INVAL, "only polmode 0 (all products) is supported");
     if (beam_avg < 1 || h->n_int % beam_avg) return fail(CORR_E_INVAL, "beam_avg must divide n_int");
     if (xmode != CORR_FP32 && !xengine_tc_supported(h->n_in))
-        return fail(CORR_E_INVAL, "tensor-core modes need n_in <= 64");
+        return fail(CORR_E_INVAL, "tensor-core modes need n_in <= 128");
     if (xmode == CORR_I8 && h->n_int > 66571) return fail(CORR_E_INVAL, "CORR_I8 needs n_int <= 66571");
     CU(cudaStreamSynchronize(h->stream));
     if (beam_avg != h->beam_avg) {
@@ -391,9 +403,18 @@ int corr_set_mode(corr_t* h, int xmode, int polmode, int beam_avg) {
         h->d_beams = h->d_beams_raw;
         if (beam_avg > 1) CU(dalloc(&h->d_beams, 2 * static_cast<size_t>(h->n_int / beam_avg) * h->n_chan));
     }
+    const bool changed = h->xmode != xmode;
     h->xmode = xmode;
     h->beam_avg = beam_avg;
-    return CORR_OK;
+    return changed ? upload_xtab(h) : CORR_OK;
+}
+
+int corr_set_xengine_stage(corr_t* h, int ks) {
+    if (int rc = check_handle(h)) return rc;
+    if (ks != 0 && (ks < 16 || ks > 512 || (ks & (ks - 1)) || ks > xengine_tc_max_ks(h->n_in)))
+        return fail(CORR_E_INVAL, "stage must be 0 or a power of two in [16, %d]", xengine_tc_max_ks(h->n_in));
+    h->ks = ks;
+    return upload_xtab(h);
 }
 
 int corr_set_max_delay(corr_t* h, int max_delay) {

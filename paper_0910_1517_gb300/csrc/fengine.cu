@@ -177,8 +177,17 @@ struct Smem {
     static_assert(X % 16 == 0 && tab % 16 == 0 && P::STAGE % 16 == 0, "bulk-copy targets are 16-byte aligned");
 };
 
+// Per-CTA control words kept in static shared memory by the kernel that runs the body.
+struct FeCtl {
+    uint64_t bar[2];
+    uint64_t tbar;
+    int abort_flag;
+    int Ds[kMaxAnt];           // integer delays, read every iteration
+};
+
+// The F-engine work of one CTA: frame block `block` of the integration described by p.
 template <int M, int MODE>
-__global__ void __launch_bounds__(kThreads, 1) fengine_kernel(const FeParams p) {
+__device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl& ctl) {
     using P = Plan<M>;
     using S = Smem<M>;
     constexpr int T = P::T, F = P::F, N = P::N;
@@ -194,15 +203,15 @@ __global__ void __launch_bounds__(kThreads, 1) fengine_kernel(const FeParams p) 
     float2* tw3 = tw2 + P::R2 * 16;                               // [R3][Ns3]
     float2* twN = tw3 + (P::R3 > 1 ? P::R3 * Ns3 : 0);            // [M/2 + 1]
     float2* tab = reinterpret_cast<float2*>(smem + S::tab);      // [pf | wcoh] of one antenna
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ __align__(8) uint64_t tbar;
-    __shared__ int abort_flag;
-    __shared__ int Ds[kMaxAnt];       // integer delays, read every iteration
+    uint64_t* bar = ctl.bar;
+    uint64_t& tbar = ctl.tbar;
+    int& abort_flag = ctl.abort_flag;
+    int* Ds = ctl.Ds;
 
     const int tid = threadIdx.x;
     const int f = tid / T;            // frame within the CTA owned by this thread's FFT group
     const int t = tid % T;            // thread within the group
-    const int t0 = blockIdx.x * F;
+    const int t0 = block * F;
     const int n_fr = min(F, p.n_int - t0);
     const bool live = f < n_fr;
     const int R = 2 * p.n_in;
@@ -456,6 +465,38 @@ __global__ void __launch_bounds__(kThreads, 1) fengine_kernel(const FeParams p) 
 }
 
 template <int M, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) fengine_kernel(const FeParams p) {
+    __shared__ __align__(8) FeCtl ctl;
+    fengine_cta<M, MODE>(p, blockIdx.x, ctl);
+}
+
+// Several integrations (sub-arrays of any supported FFT size) in one launch: CTA b runs
+// frame block b - first[s] of sub-array s, first[s] <= b < first[s + 1].
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) fengine_batched_kernel(const FeBatch* __restrict__ tab) {
+    __shared__ __align__(8) FeCtl ctl;
+    __shared__ int sub;
+    if (threadIdx.x == 0) {
+        int q = 0;
+        while (q + 1 < tab->n_sub && static_cast<int>(blockIdx.x) >= tab->first[q + 1]) ++q;
+        sub = q;
+    }
+    __syncthreads();
+    const FeParams& p = tab->p[sub];
+    const int block = blockIdx.x - tab->first[sub];
+    switch (p.n_chan) {
+        case 32: fengine_cta<32, MODE>(p, block, ctl); break;
+        case 64: fengine_cta<64, MODE>(p, block, ctl); break;
+        case 128: fengine_cta<128, MODE>(p, block, ctl); break;
+        case 256: fengine_cta<256, MODE>(p, block, ctl); break;
+        case 512: fengine_cta<512, MODE>(p, block, ctl); break;
+        case 1024: fengine_cta<1024, MODE>(p, block, ctl); break;
+        case 2048: fengine_cta<2048, MODE>(p, block, ctl); break;
+        default: break;
+    }
+}
+
+template <int M, int MODE>
 cudaError_t launch_t(const FeParams& p, cudaStream_t s) {
     using P = Plan<M>;
     const size_t smem = Smem<M>::total;
@@ -481,10 +522,12 @@ cudaError_t launch_mode(const FeParams& p, cudaStream_t s) {
     }
 }
 
-__global__ void phasor_setup_kernel(int n_ant, int n_chan, int n_fft, int n_int, int64_t g0,
+__global__ void phasor_setup_kernel(int n_ant, int n_chan, int n_fft, int n_int, int64_t g0_val,
+                                    const int64_t* __restrict__ g0_ptr,
                                     const double* __restrict__ tau, const double* __restrict__ phi0,
                                     const double* __restrict__ rate, float2* __restrict__ pf,
                                     float2* __restrict__ ff, int* __restrict__ D) {
+    const int64_t g0 = g0_ptr ? *g0_ptr : g0_val;
     const int64_t n1 = static_cast<int64_t>(n_ant) * n_chan, n2 = static_cast<int64_t>(n_ant) * n_int;
     for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < n1 + n2 + n_ant;
          q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -593,12 +636,29 @@ cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s) {
     }
 }
 
+int fengine_blocks(int n_fft, int n_int) { return (n_int + kChanFrames / (n_fft / 2) - 1) / (kChanFrames / (n_fft / 2)); }
+
+cudaError_t launch_fengine_batched(const FeBatch* dtab, int total_blocks, size_t smem, int mode, cudaStream_t s) {
+    auto go = [&](auto kern) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        kern<<<total_blocks, kThreads, smem, s>>>(dtab);
+        return cudaGetLastError();
+    };
+    switch (mode) {
+        case OUT_FP32: return go(fengine_batched_kernel<OUT_FP32>);
+        case OUT_I8: return go(fengine_batched_kernel<OUT_I8>);
+        case OUT_F16: return go(fengine_batched_kernel<OUT_F16>);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_phasor_setup(int n_ant, int n_chan, int n_fft, int n_int, int64_t g0, const double* tau,
                                 const double* phi0, const double* rate, float2* pf, float2* ff, int* D,
-                                cudaStream_t s) {
+                                cudaStream_t s, const int64_t* g0_dev) {
     const int64_t total = static_cast<int64_t>(n_ant) * (n_chan + n_int) + n_ant;
     const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4096));
-    phasor_setup_kernel<<<grid, 256, 0, s>>>(n_ant, n_chan, n_fft, n_int, g0, tau, phi0, rate, pf, ff, D);
+    phasor_setup_kernel<<<grid, 256, 0, s>>>(n_ant, n_chan, n_fft, n_int, g0, g0_dev, tau, phi0, rate, pf, ff, D);
     return cudaGetLastError();
 }
 

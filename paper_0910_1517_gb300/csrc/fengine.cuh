@@ -41,6 +41,17 @@ struct FeParams {
     unsigned* err;
 };
 
+// Several integrations in one launch (sub-arrays of uneven sizes).
+constexpr int kMaxSub = 8;
+struct FeBatch {
+    int n_sub;
+    int first[kMaxSub + 1];    // first CTA of each sub-array; first[n_sub] = total CTAs
+    FeParams p[kMaxSub];
+    int64_t g0[kMaxSub];       // global frame index of each sub-array's first frame
+};
+int fengine_blocks(int n_fft, int n_int);
+cudaError_t launch_fengine_batched(const FeBatch* dtab, int total_blocks, size_t smem, int mode, cudaStream_t s);
+
 // Dynamic shared memory needed by the F-engine for a given FFT size.
 size_t fengine_smem_bytes(int n_fft);
 int fengine_frames_per_cta(int n_fft);
@@ -49,9 +60,10 @@ std::vector<float2> fengine_twiddles(int n_fft);
 cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s);
 
 // pf, ff and D for one integration from the FP64 delay / fringe model.
+// g0_dev, when given, is read on the device instead of g0 (graph-captured launches).
 cudaError_t launch_phasor_setup(int n_ant, int n_chan, int n_fft, int n_int, int64_t g0, const double* tau,
                                 const double* phi0, const double* rate, float2* pf, float2* ff, int* D,
-                                cudaStream_t s);
+                                cudaStream_t s, const int64_t* g0_dev = nullptr);
 
 // Auto-power dumps from the FP32 K-block spectra: P[i][d][k] = sum of |Y_i[t][k]|^2 over the
 // `dump` frames of dump d (dump a multiple of 4 dividing n_int).

@@ -1,0 +1,65 @@
+// handle.cuh -- the correlator handle shared by the C ABI translation units (capi.cu, batch.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/corr.h"
+#include "fengine.cuh"
+#include "xengine.cuh"
+
+struct corr {
+    int n_ant = 0, n_pol = 0, n_in = 0, n_fft = 0, n_chan = 0, n_int = 0, n_bl = 0, npp = 0;
+    int xmode = CORR_FP32, beam_avg = 1, max_delay = 2048;
+    int dev = 0, n_sm = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_done = nullptr, ev_aux = nullptr;
+    // host-side model
+    std::vector<double> tau, phi0, rate;
+    bool scales_set = false;
+    // streaming ring
+    int8_t* d_ring = nullptr;
+    int64_t ring_ld = 0, fill = 0, seq_next = -1, seq_origin = -1, g_next = 0;
+    bool ring_started = false;
+    // device tables and outputs
+    double* d_model = nullptr;          // tau | phi0 | rate, 3 * n_ant
+    double* h_model = nullptr;          // pinned staging of the same
+    float2* d_pf = nullptr;
+    float2* d_ff = nullptr;
+    int* d_D = nullptr;
+    float2* d_wcoh = nullptr;
+    float* d_ginc = nullptr;
+    float* d_scale = nullptr;
+    float2* d_tw = nullptr;
+    void* d_spec = nullptr;
+    float* d_beams_raw = nullptr;
+    float* d_beams = nullptr;
+    float2* d_vis = nullptr;
+    int2* d_vis_int = nullptr;
+    unsigned* d_err = nullptr;
+    // bookkeeping
+    int64_t launched = 0, completed = 0;
+    int last_mode = -1;
+    // tensor-core X-engine table (one sub-array: this handle) and its work items
+    gbx::XtBatch* d_xtab = nullptr;
+    int4* d_items = nullptr;
+    int n_items = 0;
+    int ks = 0;                          // frames per operand stage (0 = largest that fits)
+    // auto-power dumps for the RFI stage (0 = off)
+    int dump = 0;
+    float* d_power = nullptr;
+    // per-stage timing: kTimedMax integrations x 5 events (before set-up and after each stage)
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;
+    int t_count = 0;
+};
+
+namespace gbx {
+// Fill a one-entry tensor-core table describing handle h (its spectra, scales and outputs).
+XtSub xt_sub_of(const corr* h);
+// Queue the integration's kernels of handle h (used by the C ABI and the batch code).
+int run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, int64_t g0, cudaStream_t s);
+void set_last_error(const char* msg);
+int fail_code(int code, const char* msg);
+}  // namespace gbx

@@ -20,9 +20,29 @@ struct XParams {
 // Plain FP32 X-engine on CUDA cores: register-tiled upper-triangular complex MAC.
 cudaError_t launch_xengine_fp32(const XParams& p, int n_sm, cudaStream_t s);
 
-// tcgen05 X-engine: G = A A^T per channel on the tensor cores, TMEM accumulators.
-// Supports 2*n_in <= 128.
-cudaError_t launch_xengine_tc(const XParams& p, int n_sm, cudaStream_t s);
-bool xengine_tc_supported(int n_in);
+// tcgen05 X-engine: G = A A^T per channel on the tensor cores, TMEM accumulators, over a
+// table of sub-arrays and a cost-ordered list of (sub-array, channel, row block) items.
+constexpr int kMaxSubX = 8;
+constexpr int kStageMaxBytes = 32768;        // bytes of one operand stage (ks/8 K-blocks x 2 n_in rows x 16 B)
+struct XtSub {
+    const __half* spec;    // [k][kb][2 n_in][8] fp16 K-block layout
+    int n_ant, n_pol, n_in, n_chan, n_int;
+    const float* scale;    // [n_in][n_chan]
+    float2* vis;           // [n_chan][n_bl][n_pol^2]
+    int2* vis_int;         // exact integer sums (int8-valued operands) or nullptr
+    int exact;
+    int ks;                // frames per operand stage: power of two, 16..512, ks/8 * 2 n_in * 16 <= kStageMaxBytes
+};
+struct XtBatch {
+    int n_sub;
+    XtSub sub[kMaxSubX];
+    int n_items;
+    const int4* items;     // (sub, channel, row block, 0)
+    unsigned* err;
+};
+bool xengine_tc_supported(int n_in);                 // 2 n_in <= 256
+int xengine_tc_max_ks(int n_in);                      // largest stage for the row count
+size_t xengine_tc_smem();
+cudaError_t launch_xengine_tc_table(const XtBatch* dtab, int n_items, int n_sm, cudaStream_t s);
 
 }  // namespace gbx

@@ -2,20 +2,27 @@
 //
 // Per channel k the visibilities are one dense contraction.  With the 2 n_in
 // real rows A[r][t], r = 2i + c (c = 0 real, 1 imaginary part of Y_i[t]),
-// the real Gram G = A A^T (M = N = 128 rows, K = n_int frames) holds every
-// product:  Re V_ij = G[2i][2j] + G[2i+1][2j+1],  Im V_ij = G[2i+1][2j] - G[2i][2j+1].
+// the real Gram G = A A^T (K = n_int frames) holds every product:
+//   Re V_ij = G[2i][2j] + G[2i+1][2j+1],  Im V_ij = G[2i+1][2j] - G[2i][2j+1].
 // A is the F-engine's K-block layout, which already is the no-swizzle K-major
 // canonical operand layout (core matrices of 8 rows x 16 bytes), so one
 // TMA-engine bulk copy per stage lands a ready operand tile and the same shared
-// memory tile is passed as both A and B.
+// memory tile serves as both A and B.
+//
+// Work items are (sub-array, channel, row block): 128 Gram rows a0..a0+127 against
+// columns b0..b0+N-1.  Up to 128 rows need one item (N <= 128, the rest of the 128
+// rows is ignored); 256 rows need two (rows 0-127 x columns 0-255, rows 128-255 x
+// columns 128-255).  A persistent CTA walks a cost-ordered item list; several
+// sub-arrays of different sizes share one launch.
 //
 // Roles (6 warps): warp 0 streams stages in (and owns the TMEM allocation),
 // warp 1 issues tcgen05.mma from one thread, warps 2-5 drain the accumulators.
-// Accumulation is chunked: every 512 frames the FP32 accumulator (double
-// buffered in TMEM) is drained and added into a running sum kept in TMEM.  For
-// int8-valued operands every product is an integer below 2^14 and a chunk sum
-// stays below 2^23, so the FP32 accumulator is exact and the running sum is
-// kept as int32: the result equals the integer MAC bit for bit.
+// Accumulation is chunked: every 512 frames the FP32 accumulator is drained
+// and added into a running sum in TMEM (columns 256-511).  Items with N <= 128
+// double-buffer the accumulator (columns 0-127 / 128-255), wider ones use one
+// buffer of N columns.  For int8-valued operands every product is an integer
+// below 2^14 and a chunk sum stays below 2^23, so the FP32 accumulator is exact
+// and the running sum is kept as int32: the result equals the integer MAC.
 #include "common.cuh"
 #include "fengine.cuh"
 #include "xengine.cuh"
@@ -25,12 +32,9 @@ namespace {
 
 constexpr int kWarps = 6;
 constexpr int kThreads = kWarps * 32;
-constexpr int kStages = 8;
-constexpr int kFramesPerStage = 64;           // 8 K-blocks of 8 frames, 4 MMAs of K = 16
-constexpr int kStagesPerChunk = 8;            // 512 frames per exact FP32 chunk
-constexpr int kRowsMax = 128;
-constexpr int kStageBytes = (kFramesPerStage / kTbHalf) * kRowsMax * 16;   // 16 KB
-constexpr int kStageStride = kStageBytes + 2048;                           // rows past R stay in bounds
+constexpr int kStages = 5;
+constexpr int kChunk = 512;                   // frames per exact FP32 chunk
+constexpr int kSlot = kStageMaxBytes + 2048;  // rows past R stay in bounds
 constexpr int kTailSlack = 32768;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColRun = 256;             // running-sum columns
@@ -45,17 +49,34 @@ struct Shared {
     int consumed;
 };
 
-__global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XParams p) {
+struct ItemGeo {
+    int sub, k, a0, b0, N, R, ntb, n_stage, n_chunk, nkb_stage;
+    bool dbl;
+};
+
+__device__ __forceinline__ ItemGeo item_geo(const XtBatch& t, int it) {
+    ItemGeo g;
+    const int4 e = t.items[it];
+    g.sub = e.x;
+    g.k = e.y;
+    const XtSub& s = t.sub[g.sub];
+    g.R = 2 * s.n_in;
+    g.a0 = 128 * e.z;
+    g.b0 = (g.R > 128) ? g.a0 : 0;
+    g.N = ((g.R - g.b0 + 15) / 16) * 16;
+    g.dbl = g.N <= 128;
+    g.ntb = s.n_int / kTbHalf;
+    g.nkb_stage = s.ks / kTbHalf;
+    g.n_stage = (s.n_int + s.ks - 1) / s.ks;
+    g.n_chunk = (s.n_int + kChunk - 1) / kChunk;
+    return g;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XtBatch* __restrict__ tab) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ Shared sh;
+    const XtBatch& t = *tab;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int R = 2 * p.n_in;
-    const int NP = ((R + 15) / 16) * 16;           // MMA N
-    const int ntb = p.n_int / kTbHalf;
-    const int n_stage_ch = (p.n_int + kFramesPerStage - 1) / kFramesPerStage;
-    const int n_ch_mine = (p.n_chan - static_cast<int>(blockIdx.x) + gridDim.x - 1) / gridDim.x;
-    const int n_chunk_ch = (n_stage_ch + kStagesPerChunk - 1) / kStagesPerChunk;
-    const __half* spec = static_cast<const __half*>(p.spec);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -84,56 +105,73 @@ __global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XParams p
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             int g = 0;
-            for (int c = 0; c < n_ch_mine && !*abort_flag; ++c) {
-                const int k = blockIdx.x + c * gridDim.x;
-                for (int st = 0; st < n_stage_ch; ++st, ++g) {
+            for (int it = blockIdx.x; it < t.n_items && !*abort_flag; it += gridDim.x) {
+                const ItemGeo ig = item_geo(t, it);
+                const XtSub& s = t.sub[ig.sub];
+                for (int st = 0; st < ig.n_stage; ++st, ++g) {
                     const int slot = g % kStages;
-                    if (!mbar_wait(&sh.empty[slot], ((g / kStages) & 1) ^ 1, p.err, ERR_WAIT_MMA)) {
+                    if (!mbar_wait(&sh.empty[slot], ((g / kStages) & 1) ^ 1, t.err, ERR_WAIT_MMA)) {
                         *abort_flag = 1;
                         break;
                     }
-                    const int kb0 = st * (kFramesPerStage / kTbHalf);
-                    const int nkb = min(kFramesPerStage / kTbHalf, ntb - kb0);
-                    const uint32_t bytes = static_cast<uint32_t>(nkb) * R * 16;
-                    const __half* src = spec + (static_cast<int64_t>(k) * ntb + kb0) * R * kTbHalf;
+                    const int kb0 = st * ig.nkb_stage;
+                    const int nkb = min(ig.nkb_stage, ig.ntb - kb0);
+                    const uint32_t bytes = static_cast<uint32_t>(nkb) * ig.R * 16;
+                    const __half* src = s.spec + (static_cast<int64_t>(ig.k) * ig.ntb + kb0) * ig.R * kTbHalf;
                     mbar_arrive_expect_tx(&sh.full[slot], bytes);
-                    bulk_g2s(smem + slot * kStageStride, src, bytes, &sh.full[slot]);
+                    bulk_g2s(smem + slot * kSlot, src, bytes, &sh.full[slot]);
                 }
             }
             // let every issued copy land before the CTA can exit
-            for (int q = sh.consumed; q < g; ++q)
+            for (int q = *(volatile int*)&sh.consumed; q < g; ++q)
                 mbar_wait(&sh.full[q % kStages], (q / kStages) & 1, nullptr, 0);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_f16_f32(128, NP);
-            const uint32_t lbo = static_cast<uint32_t>(R) * 16, sbo = 128;
-            int g = 0, cc = 0;
-            for (int c = 0; c < n_ch_mine && !*abort_flag; ++c) {
-                for (int chunk = 0; chunk < n_chunk_ch && !*abort_flag; ++chunk, ++cc) {
-                    const int b = cc & 1;
-                    if (!mbar_wait(&sh.acce[b], ((cc >> 1) & 1) ^ 1, p.err, ERR_WAIT_EPI)) {
+            int g = 0, cc = 0, use0 = 0, use1 = 0;
+            int prev_dbl = -1;
+            for (int it = blockIdx.x; it < t.n_items && !*abort_flag; it += gridDim.x) {
+                const ItemGeo ig = item_geo(t, it);
+                const XtSub& s = t.sub[ig.sub];
+                const uint32_t idesc = idesc_f16_f32(128, ig.N);
+                const uint32_t lbo = static_cast<uint32_t>(ig.R) * 16, sbo = 128;
+                const int stages_per_chunk = kChunk / s.ks;
+                for (int chunk = 0; chunk < ig.n_chunk && !*abort_flag; ++chunk, ++cc) {
+                    const int b = ig.dbl ? (cc & 1) : 0;
+                    // a single-buffered item, or a change of buffering, needs every earlier drain done
+                    bool ok = true;
+                    if (!ig.dbl || prev_dbl != static_cast<int>(ig.dbl)) {
+                        ok = mbar_wait(&sh.acce[0], (use0 & 1) ^ 1, t.err, ERR_WAIT_EPI) &&
+                             mbar_wait(&sh.acce[1], (use1 & 1) ^ 1, t.err, ERR_WAIT_EPI);
+                    } else {
+                        ok = mbar_wait(&sh.acce[b], ((b ? use1 : use0) & 1) ^ 1, t.err, ERR_WAIT_EPI);
+                    }
+                    prev_dbl = ig.dbl;
+                    if (!ok) {
                         *abort_flag = 1;
                         break;
                     }
+                    if (b) ++use1; else ++use0;
                     tc_fence_after();
-                    const uint32_t dcol = tmem + b * 128;
-                    const int st0 = chunk * kStagesPerChunk;
-                    const int st1 = min(n_stage_ch, st0 + kStagesPerChunk);
+                    const uint32_t dcol = tmem + (ig.dbl ? b * 128 : 0);
+                    const int st0 = chunk * stages_per_chunk;
+                    const int st1 = min(ig.n_stage, st0 + stages_per_chunk);
                     bool first = true;
                     for (int st = st0; st < st1; ++st, ++g) {
                         const int slot = g % kStages;
-                        if (!mbar_wait(&sh.full[slot], (g / kStages) & 1, p.err, ERR_WAIT_STAGE)) {
+                        if (!mbar_wait(&sh.full[slot], (g / kStages) & 1, t.err, ERR_WAIT_STAGE)) {
                             *abort_flag = 1;
                             break;
                         }
                         tc_fence_after();
-                        const int nkb = min(kFramesPerStage / kTbHalf, ntb - st * (kFramesPerStage / kTbHalf));
-                        const uint32_t base = smem_u32(smem + slot * kStageStride);
+                        const int nkb = min(ig.nkb_stage, ig.ntb - st * ig.nkb_stage);
+                        const uint32_t base = smem_u32(smem + slot * kSlot);
                         for (int kk = 0; kk < nkb / 2; ++kk) {
-                            const uint64_t d = smem_desc_noswizzle(base + kk * 2 * lbo, lbo, sbo);
-                            umma_f16(dcol, d, d, idesc, first ? 0u : 1u);
+                            const uint32_t kbase = base + kk * 2 * lbo;
+                            const uint64_t da = smem_desc_noswizzle(kbase + ig.a0 * 16, lbo, sbo);
+                            const uint64_t db = smem_desc_noswizzle(kbase + ig.b0 * 16, lbo, sbo);
+                            umma_f16(dcol, da, db, idesc, first ? 0u : 1u);
                             first = false;
                         }
                         umma_commit(&sh.empty[slot]);   // frees the stage once these MMAs finish
@@ -147,28 +185,33 @@ __global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XParams p
     } else {
         // ------------------------------------------------------------ epilogue (warps 2..5)
         const int q = warp & 3;                   // TMEM lane quarter this warp may access
-        const int row = 32 * q + lane;            // Gram row = TMEM lane
+        const int lrow = 32 * q + lane;           // row within the item's 128 rows = TMEM lane
         const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
-        const int n_bl = p.n_ant * (p.n_ant + 1) / 2, npp = p.n_pol * p.n_pol;
-        int cc = 0;
-        for (int c = 0; c < n_ch_mine && !*abort_flag; ++c) {
-            const int k = blockIdx.x + c * gridDim.x;
-            for (int chunk = 0; chunk < n_chunk_ch; ++chunk, ++cc) {
-                const int b = cc & 1;
-                if (!mbar_wait(&sh.accf[b], (cc >> 1) & 1, p.err, ERR_WAIT_MMA)) {
+        int cc = 0, use0 = 0, use1 = 0;
+        for (int it = blockIdx.x; it < t.n_items && !*abort_flag; it += gridDim.x) {
+            const ItemGeo ig = item_geo(t, it);
+            const XtSub& s = t.sub[ig.sub];
+            const int n_bl = s.n_ant * (s.n_ant + 1) / 2, npp = s.n_pol * s.n_pol;
+            const int row = ig.a0 + lrow;
+            for (int chunk = 0; chunk < ig.n_chunk; ++chunk, ++cc) {
+                const int b = ig.dbl ? (cc & 1) : 0;
+                const int use = b ? use1 : use0;
+                if (!mbar_wait(&sh.accf[b], use & 1, t.err, ERR_WAIT_MMA)) {
                     *abort_flag = 1;
                     break;
                 }
+                if (b) ++use1; else ++use0;
                 tc_fence_after();
-                const bool last = chunk == n_chunk_ch - 1;
-                for (int j0 = 0; j0 < NP; j0 += 32) {
+                const bool last = chunk == ig.n_chunk - 1;
+                const uint32_t acol = ig.dbl ? b * 128 : 0;
+                for (int j0 = 0; j0 < ig.N; j0 += 32) {
                     uint32_t v[32], run[32];
-                    tmem_ld32(tmem + lane_off + b * 128 + j0, v);
+                    tmem_ld32(tmem + lane_off + acol + j0, v);
                     if (chunk > 0) tmem_ld32(tmem + lane_off + kColRun + j0, run);
                     tmem_wait_ld();
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
-                        if (p.exact) {
+                        if (s.exact) {
                             const int x = __float2int_rn(__uint_as_float(v[e]));
                             run[e] = chunk > 0 ? static_cast<uint32_t>(static_cast<int>(run[e]) + x)
                                                : static_cast<uint32_t>(x);
@@ -190,28 +233,27 @@ __global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XParams p
 #pragma unroll
                         for (int jh = 0; jh < 8; ++jh) {
                             const int jp = jh + (odd ? 8 : 0);
-                            const int j = (j0 >> 1) + jp;
-                            // row 2i values and row 2i+1 values at columns 2jp, 2jp+1
+                            const int j = ((ig.b0 + j0) >> 1) + jp;
                             const uint32_t g_r0c0 = odd ? other[2 * jp] : run[2 * jp];
                             const uint32_t g_r0c1 = odd ? other[2 * jp + 1] : run[2 * jp + 1];
                             const uint32_t g_r1c0 = odd ? run[2 * jp] : other[2 * jp];
                             const uint32_t g_r1c1 = odd ? run[2 * jp + 1] : other[2 * jp + 1];
-                            if (i >= p.n_in || j >= p.n_in) continue;
-                            const int a = i / p.n_pol, pp = i % p.n_pol, a2 = j / p.n_pol, qq = j % p.n_pol;
+                            if (i >= s.n_in || j >= s.n_in) continue;
+                            const int a = i / s.n_pol, pp = i % s.n_pol, a2 = j / s.n_pol, qq = j % s.n_pol;
                             if (a > a2) continue;
-                            const int bl = a * p.n_ant - a * (a - 1) / 2 + (a2 - a);
-                            const int64_t o = (static_cast<int64_t>(k) * n_bl + bl) * npp + pp * p.n_pol + qq;
-                            const float d = p.scale[static_cast<int64_t>(i) * p.n_chan + k] *
-                                            p.scale[static_cast<int64_t>(j) * p.n_chan + k];
-                            if (p.exact) {
+                            const int bl = a * s.n_ant - a * (a - 1) / 2 + (a2 - a);
+                            const int64_t o = (static_cast<int64_t>(ig.k) * n_bl + bl) * npp + pp * s.n_pol + qq;
+                            const float d = s.scale[static_cast<int64_t>(i) * s.n_chan + ig.k] *
+                                            s.scale[static_cast<int64_t>(j) * s.n_chan + ig.k];
+                            if (s.exact) {
                                 const int re = static_cast<int>(g_r0c0) + static_cast<int>(g_r1c1);
                                 const int im = static_cast<int>(g_r1c0) - static_cast<int>(g_r0c1);
-                                if (p.vis_int) p.vis_int[o] = make_int2(re, im);
-                                p.vis[o] = make_float2(static_cast<float>(re) / d, static_cast<float>(im) / d);
+                                if (s.vis_int) s.vis_int[o] = make_int2(re, im);
+                                s.vis[o] = make_float2(static_cast<float>(re) / d, static_cast<float>(im) / d);
                             } else {
                                 const float re = __uint_as_float(g_r0c0) + __uint_as_float(g_r1c1);
                                 const float im = __uint_as_float(g_r1c0) - __uint_as_float(g_r0c1);
-                                p.vis[o] = make_float2(re / d, im / d);
+                                s.vis[o] = make_float2(re / d, im / d);
                             }
                         }
                     }
@@ -233,16 +275,23 @@ __global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XParams p
 
 }  // namespace
 
-bool xengine_tc_supported(int n_in) { return n_in >= 1 && 2 * n_in <= kRowsMax; }
+bool xengine_tc_supported(int n_in) { return n_in >= 1 && 2 * n_in <= 256; }
 
-cudaError_t launch_xengine_tc(const XParams& p, int n_sm, cudaStream_t s) {
-    if (!xengine_tc_supported(p.n_in) || p.n_int % 16 != 0) return cudaErrorInvalidValue;
-    const size_t smem = static_cast<size_t>(kStages) * kStageStride + kTailSlack;
+int xengine_tc_max_ks(int n_in) {
+    int ks = kChunk;
+    while (ks > 16 && (ks / kTbHalf) * 2 * n_in * 16 > kStageMaxBytes) ks /= 2;
+    return ks;
+}
+
+size_t xengine_tc_smem() { return static_cast<size_t>(kStages) * kSlot + kTailSlack; }
+
+cudaError_t launch_xengine_tc_table(const XtBatch* dtab, int n_items, int n_sm, cudaStream_t s) {
+    const size_t smem = xengine_tc_smem();
     cudaError_t e = cudaFuncSetAttribute(xengine_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    const int grid = std::max(1, std::min(p.n_chan, n_sm));
-    xengine_tc_kernel<<<grid, kThreads, smem, s>>>(p);
+    const int grid = std::max(1, std::min(n_items, n_sm));
+    xengine_tc_kernel<<<grid, kThreads, smem, s>>>(dtab);
     return cudaGetLastError();
 }
 

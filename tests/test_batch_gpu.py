@@ -1,0 +1,146 @@
+"""Several uneven sub-arrays in one graph-captured launch (corr_batch_*): every sub-array's
+integer visibilities equal the oracle's int64 MAC on its own requantised spectra, the batch
+agrees with the single-handle path, the graph replays correctly with new samples and frame
+counters, and the autotuner's stage choice leaves the results unchanged."""
+import numpy as np
+import pytest
+
+from fxhelp import vis_norm_error
+from synth import make_config
+
+pytestmark = pytest.mark.gpu
+
+# (n_ant, n_pol, n_fft, n_int): uneven antenna counts and FFT sizes; 64 x 2 exercises the
+# two row blocks of a 256-row Gram
+SUBS = [(4, 2, 512, 64), (8, 2, 1024, 48), (16, 2, 2048, 32), (64, 2, 256, 32)]
+CHANS = [0, 1, 57, 100]
+
+
+@pytest.fixture(scope="module")
+def env(orc):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0910_1517_gb300 import build, corr
+    build.build()
+    corr.load()
+    return torch, corr, orc
+
+
+def _dev(torch, x):
+    n_in, n = x.shape
+    xt = torch.zeros((n_in, ((n + 15) // 16) * 16 + 16), dtype=torch.int8, device="cuda")
+    xt[:, :n] = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    return xt, n
+
+
+def _handles(torch, corr, seeds, mode):
+    """Handles with delays set and scales calibrated by one FP32 integration each."""
+    hs, streams, xs = [], [], []
+    st = torch.cuda.current_stream()
+    for (na, npol, nfft, nint), seed in zip(SUBS, seeds):
+        s = make_config(2, n_ant=na, n_pol=npol, n_fft=nfft, n_int=nint, seed=seed)
+        h = corr.corr_create(na, npol, nfft, nint)
+        corr.corr_set_delays(h, s.delay, s.phi0, s.rate)
+        xt, n = _dev(torch, s.x)
+        corr.corr_integrate_device(h, xt, n_avail=n, stream=st)
+        corr.corr_set_scales(h, None)
+        corr.corr_set_mode(h, mode, 0, 1)
+        hs.append(h)
+        streams.append(s)
+        xs.append((xt, n))
+    return hs, streams, xs
+
+
+def _check_exact(corr, orc, h, s):
+    Vi = corr.corr_read_vis_int(h)
+    for c in CHANS:
+        if c >= s.n_fft // 2:
+            continue
+        q, sc = corr.corr_read_requant(h, c, 1, s.n_int)
+        Vo, _ = orc.xint(q, sc[:, c:c + 1].astype(np.float64), s.n_ant, s.n_pol)
+        assert np.array_equal(Vi[c], Vo[0].astype(np.int32)), (s.n_ant, c)
+    return Vi
+
+
+def test_batch_int8_exact_matches_oracle_and_single_handle(env):
+    torch, corr, orc = env
+    hs, streams, xs = _handles(torch, corr, [701, 702, 703, 704], corr.CORR_I8)
+    st = torch.cuda.current_stream()
+    b = corr.corr_batch_create(hs)
+    try:
+        corr.corr_batch_integrate_device(b, [x for x, _ in xs], n_avail=[n for _, n in xs], stream=st)
+        batch_vi = [_check_exact(corr, orc, h, s) for h, s in zip(hs, streams)]
+        # the same integrations one handle at a time give the same integers
+        for h, (xt, n), vb in zip(hs, xs, batch_vi):
+            corr.corr_integrate_device(h, xt, n_avail=n, stream=st)
+            assert np.array_equal(corr.corr_read_vis_int(h), vb)
+        # replay the graph with other samples and a later frame counter
+        for s_old, h, (xt, n) in zip(streams, hs, xs):
+            s2 = make_config(2, n_ant=s_old.n_ant, n_pol=s_old.n_pol, n_fft=s_old.n_fft, n_int=s_old.n_int,
+                             seed=s_old.recipe["seed"] + 50)
+            xt[:, :n] = torch.from_numpy(s2.x).cuda()
+        g0 = [3 * s.n_int for s in streams]
+        corr.corr_batch_integrate_device(b, [x for x, _ in xs], n_avail=[n for _, n in xs], g0=g0, stream=st)
+        for s_old, h, (xt, n), g in zip(streams, hs, xs, g0):
+            s2 = make_config(2, n_ant=s_old.n_ant, n_pol=s_old.n_pol, n_fft=s_old.n_fft, n_int=s_old.n_int,
+                             seed=s_old.recipe["seed"] + 50)
+            _check_exact(corr, orc, h, s2)
+            # the handles keep the delay model they were given; only the samples are new
+            # the replay used the new samples and frame counter: the FP64 spectra with that g0,
+            # requantised with the GPU's scales, give the same visibilities up to rare +-1 flips
+            ch = CHANS[:3]
+            Y = orc.fengine(s2.x, s2.n_ant, s2.n_pol, s2.n_fft, s2.n_int, s_old.delay, s_old.phi0, s_old.rate,
+                            g0=g, chans=ch)
+            _, sc = corr.corr_read_requant(h, 0, 0, s2.n_int)
+            sc64 = sc[:, ch].astype(np.float64)
+            _, Vq = orc.xint(orc.requant(Y, sc64), sc64, s2.n_ant, s2.n_pol)
+            Vg = corr.corr_read_visibilities(h).astype(np.complex128)[ch]
+            e = vis_norm_error(Vg, Vq, s2.n_ant, s2.n_pol)
+            print(f"batch replay {s2.n_ant} ant {s2.n_fft}-pt: vs oracle requantisation {e:.2e}, "
+                  f"vs FP64 {vis_norm_error(Vg, orc.xengine(Y, s2.n_ant, s2.n_pol), s2.n_ant, s2.n_pol):.2e}")
+            assert e < 2e-3
+    finally:
+        corr.corr_batch_destroy(b)
+        for h in hs:
+            corr.corr_destroy(h)
+
+
+def test_batch_autotune_keeps_results(env):
+    torch, corr, orc = env
+    hs, streams, xs = _handles(torch, corr, [801, 802, 803, 804], corr.CORR_I8)
+    st = torch.cuda.current_stream()
+    b = corr.corr_batch_create(hs)
+    try:
+        corr.corr_batch_integrate_device(b, [x for x, _ in xs], n_avail=[n for _, n in xs], stream=st)
+        before = [corr.corr_read_vis_int(h) for h in hs]
+        ks, ms = corr.corr_batch_tune(b, len(hs))
+        print("tuned frames per stage", ks.tolist(), "ms", [round(float(v), 4) for v in ms])
+        assert all(k >= 32 for k in ks) and all(m > 0 for m in ms)
+        corr.corr_batch_integrate_device(b, [x for x, _ in xs], n_avail=[n for _, n in xs], stream=st)
+        for h, v in zip(hs, before):
+            assert np.array_equal(corr.corr_read_vis_int(h), v)
+    finally:
+        corr.corr_batch_destroy(b)
+        for h in hs:
+            corr.corr_destroy(h)
+
+
+def test_batch_fp32_matches_single_handle(env):
+    torch, corr, orc = env
+    hs, streams, xs = _handles(torch, corr, [901, 902, 903, 904], corr.CORR_FP32)
+    st = torch.cuda.current_stream()
+    single = []
+    for h, (xt, n) in zip(hs, xs):
+        corr.corr_integrate_device(h, xt, n_avail=n, stream=st)
+        single.append(corr.corr_read_visibilities(h).astype(np.complex128))
+    b = corr.corr_batch_create(hs)
+    try:
+        corr.corr_batch_integrate_device(b, [x for x, _ in xs], n_avail=[n for _, n in xs], stream=st)
+        for h, s, v in zip(hs, streams, single):
+            vb = corr.corr_read_visibilities(h).astype(np.complex128)
+            assert vis_norm_error(vb, v, s.n_ant, s.n_pol) <= 1e-6
+    finally:
+        corr.corr_batch_destroy(b)
+        for h in hs:
+            corr.corr_destroy(h)
