@@ -270,6 +270,140 @@ def run_e2e(args, corr, torch, dist, s, coh, world):
     return e2e
 
 
+BATCH_SUBS = ((8, 2, 512), (16, 2, 1024), (32, 2, 2048), (64, 2, 4096))
+BATCH_N_INT = 4096
+
+
+def run_batch_leg(args, corr, torch, rank):
+    """Four uneven sub-arrays in one graph launch per step, int8 tensor-core X-engine,
+    X-engine stage sizes chosen by the autotuner."""
+    from synth import uniform_params
+    from synth.device import make_streams_device
+    stream = torch.cuda.current_stream()
+    hs, xs, na, samples = [], [], [], 0
+    for q, (n_ant, n_pol, n_fft) in enumerate(BATCH_SUBS):
+        d, w, f = uniform_params(n_ant, 4000 + q + 10 * rank, (0.0, 2000.0), (0.0, 0.1), (-math.pi, math.pi))
+        d = np.floor(d + 0.5)                       # integer sky delays for the device generator
+        n_samp = BATCH_N_INT * n_fft + 2048
+        x = make_streams_device(n_ant, n_pol, n_samp, delays=d, seed=4000 + q + 10 * rank)
+        h = corr.corr_create(n_ant, n_pol, n_fft, BATCH_N_INT)
+        corr.corr_set_delays(h, d, f, w)
+        corr.corr_integrate_device(h, x, n_avail=x.shape[1], stream=stream)
+        corr.corr_set_scales(h, None)                # calibration integration (FP32)
+        corr.corr_set_mode(h, corr.CORR_I8, 0, 1)
+        hs.append(h)
+        xs.append(x)
+        na.append(x.shape[1])
+        samples += n_ant * n_pol * BATCH_N_INT * n_fft
+    b = corr.corr_batch_create(hs)
+    try:
+        corr.corr_batch_integrate_device(b, xs, n_avail=na, stream=stream)
+        ks, ms_x = corr.corr_batch_tune(b, len(hs))
+        for _ in range(3):
+            corr.corr_batch_integrate_device(b, xs, n_avail=na, stream=stream)
+        torch.cuda.synchronize()
+        k = max(10, min(args.steps, 100))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for j in range(k):
+            corr.corr_batch_integrate_device(b, xs, n_avail=na, g0=[(j + 4) * BATCH_N_INT] * len(hs), stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+    finally:
+        corr.corr_batch_destroy(b)
+        for h in hs:
+            corr.corr_destroy(h)
+    return {"workload": "4 sub-arrays (ant, pol, FFT) = " + ", ".join(str(t) for t in BATCH_SUBS) +
+                        f", {BATCH_N_INT} spectra each, int8 tensor-core X-engine, one CUDA graph per step",
+            "value": samples / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": k,
+            "tuned_frames_per_stage": [int(v) for v in ks], "tuned_xengine_ms": [float(v) for v in ms_x],
+            "launches_per_step": f"1 graph: {len(hs)} phasor set-ups + 1 F-engine + 1 X-engine kernel"}
+
+
+def run_rfi_leg(corr, torch, n_train_int=25, n_test_int=3):
+    """Learned RFI flagger on the GMRT-shaped correlator's own 1 ms power dumps with injected
+    RFI: 4096 patches per integration; one training epoch; held-out comparison with the MAD
+    flagger."""
+    from synth.rfi import patch_masks, rfi_streams
+    stream = torch.cuda.current_stream()
+    n_in, n_fft, n_int = N_IN, N_FFT, N_INT
+    n_dump = n_int // 32
+    h = corr.corr_create(N_ANT, N_POL, n_fft, n_int)
+    corr.corr_set_power_dump(h, 32)
+    B = n_in * (n_dump // 64) * (N_CHAN // 64)
+
+    def data(n, seed):
+        xs, fs, ms = [], [], []
+        for j in range(n):
+            x, mask = rfi_streams(n_in, n_fft, n_int, seed=seed + j)
+            corr.corr_integrate_device(h, x, n_avail=n_int * n_fft, stream=stream)
+            xp = torch.empty((B, 64, 64), dtype=torch.float16, device="cuda")
+            fl = torch.empty((B, 64, 64), dtype=torch.uint8, device="cuda")
+            corr.rfi_patches(corr.corr_power_device(h), n_in, n_dump, N_CHAN, 5.0, xp, fl, None, stream=stream)
+            xs.append(xp)
+            fs.append(fl)
+            ms.append(patch_masks(mask))
+            del x
+        torch.cuda.synchronize()
+        return torch.cat(xs), torch.cat(fs), torch.cat(ms)
+
+    try:
+        t0 = time.perf_counter()
+        xtr, _, mtr = data(n_train_int, 20000)
+        xte, fte, mte = data(n_test_int, 90000)
+        t_data = time.perf_counter() - t0
+    finally:
+        corr.corr_destroy(h)
+    rng = np.random.default_rng(1)
+    p = np.zeros(corr.rfi_n_params())
+    offs = ((0, 144, 9), (160, 4608, 144), (4800, 4608, 288), (9424, 16, 16))
+    for o, n, fan in offs:
+        p[o:o + n] = rng.normal(scale=math.sqrt(2.0 / fan), size=n)
+    for o, n in ((144, 16), (4768, 32), (9408, 16)):
+        p[o:o + n] = 0.05
+    net = corr.rfi_create(256)
+    try:
+        corr.rfi_set_params(net, p)
+        g = torch.Generator(device="cuda").manual_seed(0)
+        perm = torch.randperm(xtr.shape[0], generator=g, device="cuda")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        steps = 0
+        for b0 in range(0, xtr.shape[0] - 255, 256):
+            idx = perm[b0:b0 + 256]
+            corr.rfi_train_step(net, xtr[idx].contiguous(), mtr[idx].contiguous(), 256, 2e-3, stream=stream)
+            steps += 1
+        e1.record(stream)
+        torch.cuda.synchronize()
+        train_ms = e0.elapsed_time(e1)
+        prob = torch.empty(xte.shape, dtype=torch.float32, device="cuda")
+        e0.record(stream)
+        for b0 in range(0, xte.shape[0], 256):
+            nb = min(256, xte.shape[0] - b0)
+            corr.rfi_infer(net, xte[b0:b0 + nb].contiguous(), nb, prob[b0:b0 + nb], stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        infer_ms = e0.elapsed_time(e1)
+    finally:
+        corr.rfi_destroy(net)
+
+    def rates(flags, mask):
+        f, m = flags.bool(), mask.bool()
+        return (float((m & ~f).sum()) / max(1, int(m.sum())), float((f & ~m).sum()) / max(1, int((~m).sum())))
+
+    cnn, mad = rates(prob > 0.5, mte), rates(fte, mte)
+    return {"workload": "32 ant x 2 pol, 1024 ch, 32-frame (0.98 ms) power dumps, 64x64 FP16 patches, "
+                        "injected tones 5-50 sigma and 0.1-5 ms bursts",
+            "train_patches": int(xtr.shape[0]), "test_patches": int(xte.shape[0]),
+            "occupancy": float(mte.float().mean()), "epochs": 1, "train_steps": steps,
+            "train_patches_per_s": steps * 256 / (train_ms * 1e-3),
+            "infer_patches_per_s": xte.shape[0] / (infer_ms * 1e-3),
+            "cnn": {"miss": cnn[0], "false_flag": cnn[1]}, "mad_5sigma": {"miss": mad[0], "false_flag": mad[1]},
+            "data_generation_s": t_data}
+
+
 def run_ours(args, world, rank, local_rank):
     import torch
     from paper_0910_1517_gb300 import build as libbuild
@@ -360,7 +494,6 @@ def run_ours(args, world, rank, local_rank):
     e2e = None if args.no_extras else run_e2e(args, corr, torch, dist, s, coh, world)
 
     # roofline of the dominant kernel of the FP32 step
-    # roofline of the dominant kernel of the FP32 step
     dom = 1 if st[1] >= st[2] else 2
     kname = {1: "fengine", 2: "xengine"}[dom]
     bound, ach, peak, unit, alg = stage_roofline(kname, "fp32", st[dom], pk)
@@ -380,6 +513,14 @@ def run_ours(args, world, rank, local_rank):
         cpu = cpu_baseline_auto(s.x, s)
 
     corr.corr_destroy(h)
+    del xt
+    torch.cuda.empty_cache()
+    batch = rfi = None
+    if not args.no_extras:
+        batch = run_batch_leg(args, corr, torch, rank)
+        torch.cuda.empty_cache()
+        if rank == 0:
+            rfi = run_rfi_leg(corr, torch)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -389,6 +530,7 @@ def run_ours(args, world, rank, local_rank):
             "rtf": value / (world * N_IN * SAMPLE_RATE),
             "xengine_frac_of_fp32_peak": stages["xengine"]["frac"],
             "roofline": roofline, "stages": stages, "precision_forms": modes,
+            "batched_subarrays": batch, "learned_rfi": rfi,
             "e2e": e2e, "gpu_launches": 3 * K, "clocks": clocks, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
