@@ -168,6 +168,13 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
            | (static_cast<uint32_t>(M >> 4) << 24);       // M / 16
 }
 
+// One 32-byte global store (a full L2 sector); p must be 32-byte aligned.
+__device__ __forceinline__ void st_global_v8(void* p, const uint32_t (&v)[8]) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
 // ------------------------------------------------------------- complex math
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {

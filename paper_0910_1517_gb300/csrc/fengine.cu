@@ -42,12 +42,13 @@ struct Plan {
     static constexpr int R1 = 16;
     static constexpr int R2 = (M / 16 >= 16) ? 16 : M / 16;
     static constexpr int R3 = M / (R1 * R2);                   // 1 when two passes suffice
-    static constexpr int PADM = M + M / 32;                    // padded frame length (float2)
+    static constexpr int PADM = M + M / 16;                    // padded frame length (float2)
     static constexpr int STAGE = F * N + 32;                   // staging bytes per buffer
     static_assert(F * M == kChanFrames, "CTA covers 8192 channel-frames");
 };
 
-__host__ __device__ constexpr int pad32(int i) { return i + (i >> 5); }
+// one pad element per 16: every Stockham exchange of 8-byte points is free of bank conflicts
+__host__ __device__ constexpr int pad16(int i) { return i + (i >> 4); }
 
 // cos / sin of 2 pi m / 16
 __device__ __forceinline__ constexpr float c16(int m) {
@@ -124,7 +125,7 @@ __device__ __forceinline__ void pass_load(const float2* __restrict__ src, const 
     for (int m = 0; m < PER; ++m) {
         const int b = t + m * T;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[m * R + r] = src[pad32(b + r * NB)];
+        for (int r = 0; r < R; ++r) v[m * R + r] = src[pad16(b + r * NB)];
         const int j = b % Ns;
 #pragma unroll
         for (int r = 1; r < R; ++r) v[m * R + r] = cmul(tw[r * Ns + j], v[m * R + r]);
@@ -140,7 +141,7 @@ __device__ __forceinline__ void pass_store(float2* __restrict__ dst, int t, cons
         const int b = t + m * T;
         const int base = (b / Ns) * Ns * R + (b % Ns);
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[pad32(base + r * Ns)] = v[m * R + r];
+        for (int r = 0; r < R; ++r) dst[pad16(base + r * Ns)] = v[m * R + r];
     }
 }
 
@@ -154,75 +155,115 @@ __device__ __forceinline__ void group_sync(int g) {
     }
 }
 
-// swizzle of the transposed [channel][frame] buffer: spreads a warp's same-frame stores over banks
-template <int F>
-__device__ __forceinline__ int tswz(int ch) {
-    constexpr int rows_per_line = (16 / F) > 1 ? (16 / F) : 1;
-    return (ch / rows_per_line) & (F - 1);
-}
+// Split / epilogue geometry: after the FFT every thread takes L consecutive frames of NP
+// channel pairs (k, M - k), L = the K-block run length (frames per 16-byte row), so that it
+// holds whole (channel, input) pieces of the K-block layout and writes each as one 32-byte
+// sector straight from registers -- no transposition buffer.  The TPG = L * T threads of a
+// frame group are exactly the FFT groups of its L frames.
+template <int M, int MODE>
+struct Epi {
+    using P = Plan<M>;
+    static constexpr int TB = (MODE == OUT_FP32) ? kTbFp32 : kTbHalf;
+    static constexpr int L = (P::F < TB) ? P::F : TB;    // frames per thread
+    static constexpr int NP = kE / (2 * L);                // channel pairs per thread
+    static constexpr int TPG = L * P::T;                   // threads per frame group
+    static_assert(2 * NP * L == kE && NP * TPG == M / 2, "split covers every channel of every frame once");
+};
 
 template <int M>
 struct Smem {
     using P = Plan<M>;
-    static constexpr bool kTabSmem = M <= 1024;                       // per-antenna tables staged in smem
     static constexpr int kTw = P::R2 * 16 + (P::R3 > 1 ? P::R3 * 16 * P::R2 : 0) + M / 2 + 1;
+    static constexpr int kTab = 2 * M + P::F;                          // [pf M | wcoh M | ff F] of one antenna
     static constexpr size_t stage = 0;
     static constexpr size_t X = stage + 2 * static_cast<size_t>(P::STAGE);
-    static constexpr size_t inc = X + sizeof(float2) * P::F * P::PADM;
-    static constexpr size_t coh = inc + sizeof(float) * P::F * M;
-    static constexpr size_t tw = coh + sizeof(float2) * P::F * M;
-    static constexpr size_t tab = ((tw + sizeof(float2) * kTw + 127) / 128) * 128;   // bulk-copy target
-    static constexpr size_t total = tab + (kTabSmem ? sizeof(float2) * 2 * M : 0);
+    static constexpr size_t tw = X + sizeof(float2) * P::F * P::PADM;
+    static constexpr size_t tab = ((tw + sizeof(float2) * kTw + 127) / 128) * 128;   // 2 bulk-copy targets
+    static constexpr size_t total = tab + 2 * sizeof(float2) * kTab;
     static_assert(total <= 232448, "F-engine shared memory exceeds 227 KB");
-    static_assert(X % 16 == 0 && tab % 16 == 0 && P::STAGE % 16 == 0, "bulk-copy targets are 16-byte aligned");
+    static_assert(X % 16 == 0 && tab % 16 == 0 && (sizeof(float2) * kTab) % 16 == 0 && P::STAGE % 16 == 0,
+                  "bulk-copy targets are 16-byte aligned");
 };
 
 // Per-CTA control words kept in static shared memory by the kernel that runs the body.
 struct FeCtl {
     uint64_t bar[2];
-    uint64_t tbar;
+    uint64_t tbar[2];
     int abort_flag;
     int Ds[kMaxAnt];           // integer delays, read every iteration
 };
+
+__device__ __forceinline__ uint32_t pack_half2(__half lo, __half hi) {
+    return static_cast<uint32_t>(__half_as_ushort(lo)) | (static_cast<uint32_t>(__half_as_ushort(hi)) << 16);
+}
 
 // The F-engine work of one CTA: frame block `block` of the integration described by p.
 template <int M, int MODE>
 __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl& ctl) {
     using P = Plan<M>;
     using S = Smem<M>;
+    using E = Epi<M, MODE>;
     constexpr int T = P::T, F = P::F, N = P::N;
     constexpr int Ns3 = P::R1 * P::R2;
-    constexpr int TB = (MODE == OUT_FP32) ? kTbFp32 : kTbHalf;
-    constexpr int L = (F < TB) ? F : TB;                 // frames per output run
+    constexpr int TB = E::TB, L = E::L, NP = E::NP, TPG = E::TPG;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* stage0 = smem + S::stage;
     float2* X = reinterpret_cast<float2*>(smem + S::X);           // F * PADM
-    float* inc = reinterpret_cast<float*>(smem + S::inc);        // F * M
-    float2* coh = reinterpret_cast<float2*>(smem + S::coh);      // F * M
     float2* tw2 = reinterpret_cast<float2*>(smem + S::tw);       // [R2][16]
     float2* tw3 = tw2 + P::R2 * 16;                               // [R3][Ns3]
     float2* twN = tw3 + (P::R3 > 1 ? P::R3 * Ns3 : 0);            // [M/2 + 1]
-    float2* tab = reinterpret_cast<float2*>(smem + S::tab);      // [pf | wcoh] of one antenna
+    float2* tab = reinterpret_cast<float2*>(smem + S::tab);      // 2 x [pf | wcoh | ff] of one antenna
     uint64_t* bar = ctl.bar;
-    uint64_t& tbar = ctl.tbar;
+    uint64_t* tbar = ctl.tbar;
     int& abort_flag = ctl.abort_flag;
     int* Ds = ctl.Ds;
 
     const int tid = threadIdx.x;
-    const int f = tid / T;            // frame within the CTA owned by this thread's FFT group
-    const int t = tid % T;            // thread within the group
+    const int f = tid / T;            // frame of this thread's FFT group
+    const int t = tid % T;            // thread within the FFT group
+    const int fg = tid / TPG;         // frame group of the split: frames fg*L .. fg*L + L - 1
+    const int kk = tid % TPG;         // channel pairs kk + q*TPG, q < NP
     const int t0 = block * F;
     const int n_fr = min(F, p.n_int - t0);
-    const bool live = f < n_fr;
+    const bool live = fg * L < n_fr;  // n_fr is a multiple of L: whole frame groups are live or not
     const int R = 2 * p.n_in;
+    const int64_t ntb = p.n_int / TB;
+
+    // this thread's channels and the offsets (in elements) of their K-blocks, fixed for the CTA
+    int chs[2 * NP];
+    int64_t obase[2 * NP];
+    {
+        const int kb = (t0 + fg * L) / TB;
+        const int rows = (MODE == OUT_FP32) ? rows_fp32(p.n_in) : R;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const int k = kk + q * TPG;
+            chs[2 * q] = k;
+            chs[2 * q + 1] = (k == 0) ? M / 2 : M - k;
+        }
+#pragma unroll
+        for (int c = 0; c < 2 * NP; ++c) obase[c] = (static_cast<int64_t>(chs[c]) * ntb + kb) * rows * TB;
+    }
+
+    // beam accumulators of this thread's L x 2 NP points: the incoherent sum over every input,
+    // and the coherent voltage sum of the current polarisation
+    float incr[L][2 * NP];
+    float2 cohr[L][2 * NP];
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int c = 0; c < 2 * NP; ++c) {
+            incr[l][c] = 0.0f;
+            cohr[l][c] = make_float2(0.0f, 0.0f);
+        }
 
     for (int m = tid; m < S::kTw; m += kThreads) tw2[m] = p.tw[m];
-    for (int m = tid; m < F * M; m += kThreads) inc[m] = 0.0f;
     for (int m = tid; m < p.n_ant; m += kThreads) Ds[m] = p.D[m];
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
-        mbar_init(&tbar, 1);
+        mbar_init(&tbar[0], 1);
+        mbar_init(&tbar[1], 1);
         fence_mbar_init();
         abort_flag = 0;
     }
@@ -252,28 +293,33 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
         const int64_t q = bulk_end + lane;
         if (q < end) dst[q - aligned] = static_cast<unsigned char>(row[q]);
     };
-    auto issue_tab = [&](int it) {  // phasor and beam-weight rows of the antenna of input `it`
-        if constexpr (S::kTabSmem) {
-            const int a = it % p.n_ant;
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&tbar, 2 * M * sizeof(float2));
-            bulk_g2s(tab, p.pf + static_cast<int64_t>(a) * M, M * sizeof(float2), &tbar);
-            bulk_g2s(tab + M, p.wcoh + static_cast<int64_t>(a) * M, M * sizeof(float2), &tbar);
-        }
+    // phasor, beam-weight and fringe rows of the antenna of input `it` (n_fr fringe phasors:
+    // n_fr * 8 bytes is a multiple of 16 since n_fr is F or a multiple of 16)
+    auto issue_tab = [&](int it) {
+        const int a = it % p.n_ant;
+        float2* dst = tab + (it & 1) * S::kTab;
+        uint64_t* tb = &tbar[it & 1];
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(tb, (2 * M + n_fr) * sizeof(float2));
+        bulk_g2s(dst, p.pf + static_cast<int64_t>(a) * M, M * sizeof(float2), tb);
+        bulk_g2s(dst + M, p.wcoh + static_cast<int64_t>(a) * M, M * sizeof(float2), tb);
+        bulk_g2s(dst + 2 * M, p.ff + static_cast<int64_t>(a) * p.n_int + t0, n_fr * sizeof(float2), tb);
     };
     __syncthreads();                 // Ds visible to warp 0
     if (tid < 32) issue(0);
     if (tid == 0) issue_tab(0);
-    __syncthreads();
 
     int it = 0;
     for (; it < n_iter; ++it) {
         const int pol = it / p.n_ant, a = it % p.n_ant;
         const int i = a * p.n_pol + pol;
         if (tid < 32 && it + 1 < n_iter) issue(it + 1);
-        // fringe phasor and incoherent weight: loaded now, used after the FFT
-        const float2 fr = p.ff[static_cast<int64_t>(a) * p.n_int + min(t0 + f, p.n_int - 1)];
         const float g2 = p.ginc[a];
+        float scv[2 * NP];           // requantisation scales of this thread's channels
+        if constexpr (MODE != OUT_FP32) {
+#pragma unroll
+            for (int c = 0; c < 2 * NP; ++c) scv[c] = p.scale[static_cast<int64_t>(i) * M + chs[c]];
+        }
         if (!mbar_wait(&bar[it & 1], (it >> 1) & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
         const int64_t s0 = static_cast<int64_t>(t0) * N + Ds[a];
         const unsigned char* st = stage0 + (it & 1) * P::STAGE + (s0 & 15) + f * N;
@@ -301,166 +347,142 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
             }
             Dft<16>::template run<1>(v);
         }
-        __syncthreads();  // every group left the previous iteration's transposed buffer (aliases X)
+        __syncthreads();  // the previous iteration's split has finished reading X and its antenna tables
         if (abort_flag) break;
+        if (tid == 0 && it + 1 < n_iter) issue_tab(it + 1);   // into the buffer that split just released
         pass_store<M, P::R1, 1>(Xf, t, v);
         group_sync<T>(f);
         // ---- pass 2
         pass_load<M, P::R2, P::R1>(Xf, tw2, t, v);
         group_sync<T>(f);
         pass_store<M, P::R2, P::R1>(Xf, t, v);
-        group_sync<T>(f);
         // ---- pass 3
         if constexpr (P::R3 > 1) {
+            group_sync<T>(f);
             pass_load<M, P::R3, Ns3>(Xf, tw3, t, v);
             group_sync<T>(f);
             pass_store<M, P::R3, Ns3>(Xf, t, v);
-            group_sync<T>(f);
         }
+        __syncthreads();  // every frame's FFT is in X: the split reads the frames of its group
 
-        // ---- real split, Eq. 2 phasor, beams
-        const float2* pfa;
-        const float2* wa;
-        if constexpr (S::kTabSmem) {
-            if (!mbar_wait(&tbar, it & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
-            pfa = tab;
-            wa = tab + M;
-        } else {
-            pfa = p.pf + static_cast<int64_t>(a) * M;
-            wa = p.wcoh + static_cast<int64_t>(a) * M;
+        // ---- real split, Eq. 2 phasor (fractional delay x fringe), beams, K-block stores
+        if (!mbar_wait(&tbar[it & 1], (it >> 1) & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
+        const float2* pfa = tab + (it & 1) * S::kTab;
+        const float2* wa = pfa + M;
+        const float2* fra = pfa + 2 * M;   // fringe phasors of the CTA's frames
+        if (!live) continue;
+        float2 y[L][2 * NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const int k = chs[2 * q], kc = chs[2 * q + 1];
+            const float2 wk = twN[k];
+            const float2 pk = pfa[k], pm = pfa[kc];
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                const int fl = fg * L + l;
+                const float2* Xl = X + fl * P::PADM;
+                const float2 zk = Xl[pad16(k)];
+                const float2 zm = Xl[pad16(kc)];
+                float2 xk, xmk;
+                if (k == 0) {
+                    xk = make_float2(zk.x + zk.y, 0.0f);       // DC
+                    xmk = make_float2(zm.x, -zm.y);            // channel M/2 (zm = z[M/2])
+                } else {
+                    const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+                    const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+                    const float2 wo = cmul(wk, o);
+                    xk = cadd(e, wo);
+                    const float2 d = csub(e, wo);
+                    xmk = make_float2(d.x, -d.y);
+                }
+                const float2 fr = fra[fl];
+                y[l][2 * q] = cmul(xk, cmul(pk, fr));
+                y[l][2 * q + 1] = cmul(xmk, cmul(pm, fr));
+            }
         }
-        float2 y[kE];
-        int ch[kE];
+        // beams: every (frame, channel) point belongs to exactly one thread, in registers
 #pragma unroll
-        for (int m = 0; m < kE / 2; ++m) {
-            const int k = t + m * T;                       // 0 .. M/2 - 1
-            const float2 zk = Xf[pad32(k)];
-            float2 xk, xmk;
-            int kk;
-            if (k == 0) {
-                const float2 zh = Xf[pad32(M / 2)];
-                xk = make_float2(zk.x + zk.y, 0.0f);       // DC
-                xmk = make_float2(zh.x, -zh.y);            // channel M/2
-                kk = M / 2;
-            } else {
-                const float2 zm = Xf[pad32(M - k)];
-                const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-                const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-                const float2 wo = cmul(twN[k], o);
-                xk = cadd(e, wo);
-                const float2 d = csub(e, wo);
-                xmk = make_float2(d.x, -d.y);
-                kk = M - k;
-            }
-            ch[2 * m] = k;
-            ch[2 * m + 1] = kk;
-            y[2 * m] = cmul(xk, cmul(pfa[k], fr));
-            y[2 * m + 1] = cmul(xmk, cmul(pfa[kk], fr));
-        }
-        if (live) {
-            if (a == 0) {
+        for (int c = 0; c < 2 * NP; ++c) {
+            const float2 w = wa[chs[c]];
 #pragma unroll
-                for (int e = 0; e < kE; ++e) coh[f * M + ch[e]] = make_float2(0.0f, 0.0f);
-            }
-#pragma unroll
-            for (int e = 0; e < kE; ++e) {
-                const int o = f * M + ch[e];
-                inc[o] += g2 * (y[e].x * y[e].x + y[e].y * y[e].y);
-                coh[o] = cadd(coh[o], cmul(wa[ch[e]], y[e]));
-            }
-            if (a == p.n_ant - 1) {  // this polarisation's coherent sum is complete: detect
-                float* bc = p.beams + (static_cast<int64_t>(p.n_int) + t0 + f) * M;
-#pragma unroll
-                for (int e = 0; e < kE; ++e) {
-                    const float2 c = coh[f * M + ch[e]];
-                    const float pw = c.x * c.x + c.y * c.y;
-                    bc[ch[e]] = (pol == 0) ? pw : bc[ch[e]] + pw;
+            for (int l = 0; l < L; ++l) {
+                incr[l][c] += g2 * (y[l][c].x * y[l][c].x + y[l][c].y * y[l][c].y);
+                const float2 prev = (a == 0) ? make_float2(0.0f, 0.0f) : cohr[l][c];
+                cohr[l][c] = cadd(prev, cmul(w, y[l][c]));
+                if (a == p.n_ant - 1) {  // this polarisation's coherent sum is complete: detect
+                    float* bc = p.beams + (static_cast<int64_t>(p.n_int) + t0 + fg * L + l) * M + chs[c];
+                    const float pw = cohr[l][c].x * cohr[l][c].x + cohr[l][c].y * cohr[l][c].y;
+                    *bc = (pol == 0) ? pw : *bc + pw;
                 }
             }
         }
-
-        // ---- transpose through shared memory and write the K-block layout
-        __syncthreads();  // all reads of X and of the antenna tables are done
-        if (tid == 0 && it + 1 < n_iter) issue_tab(it + 1);
-        float2* Tb = X;   // [M][F], swizzled
+        // K-block stores: one 32-byte sector per (channel, input) -- rows 2i and 2i+1, L frames
+        if constexpr (MODE == OUT_FP32) {
+            const int r0 = swz_row(2 * i);                 // rows 2i, 2i+1 are one aligned pair, order r0 & 1
+            const bool flip = r0 & 1;
+            float* spec = static_cast<float*>(p.spec);
 #pragma unroll
-        for (int e = 0; e < kE; ++e) Tb[ch[e] * F + (f ^ tswz<F>(ch[e]))] = y[e];
-        __syncthreads();
-        {
-            constexpr int RUNS = F / L;                    // output runs per channel
-            const float* sc = p.scale + static_cast<int64_t>(i) * M;
-            for (int item = tid; item < M * RUNS; item += kThreads) {
-                const int k = item / RUNS, run = item % RUNS;
-                const int fl0 = run * L;
-                if (fl0 >= n_fr) continue;
-                const int tg = t0 + fl0;                   // global frame of the run start
-                const int kb = tg / TB, off = tg % TB;
-                float2 val[L];
+            for (int c = 0; c < 2 * NP; ++c) {
+                uint32_t u[8];
 #pragma unroll
-                for (int l = 0; l < L; ++l) val[l] = Tb[k * F + ((fl0 + l) ^ tswz<F>(k))];
-                const int64_t ntb = p.n_int / TB;
-                if constexpr (MODE == OUT_FP32) {
-                    const int Rp = rows_fp32(p.n_in);
-                    const int64_t blk = (static_cast<int64_t>(k) * ntb + kb) * Rp;
-                    float* ore = static_cast<float*>(p.spec) + (blk + swz_row(2 * i)) * TB + off;
-                    float* oim = static_cast<float*>(p.spec) + (blk + swz_row(2 * i + 1)) * TB + off;
-                    float re[L], im[L];
+                for (int l = 0; l < 4; ++l) {
+                    u[l] = __float_as_uint(flip ? y[l][c].y : y[l][c].x);
+                    u[4 + l] = __float_as_uint(flip ? y[l][c].x : y[l][c].y);
+                }
+                st_global_v8(spec + obase[c] + (r0 & ~1) * TB, u);
+            }
+        } else {
+            __half* spec = static_cast<__half*>(p.spec);
+            const int off = (t0 + fg * L) % TB;
 #pragma unroll
-                    for (int l = 0; l < L; ++l) { re[l] = val[l].x; im[l] = val[l].y; }
-                    if constexpr (L == 4) {
-                        *reinterpret_cast<float4*>(ore) = make_float4(re[0], re[1], re[2], re[3]);
-                        *reinterpret_cast<float4*>(oim) = make_float4(im[0], im[1], im[2], im[3]);
+            for (int c = 0; c < 2 * NP; ++c) {
+                __half hr[L], hi[L];
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    const float xr = y[l][c].x * scv[c], xi = y[l][c].y * scv[c];
+                    if constexpr (MODE == OUT_I8) {
+                        hr[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xr))));
+                        hi[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xi))));
                     } else {
-#pragma unroll
-                        for (int l = 0; l < L; ++l) { ore[l] = re[l]; oim[l] = im[l]; }
+                        hr[l] = __float2half_rn(xr);
+                        hi[l] = __float2half_rn(xi);
                     }
-                } else {
-                    const int64_t rowbase = ((static_cast<int64_t>(k) * ntb + kb) * R + 2 * i) * TB + off;
-                    const float s = sc[k];
-                    __half re[L], im[L];
+                }
+                __half* o = spec + obase[c] + 2 * i * TB + off;
+                if constexpr (L == 8) {
+                    uint32_t u[8];
 #pragma unroll
-                    for (int l = 0; l < L; ++l) {
-                        const float xr = val[l].x * s, xi = val[l].y * s;
-                        if constexpr (MODE == OUT_I8) {
-                            const int qr = max(-127, min(127, __float2int_rn(xr)));
-                            const int qi = max(-127, min(127, __float2int_rn(xi)));
-                            re[l] = __int2half_rn(qr);
-                            im[l] = __int2half_rn(qi);
-                        } else {
-                            re[l] = __float2half_rn(xr);
-                            im[l] = __float2half_rn(xi);
-                        }
+                    for (int m = 0; m < 4; ++m) {
+                        u[m] = pack_half2(hr[2 * m], hr[2 * m + 1]);
+                        u[4 + m] = pack_half2(hi[2 * m], hi[2 * m + 1]);
                     }
-                    __half* o = static_cast<__half*>(p.spec) + rowbase;
-                    if constexpr (L == 8) {
-                        uint4 ur, ui;
-                        memcpy(&ur, re, 16);
-                        memcpy(&ui, im, 16);
-                        *reinterpret_cast<uint4*>(o) = ur;
-                        *reinterpret_cast<uint4*>(o + TB) = ui;
-                    } else if constexpr (L == 4) {
-                        uint2 ur, ui;
-                        memcpy(&ur, re, 8);
-                        memcpy(&ui, im, 8);
-                        *reinterpret_cast<uint2*>(o) = ur;
-                        *reinterpret_cast<uint2*>(o + TB) = ui;
-                    } else {
-#pragma unroll
-                        for (int l = 0; l < L; ++l) { o[l] = re[l]; o[TB + l] = im[l]; }
-                    }
+                    st_global_v8(o, u);
+                } else {                                   // half rows (F = 4 frames per CTA)
+                    static_assert(L == 4, "fp16 runs of 4 or 8 frames");
+                    *reinterpret_cast<uint2*>(o) = make_uint2(pack_half2(hr[0], hr[1]), pack_half2(hr[2], hr[3]));
+                    *reinterpret_cast<uint2*>(o + TB) = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
                 }
             }
         }
     }
 
-    // incoherent beam of this CTA's frames
+    // incoherent beam of this thread's points
     __syncthreads();
     if (!abort_flag) {
-        for (int m = tid; m < n_fr * M; m += kThreads) p.beams[static_cast<int64_t>(t0) * M + m] = inc[m];
+        if (live) {
+#pragma unroll
+            for (int l = 0; l < L; ++l)
+#pragma unroll
+                for (int c = 0; c < 2 * NP; ++c)
+                    p.beams[static_cast<int64_t>(t0 + fg * L + l) * M + chs[c]] = incr[l][c];
+        }
     } else if (tid == 0) {
-        // copies issued ahead of an aborted iteration must land before the CTA exits
+        // copies issued ahead of an aborted iteration must land before the CTA exits: the
+        // stages of iterations it and it + 1, and the antenna tables of iterations it - 1 and it
+        mbar_wait(&bar[it & 1], (it >> 1) & 1, nullptr, 0);
         if (it + 1 < n_iter) mbar_wait(&bar[(it + 1) & 1], ((it + 1) >> 1) & 1, nullptr, 0);
-        if (S::kTabSmem) mbar_wait(&tbar, it & 1, nullptr, 0);
+        if (it > 0) mbar_wait(&tbar[(it - 1) & 1], ((it - 1) >> 1) & 1, nullptr, 0);
+        mbar_wait(&tbar[it & 1], (it >> 1) & 1, nullptr, 0);
     }
 }
 
