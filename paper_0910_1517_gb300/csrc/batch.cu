@@ -138,6 +138,8 @@ int capture(corr_batch* b) {
             xp.scale = h->d_scale;
             xp.vis = h->d_vis;
             xp.err = h->d_err;
+            xp.vis_part = h->d_vis_part;
+            xp.max_split = corr::kVisSplit;
             ok = launch_xengine_fp32(xp, b->n_sm, s) == cudaSuccess;
         }
     }

@@ -155,6 +155,8 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
     xp.vis_int = h->xmode == CORR_I8 ? h->d_vis_int : nullptr;
     xp.err = h->d_err;
     xp.exact = h->xmode == CORR_I8 ? 1 : 0;
+    xp.vis_part = h->d_vis_part;
+    xp.max_split = corr::kVisSplit;
     if (h->xmode == CORR_FP32)
         CU(launch_xengine_fp32(xp, h->n_sm, s));
     else
@@ -334,10 +336,12 @@ int corr_create(corr_t** out, int n_ant, int n_pol, int n_fft, int n_int) {
     CUB(dalloc(&h->d_scale, ni * nch));
     const size_t spec_bytes = nch * static_cast<size_t>(n_int) * rows_fp32(h->n_in) * sizeof(float);
     CUB(cudaMalloc(&h->d_spec, spec_bytes));
+    CUB(cudaMemset(h->d_spec, 0, spec_bytes));   // padding rows of the FP32 layout stay zero
     CUB(dalloc(&h->d_beams_raw, 2 * static_cast<size_t>(n_int) * nch));
     h->d_beams = h->d_beams_raw;
     const size_t nvis = nch * h->n_bl * h->npp;
     CUB(dalloc(&h->d_vis, nvis));
+    CUB(dalloc(&h->d_vis_part, corr::kVisSplit * nvis));
     CUB(dalloc(&h->d_vis_int, nvis));
     CUB(dalloc(&h->d_err, 1));
     CUB(cudaMemset(h->d_err, 0, sizeof(unsigned)));
@@ -376,7 +380,7 @@ int corr_destroy(corr_t* h) {
     if (h->d_xtab) cudaFree(h->d_xtab);
     if (h->d_items) cudaFree(h->d_items);
     void* bufs[] = {h->d_ring, h->d_model, h->d_pf, h->d_ff, h->d_D, h->d_wcoh, h->d_ginc, h->d_scale,
-                    h->d_tw, h->d_spec, h->d_beams_raw, h->d_vis, h->d_vis_int, h->d_err};
+                    h->d_tw, h->d_spec, h->d_beams_raw, h->d_vis, h->d_vis_part, h->d_vis_int, h->d_err};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->d_beams && h->d_beams != h->d_beams_raw) cudaFree(h->d_beams);
@@ -404,6 +408,10 @@ int corr_set_mode(corr_t* h, int xmode, int polmode, int beam_avg) {
         if (beam_avg > 1) CU(dalloc(&h->d_beams, 2 * static_cast<size_t>(h->n_int / beam_avg) * h->n_chan));
     }
     const bool changed = h->xmode != xmode;
+    if (changed && xmode == CORR_FP32) {   // the FP32 layout's padding rows must read as zero again
+        const size_t spec_bytes = static_cast<size_t>(h->n_chan) * h->n_int * rows_fp32(h->n_in) * sizeof(float);
+        CU(cudaMemset(h->d_spec, 0, spec_bytes));
+    }
     h->xmode = xmode;
     h->beam_avg = beam_avg;
     return changed ? upload_xtab(h) : CORR_OK;

@@ -168,6 +168,11 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
            | (static_cast<uint32_t>(M >> 4) << 24);       // M / 16
 }
 
+// Barrier `id` (1..15) among the first n threads (a multiple of 32) that reach it.
+__device__ __forceinline__ void named_bar_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 // One 32-byte global store (a full L2 sector); p must be 32-byte aligned.
 __device__ __forceinline__ void st_global_v8(void* p, const uint32_t (&v)[8]) {
     asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(v[0]), "r"(v[1]),

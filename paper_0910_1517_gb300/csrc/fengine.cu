@@ -229,21 +229,17 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
     const int R = 2 * p.n_in;
     const int64_t ntb = p.n_int / TB;
 
-    // this thread's channels and the offsets (in elements) of their K-blocks, fixed for the CTA
+    // this thread's channels, fixed for the CTA; the K-block of its frames starts at element
+    // (ch * ntb + kb) * rows * TB of the spectra
     int chs[2 * NP];
-    int64_t obase[2 * NP];
-    {
-        const int kb = (t0 + fg * L) / TB;
-        const int rows = (MODE == OUT_FP32) ? rows_fp32(p.n_in) : R;
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            const int k = kk + q * TPG;
-            chs[2 * q] = k;
-            chs[2 * q + 1] = (k == 0) ? M / 2 : M - k;
-        }
-#pragma unroll
-        for (int c = 0; c < 2 * NP; ++c) obase[c] = (static_cast<int64_t>(chs[c]) * ntb + kb) * rows * TB;
+    for (int q = 0; q < NP; ++q) {
+        const int k = kk + q * TPG;
+        chs[2 * q] = k;
+        chs[2 * q + 1] = (k == 0) ? M / 2 : M - k;
     }
+    const int kb_run = (t0 + fg * L) / TB;
+    const int64_t blk_elems = static_cast<int64_t>((MODE == OUT_FP32) ? rows_fp32(p.n_in) : R) * TB;
 
     // beam accumulators of this thread's L x 2 NP points: the incoherent sum over every input,
     // and the coherent voltage sum of the current polarisation
@@ -371,12 +367,67 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
         const float2* wa = pfa + M;
         const float2* fra = pfa + 2 * M;   // fringe phasors of the CTA's frames
         if (!live) continue;
-        float2 y[L][2 * NP];
+        const int r0 = swz_row(2 * i);      // FP32 rows 2i, 2i+1: one aligned pair, real row first unless r0 is odd
+        // beams and the K-block store of channel c from its L frames
+        auto emit = [&](int c, const float2 (&yc)[L]) {
+            const float2 w = wa[chs[c]];
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                incr[l][c] += g2 * (yc[l].x * yc[l].x + yc[l].y * yc[l].y);
+                const float2 prev = (a == 0) ? make_float2(0.0f, 0.0f) : cohr[l][c];
+                cohr[l][c] = cadd(prev, cmul(w, yc[l]));
+                if (a == p.n_ant - 1) {  // this polarisation's coherent sum is complete: detect
+                    float* bc = p.beams + (static_cast<int64_t>(p.n_int) + t0 + fg * L + l) * M + chs[c];
+                    const float pw = cohr[l][c].x * cohr[l][c].x + cohr[l][c].y * cohr[l][c].y;
+                    *bc = (pol == 0) ? pw : *bc + pw;
+                }
+            }
+            // one 32-byte sector per (channel, input): rows 2i and 2i+1 over the L frames
+            const int64_t blk = (static_cast<int64_t>(chs[c]) * ntb + kb_run) * blk_elems;
+            if constexpr (MODE == OUT_FP32) {
+                const bool flip = r0 & 1;
+                uint32_t u[8];
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    u[l] = __float_as_uint(flip ? yc[l].y : yc[l].x);
+                    u[4 + l] = __float_as_uint(flip ? yc[l].x : yc[l].y);
+                }
+                st_global_v8(static_cast<float*>(p.spec) + blk + (r0 & ~1) * TB, u);
+            } else {
+                __half hr[L], hi[L];
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    const float xr = yc[l].x * scv[c], xi = yc[l].y * scv[c];
+                    if constexpr (MODE == OUT_I8) {
+                        hr[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xr))));
+                        hi[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xi))));
+                    } else {
+                        hr[l] = __float2half_rn(xr);
+                        hi[l] = __float2half_rn(xi);
+                    }
+                }
+                __half* o = static_cast<__half*>(p.spec) + blk + 2 * i * TB + (t0 + fg * L) % TB;
+                if constexpr (L == 8) {
+                    uint32_t u[8];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        u[m] = pack_half2(hr[2 * m], hr[2 * m + 1]);
+                        u[4 + m] = pack_half2(hi[2 * m], hi[2 * m + 1]);
+                    }
+                    st_global_v8(o, u);
+                } else {                                   // half rows (F = 4 frames per CTA)
+                    static_assert(L == 4, "fp16 runs of 4 or 8 frames");
+                    *reinterpret_cast<uint2*>(o) = make_uint2(pack_half2(hr[0], hr[1]), pack_half2(hr[2], hr[3]));
+                    *reinterpret_cast<uint2*>(o + TB) = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
+                }
+            }
+        };
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             const int k = chs[2 * q], kc = chs[2 * q + 1];
             const float2 wk = twN[k];
             const float2 pk = pfa[k], pm = pfa[kc];
+            float2 yk[L], ym[L];
 #pragma unroll
             for (int l = 0; l < L; ++l) {
                 const int fl = fg * L + l;
@@ -396,73 +447,11 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
                     xmk = make_float2(d.x, -d.y);
                 }
                 const float2 fr = fra[fl];
-                y[l][2 * q] = cmul(xk, cmul(pk, fr));
-                y[l][2 * q + 1] = cmul(xmk, cmul(pm, fr));
+                yk[l] = cmul(xk, cmul(pk, fr));
+                ym[l] = cmul(xmk, cmul(pm, fr));
             }
-        }
-        // beams: every (frame, channel) point belongs to exactly one thread, in registers
-#pragma unroll
-        for (int c = 0; c < 2 * NP; ++c) {
-            const float2 w = wa[chs[c]];
-#pragma unroll
-            for (int l = 0; l < L; ++l) {
-                incr[l][c] += g2 * (y[l][c].x * y[l][c].x + y[l][c].y * y[l][c].y);
-                const float2 prev = (a == 0) ? make_float2(0.0f, 0.0f) : cohr[l][c];
-                cohr[l][c] = cadd(prev, cmul(w, y[l][c]));
-                if (a == p.n_ant - 1) {  // this polarisation's coherent sum is complete: detect
-                    float* bc = p.beams + (static_cast<int64_t>(p.n_int) + t0 + fg * L + l) * M + chs[c];
-                    const float pw = cohr[l][c].x * cohr[l][c].x + cohr[l][c].y * cohr[l][c].y;
-                    *bc = (pol == 0) ? pw : *bc + pw;
-                }
-            }
-        }
-        // K-block stores: one 32-byte sector per (channel, input) -- rows 2i and 2i+1, L frames
-        if constexpr (MODE == OUT_FP32) {
-            const int r0 = swz_row(2 * i);                 // rows 2i, 2i+1 are one aligned pair, order r0 & 1
-            const bool flip = r0 & 1;
-            float* spec = static_cast<float*>(p.spec);
-#pragma unroll
-            for (int c = 0; c < 2 * NP; ++c) {
-                uint32_t u[8];
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    u[l] = __float_as_uint(flip ? y[l][c].y : y[l][c].x);
-                    u[4 + l] = __float_as_uint(flip ? y[l][c].x : y[l][c].y);
-                }
-                st_global_v8(spec + obase[c] + (r0 & ~1) * TB, u);
-            }
-        } else {
-            __half* spec = static_cast<__half*>(p.spec);
-            const int off = (t0 + fg * L) % TB;
-#pragma unroll
-            for (int c = 0; c < 2 * NP; ++c) {
-                __half hr[L], hi[L];
-#pragma unroll
-                for (int l = 0; l < L; ++l) {
-                    const float xr = y[l][c].x * scv[c], xi = y[l][c].y * scv[c];
-                    if constexpr (MODE == OUT_I8) {
-                        hr[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xr))));
-                        hi[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xi))));
-                    } else {
-                        hr[l] = __float2half_rn(xr);
-                        hi[l] = __float2half_rn(xi);
-                    }
-                }
-                __half* o = spec + obase[c] + 2 * i * TB + off;
-                if constexpr (L == 8) {
-                    uint32_t u[8];
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        u[m] = pack_half2(hr[2 * m], hr[2 * m + 1]);
-                        u[4 + m] = pack_half2(hi[2 * m], hi[2 * m + 1]);
-                    }
-                    st_global_v8(o, u);
-                } else {                                   // half rows (F = 4 frames per CTA)
-                    static_assert(L == 4, "fp16 runs of 4 or 8 frames");
-                    *reinterpret_cast<uint2*>(o) = make_uint2(pack_half2(hr[0], hr[1]), pack_half2(hr[2], hr[3]));
-                    *reinterpret_cast<uint2*>(o + TB) = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
-                }
-            }
+            emit(2 * q, yk);
+            emit(2 * q + 1, ym);
         }
     }
 

@@ -17,6 +17,7 @@ enum OutMode : int { OUT_FP32 = 0, OUT_I8 = 1, OUT_F16 = 2 };
 // row r at physical row swz_row(r): the 16-byte rows of each 128-byte line are
 // XOR-permuted by the line index, so that the CUDA-core X-engine's threads,
 // which read the same row of different 8-row groups at once, hit distinct banks.
+// Padding rows only meet padding inputs, whose products are never kept.
 // (The fp16 layout stays unswizzled: it is the tensor cores' operand image.)
 constexpr int kTbFp32 = 4;
 constexpr int kTbHalf = 8;

@@ -36,6 +36,8 @@ struct corr {
     float* d_beams_raw = nullptr;
     float* d_beams = nullptr;
     float2* d_vis = nullptr;
+    float2* d_vis_part = nullptr;   // kVisSplit partial visibility sets of the CUDA-core X-engine
+    static constexpr int kVisSplit = 4;
     int2* d_vis_int = nullptr;
     unsigned* d_err = nullptr;
     // bookkeeping

@@ -15,6 +15,8 @@ struct XParams {
     int2* vis_int;         // [n_chan][n_bl][n_pol^2] exact integer sums (I8) or nullptr
     unsigned* err;
     int exact;             // tensor-core engine: 1 = int8-valued operands, integer flush
+    float2* vis_part;      // CUDA-core engine: room for max_split partial visibility sets, or nullptr
+    int max_split;
 };
 
 // Plain FP32 X-engine on CUDA cores: register-tiled upper-triangular complex MAC.

@@ -1,9 +1,11 @@
 // xengine_fp32.cu -- the plain FP32 X-engine on CUDA cores (Sec. 2.1 MAC).
 //
-// A persistent CTA takes one channel at a time.  Its threads tile the upper
-// triangle of the n_in x n_in complex visibility matrix into 4x4 input blocks
-// (I <= J); each thread keeps its 16 complex sums in registers and walks over
-// the frames.  Frames stream into shared memory as K-blocks of 4 frames x
+// A persistent CTA takes one work unit at a time: a channel, or one of P equal
+// frame ranges of a channel (P = 2 or 4 when that spreads the units evenly over
+// the resident CTAs; a second kernel then adds the P partial visibility sets in
+// a fixed order).  Its threads tile the upper triangle of the n_in x n_in complex
+// visibility matrix into 4x4 input blocks (I <= J); each thread keeps its 16
+// complex sums in registers and walks over the frames.  Frames stream into shared memory as K-blocks of 4 frames x
 // 2 n_in rows (the layout the F-engine writes), by TMA-engine bulk copies,
 // double-buffered.  Sums are kept per 256-frame chunk and added into a second
 // set of FP32 registers, which bounds the rounding error of long integrations.
@@ -29,7 +31,7 @@ __device__ __forceinline__ void decode_tri(int idx, int nb, int& I, int& J) {
 }
 
 template <int MAXT>
-__global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p) {
+__global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p, int n_split) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[kStages];
     __shared__ __align__(8) uint64_t empty[kStages];
@@ -43,8 +45,10 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p) {
     int I = 0, J = 0;
     if (active) decode_tri(tid, nb, I, J);
     const int ntb = p.n_int / kTbFp32;
-    const int n_stage_ch = (ntb + kKbPerStage - 1) / kKbPerStage;  // stages per channel
-    const int n_ch_mine = (p.n_chan - static_cast<int>(blockIdx.x) + gridDim.x - 1) / gridDim.x;
+    const int nkb_u = ntb / n_split;                                 // K-blocks per work unit
+    const int n_stage_ch = (nkb_u + kKbPerStage - 1) / kKbPerStage;  // stages per unit
+    const int n_units = p.n_chan * n_split;
+    const int n_ch_mine = (n_units - static_cast<int>(blockIdx.x) + gridDim.x - 1) / gridDim.x;
     const int total = n_ch_mine * n_stage_ch;
     const float* spec = static_cast<const float*>(p.spec);
 
@@ -59,11 +63,12 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p) {
     __syncthreads();
     auto issue = [&](int w) {
         const int slot = w % kStages;
-        const int k = blockIdx.x + (w / n_stage_ch) * gridDim.x;
-        const int kb0 = (w % n_stage_ch) * kKbPerStage;
-        const int nkb = min(kKbPerStage, ntb - kb0);
+        const int u = blockIdx.x + (w / n_stage_ch) * gridDim.x;     // unit: channel u / n_split
+        const int kb0 = (w % n_stage_ch) * kKbPerStage;              // within the unit's frames
+        const int nkb = min(kKbPerStage, nkb_u - kb0);
         const uint32_t bytes = static_cast<uint32_t>(nkb) * R * 16;
-        const float* src = spec + (static_cast<int64_t>(k) * ntb + kb0) * R * kTbFp32;
+        const float* src =
+            spec + (static_cast<int64_t>(u / n_split) * ntb + (u % n_split) * nkb_u + kb0) * R * kTbFp32;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&full[slot], bytes);
         bulk_g2s(smem + slot * stage_bytes, src, bytes, &full[slot]);
@@ -96,7 +101,7 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p) {
         }
         if (!mbar_wait(&full[slot], (w / kStages) & 1, p.err, ERR_WAIT_STAGE)) ok = false;
         const int kb0 = (w % n_stage_ch) * kKbPerStage;
-        const int nkb = min(kKbPerStage, ntb - kb0);
+        const int nkb = min(kKbPerStage, nkb_u - kb0);
         const float4* st = reinterpret_cast<const float4*>(smem + slot * stage_bytes);
         if (active && ok) {
             for (int kb = 0; kb < nkb; ++kb) {
@@ -148,8 +153,11 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p) {
         if (lane == 0) mbar_arrive(&empty[slot]);  // this warp is done with the stage
         const bool ch_done = (w % n_stage_ch) == n_stage_ch - 1;
         if (ch_done && active && ok) {
-            const int k = blockIdx.x + (w / n_stage_ch) * gridDim.x;
+            const int u = blockIdx.x + (w / n_stage_ch) * gridDim.x;
+            const int k = u / n_split;
             const int n_bl = p.n_ant * (p.n_ant + 1) / 2, npp = p.n_pol * p.n_pol;
+            float2* out = n_split == 1 ? p.vis
+                                       : p.vis_part + static_cast<int64_t>(u % n_split) * p.n_chan * n_bl * npp;
 #pragma unroll
             for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
@@ -165,7 +173,7 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p) {
                     const int a = i / p.n_pol, pp = i % p.n_pol, a2 = j / p.n_pol, qq = j % p.n_pol;
                     if (a > a2) continue;
                     const int bl = a * p.n_ant - a * (a - 1) / 2 + (a2 - a);
-                    p.vis[(static_cast<int64_t>(k) * n_bl + bl) * npp + pp * p.n_pol + qq] = v;
+                    out[(static_cast<int64_t>(k) * n_bl + bl) * npp + pp * p.n_pol + qq] = v;
                 }
             kb_in_chunk = 0;
         }
@@ -174,6 +182,21 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p) {
     if (tid == 0) {
         // stages issued but never consumed (only after a failed wait) must land before exit
         for (int q = w; q < issued; ++q) mbar_wait(&full[q % kStages], (q / kStages) & 1, nullptr, 0);
+    }
+}
+
+// vis = sum over s of part[s], s = 0 .. n_split - 1 in order
+__global__ void vis_split_sum_kernel(const float2* __restrict__ part, float2* __restrict__ vis, int64_t n,
+                                     int n_split) {
+    for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < n;
+         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        float2 v = part[q];
+        for (int s = 1; s < n_split; ++s) {
+            const float2 x = part[static_cast<int64_t>(s) * n + q];
+            v.x += x.x;
+            v.y += x.y;
+        }
+        vis[q] = v;
     }
 }
 
@@ -191,8 +214,32 @@ cudaError_t launch_xengine_fp32(const XParams& p, int n_sm, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         int per_sm = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-        const int grid = std::max(1, std::min(p.n_chan, n_sm * std::max(per_sm, 1)));
-        kern<<<grid, threads, smem, s>>>(p);
+        const int slots = n_sm * std::max(per_sm, 1);
+        // frame split: the fewest of 1, 2, 4 parts that keep the last round of units at least
+        // 90% full (each part a whole number of stages)
+        int n_split = 1;
+        if (p.vis_part) {
+            double best = 0.0;
+            for (int P = 1; P <= std::min(4, p.max_split); P *= 2) {
+                if (P > 1 && (p.n_int / kTbFp32) % (P * kKbPerStage)) break;
+                const long units = static_cast<long>(p.n_chan) * P;
+                const long rounds = (units + slots - 1) / slots;
+                const double eff = static_cast<double>(units) / (static_cast<double>(rounds) * slots);
+                if (eff > best + 1e-9) {
+                    best = eff;
+                    n_split = P;
+                }
+                if (eff >= 0.9) break;
+            }
+        }
+        const int grid = static_cast<int>(std::max(1L, std::min(static_cast<long>(p.n_chan) * n_split,
+                                                                 static_cast<long>(slots))));
+        kern<<<grid, threads, smem, s>>>(p, n_split);
+        e = cudaGetLastError();
+        if (e != cudaSuccess || n_split == 1) return e;
+        const int64_t n = static_cast<int64_t>(p.n_chan) * (p.n_ant * (p.n_ant + 1) / 2) * p.n_pol * p.n_pol;
+        const int sgrid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 4 * n_sm));
+        vis_split_sum_kernel<<<sgrid, 256, 0, s>>>(p.vis_part, p.vis, n, n_split);
         return cudaGetLastError();
     };
     return threads <= 256 ? go(xengine_fp32_kernel<256>) : go(xengine_fp32_kernel<544>);

@@ -111,6 +111,7 @@ C2_CHANS = [0, 1, 2, 31, 32, 100, 255, 256, 333, 511, 512, 513, 700, 777, 1000, 
     (5, 2, 256, 48),       # ragged tile with two polarisations, 3 F-engine tiles
     (16, 2, 4096, 32),     # largest FFT
     (1, 2, 1024, 16),      # single antenna
+    (8, 2, 1024, 256),     # 512 channels x 64 K-blocks: the CUDA-core X-engine splits frames in 4 parts
 ])
 def test_scaled_configs_fp32_parity(env, n_ant, n_pol, n_fft, n_int):
     torch, corr, orc = env
