@@ -155,16 +155,17 @@ __device__ __forceinline__ void group_sync(int g) {
     }
 }
 
-// Split / epilogue geometry: after the FFT every thread takes L consecutive frames of NP
-// channel pairs (k, M - k), L = the K-block run length (frames per 16-byte row), so that it
-// holds whole (channel, input) pieces of the K-block layout and writes each as one 32-byte
-// sector straight from registers -- no transposition buffer.  The TPG = L * T threads of a
-// frame group are exactly the FFT groups of its L frames.
+// Split / epilogue geometry: after the FFT every thread takes L consecutive frames (8, or all
+// F when fewer) of NP channel pairs (k, M - k), a whole number of K-block runs (TB frames per
+// 16-byte row), so that it holds whole (channel, input) pieces of the K-block layout and
+// writes each run as one 32-byte sector straight from registers -- no transposition buffer.
+// The TPG = L * T threads of a frame group are exactly the FFT groups of its L frames.
 template <int M, int MODE>
 struct Epi {
     using P = Plan<M>;
     static constexpr int TB = (MODE == OUT_FP32) ? kTbFp32 : kTbHalf;
-    static constexpr int L = (P::F < TB) ? P::F : TB;    // frames per thread
+    static constexpr int L = (P::F < 8) ? P::F : 8;      // frames per thread
+    static_assert(L % TB == 0 || L < TB, "whole K-block runs, or part of one when F < TB");
     static constexpr int NP = kE / (2 * L);                // channel pairs per thread
     static constexpr int TPG = L * P::T;                   // threads per frame group
     static_assert(2 * NP * L == kE && NP * TPG == M / 2, "split covers every channel of every frame once");
@@ -386,13 +387,16 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
             const int64_t blk = (static_cast<int64_t>(chs[c]) * ntb + kb_run) * blk_elems;
             if constexpr (MODE == OUT_FP32) {
                 const bool flip = r0 & 1;
-                uint32_t u[8];
 #pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    u[l] = __float_as_uint(flip ? yc[l].y : yc[l].x);
-                    u[4 + l] = __float_as_uint(flip ? yc[l].x : yc[l].y);
+                for (int h = 0; h < L / TB; ++h) {             // consecutive K-blocks are adjacent
+                    uint32_t u[8];
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        u[l] = __float_as_uint(flip ? yc[4 * h + l].y : yc[4 * h + l].x);
+                        u[4 + l] = __float_as_uint(flip ? yc[4 * h + l].x : yc[4 * h + l].y);
+                    }
+                    st_global_v8(static_cast<float*>(p.spec) + blk + h * blk_elems + (r0 & ~1) * TB, u);
                 }
-                st_global_v8(static_cast<float*>(p.spec) + blk + (r0 & ~1) * TB, u);
             } else {
                 __half hr[L], hi[L];
 #pragma unroll
