@@ -160,7 +160,7 @@ int corr_info(corr_t* h, int64_t* out6);
  * integration also produces P [n_in][n_int/dump][n_fft/2] float32,
  * P[i][d][k] = sum over the dump's frames of |Y_i[t][k]|^2 (the paper studies
  * RFI on such 1 ms total-intensity samples, Sec. 5).  dump: 0 (off) or a
- * multiple of 4 dividing n_int.  corr_read_power copies the last integration's
+ * multiple of 8 (of 4 when n_fft = 4096) dividing n_int.  corr_read_power copies the last integration's
  * dumps to host memory `out` (may be NULL) and/or returns their device address. */
 int corr_set_power_dump(corr_t* h, int dump);
 int corr_read_power(corr_t* h, float* out, void** device_ptr);

@@ -580,18 +580,19 @@ int corr_read_spectra(corr_t* h, int k0, int nk, float* out) {
     if (int rc = settle(h, 1)) return rc;
     if (h->last_mode != CORR_FP32) return fail(CORR_E_STATE, "last integration was not CORR_FP32");
     if (!out || k0 < 0 || nk < 0 || k0 + nk > h->n_chan) return fail(CORR_E_INVAL, "channel range");
-    const int R = 2 * h->n_in, Rp = rows_fp32(h->n_in), ntb = h->n_int / kTbFp32;
-    const size_t per_ch = static_cast<size_t>(ntb) * Rp * kTbFp32;
+    const int tb = tb_fp32(h->n_chan);
+    const int R = 2 * h->n_in, Rp = rows_fp32(h->n_in), ntb = h->n_int / tb;
+    const size_t per_ch = static_cast<size_t>(ntb) * Rp * tb;
     std::vector<float> buf(per_ch * nk);
     CU(cudaMemcpy(buf.data(), static_cast<const float*>(h->d_spec) + per_ch * k0, buf.size() * sizeof(float),
                   cudaMemcpyDeviceToHost));
     for (int c = 0; c < nk; ++c)
         for (int kb = 0; kb < ntb; ++kb)
             for (int r = 0; r < R; ++r)
-                for (int e = 0; e < kTbFp32; ++e) {
-                    const int i = r / 2, cc = r % 2, t = kb * kTbFp32 + e;
+                for (int e = 0; e < tb; ++e) {
+                    const int i = r / 2, cc = r % 2, t = kb * tb + e;
                     out[((static_cast<size_t>(i) * h->n_int + t) * nk + c) * 2 + cc] =
-                        buf[((static_cast<size_t>(c) * ntb + kb) * Rp + swz_row(r)) * kTbFp32 + e];
+                        buf[(static_cast<size_t>(c) * ntb + kb) * Rp * tb + fp32_off(r, e, tb)];
                 }
     return CORR_OK;
 }
@@ -606,8 +607,8 @@ int corr_device_outputs(corr_t* h, void** vis, void** beams, void** stream) {
 
 int corr_set_power_dump(corr_t* h, int dump) {
     if (int rc = check_handle(h)) return rc;
-    if (dump < 0 || (dump > 0 && (dump % kTbFp32 || h->n_int % dump)))
-        return fail(CORR_E_INVAL, "dump must be 0 or a multiple of 4 dividing n_int");
+    if (dump < 0 || (dump > 0 && (dump % tb_fp32(h->n_chan) || h->n_int % dump)))
+        return fail(CORR_E_INVAL, "dump must be 0 or a multiple of %d dividing n_int", tb_fp32(h->n_chan));
     CU(cudaStreamSynchronize(h->stream));
     if (h->d_power) cudaFree(h->d_power);
     h->d_power = nullptr;

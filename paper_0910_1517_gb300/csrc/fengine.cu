@@ -163,7 +163,7 @@ __device__ __forceinline__ void group_sync(int g) {
 template <int M, int MODE>
 struct Epi {
     using P = Plan<M>;
-    static constexpr int TB = (MODE == OUT_FP32) ? kTbFp32 : kTbHalf;
+    static constexpr int TB = (MODE == OUT_FP32) ? tb_fp32(M) : kTbHalf;
     static constexpr int L = (P::F < 8) ? P::F : 8;      // frames per thread
     static_assert(L % TB == 0 || L < TB, "whole K-block runs, or part of one when F < TB");
     static constexpr int NP = kE / (2 * L);                // channel pairs per thread
@@ -368,7 +368,11 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
         const float2* wa = pfa + M;
         const float2* fra = pfa + 2 * M;   // fringe phasors of the CTA's frames
         if (!live) continue;
-        const int r0 = swz_row(2 * i);      // FP32 rows 2i, 2i+1: one aligned pair, real row first unless r0 is odd
+        // FP32 piece of input i in a K-block: granules m*PG .. m*PG + PG - 1 of row group G (PG = TB/2:
+        // the re row's TB/4 granules, then the im row's), XOR-placed by s = G & 7
+        constexpr int PG = TB / 2;
+        const int G = (2 * i) >> 3, s = G & 7;
+        const int pstart = G * 8 * TB + ((((i & 3) ^ (s / PG)) * PG) << 2);   // floats from the block start
         // beams and the K-block store of channel c from its L frames
         auto emit = [&](int c, const float2 (&yc)[L]) {
             const float2 w = wa[chs[c]];
@@ -386,16 +390,55 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
             // one 32-byte sector per (channel, input): rows 2i and 2i+1 over the L frames
             const int64_t blk = (static_cast<int64_t>(chs[c]) * ntb + kb_run) * blk_elems;
             if constexpr (MODE == OUT_FP32) {
-                const bool flip = r0 & 1;
-#pragma unroll
-                for (int h = 0; h < L / TB; ++h) {             // consecutive K-blocks are adjacent
+                float* spec = static_cast<float*>(p.spec);
+                if constexpr (TB == 4) {
+                    // 32-byte piece: granule slot j' = c ^ (s & 1) holds component c (0 re, 1 im)
+                    const bool flip = s & 1;
                     uint32_t u[8];
 #pragma unroll
                     for (int l = 0; l < 4; ++l) {
-                        u[l] = __float_as_uint(flip ? yc[4 * h + l].y : yc[4 * h + l].x);
-                        u[4 + l] = __float_as_uint(flip ? yc[4 * h + l].x : yc[4 * h + l].y);
+                        u[l] = __float_as_uint(flip ? yc[l].y : yc[l].x);
+                        u[4 + l] = __float_as_uint(flip ? yc[l].x : yc[l].y);
                     }
-                    st_global_v8(static_cast<float*>(p.spec) + blk + h * blk_elems + (r0 & ~1) * TB, u);
+                    st_global_v8(spec + blk + pstart, u);
+                } else {
+                    // 64-byte piece: slot j' = (2 c + h) ^ (s & 3), h = frames 0-3 / 4-7.  Each lane pair
+                    // writes one piece per instruction (a full 64-byte request): the even lane slots 0-1
+                    // (component cA), the odd lane slots 2-3 (component 1 - cA); first the even lane's
+                    // channel, then the odd lane's, trading the component each needs by a shuffle.
+                    static_assert(TB == 8 && L == 8, "FP32 runs of 8 frames");
+                    const bool odd = kk & 1;
+                    const int cA = (s >> 1) & 1;
+                    const bool hswap = s & 1;
+                    const int chp = __shfl_xor_sync(0xffffffffu, chs[c], 1);
+                    const int csend = odd ? cA : 1 - cA;
+                    float mine[8], recv[8];
+#pragma unroll
+                    for (int l = 0; l < 8; ++l) {
+                        const float own_keep = (odd ? 1 - cA : cA) ? yc[l].y : yc[l].x;
+                        const float own_send = csend ? yc[l].y : yc[l].x;
+                        mine[l] = own_keep;
+                        recv[l] = __shfl_xor_sync(0xffffffffu, own_send, 1);
+                    }
+                    auto put = [&](int ch, const float (&v)[8]) {
+                        uint32_t u[8];
+#pragma unroll
+                        for (int l = 0; l < 4; ++l) {   // static indices: v stays in registers
+                            u[l] = __float_as_uint(hswap ? v[4 + l] : v[l]);
+                            u[4 + l] = __float_as_uint(hswap ? v[l] : v[4 + l]);
+                        }
+                        st_global_v8(spec + (static_cast<int64_t>(ch) * ntb + kb_run) * blk_elems + pstart + (odd ? 8 : 0), u);
+                    };
+                    // piece of the even lane's channel, then of the odd lane's: both lanes of a pair
+                    // issue the same two stores (selects, no divergence)
+                    float d0[8], d1[8];
+#pragma unroll
+                    for (int l = 0; l < 8; ++l) {
+                        d0[l] = odd ? recv[l] : mine[l];
+                        d1[l] = odd ? mine[l] : recv[l];
+                    }
+                    put(odd ? chp : chs[c], d0);
+                    put(odd ? chs[c] : chp, d1);
                 }
             } else {
                 __half hr[L], hi[L];
@@ -573,16 +616,19 @@ __global__ void power_dump_kernel(const float* __restrict__ spec, int n_in, int 
                                   float* __restrict__ P) {
     const int d = blockIdx.x, k = blockIdx.y * 32 + threadIdx.x;
     if (k >= n_chan) return;
-    const int Rp = rows_fp32(n_in), ntb = n_int / kTbFp32, n_dump = n_int / dump;
-    const int kb0 = d * dump / kTbFp32, nkb = dump / kTbFp32;
+    const int tb = tb_fp32(n_chan);
+    const int Rp = rows_fp32(n_in), ntb = n_int / tb, n_dump = n_int / dump;
+    const int kb0 = d * dump / tb, nkb = dump / tb;
     for (int i = threadIdx.y; i < n_in; i += blockDim.y) {
         float acc = 0.0f;
         for (int kb = kb0; kb < kb0 + nkb; ++kb) {
-            const float* blk = spec + (static_cast<int64_t>(k) * ntb + kb) * Rp * kTbFp32;
-            const float4 re = *reinterpret_cast<const float4*>(blk + swz_row(2 * i) * kTbFp32);
-            const float4 im = *reinterpret_cast<const float4*>(blk + swz_row(2 * i + 1) * kTbFp32);
-            acc += re.x * re.x + re.y * re.y + re.z * re.z + re.w * re.w;
-            acc += im.x * im.x + im.y * im.y + im.z * im.z + im.w * im.w;
+            const float* blk = spec + (static_cast<int64_t>(k) * ntb + kb) * Rp * tb;
+            for (int e = 0; e < tb; e += 4) {            // one 4-frame granule of each row at a time
+                const float4 re = *reinterpret_cast<const float4*>(blk + fp32_off(2 * i, e, tb));
+                const float4 im = *reinterpret_cast<const float4*>(blk + fp32_off(2 * i + 1, e, tb));
+                acc += re.x * re.x + re.y * re.y + re.z * re.z + re.w * re.w;
+                acc += im.x * im.x + im.y * im.y + im.z * im.z + im.w * im.w;
+            }
         }
         P[(static_cast<int64_t>(i) * n_dump + d) * n_chan + k] = acc;
     }
@@ -679,7 +725,8 @@ cudaError_t launch_phasor_setup(int n_ant, int n_chan, int n_fft, int n_int, int
 
 cudaError_t launch_power_dumps(const float* spec, int n_in, int n_chan, int n_int, int dump, float* P,
                                cudaStream_t s) {
-    if (dump < kTbFp32 || dump % kTbFp32 || n_int % dump) return cudaErrorInvalidValue;
+    const int tb = tb_fp32(n_chan);
+    if (dump < tb || dump % tb || n_int % dump) return cudaErrorInvalidValue;
     const dim3 grid(n_int / dump, (n_chan + 31) / 32), block(32, 8);
     power_dump_kernel<<<grid, block, 0, s>>>(spec, n_in, n_chan, n_int, dump, P);
     return cudaGetLastError();

@@ -11,19 +11,27 @@ enum OutMode : int { OUT_FP32 = 0, OUT_I8 = 1, OUT_F16 = 2 };
 
 // Spectra hand-off layout ("K-block layout"), shared by every X-engine:
 //   S[k][kb][r][TB]   k channel, kb = t / TB, r = 2*i + c (c = 0 re, 1 im), TB = t % TB
-// with TB = 4 (fp32) or 8 (fp16).  One (k, kb) block is R = 2*n_in rows of 16 bytes,
-// i.e. exactly the no-swizzle K-major canonical layout of a tcgen05 operand tile.
-// The FP32 layout pads the rows of a block to Rp = round_up(2 n_in, 8) and stores
-// row r at physical row swz_row(r): the 16-byte rows of each 128-byte line are
-// XOR-permuted by the line index, so that the CUDA-core X-engine's threads,
-// which read the same row of different 8-row groups at once, hit distinct banks.
-// Padding rows only meet padding inputs, whose products are never kept.
-// (The fp16 layout stays unswizzled: it is the tensor cores' operand image.)
-constexpr int kTbFp32 = 4;
+// One (k, kb) block holds every input's rows for TB consecutive frames.
+// fp16 (tensor-core X-engine): TB = 8, R = 2 n_in unswizzled rows of 16 bytes -- exactly
+// the no-swizzle K-major canonical layout of a tcgen05 operand tile.
+// FP32 (CUDA-core X-engine): TB = tb_fp32(n_chan) = 8 frames (4 when an F-engine CTA covers
+// only 4 frames, n_chan = 2048), rows padded to Rp = round_up(2 n_in, 8).  The block is cut
+// into 16-byte granules of 4 frames of one row, 8 rows (one input group of 4) per row group
+// G, and granule g = (r % 8) * TB/4 + (frame % TB) / 4 of group G sits at position
+// g ^ (G & 7): the CUDA-core X-engine's threads, which read the same granule of different
+// row groups at once, then hit distinct banks, while the re and im rows of one input over
+// the TB frames stay one contiguous, aligned 8 * TB-byte piece (the F-engine writes each
+// piece in one store instruction).  Padding rows only meet padding inputs, whose products
+// are never kept.
 constexpr int kTbHalf = 8;
 
-__host__ __device__ __forceinline__ int rows_fp32(int n_in) { return ((2 * n_in + 7) / 8) * 8; }
-__host__ __device__ __forceinline__ int swz_row(int r) { return (r & ~7) | ((r & 7) ^ ((r >> 3) & 7)); }
+__host__ __device__ constexpr int tb_fp32(int n_chan) { return n_chan >= 2048 ? 4 : 8; }
+__host__ __device__ constexpr int rows_fp32(int n_in) { return ((2 * n_in + 7) / 8) * 8; }
+// float offset of row r, frame e (0 <= e < tb) inside one FP32 K-block
+__host__ __device__ constexpr int fp32_off(int r, int e, int tb) {
+    const int G = r >> 3, g = (r & 7) * (tb >> 2) + (e >> 2);
+    return G * 8 * tb + ((g ^ (G & 7)) << 2) + (e & 3);
+}
 
 struct FeParams {
     const int8_t* x;       // input rows, row i at x + i*ld
@@ -67,7 +75,7 @@ cudaError_t launch_phasor_setup(int n_ant, int n_chan, int n_fft, int n_int, int
                                 cudaStream_t s, const int64_t* g0_dev = nullptr);
 
 // Auto-power dumps from the FP32 K-block spectra: P[i][d][k] = sum of |Y_i[t][k]|^2 over the
-// `dump` frames of dump d (dump a multiple of 4 dividing n_int).
+// `dump` frames of dump d (dump a multiple of tb_fp32(n_chan) dividing n_int).
 cudaError_t launch_power_dumps(const float* spec, int n_in, int n_chan, int n_int, int dump, float* P,
                                cudaStream_t s);
 

@@ -5,10 +5,11 @@
 // the resident CTAs; a second kernel then adds the P partial visibility sets in
 // a fixed order).  Its threads tile the upper triangle of the n_in x n_in complex
 // visibility matrix into 4x4 input blocks (I <= J); each thread keeps its 16
-// complex sums in registers and walks over the frames.  Frames stream into shared memory as K-blocks of 4 frames x
-// 2 n_in rows (the layout the F-engine writes), by TMA-engine bulk copies,
-// double-buffered.  Sums are kept per 256-frame chunk and added into a second
-// set of FP32 registers, which bounds the rounding error of long integrations.
+// complex sums in registers and walks over the frames.  Frames stream into shared
+// memory as the F-engine's FP32 K-blocks (TB frames x Rp rows in 16-byte granules)
+// by TMA-engine bulk copies into a ring of stages.  Sums are kept per 256-frame
+// chunk and added into running sums in shared memory, which bounds the rounding
+// error of long integrations.
 #include "common.cuh"
 #include "fengine.cuh"
 #include "xengine.cuh"
@@ -16,9 +17,9 @@
 namespace gbx {
 namespace {
 
-constexpr int kKbPerStage = 8;              // 32 frames per stage
+constexpr int kStageFrames = 32;            // frames per stage
 constexpr int kStages = 3;
-constexpr int kChunkKb = 64;                // 256 frames per FP32 partial sum
+constexpr int kChunkSlices = 64;            // 256 frames (64 slices of 4) per FP32 partial sum
 
 __device__ __forceinline__ void decode_tri(int idx, int nb, int& I, int& J) {
     I = 0;
@@ -30,13 +31,16 @@ __device__ __forceinline__ void decode_tri(int idx, int nb, int& I, int& J) {
     J = I + rem;
 }
 
-template <int MAXT>
+// TB: frames per K-block of the FP32 layout (4 or 8); a K-block is TB/4 slices of 4 frames,
+// each slice one 16-byte granule per row
+template <int MAXT, int TB>
 __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p, int n_split) {
+    constexpr int TQ = TB / 4, KBS = kStageFrames / TB;   // slices per K-block, K-blocks per stage
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[kStages];
     __shared__ __align__(8) uint64_t empty[kStages];
     const int R = rows_fp32(p.n_in);             // rows per K-block, a multiple of 8
-    const int stage_bytes = kKbPerStage * R * 16;
+    const int stage_bytes = kStageFrames * R * 4;
     float* part = reinterpret_cast<float*>(smem + kStages * stage_bytes);   // [32][blockDim] chunk sums
     const int nb = (p.n_in + 3) / 4;
     const int n_work = nb * (nb + 1) / 2;
@@ -44,9 +48,9 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p, int
     const bool active = tid < n_work;
     int I = 0, J = 0;
     if (active) decode_tri(tid, nb, I, J);
-    const int ntb = p.n_int / kTbFp32;
+    const int ntb = p.n_int / TB;
     const int nkb_u = ntb / n_split;                                 // K-blocks per work unit
-    const int n_stage_ch = (nkb_u + kKbPerStage - 1) / kKbPerStage;  // stages per unit
+    const int n_stage_ch = (nkb_u + KBS - 1) / KBS;                  // stages per unit
     const int n_units = p.n_chan * n_split;
     const int n_ch_mine = (n_units - static_cast<int>(blockIdx.x) + gridDim.x - 1) / gridDim.x;
     const int total = n_ch_mine * n_stage_ch;
@@ -64,11 +68,11 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p, int
     auto issue = [&](int w) {
         const int slot = w % kStages;
         const int u = blockIdx.x + (w / n_stage_ch) * gridDim.x;     // unit: channel u / n_split
-        const int kb0 = (w % n_stage_ch) * kKbPerStage;              // within the unit's frames
-        const int nkb = min(kKbPerStage, nkb_u - kb0);
-        const uint32_t bytes = static_cast<uint32_t>(nkb) * R * 16;
+        const int kb0 = (w % n_stage_ch) * KBS;                      // within the unit's frames
+        const int nkb = min(KBS, nkb_u - kb0);
+        const uint32_t bytes = static_cast<uint32_t>(nkb) * R * TB * 4;
         const float* src =
-            spec + (static_cast<int64_t>(u / n_split) * ntb + (u % n_split) * nkb_u + kb0) * R * kTbFp32;
+            spec + (static_cast<int64_t>(u / n_split) * ntb + (u % n_split) * nkb_u + kb0) * R * TB;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&full[slot], bytes);
         bulk_g2s(smem + slot * stage_bytes, src, bytes, &full[slot]);
@@ -100,27 +104,28 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p, int
             }
         }
         if (!mbar_wait(&full[slot], (w / kStages) & 1, p.err, ERR_WAIT_STAGE)) ok = false;
-        const int kb0 = (w % n_stage_ch) * kKbPerStage;
-        const int nkb = min(kKbPerStage, nkb_u - kb0);
+        const int kb0 = (w % n_stage_ch) * KBS;
+        const int nkb = min(KBS, nkb_u - kb0);
         const float4* st = reinterpret_cast<const float4*>(smem + slot * stage_bytes);
         if (active && ok) {
-            for (int kb = 0; kb < nkb; ++kb) {
-                // rows 8I..8I+7 and 8J..8J+7 are one 128-byte line each; row q of line L sits
-                // at position q ^ (L & 7), so a warp's loads of one q spread over the banks
-                const float4* blk = st + kb * R;
-                const float4* li = blk + 8 * I;
-                const float4* lj = blk + 8 * J;
+            for (int sl = 0; sl < nkb * TQ; ++sl) {
+                // rows 8I..8I+7 (and 8J..8J+7) are row group I (J): 8 TQ granules, granule g of group
+                // G at position g ^ (G & 7), so a warp's loads of one granule spread over the banks
+                const int h = sl % TQ;
+                const float4* blk = st + (sl / TQ) * R * TQ;
+                const float4* li = blk + 8 * TQ * I;
+                const float4* lj = blk + 8 * TQ * J;
                 const int si = I & 7, sj = J & 7;
                 float4 ar[4], ai[4];
 #pragma unroll
                 for (int ii = 0; ii < 4; ++ii) {
-                    ar[ii] = li[(2 * ii) ^ si];
-                    ai[ii] = li[(2 * ii + 1) ^ si];
+                    ar[ii] = li[(2 * ii * TQ + h) ^ si];
+                    ai[ii] = li[((2 * ii + 1) * TQ + h) ^ si];
                 }
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) {
-                    const float4 br = lj[(2 * jj) ^ sj];
-                    const float4 bi = lj[(2 * jj + 1) ^ sj];
+                    const float4 br = lj[(2 * jj * TQ + h) ^ sj];
+                    const float4 bi = lj[((2 * jj + 1) * TQ + h) ^ sj];
 #pragma unroll
                     for (int ii = 0; ii < 4; ++ii) {
                         float2 c = acc[ii][jj];
@@ -136,7 +141,7 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p, int
                         acc[ii][jj] = c;
                     }
                 }
-                if (++kb_in_chunk == kChunkKb) {   // fold this chunk's FP32 sums into the running ones
+                if (++kb_in_chunk == kChunkSlices) {   // fold this chunk's FP32 sums into the running ones
                     kb_in_chunk = 0;
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
@@ -207,7 +212,8 @@ cudaError_t launch_xengine_fp32(const XParams& p, int n_sm, cudaStream_t s) {
     const int n_work = nb * (nb + 1) / 2;
     const int threads = ((n_work + 31) / 32) * 32;
     if (threads > 544) return cudaErrorInvalidValue;
-    const size_t smem = kStages * (static_cast<size_t>(kKbPerStage) * rows_fp32(p.n_in) * 16) +
+    const int tb = tb_fp32(p.n_chan);
+    const size_t smem = kStages * (static_cast<size_t>(kStageFrames) * rows_fp32(p.n_in) * 4) +
                         32 * sizeof(float) * threads;
     auto go = [&](auto kern) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -221,7 +227,7 @@ cudaError_t launch_xengine_fp32(const XParams& p, int n_sm, cudaStream_t s) {
         if (p.vis_part) {
             double best = 0.0;
             for (int P = 1; P <= std::min(4, p.max_split); P *= 2) {
-                if (P > 1 && (p.n_int / kTbFp32) % (P * kKbPerStage)) break;
+                if (P > 1 && (p.n_int / tb) % (P * (kStageFrames / tb))) break;
                 const long units = static_cast<long>(p.n_chan) * P;
                 const long rounds = (units + slots - 1) / slots;
                 const double eff = static_cast<double>(units) / (static_cast<double>(rounds) * slots);
@@ -242,7 +248,8 @@ cudaError_t launch_xengine_fp32(const XParams& p, int n_sm, cudaStream_t s) {
         vis_split_sum_kernel<<<sgrid, 256, 0, s>>>(p.vis_part, p.vis, n, n_split);
         return cudaGetLastError();
     };
-    return threads <= 256 ? go(xengine_fp32_kernel<256>) : go(xengine_fp32_kernel<544>);
+    if (tb == 8) return threads <= 256 ? go(xengine_fp32_kernel<256, 8>) : go(xengine_fp32_kernel<544, 8>);
+    return threads <= 256 ? go(xengine_fp32_kernel<256, 4>) : go(xengine_fp32_kernel<544, 4>);
 }
 
 }  // namespace gbx
