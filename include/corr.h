@@ -110,8 +110,29 @@ int corr_set_scales(corr_t* h, const float* scale);
  * continue the previous push, else the partial integration is dropped, the
  * stream restarts at seq and CORR_E_DATALOSS is returned.  Whenever
  * n_int * n_fft + max_delay samples are buffered an integration is launched
- * asynchronously on the handle's stream.  x is copied before return. */
+ * asynchronously on the handle's stream.  x is copied before return (on the
+ * handle's copy stream, into one of two sample rings), so the copy of the next
+ * integration's samples overlaps the correlation of this one; results come from
+ * corr_read_* (last launched integration) or from an output ring. */
 int corr_push_samples(corr_t* h, const int8_t* x, int64_t n, int64_t seq);
+
+/* Ring of host output slots for the streaming ingest: after each integration a
+ * push launches, its visibilities (and, if beams != NULL, its beams) are copied
+ * into slot j % n_slots, j = 0, 1, ... counting those integrations, in stream
+ * order -- the results of integration j no longer block the push of j + 1.
+ * vis: n_slots x [n_fft/2][n_bl][n_pol^2] complex64 (re, im float pairs);
+ * beams: n_slots x [2][n_int/beam_avg][n_fft/2] float32; host memory, pinned
+ * (cudaHostAlloc) for the copies to run asynchronously.  A slot is rewritten
+ * n_slots integrations later; the caller reads it before then.  vis = NULL
+ * removes the ring.  Waits for queued work first.  CORR_E_INVAL for n_slots
+ * outside [1, 4096]. */
+int corr_set_output_ring(corr_t* h, float* vis, float* beams, int n_slots);
+
+/* Block until the results of streaming integration `index` are in their slot;
+ * *slot (may be NULL) receives the slot number.  CORR_E_AGAIN: not launched
+ * yet (push more samples); CORR_E_STATE: no ring, or the slot was reused since;
+ * CORR_E_TIMEOUT: a kernel's bounded wait ran out, results invalid. */
+int corr_wait_output(corr_t* h, int64_t index, int* slot);
 
 /* As corr_push_samples with x in device memory (row stride n); the copies are
  * ordered after work already on `stream` (a cudaStream_t; NULL and

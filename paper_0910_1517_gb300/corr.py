@@ -33,6 +33,8 @@ SIGNATURES = {
     "corr_set_scales": ([_P, _P], _I),
     "corr_push_samples": ([_P, _P, _L, _L], _I),
     "corr_push_samples_device": ([_P, _P, _L, _L, _P], _I),
+    "corr_set_output_ring": ([_P, _P, _P, _I], _I),
+    "corr_wait_output": ([_P, _L, ctypes.POINTER(ctypes.c_int)], _I),
     "corr_integrate_device": ([_P, _P, _L, _L, _L, _P], _I),
     "corr_read_visibilities": ([_P, _P, _I], _I),
     "corr_read_beams": ([_P, _P, _I], _I),
@@ -169,6 +171,23 @@ def corr_push_samples(h, x, seq: int, allow_dataloss: bool = False):
 
 def corr_push_samples_device(h, x, seq: int, stream=None):
     return _ok(load().corr_push_samples_device(h, _ptr(x), x.shape[1], seq, _stream(stream)))
+
+
+def corr_set_output_ring(h, vis, beams=None, n_slots=None):
+    """vis: pinned float32 [n_slots][n_chan][n_bl][npp][2] (numpy/tensor) or None to remove the
+    ring; beams: pinned float32 [n_slots][2][n_int/beam_avg][n_chan] or None; n_slots defaults
+    to vis.shape[0]."""
+    if vis is None:
+        return _ok(load().corr_set_output_ring(h, None, None, 0))
+    n = vis.shape[0] if n_slots is None else n_slots
+    return _ok(load().corr_set_output_ring(h, _ptr(vis), _ptr(beams), n))
+
+
+def corr_wait_output(h, index: int) -> int:
+    """Block until streaming integration `index` is in its host slot; returns the slot."""
+    slot = ctypes.c_int(-1)
+    _ok(load().corr_wait_output(h, index, ctypes.byref(slot)))
+    return slot.value
 
 
 def corr_integrate_device(h, x, n_avail=None, g0: int = 0, stream=None, ld=None):

@@ -72,10 +72,15 @@ int mark(corr* h, int b, cudaStream_t s) {
 
 int alloc_ring(corr* h) {
     if (h->d_ring) cudaFree(h->d_ring);
-    h->d_ring = nullptr;
+    if (h->d_ring2) cudaFree(h->d_ring2);
+    h->d_ring = h->d_ring2 = nullptr;
+    h->cur_ring = 0;
     h->ring_ld = ((ring_need(h) + 64 + 255) / 256) * 256;
-    CU(dalloc(&h->d_ring, static_cast<size_t>(h->ring_ld) * h->n_in));
-    CU(cudaMemset(h->d_ring, 0, static_cast<size_t>(h->ring_ld) * h->n_in));
+    const size_t bytes = static_cast<size_t>(h->ring_ld) * h->n_in;
+    CU(dalloc(&h->d_ring, bytes));
+    CU(dalloc(&h->d_ring2, bytes));
+    CU(cudaMemset(h->d_ring, 0, bytes));
+    CU(cudaMemset(h->d_ring2, 0, bytes));
     return CORR_OK;
 }
 
@@ -112,10 +117,17 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
     if (h->xmode != CORR_FP32 && !h->scales_set)
         return fail(CORR_E_STATE, "CORR_I8 / CORR_F16 need requantisation scales (corr_set_scales)");
     const int nd = h->n_ant;
-    std::memcpy(h->h_model, h->tau.data(), nd * sizeof(double));
-    std::memcpy(h->h_model + nd, h->phi0.data(), nd * sizeof(double));
-    std::memcpy(h->h_model + 2 * nd, h->rate.data(), nd * sizeof(double));
-    CU(cudaMemcpyAsync(h->d_model, h->h_model, 3 * nd * sizeof(double), cudaMemcpyHostToDevice, s));
+    // stage the model in a pinned slot no queued copy still reads (integrations may be queued
+    // back to back while earlier ones run)
+    const int ms = h->model_slot;
+    h->model_slot = (ms + 1) % corr::kModelSlots;
+    double* hm = h->h_model + 3 * static_cast<size_t>(nd) * (1 + ms);
+    CU(cudaEventSynchronize(h->ev_model[ms]));
+    std::memcpy(hm, h->tau.data(), nd * sizeof(double));
+    std::memcpy(hm + nd, h->phi0.data(), nd * sizeof(double));
+    std::memcpy(hm + 2 * nd, h->rate.data(), nd * sizeof(double));
+    CU(cudaMemcpyAsync(h->d_model, hm, 3 * nd * sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(cudaEventRecord(h->ev_model[ms], s));
     if (int rc = mark(h, 0, s)) return rc;
     CU(launch_phasor_setup(h->n_ant, h->n_chan, h->n_fft, h->n_int, g0, h->d_model, h->d_model + nd,
                            h->d_model + 2 * nd, h->d_pf, h->d_ff, h->d_D, s));
@@ -238,7 +250,26 @@ int check_handle(corr* h) {
 
 // Append n samples per input (host or device rows of pitch spitch) to the ring,
 // launching integrations as it fills.  kind is the cudaMemcpyKind of the copy.
-int ingest(corr* h, const int8_t* x, int64_t spitch, int64_t n, int64_t seq, cudaMemcpyKind kind, bool sync_copy) {
+// Results of the integration just queued on h->stream into the host output ring, if set.
+int enqueue_output(corr* h, int64_t index) {
+    if (!h->out_vis) return CORR_OK;
+    const int slot = static_cast<int>(index % h->n_slots);
+    const size_t nv = static_cast<size_t>(h->n_chan) * h->n_bl * h->npp * 2;
+    const size_t nb = 2 * static_cast<size_t>(h->n_int / h->beam_avg) * h->n_chan;
+    h->slot_of[slot] = index;
+    CU(cudaMemcpyAsync(h->out_vis + nv * slot, h->d_vis, nv * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (h->out_beams)
+        CU(cudaMemcpyAsync(h->out_beams + nb * slot, h->d_beams, nb * sizeof(float), cudaMemcpyDeviceToHost,
+                           h->stream));
+    CU(cudaEventRecord(h->ev_out[slot], h->stream));
+    return CORR_OK;
+}
+
+// Streaming ingest of n samples per input from x (row pitch spitch).  Copies run on the copy
+// stream into the current ring; a full ring launches its integration on h->stream (after the
+// copies) and the next integration fills the other ring, once the integration before that is
+// done with it.  Returns when x has been read (host sources; device sources stay stream-ordered).
+int ingest(corr* h, const int8_t* x, int64_t spitch, int64_t n, int64_t seq, cudaMemcpyKind kind) {
     int rc = CORR_OK;
     if (!h->ring_started) {
         h->ring_started = true;
@@ -247,7 +278,7 @@ int ingest(corr* h, const int8_t* x, int64_t spitch, int64_t n, int64_t seq, cud
         h->g_next = 0;
         h->fill = 0;
     } else if (seq != h->seq_next) {
-        // gap or overlap: drop the partial integration, restart the ring at seq
+        // gap or overlap: drop the partial integration, restart the current ring at seq
         const int64_t gap = seq - h->seq_next;
         h->fill = 0;
         h->seq_next = seq;
@@ -256,30 +287,40 @@ int ingest(corr* h, const int8_t* x, int64_t spitch, int64_t n, int64_t seq, cud
         rc = CORR_E_DATALOSS;
     }
     const int64_t need = ring_need(h);
+    const int64_t body = static_cast<int64_t>(h->n_int) * h->n_fft;
     int64_t done = 0;
     while (done < n) {
+        int8_t* ring = h->cur_ring ? h->d_ring2 : h->d_ring;
         const int64_t take = std::min(n - done, need - h->fill);
-        CU(cudaMemcpy2DAsync(h->d_ring + h->fill, h->ring_ld, x + done, spitch, take, h->n_in, kind, h->stream));
+        CU(cudaMemcpy2DAsync(ring + h->fill, h->ring_ld, x + done, spitch, take, h->n_in, kind, h->cstream));
         h->fill += take;
         done += take;
         if (h->fill == need) {
             if (max_int_delay(h) > h->max_delay)
                 return fail(CORR_E_RANGE, "a delay exceeds max_delay = %d", h->max_delay);
-            int r = run_integration(h, h->d_ring, h->ring_ld, need, h->g_next, h->stream);
-            if (r != CORR_OK) return r;
-            // keep the last max_delay samples: they begin the next integration (overlap, Sec. 2.3.2)
-            const int64_t body = static_cast<int64_t>(h->n_int) * h->n_fft;
+            const int r = h->cur_ring, nx = r ^ 1;
+            CU(cudaEventRecord(h->ev_ready[r], h->cstream));
+            CU(cudaStreamWaitEvent(h->stream, h->ev_ready[r], 0));
+            if (int e = run_integration(h, ring, h->ring_ld, need, h->g_next, h->stream)) return e;
+            CU(cudaEventRecord(h->ev_free[r], h->stream));
+            if (int e = enqueue_output(h, h->n_streamed)) return e;
+            // the next integration fills the other ring, once the integration two back is done
+            // with it, beginning with this one's last max_delay samples (overlap, Sec. 2.3.2)
+            int8_t* next = nx ? h->d_ring2 : h->d_ring;
+            CU(cudaStreamWaitEvent(h->cstream, h->ev_free[nx], 0));
             if (h->max_delay > 0)
-                CU(cudaMemcpy2DAsync(h->d_ring, h->ring_ld, h->d_ring + body, h->ring_ld, h->max_delay, h->n_in,
-                                     cudaMemcpyDeviceToDevice, h->stream));
+                CU(cudaMemcpy2DAsync(next, h->ring_ld, ring + body, h->ring_ld, h->max_delay, h->n_in,
+                                     cudaMemcpyDeviceToDevice, h->cstream));
+            h->cur_ring = nx;
             h->fill = h->max_delay;
             h->g_next += h->n_int;
+            h->n_streamed += 1;
         }
     }
     h->seq_next += n;
-    if (sync_copy) {
-        CU(cudaEventRecord(h->ev_aux, h->stream));
-        CU(cudaEventSynchronize(h->ev_aux));
+    if (kind == cudaMemcpyHostToDevice) {   // the caller may reuse x
+        CU(cudaEventRecord(h->ev_copied, h->cstream));
+        CU(cudaEventSynchronize(h->ev_copied));
     }
     return rc;
 }
@@ -323,11 +364,18 @@ int corr_create(corr_t** out, int n_ant, int n_pol, int n_fft, int n_int) {
     CUB(cudaGetDevice(&h->dev));
     CUB(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->dev));
     CUB(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CUB(cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
     CUB(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
     CUB(cudaEventCreateWithFlags(&h->ev_aux, cudaEventDisableTiming));
+    CUB(cudaEventCreateWithFlags(&h->ev_copied, cudaEventDisableTiming));
+    for (int r = 0; r < 2; ++r) {
+        CUB(cudaEventCreateWithFlags(&h->ev_ready[r], cudaEventDisableTiming));
+        CUB(cudaEventCreateWithFlags(&h->ev_free[r], cudaEventDisableTiming));
+    }
     const size_t nch = h->n_chan, na = n_ant, ni = h->n_in;
     CUB(dalloc(&h->d_model, 3 * na));
-    CUB(cudaMallocHost(reinterpret_cast<void**>(&h->h_model), 3 * na * sizeof(double)));
+    CUB(cudaMallocHost(reinterpret_cast<void**>(&h->h_model), (1 + corr::kModelSlots) * 3 * na * sizeof(double)));
+    for (cudaEvent_t& e : h->ev_model) CUB(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     CUB(dalloc(&h->d_pf, na * nch));
     CUB(dalloc(&h->d_ff, na * static_cast<size_t>(n_int)));
     CUB(dalloc(&h->d_D, na));
@@ -379,7 +427,8 @@ int corr_destroy(corr_t* h) {
     if (h->d_power) cudaFree(h->d_power);
     if (h->d_xtab) cudaFree(h->d_xtab);
     if (h->d_items) cudaFree(h->d_items);
-    void* bufs[] = {h->d_ring, h->d_model, h->d_pf, h->d_ff, h->d_D, h->d_wcoh, h->d_ginc, h->d_scale,
+    if (h->cstream) cudaStreamSynchronize(h->cstream);
+    void* bufs[] = {h->d_ring, h->d_ring2, h->d_model, h->d_pf, h->d_ff, h->d_D, h->d_wcoh, h->d_ginc, h->d_scale,
                     h->d_tw, h->d_spec, h->d_beams_raw, h->d_vis, h->d_vis_part, h->d_vis_int, h->d_err};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -388,6 +437,15 @@ int corr_destroy(corr_t* h) {
     for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
     if (h->ev_done) cudaEventDestroy(h->ev_done);
     if (h->ev_aux) cudaEventDestroy(h->ev_aux);
+    if (h->ev_copied) cudaEventDestroy(h->ev_copied);
+    for (int r = 0; r < 2; ++r) {
+        if (h->ev_ready[r]) cudaEventDestroy(h->ev_ready[r]);
+        if (h->ev_free[r]) cudaEventDestroy(h->ev_free[r]);
+    }
+    for (cudaEvent_t e : h->ev_out) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->ev_model)
+        if (e) cudaEventDestroy(e);
+    if (h->cstream) cudaStreamDestroy(h->cstream);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return CORR_OK;
@@ -398,9 +456,12 @@ int corr_set_mode(corr_t* h, int xmode, int polmode, int beam_avg) {
     if (xmode != CORR_FP32 && xmode != CORR_I8 && xmode != CORR_F16) return fail(CORR_E_INVAL, "unknown xmode");
     if (polmode != 0) return fail(CORR_E_INVAL, "only polmode 0 (all products) is supported");
     if (beam_avg < 1 || h->n_int % beam_avg) return fail(CORR_E_INVAL, "beam_avg must divide n_int");
+    if (h->out_beams && beam_avg != h->beam_avg)
+        return fail(CORR_E_STATE, "beam_avg sizes the output ring's beam slots: remove the ring first");
     if (xmode != CORR_FP32 && !xengine_tc_supported(h->n_in))
         return fail(CORR_E_INVAL, "tensor-core modes need n_in <= 128");
     if (xmode == CORR_I8 && h->n_int > 66571) return fail(CORR_E_INVAL, "CORR_I8 needs n_int <= 66571");
+    CU(cudaStreamSynchronize(h->cstream));
     CU(cudaStreamSynchronize(h->stream));
     if (beam_avg != h->beam_avg) {
         if (h->d_beams != h->d_beams_raw) cudaFree(h->d_beams);
@@ -494,7 +555,43 @@ int corr_push_samples(corr_t* h, const int8_t* x, int64_t n, int64_t seq) {
     if (n == 0) return CORR_OK;
     if (!h->d_ring)
         if (int rc = alloc_ring(h)) return rc;
-    return ingest(h, x, n, n, seq, cudaMemcpyHostToDevice, true);
+    return ingest(h, x, n, n, seq, cudaMemcpyHostToDevice);
+}
+
+int corr_set_output_ring(corr_t* h, float* vis, float* beams, int n_slots) {
+    if (int rc = check_handle(h)) return rc;
+    if (vis && (n_slots < 1 || n_slots > 4096)) return fail(CORR_E_INVAL, "n_slots must be in [1, 4096]");
+    CU(cudaStreamSynchronize(h->cstream));
+    CU(cudaStreamSynchronize(h->stream));
+    for (cudaEvent_t e : h->ev_out) cudaEventDestroy(e);
+    h->ev_out.clear();
+    h->slot_of.clear();
+    h->out_vis = h->out_beams = nullptr;
+    h->n_slots = 0;
+    if (!vis) return CORR_OK;
+    h->ev_out.resize(n_slots, nullptr);
+    for (cudaEvent_t& e : h->ev_out) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    h->slot_of.assign(n_slots, -1);
+    h->out_vis = vis;
+    h->out_beams = beams;
+    h->n_slots = n_slots;
+    return CORR_OK;
+}
+
+int corr_wait_output(corr_t* h, int64_t index, int* slot) {
+    if (int rc = check_handle(h)) return rc;
+    if (!h->out_vis) return fail(CORR_E_STATE, "no output ring (corr_set_output_ring)");
+    if (index < 0) return fail(CORR_E_INVAL, "index must be >= 0");
+    if (index >= h->n_streamed) return fail(CORR_E_AGAIN, "integration %lld not launched yet", (long long)index);
+    const int s = static_cast<int>(index % h->n_slots);
+    if (h->slot_of[s] != index) return fail(CORR_E_STATE, "slot %d has been reused since integration %lld", s,
+                                            (long long)index);
+    CU(cudaEventSynchronize(h->ev_out[s]));
+    unsigned err = 0;
+    CU(cudaMemcpy(&err, h->d_err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) return fail(CORR_E_TIMEOUT, "a kernel wait timed out (error bits 0x%x); results invalid", err);
+    if (slot) *slot = s;
+    return CORR_OK;
 }
 
 int corr_push_samples_device(corr_t* h, const int8_t* x, int64_t n, int64_t seq, void* stream) {
@@ -505,8 +602,8 @@ int corr_push_samples_device(corr_t* h, const int8_t* x, int64_t n, int64_t seq,
         if (int rc = alloc_ring(h)) return rc;
     // order the copy after the caller's producer work
     CU(cudaEventRecord(h->ev_aux, static_cast<cudaStream_t>(stream)));
-    CU(cudaStreamWaitEvent(h->stream, h->ev_aux, 0));
-    return ingest(h, x, n, n, seq, cudaMemcpyDeviceToDevice, false);
+    CU(cudaStreamWaitEvent(h->cstream, h->ev_aux, 0));
+    return ingest(h, x, n, n, seq, cudaMemcpyDeviceToDevice);
 }
 
 int corr_integrate_device(corr_t* h, const int8_t* x, int64_t ld, int64_t n_avail, int64_t g0, void* stream) {

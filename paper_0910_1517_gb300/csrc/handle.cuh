@@ -18,13 +18,31 @@ struct corr {
     // host-side model
     std::vector<double> tau, phi0, rate;
     bool scales_set = false;
-    // streaming ring
+    // streaming ingest: two sample rings; integration j is filled into ring j % 2 on the copy
+    // stream while integration j - 1 is correlated on `stream` (the rings hand over their last
+    // max_delay samples).  ev_ready[r]: ring r's samples have landed; ev_free[r]: the last
+    // integration that read ring r is done with it.
     int8_t* d_ring = nullptr;
+    int8_t* d_ring2 = nullptr;
+    int cur_ring = 0;
     int64_t ring_ld = 0, fill = 0, seq_next = -1, seq_origin = -1, g_next = 0;
     bool ring_started = false;
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr}, ev_copied = nullptr;
+    int64_t n_streamed = 0;              // integrations launched from the rings since the stream started
+    // ring of host output slots: integration j's visibilities / beams land in slot j % n_slots
+    float* out_vis = nullptr;
+    float* out_beams = nullptr;
+    int n_slots = 0;
+    std::vector<cudaEvent_t> ev_out;     // per slot: its last copy has landed
+    std::vector<int64_t> slot_of;        // per slot: the integration it holds (or is receiving)
     // device tables and outputs
     double* d_model = nullptr;          // tau | phi0 | rate, 3 * n_ant
-    double* h_model = nullptr;          // pinned staging of the same
+    double* h_model = nullptr;          // pinned staging of the same: 1 + kModelSlots copies (the first
+                                        // for graph-captured batches, the rest a ring for queued integrations)
+    static constexpr int kModelSlots = 4;
+    cudaEvent_t ev_model[kModelSlots] = {};
+    int model_slot = 0;
     float2* d_pf = nullptr;
     float2* d_ff = nullptr;
     int* d_D = nullptr;
