@@ -123,9 +123,11 @@ int corr_push_samples(corr_t* h, const int8_t* x, int64_t n, int64_t seq);
  * vis: n_slots x [n_fft/2][n_bl][n_pol^2] complex64 (re, im float pairs);
  * beams: n_slots x [2][n_int/beam_avg][n_fft/2] float32; host memory, pinned
  * (cudaHostAlloc) for the copies to run asynchronously.  A slot is rewritten
- * n_slots integrations later; the caller reads it before then.  vis = NULL
- * removes the ring.  Waits for queued work first.  CORR_E_INVAL for n_slots
- * outside [1, 4096]. */
+ * n_slots integrations later; the caller reads it before then.  While a ring
+ * is set the device outputs are double-buffered (integration j writes buffer
+ * j % 2, copied back on a separate stream while j + 1 runs) and beam_avg is
+ * fixed.  vis = NULL removes the ring.  Waits for queued work first.
+ * CORR_E_INVAL for n_slots outside [1, 4096]; CORR_E_STATE for a batch member. */
 int corr_set_output_ring(corr_t* h, float* vis, float* beams, int n_slots);
 
 /* Block until the results of streaming integration `index` are in their slot;
@@ -205,7 +207,9 @@ int corr_stage_times(corr_t* h, float* ms4, int* n);
  * functional pipeline over several time slices concurrently (Sec. 2.3.2); here
  * the concurrency is across independent observations.  Results are read per
  * handle with the functions above.  The handles stay owned by the caller and
- * must outlive the batch.  corr_batch_integrate_device takes per-sub-array
+ * must outlive the batch; a handle with an output ring (corr_set_output_ring)
+ * cannot join one (CORR_E_STATE), nor can a batch member get a ring.
+ * corr_batch_integrate_device takes per-sub-array
  * device sample pointers, row strides, readable samples and first global
  * frames (arrays of n_sub); the graph is captured on the first call.
  * corr_batch_tune times every allowed X-engine stage size per sub-array on the

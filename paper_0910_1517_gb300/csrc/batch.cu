@@ -172,13 +172,17 @@ int corr_batch_create(corr_batch_t** out, int n_sub, corr_t* const* subs) {
     for (int s = 0; s < n_sub; ++s) {
         if (!subs[s]) return bfail(CORR_E_INVAL, "null sub-array handle");
         if (subs[s]->xmode != subs[0]->xmode) return bfail(CORR_E_INVAL, "sub-arrays must share one precision mode");
+        if (subs[s]->out_vis) return bfail(CORR_E_STATE, "a sub-array handle has an output ring (double-buffered outputs)");
         for (int q = 0; q < s; ++q)
             if (subs[q] == subs[s]) return bfail(CORR_E_INVAL, "a handle appears twice");
     }
     corr_batch* b = new corr_batch();
     b->n_sub = n_sub;
     b->xmode = subs[0]->xmode;
-    for (int s = 0; s < n_sub; ++s) b->h[s] = subs[s];
+    for (int s = 0; s < n_sub; ++s) {
+        b->h[s] = subs[s];
+        subs[s]->batch_refs += 1;
+    }
     auto bail = [&](const char* m) {
         corr_batch_destroy(b);
         return bfail(CORR_E_NOMEM, m);
@@ -224,6 +228,8 @@ int corr_batch_destroy(corr_batch_t* b) {
     if (b->h_xt) cudaFreeHost(b->h_xt);
     if (b->done) cudaEventDestroy(b->done);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (int q = 0; q < b->n_sub; ++q)   // the handles outlive their batches
+        if (b->h[q]) b->h[q]->batch_refs -= 1;
     delete b;
     return CORR_OK;
 }

@@ -172,7 +172,7 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
     if (h->xmode == CORR_FP32)
         CU(launch_xengine_fp32(xp, h->n_sm, s));
     else
-        CU(launch_xengine_tc_table(h->d_xtab, h->n_items, h->n_sm, s));
+        CU(launch_xengine_tc_table(h->out_buf == 1 ? h->xtab_b1 : h->d_xtab, h->n_items, h->n_sm, s));
     if (h->dump > 0) {
         if (h->xmode != CORR_FP32) return fail(CORR_E_STATE, "power dumps need the CORR_FP32 spectra");
         CU(launch_power_dumps(static_cast<const float*>(h->d_spec), h->n_in, h->n_chan, h->n_int, h->dump,
@@ -218,8 +218,23 @@ int upload_xtab(corr* h) {
     t.items = h->d_items;
     t.err = h->d_err;
     CU(cudaDeviceSynchronize());
+    if (h->xtab_b1) {                    // double-buffered outputs: one table per buffer
+        t.sub[0].vis = h->vis_b[0];
+        CU(cudaMemcpy(h->d_xtab, &t, sizeof t, cudaMemcpyHostToDevice));
+        t.sub[0].vis = h->vis_b[1];
+        CU(cudaMemcpy(h->xtab_b1, &t, sizeof t, cudaMemcpyHostToDevice));
+        return CORR_OK;
+    }
     CU(cudaMemcpy(h->d_xtab, &t, sizeof t, cudaMemcpyHostToDevice));
     return CORR_OK;
+}
+
+// Point the handle's outputs at buffer b of the double-buffered pair.
+void select_outputs(corr* h, int b) {
+    h->out_buf = b;
+    h->d_vis = h->vis_b[b];
+    h->d_beams_raw = h->beams_raw_b[b];
+    h->d_beams = h->beams_b[b];
 }
 
 // Wait for (or poll) the last launched integration; check the device error word.
@@ -250,18 +265,23 @@ int check_handle(corr* h) {
 
 // Append n samples per input (host or device rows of pitch spitch) to the ring,
 // launching integrations as it fills.  kind is the cudaMemcpyKind of the copy.
-// Results of the integration just queued on h->stream into the host output ring, if set.
+// Results of the integration just queued on h->stream (in output buffer h->out_buf) into the
+// host output ring: copied on the output stream, which then frees the buffer.
 int enqueue_output(corr* h, int64_t index) {
     if (!h->out_vis) return CORR_OK;
-    const int slot = static_cast<int>(index % h->n_slots);
+    const int slot = static_cast<int>(index % h->n_slots), b = h->out_buf;
     const size_t nv = static_cast<size_t>(h->n_chan) * h->n_bl * h->npp * 2;
     const size_t nb = 2 * static_cast<size_t>(h->n_int / h->beam_avg) * h->n_chan;
     h->slot_of[slot] = index;
-    CU(cudaMemcpyAsync(h->out_vis + nv * slot, h->d_vis, nv * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaEventRecord(h->ev_int_done, h->stream));
+    CU(cudaStreamWaitEvent(h->ostream, h->ev_int_done, 0));
+    CU(cudaMemcpyAsync(h->out_vis + nv * slot, h->vis_b[b], nv * sizeof(float), cudaMemcpyDeviceToHost,
+                       h->ostream));
     if (h->out_beams)
-        CU(cudaMemcpyAsync(h->out_beams + nb * slot, h->d_beams, nb * sizeof(float), cudaMemcpyDeviceToHost,
-                           h->stream));
-    CU(cudaEventRecord(h->ev_out[slot], h->stream));
+        CU(cudaMemcpyAsync(h->out_beams + nb * slot, h->beams_b[b], nb * sizeof(float), cudaMemcpyDeviceToHost,
+                           h->ostream));
+    CU(cudaEventRecord(h->ev_out[slot], h->ostream));
+    CU(cudaEventRecord(h->ev_buf_free[b], h->ostream));
     return CORR_OK;
 }
 
@@ -301,6 +321,11 @@ int ingest(corr* h, const int8_t* x, int64_t spitch, int64_t n, int64_t seq, cud
             const int r = h->cur_ring, nx = r ^ 1;
             CU(cudaEventRecord(h->ev_ready[r], h->cstream));
             CU(cudaStreamWaitEvent(h->stream, h->ev_ready[r], 0));
+            if (h->out_vis) {            // output buffer j % 2, once its copy to the host slot is done
+                const int b = static_cast<int>(h->n_streamed & 1);
+                CU(cudaStreamWaitEvent(h->stream, h->ev_buf_free[b], 0));
+                select_outputs(h, b);
+            }
             if (int e = run_integration(h, ring, h->ring_ld, need, h->g_next, h->stream)) return e;
             CU(cudaEventRecord(h->ev_free[r], h->stream));
             if (int e = enqueue_output(h, h->n_streamed)) return e;
@@ -428,6 +453,14 @@ int corr_destroy(corr_t* h) {
     if (h->d_xtab) cudaFree(h->d_xtab);
     if (h->d_items) cudaFree(h->d_items);
     if (h->cstream) cudaStreamSynchronize(h->cstream);
+    if (h->ostream) cudaStreamSynchronize(h->ostream);
+    if (h->vis_b[1]) {                   // the second output buffers (the current may be either)
+        select_outputs(h, 0);
+        if (h->beams_b[1] != h->beams_raw_b[1]) cudaFree(h->beams_b[1]);
+        cudaFree(h->beams_raw_b[1]);
+        cudaFree(h->vis_b[1]);
+    }
+    if (h->xtab_b1) cudaFree(h->xtab_b1);
     void* bufs[] = {h->d_ring, h->d_ring2, h->d_model, h->d_pf, h->d_ff, h->d_D, h->d_wcoh, h->d_ginc, h->d_scale,
                     h->d_tw, h->d_spec, h->d_beams_raw, h->d_vis, h->d_vis_part, h->d_vis_int, h->d_err};
     for (void* b : bufs)
@@ -445,6 +478,10 @@ int corr_destroy(corr_t* h) {
     for (cudaEvent_t e : h->ev_out) cudaEventDestroy(e);
     for (cudaEvent_t e : h->ev_model)
         if (e) cudaEventDestroy(e);
+    if (h->ev_int_done) cudaEventDestroy(h->ev_int_done);
+    for (cudaEvent_t e : h->ev_buf_free)
+        if (e) cudaEventDestroy(e);
+    if (h->ostream) cudaStreamDestroy(h->ostream);
     if (h->cstream) cudaStreamDestroy(h->cstream);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -456,8 +493,8 @@ int corr_set_mode(corr_t* h, int xmode, int polmode, int beam_avg) {
     if (xmode != CORR_FP32 && xmode != CORR_I8 && xmode != CORR_F16) return fail(CORR_E_INVAL, "unknown xmode");
     if (polmode != 0) return fail(CORR_E_INVAL, "only polmode 0 (all products) is supported");
     if (beam_avg < 1 || h->n_int % beam_avg) return fail(CORR_E_INVAL, "beam_avg must divide n_int");
-    if (h->out_beams && beam_avg != h->beam_avg)
-        return fail(CORR_E_STATE, "beam_avg sizes the output ring's beam slots: remove the ring first");
+    if (h->out_vis && beam_avg != h->beam_avg)
+        return fail(CORR_E_STATE, "beam_avg sizes the output ring and its buffers: remove the ring first");
     if (xmode != CORR_FP32 && !xengine_tc_supported(h->n_in))
         return fail(CORR_E_INVAL, "tensor-core modes need n_in <= 128");
     if (xmode == CORR_I8 && h->n_int > 66571) return fail(CORR_E_INVAL, "CORR_I8 needs n_int <= 66571");
@@ -561,14 +598,52 @@ int corr_push_samples(corr_t* h, const int8_t* x, int64_t n, int64_t seq) {
 int corr_set_output_ring(corr_t* h, float* vis, float* beams, int n_slots) {
     if (int rc = check_handle(h)) return rc;
     if (vis && (n_slots < 1 || n_slots > 4096)) return fail(CORR_E_INVAL, "n_slots must be in [1, 4096]");
+    if (vis && h->batch_refs > 0) return fail(CORR_E_STATE, "the handle belongs to a batch (captured graph)");
     CU(cudaStreamSynchronize(h->cstream));
     CU(cudaStreamSynchronize(h->stream));
+    if (h->ostream) CU(cudaStreamSynchronize(h->ostream));
     for (cudaEvent_t e : h->ev_out) cudaEventDestroy(e);
     h->ev_out.clear();
     h->slot_of.clear();
     h->out_vis = h->out_beams = nullptr;
     h->n_slots = 0;
+    const size_t nv = static_cast<size_t>(h->n_chan) * h->n_bl * h->npp;
+    const size_t nraw = 2 * static_cast<size_t>(h->n_int) * h->n_chan;
+    const size_t navg = 2 * static_cast<size_t>(h->n_int / h->beam_avg) * h->n_chan;
+    if (h->vis_b[1]) {
+        // back to single outputs: keep the last results readable in buffer 0
+        if (h->out_buf == 1) {
+            CU(cudaMemcpy(h->vis_b[0], h->vis_b[1], nv * sizeof(float2), cudaMemcpyDeviceToDevice));
+            CU(cudaMemcpy(h->beams_raw_b[0], h->beams_raw_b[1], nraw * sizeof(float), cudaMemcpyDeviceToDevice));
+            if (h->beams_b[1] != h->beams_raw_b[1])
+                CU(cudaMemcpy(h->beams_b[0], h->beams_b[1], navg * sizeof(float), cudaMemcpyDeviceToDevice));
+            select_outputs(h, 0);
+        }
+        if (h->beams_b[1] != h->beams_raw_b[1]) cudaFree(h->beams_b[1]);
+        cudaFree(h->beams_raw_b[1]);
+        cudaFree(h->vis_b[1]);
+        if (h->xtab_b1) cudaFree(h->xtab_b1);
+        h->vis_b[1] = nullptr;
+        h->beams_raw_b[1] = h->beams_b[1] = nullptr;
+        h->xtab_b1 = nullptr;
+        if (int rc = upload_xtab(h)) return rc;
+    }
     if (!vis) return CORR_OK;
+    h->vis_b[0] = h->d_vis;
+    h->beams_raw_b[0] = h->d_beams_raw;
+    h->beams_b[0] = h->d_beams;
+    h->out_buf = 0;
+    CU(dalloc(&h->vis_b[1], nv));
+    CU(dalloc(&h->beams_raw_b[1], nraw));
+    h->beams_b[1] = h->beams_raw_b[1];
+    if (h->beam_avg > 1) CU(dalloc(&h->beams_b[1], navg));
+    if (h->d_xtab) CU(cudaMalloc(&h->xtab_b1, sizeof(XtBatch)));
+    if (int rc = upload_xtab(h)) return rc;
+    if (!h->ostream) {
+        CU(cudaStreamCreateWithFlags(&h->ostream, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&h->ev_int_done, cudaEventDisableTiming));
+        for (cudaEvent_t& e : h->ev_buf_free) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     h->ev_out.resize(n_slots, nullptr);
     for (cudaEvent_t& e : h->ev_out) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     h->slot_of.assign(n_slots, -1);

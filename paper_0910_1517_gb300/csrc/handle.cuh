@@ -36,6 +36,17 @@ struct corr {
     int n_slots = 0;
     std::vector<cudaEvent_t> ev_out;     // per slot: its last copy has landed
     std::vector<int64_t> slot_of;        // per slot: the integration it holds (or is receiving)
+    // while an output ring is set the outputs are double-buffered: streamed integration j writes
+    // buffer j % 2 (d_vis, d_beams_raw, d_beams point at the current one), and the output stream
+    // copies it to the host slot while integration j + 1 runs
+    float2* vis_b[2] = {nullptr, nullptr};
+    float* beams_raw_b[2] = {nullptr, nullptr};
+    float* beams_b[2] = {nullptr, nullptr};
+    gbx::XtBatch* xtab_b1 = nullptr;     // tensor-core table naming buffer 1
+    int out_buf = 0;
+    cudaStream_t ostream = nullptr;
+    cudaEvent_t ev_int_done = nullptr, ev_buf_free[2] = {nullptr, nullptr};
+    int batch_refs = 0;                  // batches (captured graphs) holding this handle's buffers
     // device tables and outputs
     double* d_model = nullptr;          // tau | phi0 | rate, 3 * n_ant
     double* h_model = nullptr;          // pinned staging of the same: 1 + kModelSlots copies (the first

@@ -32,11 +32,32 @@ def _stream():
     return s, body
 
 
-def _reference(torch, corr, s, body, j):
+def _scales(torch, corr, s, body):
+    """Requantisation scales from one FP32 integration of the stream's start."""
+    h = corr.corr_create(N_ANT, N_POL, N_FFT, N_INT)
+    try:
+        corr.corr_set_delays(h, s.delay, s.phi0, s.rate)
+        n = body + MAX_DELAY
+        xt = torch.zeros((s.n_in, ((n + 15) // 16) * 16 + 16), dtype=torch.int8, device="cuda")
+        xt[:, :n] = torch.from_numpy(np.ascontiguousarray(s.x[:, :n])).cuda()
+        corr.corr_integrate_device(h, xt, n_avail=n, stream=torch.cuda.current_stream())
+        corr.corr_set_scales(h, None)
+        corr.corr_set_mode(h, corr.CORR_I8, 0, 1)
+        corr.corr_integrate_device(h, xt, n_avail=n, stream=torch.cuda.current_stream())
+        _, sc = corr.corr_read_requant(h, 0, 0, N_INT)
+        return np.ascontiguousarray(sc, dtype=np.float32)
+    finally:
+        corr.corr_destroy(h)
+
+
+def _reference(torch, corr, s, body, j, mode=0, scales=None):
     """Integration j on its own, straight from device memory."""
     h = corr.corr_create(N_ANT, N_POL, N_FFT, N_INT)
     try:
         corr.corr_set_delays(h, s.delay, s.phi0, s.rate)
+        if scales is not None:
+            corr.corr_set_scales(h, scales)
+        corr.corr_set_mode(h, mode, 0, 1)
         n = body + MAX_DELAY
         xt = torch.zeros((s.n_in, ((n + 15) // 16) * 16 + 16), dtype=torch.int8, device="cuda")
         xt[:, :n] = torch.from_numpy(np.ascontiguousarray(s.x[:, j * body:j * body + n])).cuda()
@@ -46,9 +67,11 @@ def _reference(torch, corr, s, body, j):
         corr.corr_destroy(h)
 
 
-def test_output_ring_matches_direct_integrations(env):
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp32", "i8"])
+def test_output_ring_matches_direct_integrations(env, mode):
     torch, corr = env
     s, body = _stream()
+    scales = _scales(torch, corr, s, body) if mode == corr.CORR_I8 else None
     n_bl = N_ANT * (N_ANT + 1) // 2
     n_slots = 3
     vis = torch.empty((n_slots, N_FFT // 2, n_bl, N_POL ** 2, 2), dtype=torch.float32).pin_memory()
@@ -57,6 +80,9 @@ def test_output_ring_matches_direct_integrations(env):
     try:
         corr.corr_set_max_delay(h, MAX_DELAY)
         corr.corr_set_delays(h, s.delay, s.phi0, s.rate)
+        if scales is not None:
+            corr.corr_set_scales(h, scales)
+        corr.corr_set_mode(h, mode, 0, 1)
         corr.corr_set_output_ring(h, vis.numpy(), beams.numpy(), n_slots)
         with pytest.raises(corr.CorrError) as ei:
             corr.corr_wait_output(h, 0)
@@ -80,7 +106,7 @@ def test_output_ring_matches_direct_integrations(env):
             corr.corr_wait_output(h, 0)                  # its slot now holds integration 3
         assert ei.value.code == -7
         for j in range(N_INTEG):
-            V_ref, B_ref = _reference(torch, corr, s, body, j)
+            V_ref, B_ref = _reference(torch, corr, s, body, j, mode, scales)
             V, B = got[j]
             assert np.array_equal(V.reshape(-1), V_ref.view(np.float32).reshape(-1)), j
             assert np.array_equal(B.reshape(B_ref.shape), B_ref), j
@@ -103,6 +129,18 @@ def test_output_ring_arguments(env):
             corr.corr_set_output_ring(h, v, None, 0)
         assert ei.value.code == -1
         corr.corr_set_output_ring(h, v, None, 1)
+        with pytest.raises(corr.CorrError) as ei:       # double-buffered outputs: not in a batch
+            corr.corr_batch_create([h])
+        assert ei.value.code == -7
+        corr.corr_set_output_ring(h, None)
+        b = corr.corr_batch_create([h])
+        try:
+            with pytest.raises(corr.CorrError) as ei:   # nor a ring on a batch member
+                corr.corr_set_output_ring(h, v, None, 1)
+            assert ei.value.code == -7
+        finally:
+            corr.corr_batch_destroy(b)
+        corr.corr_set_output_ring(h, v, None, 1)        # free again once the batch is gone
         corr.corr_set_output_ring(h, None)
     finally:
         corr.corr_destroy(h)
