@@ -199,7 +199,7 @@ int corr_batch_create(corr_batch_t** out, int n_sub, corr_t* const* subs) {
     b->fe_blocks = 0;
     for (int s = 0; s < n_sub; ++s) {
         b->h_fe->first[s] = b->fe_blocks;
-        b->fe_blocks += fengine_blocks(subs[s]->n_fft, subs[s]->n_int);
+        b->fe_blocks += (fengine_blocks(subs[s]->n_fft, subs[s]->n_int) + 1) & ~1;   // even: cluster pairs
         b->fe_smem = std::max(b->fe_smem, fengine_smem_bytes(subs[s]->n_fft));
     }
     b->h_fe->first[n_sub] = b->fe_blocks;

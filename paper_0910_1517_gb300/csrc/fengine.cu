@@ -165,6 +165,10 @@ struct Epi {
     using P = Plan<M>;
     static constexpr int TB = (MODE == OUT_FP32) ? tb_fp32(M) : kTbHalf;
     static constexpr int L = (P::F < 8) ? P::F : 8;      // frames per thread
+    // fp16 runs of 8 frames from 4-frame CTAs (n_chan 2048): the two CTAs of a cluster (consecutive
+    // frame blocks) trade halves of their channels through distributed shared memory, so that each
+    // writes whole 32-byte pieces (8 frames x re, im) of its half of the channels
+    static constexpr bool kPair = (M == 2048 && MODE != OUT_FP32);
     static_assert(L % TB == 0 || L < TB, "whole K-block runs, or part of one when F < TB");
     static constexpr int NP = kE / (2 * L);                // channel pairs per thread
     static constexpr int TPG = L * P::T;                   // threads per frame group
@@ -180,7 +184,10 @@ struct Smem {
     static constexpr size_t X = stage + 2 * static_cast<size_t>(P::STAGE);
     static constexpr size_t tw = X + sizeof(float2) * P::F * P::PADM;
     static constexpr size_t tab = ((tw + sizeof(float2) * kTw + 127) / 128) * 128;   // 2 bulk-copy targets
-    static constexpr size_t total = tab + 2 * sizeof(float2) * kTab;
+    // cluster-pair exchange buffer (n_chan 2048): [4 slots (re, im) x (rank 0, 1)][M/2 channels] of 4
+    // fp16 frames (8 bytes): a warp's writes and reads of consecutive channels are conflict-free
+    static constexpr size_t xch = ((tab + 2 * sizeof(float2) * kTab + 127) / 128) * 128;
+    static constexpr size_t total = xch + (M == 2048 ? static_cast<size_t>(M / 2) * 32 : 0);
     static_assert(total <= 232448, "F-engine shared memory exceeds 227 KB");
     static_assert(X % 16 == 0 && tab % 16 == 0 && (sizeof(float2) * kTab) % 16 == 0 && P::STAGE % 16 == 0,
                   "bulk-copy targets are 16-byte aligned");
@@ -191,6 +198,7 @@ struct FeCtl {
     uint64_t bar[2];
     uint64_t tbar[2];
     int abort_flag;
+    int peer_abort;            // the cluster partner's abort flag (paired CTAs)
     int Ds[kMaxAnt];           // integer delays, read every iteration
 };
 
@@ -225,8 +233,12 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
     const int fg = tid / TPG;         // frame group of the split: frames fg*L .. fg*L + L - 1
     const int kk = tid % TPG;         // channel pairs kk + q*TPG, q < NP
     const int t0 = block * F;
+    if (t0 >= p.n_int) return;        // padding CTA of a batched launch (never a cluster-paired one)
     const int n_fr = min(F, p.n_int - t0);
     const bool live = fg * L < n_fr;  // n_fr is a multiple of L: whole frame groups are live or not
+    constexpr bool kPair = E::kPair;
+    unsigned char* xch = smem + S::xch;
+    const uint32_t rank = kPair ? cluster_ctarank() : 0;   // frames 4 rank .. of the pair's 8
     const int R = 2 * p.n_in;
     const int64_t ntb = p.n_int / TB;
 
@@ -263,8 +275,10 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
         mbar_init(&tbar[1], 1);
         fence_mbar_init();
         abort_flag = 0;
+        ctl.peer_abort = 0;
     }
     __syncthreads();
+    if constexpr (kPair) cluster_sync();   // both CTAs of the pair are running before any remote write
 
     const int n_iter = p.n_in;  // polarisation-major order: it = pol * n_ant + a
     // Called by all of warp 0: lane 0 issues the bulk copy of the F frames of input `it`
@@ -345,7 +359,7 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
             Dft<16>::template run<1>(v);
         }
         __syncthreads();  // the previous iteration's split has finished reading X and its antenna tables
-        if (abort_flag) break;
+        if (!kPair && abort_flag) break;  // a paired CTA leaves with its partner, after the exchange
         if (tid == 0 && it + 1 < n_iter) issue_tab(it + 1);   // into the buffer that split just released
         pass_store<M, P::R1, 1>(Xf, t, v);
         group_sync<T>(f);
@@ -367,7 +381,7 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
         const float2* pfa = tab + (it & 1) * S::kTab;
         const float2* wa = pfa + M;
         const float2* fra = pfa + 2 * M;   // fringe phasors of the CTA's frames
-        if (!live) continue;
+        if (live) {
         // FP32 piece of input i in a K-block: granules m*PG .. m*PG + PG - 1 of row group G (PG = TB/2:
         // the re row's TB/4 granules, then the im row's), XOR-placed by s = G & 7
         constexpr int PG = TB / 2;
@@ -462,10 +476,25 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
                         u[4 + m] = pack_half2(hi[2 * m], hi[2 * m + 1]);
                     }
                     st_global_v8(o, u);
-                } else {                                   // half rows (F = 4 frames per CTA)
-                    static_assert(L == 4, "fp16 runs of 4 or 8 frames");
-                    *reinterpret_cast<uint2*>(o) = make_uint2(pack_half2(hr[0], hr[1]), pack_half2(hr[2], hr[3]));
-                    *reinterpret_cast<uint2*>(o + TB) = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
+                } else {
+                    // 4-frame halves of the 8-frame run: into the exchange buffer of the CTA of the
+                    // pair that writes this channel (rank 0: channels < M/2), at frame offset 4 rank
+                    static_assert(L == 4 && kPair, "fp16 runs of 4 frames only in cluster pairs");
+                    (void)o;
+                    const int ch = chs[c];
+                    const uint32_t owner = ch < M / 2 ? 0u : 1u;
+                    // slot 2c + rank (c = 0 re, 1 im), word ch % (M/2)
+                    unsigned char* dre = xch + (static_cast<size_t>(rank) * (M / 2) + ch % (M / 2)) * 8;
+                    unsigned char* dim = dre + static_cast<size_t>(M) * 8;
+                    const uint2 vr = make_uint2(pack_half2(hr[0], hr[1]), pack_half2(hr[2], hr[3]));
+                    const uint2 vi = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
+                    if (owner == rank) {
+                        *reinterpret_cast<uint2*>(dre) = vr;
+                        *reinterpret_cast<uint2*>(dim) = vi;
+                    } else {
+                        st_cluster_v2(cluster_map(dre, owner), vr.x, vr.y);
+                        st_cluster_v2(cluster_map(dim, owner), vi.x, vi.y);
+                    }
                 }
             }
         };
@@ -499,6 +528,27 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
             }
             emit(2 * q, yk);
             emit(2 * q + 1, ym);
+        }
+        }  // live
+        if constexpr (kPair) {
+            // the pair's exchange is complete (and both CTAs know whether either must stop): write
+            // this CTA's half of the channels as whole 8-frame pieces (rows 2i, 2i+1: 32 bytes)
+            if (tid == 0) st_cluster_u32(cluster_map(&ctl.peer_abort, rank ^ 1u), static_cast<uint32_t>(abort_flag));
+            cluster_sync();
+            if (abort_flag || ctl.peer_abort) {
+                abort_flag = 1;
+                break;                        // both CTAs of the pair, at the same iteration
+            }
+            const int64_t kb8 = (t0 - 4 * static_cast<int>(rank)) / TB;
+            __half* spec = static_cast<__half*>(p.spec);
+            const uint2* xw = reinterpret_cast<const uint2*>(xch);   // [slot][M/2]
+            for (int j = tid; j < M / 2; j += kThreads) {
+                const int ch = static_cast<int>(rank) * (M / 2) + j;
+                const uint2 r0 = xw[j], r1 = xw[M / 2 + j], i0 = xw[M + j], i1 = xw[3 * (M / 2) + j];
+                const uint32_t u[8] = {r0.x, r0.y, r1.x, r1.y, i0.x, i0.y, i1.x, i1.y};
+                st_global_v8(spec + (static_cast<int64_t>(ch) * ntb + kb8) * blk_elems + 2 * i * TB, u);
+            }
+            cluster_sync();                   // both have read their buffers before the next exchange
         }
     }
 
@@ -562,6 +612,24 @@ cudaError_t launch_t(const FeParams& p, cudaStream_t s) {
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const int grid = (p.n_int + P::F - 1) / P::F;
+    if constexpr (Epi<M, MODE>::kPair) {
+        // clusters of two consecutive frame blocks (grid is even: n_int is a multiple of 16)
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, fengine_kernel<M, MODE>, p);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
     fengine_kernel<M, MODE><<<grid, kThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
@@ -700,10 +768,26 @@ cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s) {
 int fengine_blocks(int n_fft, int n_int) { return (n_int + kChanFrames / (n_fft / 2) - 1) / (kChanFrames / (n_fft / 2)); }
 
 cudaError_t launch_fengine_batched(const FeBatch* dtab, int total_blocks, size_t smem, int mode, cudaStream_t s) {
+    // clusters of two: every sub-array's first block is even (batch code pads the block counts),
+    // so the 4096-point fp16 sub-arrays get their frame-block pairs
+    if (total_blocks % 2) return cudaErrorInvalidValue;
     auto go = [&](auto kern) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        kern<<<total_blocks, kThreads, smem, s>>>(dtab);
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(total_blocks);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, kern, dtab);
+        if (e != cudaSuccess) return e;
         return cudaGetLastError();
     };
     switch (mode) {

@@ -11,9 +11,9 @@ from synth import make_config
 pytestmark = pytest.mark.gpu
 
 # (n_ant, n_pol, n_fft, n_int): uneven antenna counts and FFT sizes; 64 x 2 exercises the
-# two row blocks of a 256-row Gram
-SUBS = [(4, 2, 512, 64), (8, 2, 1024, 48), (16, 2, 2048, 32), (64, 2, 256, 32)]
-CHANS = [0, 1, 57, 100]
+# two row blocks of a 256-row Gram, the 4096-point FFT the cluster-paired F-engine CTAs
+SUBS = [(4, 2, 512, 64), (8, 2, 1024, 48), (16, 2, 2048, 32), (64, 2, 256, 32), (6, 2, 4096, 32)]
+CHANS = [0, 1, 57, 100, 1023, 1024, 2047]
 
 
 @pytest.fixture(scope="module")
@@ -65,7 +65,7 @@ def _check_exact(corr, orc, h, s):
 
 def test_batch_int8_exact_matches_oracle_and_single_handle(env):
     torch, corr, orc = env
-    hs, streams, xs = _handles(torch, corr, [701, 702, 703, 704], corr.CORR_I8)
+    hs, streams, xs = _handles(torch, corr, [701, 702, 703, 704, 705], corr.CORR_I8)
     st = torch.cuda.current_stream()
     b = corr.corr_batch_create(hs)
     try:
@@ -108,7 +108,7 @@ def test_batch_int8_exact_matches_oracle_and_single_handle(env):
 
 def test_batch_autotune_keeps_results(env):
     torch, corr, orc = env
-    hs, streams, xs = _handles(torch, corr, [801, 802, 803, 804], corr.CORR_I8)
+    hs, streams, xs = _handles(torch, corr, [801, 802, 803, 804, 805], corr.CORR_I8)
     st = torch.cuda.current_stream()
     b = corr.corr_batch_create(hs)
     try:
@@ -128,7 +128,7 @@ def test_batch_autotune_keeps_results(env):
 
 def test_batch_fp32_matches_single_handle(env):
     torch, corr, orc = env
-    hs, streams, xs = _handles(torch, corr, [901, 902, 903, 904], corr.CORR_FP32)
+    hs, streams, xs = _handles(torch, corr, [901, 902, 903, 904, 905], corr.CORR_FP32)
     st = torch.cuda.current_stream()
     single = []
     for h, (xt, n) in zip(hs, xs):

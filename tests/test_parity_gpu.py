@@ -138,13 +138,20 @@ def _calibrated_scales(env, s):
     return r["h"]
 
 
-def test_i8_bit_exact_on_requantised_spectra(env):
+# GMRT shape, and the 4096-point FFT whose 4-frame CTAs trade channel halves in cluster pairs
+# (channels 1023 / 1024 straddle the halves)
+TC_SHAPES = [dict(n_int=128), dict(n_ant=16, n_fft=4096, n_int=64)]
+TC_CHANS = {2048: [0, 1, 100, 333, 512, 777, 1023], 4096: [0, 1, 100, 1023, 1024, 1500, 2047]}
+
+
+@pytest.mark.parametrize("shape", TC_SHAPES, ids=["gmrt", "fft4096"])
+def test_i8_bit_exact_on_requantised_spectra(env, shape):
     torch, corr, orc = env
-    s = make_config(2, n_int=128, seed=3003)
+    s = make_config(2, seed=3003, **shape)
     h = _calibrated_scales(env, s)
     r = run_gpu(env, s, mode=corr.CORR_I8, handle=h)
     Vi = corr.corr_read_vis_int(h)
-    chans = [0, 1, 100, 333, 512, 777, 1023]
+    chans = TC_CHANS[s.n_fft]
     for c in chans:
         q, sc = corr.corr_read_requant(h, c, 1, s.n_int)
         Vo, Vd = orc.xint(q, sc[:, c:c + 1].astype(np.float64), s.n_ant, s.n_pol)
@@ -166,12 +173,13 @@ def test_i8_bit_exact_on_requantised_spectra(env):
     corr.corr_destroy(h)
 
 
-def test_f16_mode_accuracy(env):
+@pytest.mark.parametrize("shape", TC_SHAPES, ids=["gmrt", "fft4096"])
+def test_f16_mode_accuracy(env, shape):
     torch, corr, orc = env
-    s = make_config(2, n_int=128, seed=3004)
+    s = make_config(2, seed=3004, **shape)
     h = _calibrated_scales(env, s)
     r = run_gpu(env, s, mode=corr.CORR_F16, handle=h)
-    chans = [0, 5, 100, 333, 640, 777, 1023]
+    chans = TC_CHANS[s.n_fft]
     Y, V = oracle_all(orc, s, chans=chans)
     e_v = vis_norm_error(r["V"][chans], V, s.n_ant, s.n_pol)
     Bi, Bc = orc.beams(Y, s.n_ant, s.n_pol, s.n_fft, chans=chans)
