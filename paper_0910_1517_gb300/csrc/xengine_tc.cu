@@ -17,12 +17,13 @@
 //
 // Roles (6 warps): warp 0 streams stages in (and owns the TMEM allocation),
 // warp 1 issues tcgen05.mma from one thread, warps 2-5 drain the accumulators.
-// Accumulation is chunked: every 512 frames the FP32 accumulator is drained
+// Accumulation is chunked: every 1024 frames the FP32 accumulator is drained
 // and added into a running sum in TMEM (columns 256-511).  Items with N <= 128
 // double-buffer the accumulator (columns 0-127 / 128-255), wider ones use one
-// buffer of N columns.  For int8-valued operands every product is an integer
-// below 2^14 and a chunk sum stays below 2^23, so the FP32 accumulator is exact
-// and the running sum is kept as int32: the result equals the integer MAC.
+// buffer of N columns.  For int8-valued operands every product is an integer of
+// magnitude at most 127^2 = 16129 and a chunk sum at most 1024 * 16129 =
+// 16,516,096 < 2^24, so the FP32 accumulator is exact and the running sum is kept
+// as int32: the result equals the integer MAC.
 #include "common.cuh"
 #include "fengine.cuh"
 #include "xengine.cuh"
@@ -33,7 +34,7 @@ namespace {
 constexpr int kWarps = 6;
 constexpr int kThreads = kWarps * 32;
 constexpr int kStages = 5;
-constexpr int kChunk = 512;                   // frames per exact FP32 chunk
+constexpr int kChunk = 1024;                  // frames per exact FP32 chunk
 constexpr int kSlot = kStageMaxBytes + 2048;  // rows past R stay in bounds
 constexpr int kTailSlack = 32768;
 constexpr uint32_t kTmemCols = 512;
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XtBatch* 
 bool xengine_tc_supported(int n_in) { return n_in >= 1 && 2 * n_in <= 256; }
 
 int xengine_tc_max_ks(int n_in) {
-    int ks = kChunk;
+    int ks = 512;                                  // stages of at most 512 frames
     while (ks > 16 && (ks / kTbHalf) * 2 * n_in * 16 > kStageMaxBytes) ks /= 2;
     return ks;
 }
