@@ -198,7 +198,8 @@ struct FeCtl {
     uint64_t bar[2];
     uint64_t tbar[2];
     int abort_flag;
-    int peer_abort;            // the cluster partner's abort flag (paired CTAs)
+    uint64_t xfull;            // paired CTAs: the partner's half of this input's exchange has landed
+    uint64_t xempty;           // paired CTAs: the partner has read its exchange buffer (we may write it)
     int Ds[kMaxAnt];           // integer delays, read every iteration
 };
 
@@ -273,12 +274,30 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
         mbar_init(&bar[1], 1);
         mbar_init(&tbar[0], 1);
         mbar_init(&tbar[1], 1);
+        if constexpr (kPair) {
+            mbar_init(&ctl.xfull, 1);
+            mbar_init(&ctl.xempty, 1);
+        }
         fence_mbar_init();
         abort_flag = 0;
-        ctl.peer_abort = 0;
     }
     __syncthreads();
-    if constexpr (kPair) cluster_sync();   // both CTAs of the pair are running before any remote write
+    // Paired CTAs trade channel halves each input: the partner's 4-frame halves of the channels
+    // this CTA writes arrive by st.async, completing bytes on xfull; before writing into the
+    // partner's buffer a CTA waits on xempty, which the partner's arrive completes once it has
+    // read that buffer.  All waits are bounded; one cluster barrier at exit keeps both CTAs
+    // resident while the other may still write into them.
+    constexpr uint32_t kXBytes = (M / 2) * 16;           // partner's re + im halves of our channels
+    uint32_t peer_xfull = 0, peer_xempty = 0;
+    if constexpr (kPair) {
+        cluster_sync();                                  // both CTAs and their barriers exist
+        peer_xfull = cluster_map(&ctl.xfull, rank ^ 1u);
+        peer_xempty = cluster_map(&ctl.xempty, rank ^ 1u);
+        if (tid == 0) {
+            mbar_arrive_expect_tx(&ctl.xfull, kXBytes);  // input 0's exchange
+            mbar_arrive_remote(peer_xempty);             // the partner may write into our buffer
+        }
+    }
 
     const int n_iter = p.n_in;  // polarisation-major order: it = pol * n_ant + a
     // Called by all of warp 0: lane 0 issues the bulk copy of the F frames of input `it`
@@ -359,7 +378,11 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
             Dft<16>::template run<1>(v);
         }
         __syncthreads();  // the previous iteration's split has finished reading X and its antenna tables
-        if (!kPair && abort_flag) break;  // a paired CTA leaves with its partner, after the exchange
+        if (abort_flag) break;
+        if (kPair && tid == 0 && it > 0) {               // every thread has read the last exchange
+            mbar_arrive_expect_tx(&ctl.xfull, kXBytes);
+            mbar_arrive_remote(peer_xempty);
+        }
         if (tid == 0 && it + 1 < n_iter) issue_tab(it + 1);   // into the buffer that split just released
         pass_store<M, P::R1, 1>(Xf, t, v);
         group_sync<T>(f);
@@ -381,6 +404,9 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
         const float2* pfa = tab + (it & 1) * S::kTab;
         const float2* wa = pfa + M;
         const float2* fra = pfa + 2 * M;   // fringe phasors of the CTA's frames
+        if constexpr (kPair) {   // the partner has read its exchange buffer: this input's halves may go in
+            if (!mbar_wait_cluster(&ctl.xempty, it & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
+        }
         if (live) {
         // FP32 piece of input i in a K-block: granules m*PG .. m*PG + PG - 1 of row group G (PG = TB/2:
         // the re row's TB/4 granules, then the im row's), XOR-placed by s = G & 7
@@ -492,8 +518,8 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
                         *reinterpret_cast<uint2*>(dre) = vr;
                         *reinterpret_cast<uint2*>(dim) = vi;
                     } else {
-                        st_cluster_v2(cluster_map(dre, owner), vr.x, vr.y);
-                        st_cluster_v2(cluster_map(dim, owner), vi.x, vi.y);
+                        st_async_v2(cluster_map(dre, owner), vr.x, vr.y, peer_xfull);
+                        st_async_v2(cluster_map(dim, owner), vi.x, vi.y, peer_xfull);
                     }
                 }
             }
@@ -531,14 +557,10 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
         }
         }  // live
         if constexpr (kPair) {
-            // the pair's exchange is complete (and both CTAs know whether either must stop): write
+            // our halves are in (local stores, barrier) and the partner's have landed (xfull): write
             // this CTA's half of the channels as whole 8-frame pieces (rows 2i, 2i+1: 32 bytes)
-            if (tid == 0) st_cluster_u32(cluster_map(&ctl.peer_abort, rank ^ 1u), static_cast<uint32_t>(abort_flag));
-            cluster_sync();
-            if (abort_flag || ctl.peer_abort) {
-                abort_flag = 1;
-                break;                        // both CTAs of the pair, at the same iteration
-            }
+            __syncthreads();
+            if (!mbar_wait_cluster(&ctl.xfull, it & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
             const int64_t kb8 = (t0 - 4 * static_cast<int>(rank)) / TB;
             __half* spec = static_cast<__half*>(p.spec);
             const uint2* xw = reinterpret_cast<const uint2*>(xch);   // [slot][M/2]
@@ -548,7 +570,6 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
                 const uint32_t u[8] = {r0.x, r0.y, r1.x, r1.y, i0.x, i0.y, i1.x, i1.y};
                 st_global_v8(spec + (static_cast<int64_t>(ch) * ntb + kb8) * blk_elems + 2 * i * TB, u);
             }
-            cluster_sync();                   // both have read their buffers before the next exchange
         }
     }
 
@@ -570,6 +591,7 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
         if (it > 0) mbar_wait(&tbar[(it - 1) & 1], ((it - 1) >> 1) & 1, nullptr, 0);
         mbar_wait(&tbar[it & 1], (it >> 1) & 1, nullptr, 0);
     }
+    if constexpr (kPair) cluster_sync();   // neither CTA leaves while the other may still write into it
 }
 
 template <int M, int MODE>
