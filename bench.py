@@ -431,6 +431,13 @@ def run_ours(args, world, rank, local_rank):
         dist.barrier()
     corr.load()
     pk = peaks()
+    if args.leg != "all":                                 # one extra leg alone (profiling runs)
+        res = run_batch_leg(args, corr, torch, rank) if args.leg == "batched" else run_rfi_leg(corr, torch)
+        if rank == 0:
+            print(json.dumps({"leg": args.leg, **res}), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return 0
 
     s = make_config(2, seed=1002 + rank, n_int=N_INT)    # this rank's time slice
     n_avail = s.x.shape[1]
@@ -558,6 +565,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--no-extras", action="store_true",
                     help="time only the FP32 step (no precision forms, no end-to-end leg); for profiling runs")
+    ap.add_argument("--leg", choices=("all", "batched", "rfi"), default="all",
+                    help="run only the batched sub-array leg or only the learned-RFI leg (profiling runs)")
     ap.add_argument("--n-int", type=int, default=N_INT,
                     help="spectra per integration (default 8192, the GMRT-scale workload; smaller for profiling)")
     args = ap.parse_args()
