@@ -80,6 +80,40 @@ def peaks():
     return p
 
 
+# ------------------------------------------------------ ranks (one per GPU)
+
+def world_env():
+    """(world size, rank, local rank) as torchrun exports them; (1, 0, 0) when run directly."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def slice_seed(rank):
+    """Seed of this rank's time slice of the synthetic sky: every rank correlates its own data."""
+    return 1002 + rank
+
+
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (a whole-job time is its slowest rank's); x without ranks."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput: each of `world` ranks processed units_per_rank within `seconds`."""
+    return world * units_per_rank / seconds
+
+
+def emit(line, rank):
+    """The one JSON line of a run, printed by rank 0 only."""
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -223,7 +257,7 @@ def run_reference(args, world, rank):
                          "sample": f"each step: FP64 direct-DFT oracle on {nf} spectra x 64 inputs x 1024 channels"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    emit(line, rank)
     return 0
 
 
@@ -267,11 +301,8 @@ def run_e2e(args, corr, torch, dist, s, coh, world):
             corr.corr_wait_output(he, j + q - 1)          # the previous one's results, in host memory
     corr.corr_wait_output(he, j + k3 - 1)
     dt = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([dt], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
-    e2e = {"value": world * k3 * step_samples() / dt, "unit": UNIT, "h2d_bytes_per_step": N_IN * body,
+    dt = max_over_ranks(dt, dist, "cuda")
+    e2e = {"value": job_rate(world, k3 * step_samples(), dt), "unit": UNIT, "h2d_bytes_per_step": N_IN * body,
            "d2h_bytes_per_step": (hv.numel() + hb.numel()) * 4 // n_slots, "steps": k3,
            "ms_per_step": 1e3 * dt / k3,
            "path": "corr_push_samples (pinned host, two sample rings) + corr_wait_output (visibilities and "
@@ -433,13 +464,12 @@ def run_ours(args, world, rank, local_rank):
     pk = peaks()
     if args.leg != "all":                                 # one extra leg alone (profiling runs)
         res = run_batch_leg(args, corr, torch, rank) if args.leg == "batched" else run_rfi_leg(corr, torch)
-        if rank == 0:
-            print(json.dumps({"leg": args.leg, **res}), flush=True)
+        emit({"leg": args.leg, **res}, rank)
         if dist:
             dist.destroy_process_group()
         return 0
 
-    s = make_config(2, seed=1002 + rank, n_int=N_INT)    # this rank's time slice
+    s = make_config(2, seed=slice_seed(rank), n_int=N_INT)    # this rank's time slice
     n_avail = s.x.shape[1]
     ld = ((n_avail + 15) // 16) * 16 + 16
     xt = torch.zeros((N_IN, ld), dtype=torch.int8, device="cuda")
@@ -479,15 +509,12 @@ def run_ours(args, world, rank, local_rank):
         ms = e0.elapsed_time(e1)
         st, n = corr.corr_stage_times(h)
         corr.corr_set_timing(h, 0)
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
         return ms, st / max(n, 1), clocks
 
     K, W = args.steps, args.warmup
     ms, st, clocks = timed(corr.CORR_FP32, K, W, sample_clocks=True)
-    value = world * K * step_samples() / (ms * 1e-3)
+    value = job_rate(world, K * step_samples(), ms * 1e-3)
     stage_names = ["phasor_setup", "fengine", "xengine", "beam_average"]
 
     # precision forms of the X-engine on the same data (scales from this FP32 integration's autos)
@@ -497,7 +524,7 @@ def run_ours(args, world, rank, local_rank):
         k2 = max(10, min(K, 100))
         ms2, st2, _ = timed(m, k2, 3)
         modes[name] = {
-            "value": world * k2 * step_samples() / (ms2 * 1e-3), "ms_per_step": ms2 / k2,
+            "value": job_rate(world, k2 * step_samples(), ms2 * 1e-3), "ms_per_step": ms2 / k2,
             "stage_ms": dict(zip(stage_names, [round(v, 4) for v in st2])),
             "xengine_speedup_vs_fp32": st[2] / st2[2], "step_speedup_vs_fp32": (ms / K) / (ms2 / k2),
             "xengine_tensor_frac_of_sustained_peak": tensor_fraction(st2[2], pk),
@@ -538,6 +565,7 @@ def run_ours(args, world, rank, local_rank):
         torch.cuda.empty_cache()
         if rank == 0:
             rfi = run_rfi_leg(corr, torch)
+    line = None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -550,7 +578,7 @@ def run_ours(args, world, rank, local_rank):
             "batched_subarrays": batch, "learned_rfi": rfi,
             "e2e": e2e, "gpu_launches": 3 * K, "clocks": clocks, "cpu_baseline": cpu,
         }
-        print(json.dumps(line), flush=True)
+    emit(line, rank)
     if dist:
         dist.destroy_process_group()
     return 0
@@ -574,9 +602,7 @@ def main():
         set_n_int(args.n_int)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local_rank = world_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)
     return run_ours(args, world, rank, local_rank)
