@@ -8,13 +8,18 @@ real FFT -> 1024 channels, 8192 spectra (~0.25 s of sky data, 1.07 GB of
 samples), incoherent beam over 32 antennas and coherent beam over antennas
 0-29, 528 baselines x 4 products accumulated in FP32.  Inputs are seeded
 synthetic streams resident in HBM; at 1.07 GB per step they are larger than L2.
+The timed step's X-engine is the FP32 form on the tcgen05 tensor cores
+(CORR_FP32TC: FP32 spectra as exact fp16 hi + lo pairs, error within the FP32
+bound); --xmode fp32 times the plain CUDA-core FP32 form instead, and both are
+reported.
 
 value   antenna-samples/s over all ranks (device-resident input)
 e2e     the same through corr_push_samples from pinned host memory plus the
         read-back of visibilities and beams, copies inside the timed region
 The JSON line also carries the real-time factor, the per-stage times, the
-roofline of the dominant kernel, the int8 / FP16 tensor-core forms of the
-X-engine (same data) with their speedups, clocks seen during the timed
+roofline of the dominant kernel, every form of the X-engine (plain FP32 on CUDA
+cores, FP32 / int8 / FP16 on tensor cores, same data) with its speedup over the
+plain FP32 form, clocks seen during the timed
 region and the FP64 oracle timed on a bounded sample of the same workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -49,9 +54,16 @@ CONFIG = {
     "workload": "GMRT-scale FP32 FX correlator + beamformer: 32 ant x 2 pol int8 at 66.67 MS/s, "
                 "2048-pt FFT -> 1024 ch, 8192 spectra/integration, 528 baselines x 4 products, "
                 "incoherent (32 ant) + coherent (30 ant) beams",
-    "n_ant": N_ANT, "n_pol": N_POL, "n_fft": N_FFT, "n_int": N_INT, "xmode": "fp32",
+    "n_ant": N_ANT, "n_pol": N_POL, "n_fft": N_FFT, "n_int": N_INT, "xmode": "fp32tc",
     "l2": "inputs larger than L2 (1.07 GB of samples per step)",
     "parallelism": "time slices across ranks (replicas), no data-path collective",
+}
+FORMS = {
+    "fp32": "plain FP32: FP32 spectra, X-engine FP32 multiply-adds on the CUDA cores",
+    "fp32tc": "FP32 spectra held as fp16 hi + lo planes (v = hi + lo to 2^-22 |v|), X-engine on tcgen05: "
+              "H H^T in 128-frame FP32 chunks, H L^T + L H^T in a separate accumulator; FP32 accuracy bound",
+    "i8": "per-channel scaled int8 requantisation, exact integer X-engine on tcgen05",
+    "f16": "per-channel scaled FP16 requantisation, X-engine on tcgen05 with FP32 accumulation",
 }
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -171,7 +183,7 @@ def step_samples():
 def stage_roofline(stage, mode, ms, pk):
     """(bound, achieved, peak, unit, algorithmic amount per launch) of one kernel."""
     if stage == "fengine":
-        out_b = N_CHAN * N_INT * 2 * N_IN * (4 if mode == "fp32" else 2)
+        out_b = N_CHAN * N_INT * 2 * N_IN * (4 if mode in ("fp32", "fp32tc") else 2)
         alg = N_IN * N_INT * N_FFT + out_b + 2 * N_INT * N_CHAN * 4
         return "hbm", alg / (ms * 1e-3) / 1e9, pk["hbm_gbs"], "GB/s", alg
     if stage == "xengine" and mode == "fp32":
@@ -179,14 +191,15 @@ def stage_roofline(stage, mode, ms, pk):
         alg = 8.0 * N_CHAN * N_INT * N_IN * (N_IN + 1) / 2
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
         return "alu", alg / (ms * 1e-3) / 1e12, peak, "TFLOP/s", alg
-    # tensor-core X-engine: the fp16 operand read from HBM bounds it
-    alg = N_CHAN * N_INT * 2 * N_IN * 2 + N_CHAN * N_BL * 4 * 8
+    # tensor-core X-engine: the fp16 operand planes read from HBM bound it (two for fp32tc)
+    planes = 2 if mode == "fp32tc" else 1
+    alg = N_CHAN * N_INT * 2 * N_IN * 2 * planes + N_CHAN * N_BL * 4 * 8
     return "hbm", alg / (ms * 1e-3) / 1e9, pk["hbm_gbs"], "GB/s", alg
 
 
-def tensor_fraction(ms, pk):
-    """Executed tcgen05 flops (full 128x128 Gram per channel) vs the dense fp16 peak."""
-    executed = 2.0 * N_CHAN * N_INT * (2 * N_IN) ** 2
+def tensor_fraction(ms, pk, mmas=1):
+    """Executed tcgen05 flops (full 128x128 Gram per channel, `mmas` products) vs the dense fp16 peak."""
+    executed = 2.0 * mmas * N_CHAN * N_INT * (2 * N_IN) ** 2
     return executed / (ms * 1e-3) / 1e12 / pk["bf16_tflops_sustained"]
 
 
@@ -263,7 +276,7 @@ def run_reference(args, world, rank):
 
 # -------------------------------------------------------------------- ours
 
-def run_e2e(args, corr, torch, dist, s, coh, world):
+def run_e2e(args, corr, torch, dist, s, coh, world, xmode):
     """The public streaming path: samples pushed from pinned host memory (corr_push_samples,
     two sample rings so the copy of integration j + 1 overlaps the correlation of j) and every
     integration's visibilities and beams copied back into a ring of pinned host slots
@@ -279,6 +292,7 @@ def run_e2e(args, corr, torch, dist, s, coh, world):
     he = corr.corr_create(N_ANT, N_POL, N_FFT, N_INT)
     corr.corr_set_delays(he, s.delay, s.phi0, s.rate)
     corr.corr_set_beam_weights(he, None, None, None, coh)
+    corr.corr_set_mode(he, xmode, 0, 1)
     corr.corr_set_output_ring(he, hv.numpy(), hb.numpy(), n_slots)
     seq = 0
     corr.corr_push_samples(he, hx0.numpy(), seq)            # first integration + the delay overlap
@@ -513,42 +527,52 @@ def run_ours(args, world, rank, local_rank):
         return ms, st / max(n, 1), clocks
 
     K, W = args.steps, args.warmup
-    ms, st, clocks = timed(corr.CORR_FP32, K, W, sample_clocks=True)
+    all_forms = {"fp32": corr.CORR_FP32, "fp32tc": corr.CORR_FP32TC, "i8": corr.CORR_I8, "f16": corr.CORR_F16}
+    ms, st, clocks = timed(all_forms[args.xmode], K, W, sample_clocks=True)
     value = job_rate(world, K * step_samples(), ms * 1e-3)
     stage_names = ["phasor_setup", "fengine", "xengine", "beam_average"]
 
-    # precision forms of the X-engine on the same data (scales from this FP32 integration's autos)
+    # the other forms of the X-engine on the same data (scales for i8 / f16 from the last
+    # integration's autos); speedups are against the plain CUDA-core FP32 form
     corr.corr_set_scales(h, None)
-    modes = {}
-    for name, m in (() if args.no_extras else (("i8", corr.CORR_I8), ("f16", corr.CORR_F16))):
+    runs = {args.xmode: (ms / K, st)}
+    for name, m in (() if args.no_extras else all_forms.items()):
+        if name in runs:
+            continue
         k2 = max(10, min(K, 100))
         ms2, st2, _ = timed(m, k2, 3)
-        modes[name] = {
-            "value": job_rate(world, k2 * step_samples(), ms2 * 1e-3), "ms_per_step": ms2 / k2,
-            "stage_ms": dict(zip(stage_names, [round(v, 4) for v in st2])),
-            "xengine_speedup_vs_fp32": st[2] / st2[2], "step_speedup_vs_fp32": (ms / K) / (ms2 / k2),
-            "xengine_tensor_frac_of_sustained_peak": tensor_fraction(st2[2], pk),
-        }
+        runs[name] = (ms2 / k2, st2)
+    modes = {}
+    for name, (step_ms, st2) in runs.items():
+        d = {"value": job_rate(world, step_samples(), step_ms * 1e-3), "ms_per_step": step_ms,
+             "stage_ms": dict(zip(stage_names, [round(v, 4) for v in st2]))}
+        if "fp32" in runs and name != "fp32":
+            d["xengine_speedup_vs_fp32"] = runs["fp32"][1][2] / st2[2]
+            d["step_speedup_vs_fp32"] = runs["fp32"][0] / step_ms
+        if name != "fp32":
+            d["xengine_tensor_frac_of_sustained_peak"] = tensor_fraction(st2[2], pk, 3 if name == "fp32tc" else 1)
         bound, ach, peak, unit, _ = stage_roofline("xengine", name, st2[2], pk)
-        modes[name]["xengine_roofline"] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-                                           "frac": ach / peak}
-    corr.corr_set_mode(h, corr.CORR_FP32, 0, 1)
+        d["xengine_roofline"] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak}
+        d["form"] = FORMS[name]
+        modes[name] = d
+    corr.corr_set_mode(h, all_forms[args.xmode], 0, 1)
 
     # end to end through the public API: pinned host samples in, visibilities + beams out
-    e2e = None if args.no_extras else run_e2e(args, corr, torch, dist, s, coh, world)
+    e2e = None if args.no_extras else run_e2e(args, corr, torch, dist, s, coh, world, all_forms[args.xmode])
 
-    # roofline of the dominant kernel of the FP32 step
+    # roofline of the dominant kernel of the timed step
     dom = 1 if st[1] >= st[2] else 2
     kname = {1: "fengine", 2: "xengine"}[dom]
-    bound, ach, peak, unit, alg = stage_roofline(kname, "fp32", st[dom], pk)
-    kern_id = {"fengine": "fengine_kernel", "xengine": "xengine_fp32_kernel"}[kname]
+    bound, ach, peak, unit, alg = stage_roofline(kname, args.xmode, st[dom], pk)
+    kern_id = "fengine_kernel" if kname == "fengine" else \
+        ("xengine_fp32_kernel" if args.xmode == "fp32" else "xengine_tc_kernel")
     roofline = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
                 "traffic": traffic_for(kern_id), "kernel": kern_id,
                 "algorithmic_per_launch": alg, "peak_source": pk["source"],
                 "avg_launch_ms": st[dom]}
     stages = {}
     for i, nme in ((1, "fengine"), (2, "xengine")):
-        b, a, p, u, _ = stage_roofline(nme, "fp32", st[i], pk)
+        b, a, p, u, _ = stage_roofline(nme, args.xmode, st[i], pk)
         stages[nme] = {"ms": st[i], "bound": b, "achieved": a, "peak": p, "unit": u, "frac": a / p}
     stages["phasor_setup"] = {"ms": st[0]}
 
@@ -571,9 +595,9 @@ def run_ours(args, world, rank, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (seeded Gaussian sky + noise + tones, GMRT shapes)",
-            "config": CONFIG,
+            "config": {**CONFIG, "xmode": args.xmode},
             "rtf": value / (world * N_IN * SAMPLE_RATE),
-            "xengine_frac_of_fp32_peak": stages["xengine"]["frac"],
+            "xengine_frac_of_fp32_peak": modes["fp32"]["xengine_roofline"]["frac"] if "fp32" in modes else None,
             "roofline": roofline, "stages": stages, "precision_forms": modes,
             "batched_subarrays": batch, "learned_rfi": rfi,
             "e2e": e2e, "gpu_launches": 3 * K, "clocks": clocks, "cpu_baseline": cpu,
@@ -595,6 +619,8 @@ def main():
                     help="time only the FP32 step (no precision forms, no end-to-end leg); for profiling runs")
     ap.add_argument("--leg", choices=("all", "batched", "rfi"), default="all",
                     help="run only the batched sub-array leg or only the learned-RFI leg (profiling runs)")
+    ap.add_argument("--xmode", choices=("fp32tc", "fp32"), default="fp32tc",
+                    help="form of the timed step: FP32 on the tensor cores (default) or the plain CUDA-core FP32 form")
     ap.add_argument("--n-int", type=int, default=N_INT,
                     help="spectra per integration (default 8192, the GMRT-scale workload; smaller for profiling)")
     args = ap.parse_args()

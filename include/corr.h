@@ -24,7 +24,13 @@
  * channel) scales, q = clamp(rint(Y*s), +-127), and accumulates q_i conj(q_j)
  * exactly (integer result, bit-exact), then divides by s_i s_j.  CORR_F16
  * rounds Y*s to FP16 and accumulates in FP32.  Both run the X-engine on the
- * tcgen05 tensor cores.  Beams are always formed from the FP32 spectra.
+ * tcgen05 tensor cores.  CORR_FP32TC is the FP32 X-engine of CORR_FP32 moved
+ * to the tensor cores without losing FP32 accuracy: each FP32 value v = Y * 2^-e
+ * (e = log2(n_fft) - 8, so |v| < 2^15 for any int8 input) is stored as fp16
+ * hi = rn(v), lo = rn(v - hi), which holds v to 2^-22 |v|; the Gram is
+ * H H^T + H L^T + L H^T with exact fp16 products, accumulated in FP32 over
+ * 128-frame chunks that are added in FP32, then multiplied by 2^2e.  No scales
+ * are needed.  Beams are always formed from the FP32 spectra.
  *
  * Ownership: the library allocates and owns every device buffer and one CUDA
  * stream per handle; callers own every host buffer and any device buffer they
@@ -58,7 +64,7 @@ enum {
     CORR_E_TIMEOUT = -8    /* a kernel's bounded wait ran out; results invalid */
 };
 
-enum { CORR_FP32 = 0, CORR_I8 = 1, CORR_F16 = 2 };  /* X-engine precision */
+enum { CORR_FP32 = 0, CORR_I8 = 1, CORR_F16 = 2, CORR_FP32TC = 3 };  /* X-engine precision */
 
 /* Create a correlator for n_ant antennas x n_pol (1 or 2) polarisations
  * (n_in = n_ant * n_pol <= 128), an n_fft-point real FFT (power of two,
@@ -73,7 +79,8 @@ int corr_destroy(corr_t* h);
 const char* corr_last_error(void);
 
 /* Precision mode, polarisation products and beam time averaging.
- * xmode: CORR_FP32 | CORR_I8 | CORR_F16.  polmode must be 0 (all n_pol^2
+ * xmode: CORR_FP32 | CORR_I8 | CORR_F16 | CORR_FP32TC (the last three need
+ * n_in <= 128; CORR_FP32TC is not available in batches).  polmode must be 0 (all n_pol^2
  * products are produced).  beam_avg >= 1 must divide n_int. */
 int corr_set_mode(corr_t* h, int xmode, int polmode, int beam_avg);
 
@@ -97,7 +104,8 @@ int corr_set_beam_weights(corr_t* h, const float* gain, const float* theta,
 
 /* Frames per operand stage of the tensor-core X-engine (a tile-shape choice, normally
  * made by corr_batch_tune): 0 = the largest that fits, else a power of two in
- * [16, 512] with (ks / 8) * 2 n_in * 16 <= 32768 bytes. */
+ * [16, 512] with (ks / 8) * 2 n_in * 16 <= 32768 bytes.  CORR_FP32TC stages carry
+ * two planes: there the stage used is min(ks, largest two-plane stage, 256). */
 int corr_set_xengine_stage(corr_t* h, int ks);
 
 /* Requantisation scales s [n_in][n_fft/2] for CORR_I8 / CORR_F16.  NULL
@@ -168,7 +176,8 @@ int corr_read_vis_int(corr_t* h, int32_t* out, int blocking);
 int corr_read_requant(corr_t* h, int k0, int nk, int8_t* q, float* scale);
 
 /* FP32 spectra Y of the last CORR_FP32 integration for channels k0..k0+nk-1,
- * out [n_in][n_int][nk] complex64 (re, im pairs). */
+ * out [n_in][n_int][nk] complex64 (re, im pairs).  After a CORR_FP32TC
+ * integration: (hi + lo) * 2^e, the values its X-engine multiplied. */
 int corr_read_spectra(corr_t* h, int k0, int nk, float* out);
 
 /* Device pointers of the result buffers of handle h (valid until destroy):

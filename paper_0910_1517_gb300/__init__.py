@@ -8,6 +8,7 @@ from . import corr  # noqa: F401
 from .corr import (  # noqa: F401
     CORR_F16,
     CORR_FP32,
+    CORR_FP32TC,
     CORR_I8,
     CorrError,
 )

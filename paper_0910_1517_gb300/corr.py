@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgb300corr.so")
 
-CORR_FP32, CORR_I8, CORR_F16 = 0, 1, 2
+CORR_FP32, CORR_I8, CORR_F16, CORR_FP32TC = 0, 1, 2, 3
 CODES = {0: "CORR_OK", -1: "CORR_E_INVAL", -2: "CORR_E_RANGE", -3: "CORR_E_AGAIN", -4: "CORR_E_DATALOSS",
          -5: "CORR_E_CUDA", -6: "CORR_E_NOMEM", -7: "CORR_E_STATE", -8: "CORR_E_TIMEOUT"}
 

@@ -33,7 +33,12 @@ struct XtSub {
     float2* vis;           // [n_chan][n_bl][n_pol^2]
     int2* vis_int;         // exact integer sums (int8-valued operands) or nullptr
     int exact;
-    int ks;                // frames per operand stage: power of two, 16..512, ks/8 * 2 n_in * 16 <= kStageMaxBytes
+    int ks;                // frames per operand stage: power of two, 16..512, planes * ks/8 * 2 n_in * 16 <= kStageMaxBytes
+    // two-plane FP32 form: spec holds hi, spec_lo lo (v = hi + lo); G = H H^T + H L^T + L H^T,
+    // multiplied by descale instead of divided by scale products.  nullptr: one plane.
+    const __half* spec_lo;
+    float descale;
+    int chunk;             // frames per TMEM accumulation chunk: power of two, multiple of ks
 };
 struct XtBatch {
     int n_sub;
@@ -43,7 +48,7 @@ struct XtBatch {
     unsigned* err;
 };
 bool xengine_tc_supported(int n_in);                 // 2 n_in <= 256
-int xengine_tc_max_ks(int n_in);                      // largest stage for the row count
+int xengine_tc_max_ks(int n_in, int planes = 1);     // largest stage for the row count
 size_t xengine_tc_smem();
 cudaError_t launch_xengine_tc_table(const XtBatch* dtab, int n_items, int n_sm, cudaStream_t s);
 

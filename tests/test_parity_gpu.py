@@ -8,6 +8,8 @@ Tolerances (the arithmetic behind them is in the design notes):
   CORR_I8      integer visibilities equal the oracle's int64 MAC on the GPU's own
                requantised spectra, bit for bit
   CORR_F16     normalised error vs FP64 on raw samples <= 2e-2 (reported)
+  CORR_FP32TC  the FP32 visibility bound above; beams bit-identical to CORR_FP32's;
+               the split spectra (hi + lo) 2^e within 2^-21 |Y| + 2^(e-24) of CORR_FP32's
 """
 import math
 
@@ -190,6 +192,60 @@ def test_f16_mode_accuracy(env, shape):
     corr.corr_destroy(h)
 
 
+@pytest.mark.parametrize("n_ant,n_pol,n_fft,n_int", [
+    (32, 2, 2048, 512),    # GMRT shape, four 128-frame accumulation chunks
+    (5, 2, 256, 48),       # ragged rows (R = 20), one short chunk, 3 F-engine tiles
+    (3, 1, 64, 16),        # smallest FFT and integration, one polarisation
+    (16, 2, 4096, 64),     # 4-frame F-engine CTAs: 8-byte half-row stores of both planes
+    (64, 2, 512, 272),     # 256 Gram rows: two work items per channel; ragged last chunk
+])
+def test_fp32tc_split_tensor_core_parity(env, n_ant, n_pol, n_fft, n_int):
+    torch, corr, orc = env
+    s = make_config(2, n_ant=n_ant, n_pol=n_pol, n_fft=n_fft, n_int=n_int, seed=5000 + n_fft + n_ant)
+    chans = sorted({c for c in C2_CHANS if c < n_fft // 2} | {n_fft // 2 - 1, n_fft // 4})
+    r32 = run_gpu(env, s, want_spec=(0, n_fft // 2))
+    rtc = run_gpu(env, s, mode=corr.CORR_FP32TC, want_spec=(0, n_fft // 2))
+    Y, V = oracle_all(orc, s, chans=chans)
+    e_v = vis_norm_error(rtc["V"][chans], V, s.n_ant, s.n_pol)
+    e_v32 = vis_norm_error(r32["V"][chans], V, s.n_ant, s.n_pol)
+    # the split planes hold the FP32 spectra to 2^-22 relative (subnormal lo: 2^-25 absolute, scaled)
+    e = int(round(math.log2(n_fft))) - 8
+    bound = 2.0 ** -21 * np.abs(r32["Y"]) + 2.0 ** (e - 24)
+    split_ok = np.all(np.abs(rtc["Y"].real - r32["Y"].real) <= bound) and \
+        np.all(np.abs(rtc["Y"].imag - r32["Y"].imag) <= bound)
+    print(f"{(n_ant, n_pol, n_fft, n_int)}: fp32tc vis {e_v:.2e} (CUDA-core fp32 {e_v32:.2e})")
+    assert split_ok
+    assert np.array_equal(rtc["B"], r32["B"])       # beams come from the same FP32 spectra
+    assert e_v <= FP32_TOL
+    for q in (rtc, r32):
+        corr.corr_destroy(q["h"])
+
+
+def test_fp32tc_mode_errors(env):
+    torch, corr, orc = env
+    h = corr.corr_create(4, 2, 256, 16)
+    try:
+        with pytest.raises(corr.CorrError) as ei:      # a batch member cannot switch to it
+            b = corr.corr_batch_create([h])
+            try:
+                corr.corr_set_mode(h, corr.CORR_FP32TC, 0, 1)
+            finally:
+                corr.corr_batch_destroy(b)
+        assert ei.value.code == -7
+        corr.corr_set_mode(h, corr.CORR_FP32TC, 0, 1)
+        with pytest.raises(corr.CorrError) as ei:      # nor can an FP32TC handle join a batch
+            corr.corr_batch_create([h])
+        assert ei.value.code == -1
+        with pytest.raises(corr.CorrError) as ei:      # power dumps need the FP32 layout
+            corr.corr_set_power_dump(h, 8)
+            s = make_config(1, n_fft=256, n_int=16)
+            xt, n = to_device(torch, s.x)
+            corr.corr_integrate_device(h, xt, n_avail=n, stream=torch.cuda.current_stream())
+        assert ei.value.code == -7
+    finally:
+        corr.corr_destroy(h)
+
+
 def test_streaming_push_matches_oracle_across_integrations(env):
     """Two consecutive integrations pushed from host memory in uneven chunks: the
     delay overlap carries over and the fringe phase follows the global frame count."""
@@ -284,4 +340,10 @@ def test_full_scale_fp32_sampled_channels(env, c2_full):
     print(f"full scale i8 vs FP64: {e_i8:.2e}")
     assert e_i8 <= 5e-2
     assert math.isfinite(e_i8)
+    # the FP32 X-engine on the tensor cores: 64 chunks of 128 frames, the same FP32 bound
+    r3 = run_gpu(env, s, mode=corr.CORR_FP32TC, handle=r["h"])
+    e_tc = vis_norm_error(r3["V"][FULL_CHANS], V, s.n_ant, s.n_pol)
+    print(f"full scale fp32tc vs FP64: {e_tc:.2e}")
+    assert e_tc <= FP32_TOL
+    assert np.array_equal(r3["B"], r["B"])
     corr.corr_destroy(r["h"])
