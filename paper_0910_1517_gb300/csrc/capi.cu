@@ -104,12 +104,11 @@ int upload_beam_weights(corr* h, const float* gain, const float* theta, const ui
     return CORR_OK;
 }
 
-// F-engine output mode of an X-engine precision mode
+// F-engine output mode of an X-engine precision mode (CORR_FP32TC reads the FP32 spectra)
 int fe_mode(int xmode) {
     switch (xmode) {
         case CORR_I8: return OUT_I8;
         case CORR_F16: return OUT_F16;
-        case CORR_FP32TC: return OUT_F16X2;
         default: return OUT_FP32;
     }
 }
@@ -119,12 +118,6 @@ int split_exp(const corr* h) {
     int e = -8;
     for (int n = h->n_fft; n > 1; n >>= 1) ++e;
     return e;
-}
-
-// The lo plane of CORR_FP32TC sits right after the hi plane in the spectra buffer (two fp16
-// planes of 2 n_in rows fit in the FP32 layout's n_chan * n_int * rows_fp32(n_in) floats).
-void* spec_lo_plane(const corr* h) {
-    return static_cast<__half*>(h->d_spec) + static_cast<size_t>(h->n_chan) * h->n_int * 2 * h->n_in;
 }
 
 constexpr int kSplitChunk = 128;   // frames per TMEM accumulation chunk of CORR_FP32TC
@@ -141,7 +134,8 @@ int max_int_delay(const corr* h) {
 int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, int64_t g0, cudaStream_t s) {
     if ((h->xmode == CORR_I8 || h->xmode == CORR_F16) && !h->scales_set)
         return fail(CORR_E_STATE, "CORR_I8 / CORR_F16 need requantisation scales (corr_set_scales)");
-    if (h->dump > 0 && h->xmode != CORR_FP32) return fail(CORR_E_STATE, "power dumps need the CORR_FP32 spectra");
+    if (h->dump > 0 && h->xmode != CORR_FP32 && h->xmode != CORR_FP32TC)
+        return fail(CORR_E_STATE, "power dumps need the FP32 spectra (CORR_FP32 or CORR_FP32TC)");
     const int nd = h->n_ant;
     // stage the model in a pinned slot no queued copy still reads (integrations may be queued
     // back to back while earlier ones run)
@@ -174,8 +168,6 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
     fp.ginc = h->d_ginc;
     fp.scale = h->d_scale;
     fp.spec = h->d_spec;
-    fp.spec_lo = spec_lo_plane(h);
-    fp.split_scale = std::ldexp(1.0f, -split_exp(h));
     fp.beams = h->d_beams_raw;
     fp.tw = h->d_tw;
     fp.err = h->d_err;
@@ -200,7 +192,8 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
     if (h->xmode == CORR_FP32)
         CU(launch_xengine_fp32(xp, h->n_sm, s));
     else
-        CU(launch_xengine_tc_table(h->out_buf == 1 ? h->xtab_b1 : h->d_xtab, h->n_items, h->n_sm, s));
+        CU(launch_xengine_tc_table(h->out_buf == 1 ? h->xtab_b1 : h->d_xtab, h->n_items, h->n_sm, s,
+                                   h->xmode == CORR_FP32TC));
     if (h->dump > 0) {
         CU(launch_power_dumps(static_cast<const float*>(h->d_spec), h->n_in, h->n_chan, h->n_int, h->dump,
                               h->d_power, s));
@@ -227,13 +220,18 @@ gbx::XtSub gbx::xt_sub_of(const corr* h) {
     x.vis = h->d_vis;
     x.vis_int = h->xmode == CORR_I8 ? h->d_vis_int : nullptr;
     x.exact = h->xmode == CORR_I8 ? 1 : 0;
-    const bool two = h->xmode == CORR_FP32TC;
-    const int max_ks = xengine_tc_max_ks(h->n_in, two ? 2 : 1);
-    x.ks = h->ks > 0 ? std::min(h->ks, max_ks) : max_ks;
-    x.spec_lo = two ? static_cast<const __half*>(spec_lo_plane(h)) : nullptr;
-    x.descale = std::ldexp(1.0f, 2 * split_exp(h));
-    x.chunk = two ? kSplitChunk : 1024;
-    if (two) x.ks = std::min(x.ks, kSplitChunk);
+    if (h->xmode == CORR_FP32TC) {
+        const int max_ks = std::min(xengine_tc_ks_fp32(h->n_in), kSplitChunk);
+        x.ks = h->ks > 0 ? std::min(h->ks, max_ks) : max_ks;
+        x.spec32 = static_cast<const float*>(h->d_spec);
+        x.split_scale = std::ldexp(1.0f, -split_exp(h));
+        x.descale = std::ldexp(1.0f, 2 * split_exp(h));
+        x.chunk = kSplitChunk;
+    } else {
+        const int max_ks = xengine_tc_max_ks(h->n_in);
+        x.ks = h->ks > 0 ? std::min(h->ks, max_ks) : max_ks;
+        x.chunk = 1024;
+    }
     return x;
 }
 
@@ -789,26 +787,6 @@ int corr_read_spectra(corr_t* h, int k0, int nk, float* out) {
     if (h->last_mode != CORR_FP32 && h->last_mode != CORR_FP32TC)
         return fail(CORR_E_STATE, "last integration was not CORR_FP32 or CORR_FP32TC");
     if (!out || k0 < 0 || nk < 0 || k0 + nk > h->n_chan) return fail(CORR_E_INVAL, "channel range");
-    if (h->last_mode == CORR_FP32TC) {   // (hi + lo) * 2^e from the two fp16 planes
-        const int R = 2 * h->n_in, ntb = h->n_int / kTbHalf;
-        const size_t per_ch = static_cast<size_t>(h->n_int) * R;
-        std::vector<__half> hi(per_ch * nk), lo(per_ch * nk);
-        CU(cudaMemcpy(hi.data(), static_cast<const __half*>(h->d_spec) + per_ch * k0, hi.size() * sizeof(__half),
-                      cudaMemcpyDeviceToHost));
-        CU(cudaMemcpy(lo.data(), static_cast<const __half*>(spec_lo_plane(h)) + per_ch * k0,
-                      lo.size() * sizeof(__half), cudaMemcpyDeviceToHost));
-        const int e = split_exp(h);
-        for (int c = 0; c < nk; ++c)
-            for (int kb = 0; kb < ntb; ++kb)
-                for (int r = 0; r < R; ++r)
-                    for (int f = 0; f < kTbHalf; ++f) {
-                        const size_t q = ((static_cast<size_t>(c) * ntb + kb) * R + r) * kTbHalf + f;
-                        const int i = r / 2, cc = r % 2, t = kb * kTbHalf + f;
-                        out[((static_cast<size_t>(i) * h->n_int + t) * nk + c) * 2 + cc] =
-                            std::ldexp(__half2float(hi[q]) + __half2float(lo[q]), e);
-                    }
-        return CORR_OK;
-    }
     const int tb = tb_fp32(h->n_chan);
     const int R = 2 * h->n_in, Rp = rows_fp32(h->n_in), ntb = h->n_int / tb;
     const size_t per_ch = static_cast<size_t>(ntb) * Rp * tb;

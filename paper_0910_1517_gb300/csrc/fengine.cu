@@ -168,8 +168,7 @@ struct Epi {
     // fp16 runs of 8 frames from 4-frame CTAs (n_chan 2048): the two CTAs of a cluster (consecutive
     // frame blocks) trade halves of their channels through distributed shared memory, so that each
     // writes whole 32-byte pieces (8 frames x re, im) of its half of the channels
-    // (the split pair of planes keeps 4-frame runs: twice the exchange would not fit)
-    static constexpr bool kPair = (M == 2048 && (MODE == OUT_I8 || MODE == OUT_F16));
+    static constexpr bool kPair = (M == 2048 && MODE != OUT_FP32);
     static_assert(L % TB == 0 || L < TB, "whole K-block runs, or part of one when F < TB");
     static constexpr int NP = kE / (2 * L);                // channel pairs per thread
     static constexpr int TPG = L * P::T;                   // threads per frame group
@@ -347,12 +346,9 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
         if (tid < 32 && it + 1 < n_iter) issue(it + 1);
         const float g2 = p.ginc[a];
         float scv[2 * NP];           // requantisation scales of this thread's channels
-        if constexpr (MODE == OUT_I8 || MODE == OUT_F16) {
+        if constexpr (MODE != OUT_FP32) {
 #pragma unroll
             for (int c = 0; c < 2 * NP; ++c) scv[c] = p.scale[static_cast<int64_t>(i) * M + chs[c]];
-        } else if constexpr (MODE == OUT_F16X2) {
-#pragma unroll
-            for (int c = 0; c < 2 * NP; ++c) scv[c] = p.split_scale;
         }
         if (!mbar_wait(&bar[it & 1], (it >> 1) & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
         const int64_t s0 = static_cast<int64_t>(t0) * N + Ds[a];
@@ -483,39 +479,6 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
                     }
                     put(odd ? chp : chs[c], d0);
                     put(odd ? chs[c] : chp, d1);
-                }
-            } else if constexpr (MODE == OUT_F16X2) {
-                // hi = rn16(v), lo = rn16(v - hi): v - hi is exact, so hi + lo is v to 2^-22 |v|
-                __half hr[L], hi[L], lr[L], li[L];
-#pragma unroll
-                for (int l = 0; l < L; ++l) {
-                    const float xr = yc[l].x * scv[c], xi = yc[l].y * scv[c];
-                    hr[l] = __float2half_rn(xr);
-                    hi[l] = __float2half_rn(xi);
-                    lr[l] = __float2half_rn(xr - __half2float(hr[l]));
-                    li[l] = __float2half_rn(xi - __half2float(hi[l]));
-                }
-                const int64_t off = blk + 2 * i * TB + (t0 + fg * L) % TB;
-                __half* oh = static_cast<__half*>(p.spec) + off;
-                __half* ol = static_cast<__half*>(p.spec_lo) + off;
-                if constexpr (L == 8) {
-                    uint32_t u[8], w[8];
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        u[m] = pack_half2(hr[2 * m], hr[2 * m + 1]);
-                        u[4 + m] = pack_half2(hi[2 * m], hi[2 * m + 1]);
-                        w[m] = pack_half2(lr[2 * m], lr[2 * m + 1]);
-                        w[4 + m] = pack_half2(li[2 * m], li[2 * m + 1]);
-                    }
-                    st_global_v8(oh, u);
-                    st_global_v8(ol, w);
-                } else {
-                    // 4-frame CTAs (n_chan 2048): half of each 16-byte row, re and im rows apart
-                    static_assert(L == 4, "split runs of 8 or 4 frames");
-                    *reinterpret_cast<uint2*>(oh) = make_uint2(pack_half2(hr[0], hr[1]), pack_half2(hr[2], hr[3]));
-                    *reinterpret_cast<uint2*>(oh + TB) = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
-                    *reinterpret_cast<uint2*>(ol) = make_uint2(pack_half2(lr[0], lr[1]), pack_half2(lr[2], lr[3]));
-                    *reinterpret_cast<uint2*>(ol + TB) = make_uint2(pack_half2(li[0], li[1]), pack_half2(li[2], li[3]));
                 }
             } else {
                 __half hr[L], hi[L];
@@ -820,7 +783,6 @@ cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s) {
         case OUT_FP32: return launch_mode<OUT_FP32>(p, s);
         case OUT_I8: return launch_mode<OUT_I8>(p, s);
         case OUT_F16: return launch_mode<OUT_F16>(p, s);
-        case OUT_F16X2: return launch_mode<OUT_F16X2>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }

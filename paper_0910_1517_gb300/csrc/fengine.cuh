@@ -7,10 +7,7 @@
 
 namespace gbx {
 
-// OUT_F16X2: FP32 spectra as an exact-to-2^-22 pair of fp16 planes for the tensor cores:
-// v = Y * split_scale (a power of two, so the scaling is exact), hi = rn16(v), lo = rn16(v - hi)
-// (v - hi is exact in FP32), hi in `spec` and lo in `spec_lo`, both in the fp16 layout.
-enum OutMode : int { OUT_FP32 = 0, OUT_I8 = 1, OUT_F16 = 2, OUT_F16X2 = 3 };
+enum OutMode : int { OUT_FP32 = 0, OUT_I8 = 1, OUT_F16 = 2 };
 
 // Spectra hand-off layout ("K-block layout"), shared by every X-engine:
 //   S[k][kb][r][TB]   k channel, kb = t / TB, r = 2*i + c (c = 0 re, 1 im), TB = t % TB
@@ -48,8 +45,6 @@ struct FeParams {
     const float* ginc;     // [n_ant] incoherent weight g_a^2, 0 if unselected
     const float* scale;    // [n_in][n_chan] requantisation scales (I8 / F16)
     void* spec;            // spectra in the K-block layout
-    void* spec_lo;         // OUT_F16X2: the low fp16 plane (same layout), else unused
-    float split_scale;     // OUT_F16X2: power-of-two scale applied before the split
     float* beams;          // [2][n_int][n_chan] raw-resolution beams (0 inc, 1 coh)
     const float2* tw;      // FFT twiddles laid out by fengine_twiddles()
     unsigned* err;

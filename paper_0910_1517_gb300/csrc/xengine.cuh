@@ -26,6 +26,7 @@ cudaError_t launch_xengine_fp32(const XParams& p, int n_sm, cudaStream_t s);
 // table of sub-arrays and a cost-ordered list of (sub-array, channel, row block) items.
 constexpr int kMaxSubX = 8;
 constexpr int kStageMaxBytes = 32768;        // bytes of one operand stage (ks/8 K-blocks x 2 n_in rows x 16 B)
+constexpr int kStage2Bytes = 32768;          // FP32 form: bytes of one FP32 stage (ks x rows_fp32(n_in) x 4 B)
 struct XtSub {
     const __half* spec;    // [k][kb][2 n_in][8] fp16 K-block layout
     int n_ant, n_pol, n_in, n_chan, n_int;
@@ -33,14 +34,17 @@ struct XtSub {
     float2* vis;           // [n_chan][n_bl][n_pol^2]
     int2* vis_int;         // exact integer sums (int8-valued operands) or nullptr
     int exact;
-    int ks;                // frames per operand stage: power of two, 16..512, planes * ks/8 * 2 n_in * 16 <= kStageMaxBytes
-    // two-plane FP32 form: spec holds hi, spec_lo lo (v = hi + lo); G = H H^T + H L^T + L H^T,
-    // multiplied by descale instead of divided by scale products.  nullptr: one plane.
-    const __half* spec_lo;
-    float descale;
+    int ks;                // frames per operand stage: power of two, 16..512, ks/8 * 2 n_in * 16 <= kStageMaxBytes
+                           // (FP32 form: ks * rows_fp32(n_in) * 4 <= kStage2Bytes)
+    // FP32 form on the tensor cores: spec32 holds the FP32 spectra (the CUDA-core engine's
+    // layout); each stage is split on chip into fp16 hi + lo planes of v = Y * split_scale, and
+    // G = H H^T + H L^T + L H^T is multiplied by descale instead of divided by scale products.
+    // nullptr: spec holds one fp16 plane.
+    const float* spec32;
+    float split_scale, descale;
     int chunk;             // frames per TMEM accumulation chunk: power of two, multiple of ks
 };
-struct XtBatch {
+struct XtBatch {          // (the FP32 form, spec32 set, runs alone: launch with fp32_in)
     int n_sub;
     XtSub sub[kMaxSubX];
     int n_items;
@@ -48,8 +52,9 @@ struct XtBatch {
     unsigned* err;
 };
 bool xengine_tc_supported(int n_in);                 // 2 n_in <= 256
-int xengine_tc_max_ks(int n_in, int planes = 1);     // largest stage for the row count
+int xengine_tc_max_ks(int n_in);                      // largest fp16 stage for the row count
+int xengine_tc_ks_fp32(int n_in);                     // largest FP32-form stage (FP32 slot <= kStage2Bytes)
 size_t xengine_tc_smem();
-cudaError_t launch_xengine_tc_table(const XtBatch* dtab, int n_items, int n_sm, cudaStream_t s);
+cudaError_t launch_xengine_tc_table(const XtBatch* dtab, int n_items, int n_sm, cudaStream_t s, bool fp32_in = false);
 
 }  // namespace gbx

@@ -15,10 +15,12 @@
 // columns 128-255).  A persistent CTA walks a cost-ordered item list; several
 // sub-arrays of different sizes share one launch.
 //
-// Roles (10 warps): warp 0 streams stages in (and owns the TMEM allocation),
-// warp 1 issues tcgen05.mma from one thread, warps 2-9 drain the accumulators
-// (warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. Gram rows, and the column half
-// (w - 2) / 4 of them).
+// Roles: warp 0 streams stages in (and owns the TMEM allocation), warp 1 issues
+// tcgen05.mma from one thread.  One-plane forms (10 warps): warps 2-9 drain the
+// accumulators (warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. Gram rows, and
+// the column half (w - 2) / 4 of them; 168 registers a thread hold the running
+// sums).  FP32 form (16 warps, 128 registers): warps 2-5 drain (all columns of
+// their lanes, running sums in TMEM), warps 6-15 convert the FP32 stages.
 // Accumulation is chunked: every `chunk` frames the FP32 accumulator is drained
 // and added into a running sum.  Items with N <= 128 rotate over four 128-column
 // accumulators (the MMAs run up to three chunks ahead of the drain) and keep the
@@ -29,16 +31,20 @@
 // 16,516,096 < 2^24, so the FP32 accumulator is exact and the running sum is kept
 // as int32: the result equals the integer MAC.
 //
-// Two-plane FP32 form: each FP32 value v (scaled by a power of two) arrives as
-// fp16 hi + lo with |v - hi - lo| <= 2^-22 |v|.  Every stage carries both planes
-// and each 16-frame step issues three MMAs, H H^T + H L^T + L H^T (the dropped
-// L L^T is below 2^-22 of the product).  fp16 x fp16 products are exact in FP32,
-// but the tensor core's FP32 accumulation drops low bits of every partial sum, a
+// FP32 form: the stages hold FP32 spectra in the CUDA-core engine's layout; ten
+// converter warps split each FP32 value v (scaled by a power of two) into fp16
+// hi (v rounded to 11 significant bits) and lo = v - hi rounded to fp16, so
+// |v - hi - lo| <= 2^-22 |v|, and write both planes as canonical operand tiles;
+// each 16-frame step then issues three MMAs, H H^T + H L^T + L H^T (the dropped
+// L L^T is below 2^-22 of the product).  The F-engine thus writes FP32 once and
+// the X-engine reads it once.  fp16 x fp16 products are exact in FP32, but the
+// tensor core's FP32 accumulation drops low bits of every partial sum, a
 // loss that grows with the accumulator's size and the number of steps.  So the
 // dominant H H^T term is accumulated in 128-frame chunks that the CUDA cores add
-// in FP32, while the cross terms, 2^-11 of it, go to a separate accumulator
-// (columns 384-511) over the whole integration: narrow items then rotate over
-// three chunk accumulators.
+// in FP32, while the cross terms, 2^-11 of it, go to a separate accumulator over
+// the whole integration: narrow items then alternate two chunk accumulators
+// (columns 0-255), keep the cross terms in columns 256-383 and the running sums
+// in columns 384-511.
 #include "common.cuh"
 #include "fengine.cuh"
 #include "xengine.cuh"
@@ -46,34 +52,50 @@
 namespace gbx {
 namespace {
 
-constexpr int kWarps = 10;
-constexpr int kEpiThreads = (kWarps - 2) * 32;
-constexpr int kThreads = kWarps * 32;
-constexpr int kStages = 5;
+constexpr int kWarps1 = 10;                   // one-plane forms
+constexpr int kWarps2 = 16;                   // FP32 form
+constexpr int kEpiThreads1 = 8 * 32;          // drain threads, one-plane forms
+constexpr int kEpiThreads2 = 4 * 32;          // drain threads, FP32 form
+constexpr int kConvWarp0 = 6;                 // FP32 form: first converter warp
+constexpr int kConvWarps = kWarps2 - kConvWarp0;
+constexpr int kConvThreads = kConvWarps * 32;
+constexpr int kStages = 5;                    // fp16 operand slots (one-plane forms)
 constexpr int kSlot = kStageMaxBytes + 2048;  // rows past R stay in bounds
 constexpr int kTailSlack = 32768;
+// FP32 form: stages of kStage2Bytes of FP32 each, five in flight.  An operand slot takes ks * 2 n_in * 4 bytes plus the rows the
+// 128-row MMA reads past R; ks * rows_fp32(n_in) * 4 <= kStage2Bytes bounds that by
+// kStage2Bytes + (128 - 64) * 16 (R < 64 leaves more room).
+constexpr int kOpStages2 = 2;                 // operand slots ...
+constexpr int kF32Stages = 5;                 // ... and the FP32 slots after them
+constexpr int kSlot2 = kStage2Bytes + 1024;
+constexpr int kSmemBytes = kOpStages2 * kSlot2 + kF32Stages * kStage2Bytes;
+static_assert(kStages * kSlot + kTailSlack <= kSmemBytes && kSmemBytes <= 227 * 1024 - 1024, "shared memory");
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColRun = 256;             // running-sum columns of wide items
 constexpr int kAccBufs = 4;                   // 128-column accumulators of narrow items
-constexpr uint32_t kColX = 384;               // two-plane narrow items: the cross-term accumulator
-constexpr int kXBit = 4;                      // its parity bit in the phase words
+constexpr uint32_t kColX = 256;               // FP32-form narrow items: the cross-term accumulator
+constexpr uint32_t kColRun2 = 384;            // FP32-form narrow items: the running sums
+constexpr int kXBit = 4;                      // the cross-term accumulator's parity bit in the phase words
 
 struct Shared {
-    uint64_t full[kStages];
-    uint64_t empty[kStages];
+    uint64_t full[kStages];       // operand slot ready (bulk copy landed, or converted)
+    uint64_t empty[kStages];      // operand slot consumed by the MMAs
+    uint64_t f32full[kF32Stages];   // FP32 slot landed
+    uint64_t f32empty[kF32Stages];  // FP32 slot converted
     uint64_t accf[kAccBufs];
     uint64_t acce[kAccBufs];
     uint64_t xf;                  // cross-term accumulator complete (MMA -> epilogue)
     uint64_t xe;                  // cross-term accumulator drained (epilogue -> MMA)
     uint32_t taddr;
     int abort_flag;
-    int consumed;
+    int consumed;                 // stages whose bulk copies the consumer has seen land
 };
 
 struct ItemGeo {
     int sub, k, a0, b0, N, R, ntb, n_stage, n_chunk, nkb_stage;
-    bool dbl;      // N <= 128: rotating 128-column accumulators, running sums in registers
-    bool sep;      // dbl and two planes: cross terms in their own accumulator
+    int Rp, tb32, ntb32;   // FP32 form: padded rows, frames per FP32 K-block, FP32 K-blocks per channel
+    bool dbl;      // N <= 128: rotating 128-column accumulators
+    bool sep;      // dbl and FP32 form: cross terms in their own accumulator, TMEM running sums
     int nbuf;      // accumulators the item rotates over
 };
 
@@ -87,9 +109,12 @@ __device__ __forceinline__ ItemGeo item_geo(const XtBatch& t, int it) {
     g.a0 = 128 * e.z;
     g.b0 = (g.R > 128) ? g.a0 : 0;
     g.N = ((g.R - g.b0 + 15) / 16) * 16;
+    g.Rp = rows_fp32(s.n_in);
+    g.tb32 = tb_fp32(s.n_chan);
+    g.ntb32 = s.n_int / g.tb32;
     g.dbl = g.N <= 128;
-    g.sep = g.dbl && s.spec_lo != nullptr;
-    g.nbuf = !g.dbl ? 1 : (g.sep ? 3 : kAccBufs);
+    g.sep = g.dbl && s.spec32 != nullptr;
+    g.nbuf = !g.dbl ? 1 : (g.sep ? 2 : kAccBufs);
     g.ntb = s.n_int / kTbHalf;
     g.nkb_stage = s.ks / kTbHalf;
     g.n_stage = (s.n_int + s.ks - 1) / s.ks;
@@ -108,26 +133,28 @@ __device__ __forceinline__ uint32_t chunk_add(int exact, bool have, uint32_t run
     return __float_as_uint(have ? __uint_as_float(run) + x : x);
 }
 
-// Final sums of Gram row `row`, columns b0 + j0 .. b0 + j0 + 31 (every lane of the warp calls it):
-// rows 2i and 2i+1 sit in adjacent lanes.  The even lane writes input pairs (i, j) for the first 8
-// column pairs of the piece and the odd lane for the last 8; per column pair each lane sends its
-// partner the two sums the partner lacks.
+// Final sums of Gram row `row`, columns b0 + j0 .. b0 + j0 + W - 1 (every lane of the warp calls
+// it): rows 2i and 2i+1 sit in adjacent lanes.  The even lane writes input pairs (i, j) for the
+// first W/4 column pairs of the piece and the odd lane for the last W/4; per column pair each lane
+// sends its partner the two sums the partner lacks.
+template <int W>
 __device__ __forceinline__ void write_piece(const XtSub& s, const ItemGeo& ig, int row, int j0,
-                                            const uint32_t (&run)[32]) {
+                                            const uint32_t (&run)[W]) {
+    constexpr int H = W / 2;                       // columns of the odd lane's half
     const int n_bl = s.n_ant * (s.n_ant + 1) / 2, npp = s.n_pol * s.n_pol;
     const bool odd = row & 1;
     const int i = row >> 1;
 #pragma unroll
-    for (int jh = 0; jh < 8; ++jh) {
-        const uint32_t r0 = __shfl_xor_sync(0xffffffffu, odd ? run[2 * jh] : run[2 * jh + 16], 1);
-        const uint32_t r1 = __shfl_xor_sync(0xffffffffu, odd ? run[2 * jh + 1] : run[2 * jh + 17], 1);
-        const int jp = jh + (odd ? 8 : 0);
+    for (int jh = 0; jh < W / 4; ++jh) {
+        const uint32_t r0 = __shfl_xor_sync(0xffffffffu, odd ? run[2 * jh] : run[2 * jh + H], 1);
+        const uint32_t r1 = __shfl_xor_sync(0xffffffffu, odd ? run[2 * jh + 1] : run[2 * jh + H + 1], 1);
+        const int jp = jh + (odd ? W / 4 : 0);
         const int j = ((ig.b0 + j0) >> 1) + jp;
         // G[2i][2j], G[2i][2j+1], G[2i+1][2j], G[2i+1][2j+1]
         const uint32_t g_r0c0 = odd ? r0 : run[2 * jh];
         const uint32_t g_r0c1 = odd ? r1 : run[2 * jh + 1];
-        const uint32_t g_r1c0 = odd ? run[2 * jh + 16] : r0;
-        const uint32_t g_r1c1 = odd ? run[2 * jh + 17] : r1;
+        const uint32_t g_r1c0 = odd ? run[2 * jh + H] : r0;
+        const uint32_t g_r1c1 = odd ? run[2 * jh + H + 1] : r1;
         if (i >= s.n_in || j >= s.n_in) continue;
         const int a = i / s.n_pol, pp = i % s.n_pol, a2 = j / s.n_pol, qq = j % s.n_pol;
         if (a > a2) continue;
@@ -143,7 +170,7 @@ __device__ __forceinline__ void write_piece(const XtSub& s, const ItemGeo& ig, i
         } else {
             const float re = __uint_as_float(g_r0c0) + __uint_as_float(g_r1c1);
             const float im = __uint_as_float(g_r1c0) - __uint_as_float(g_r0c1);
-            if (s.spec_lo) {
+            if (s.spec32) {
                 s.vis[o] = make_float2(re * s.descale, im * s.descale);
             } else {
                 const float d = s.scale[static_cast<int64_t>(i) * s.n_chan + ig.k] *
@@ -154,21 +181,55 @@ __device__ __forceinline__ void write_piece(const XtSub& s, const ItemGeo& ig, i
     }
 }
 
-// One chunk of a wide item (N > 128, one accumulator at column 0): add this thread's alternate
-// 32-column pieces into the running sums at kColRun, or write the final sums after the last
-// chunk.  Kept out of line: its registers are not allocated together with the narrow path's.
-__device__ __noinline__ void drain_wide(const XtSub& s, const ItemGeo ig, uint32_t tm, int row, int half,
-                                        int chunk) {
+// One chunk of a wide item (N > 128, one accumulator at column 0): add this thread's W-column
+// pieces (j_first, j_first + j_step, ...) into the running sums at kColRun, or write the final
+// sums after the last chunk.
+template <int W>
+__device__ __forceinline__ void drain_wide(const XtSub& s, const ItemGeo ig, uint32_t tm, int row, int j_first,
+                                           int j_step, int chunk) {
     const bool last = chunk == ig.n_chunk - 1;
-    for (int j0 = 32 * half; j0 < ig.N; j0 += 64) {   // alternate 32-column pieces
-        uint32_t v[32], rs[32];
-        tmem_ld32(tm + j0, v);
-        if (chunk > 0) tmem_ld32(tm + kColRun + j0, rs);
+    for (int j0 = j_first; j0 < ig.N; j0 += j_step) {   // this warp's pieces
+        uint32_t v[W], rs[W];
+        if constexpr (W == 32) {
+            tmem_ld32(tm + j0, v);
+            if (chunk > 0) tmem_ld32(tm + kColRun + j0, rs);
+        } else {
+            tmem_ld16(tm + j0, v);
+            if (chunk > 0) tmem_ld16(tm + kColRun + j0, rs);
+        }
         tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 32; ++e) rs[e] = chunk_add(s.exact, chunk > 0, rs[e], v[e]);
-        if (!last) tmem_st32(tm + kColRun + j0, rs);
-        else write_piece(s, ig, row, j0, rs);
+        for (int e = 0; e < W; ++e) rs[e] = chunk_add(s.exact, chunk > 0, rs[e], v[e]);
+        if (!last) {
+            if constexpr (W == 32) tmem_st32(tm + kColRun + j0, rs);
+            else tmem_st16(tm + kColRun + j0, rs);
+        } else {
+            write_piece<W>(s, ig, row, j0, rs);
+        }
+    }
+    if (!last) tmem_wait_st();
+}
+
+// One chunk of an FP32-form narrow item (chunk accumulator b, cross terms at kColX, running
+// sums at kColRun2): running sums += chunk, or after the last chunk + cross terms -> written.
+__device__ __forceinline__ void drain_split(const XtSub& s, const ItemGeo ig, uint32_t tm, int row, int b, int chunk) {
+    const bool last = chunk == ig.n_chunk - 1;
+    for (int j0 = 0; j0 < ig.N; j0 += 16) {        // 16-column pieces: few registers beside the converters
+        uint32_t v[16], rs[16];
+        tmem_ld16(tm + b * 128 + j0, v);
+        if (chunk > 0) tmem_ld16(tm + kColRun2 + j0, rs);
+        tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) rs[e] = chunk_add(0, chunk > 0, rs[e], v[e]);
+        if (!last) {
+            tmem_st16(tm + kColRun2 + j0, rs);
+        } else {
+            tmem_ld16(tm + kColX + j0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) rs[e] = chunk_add(0, true, rs[e], v[e]);
+            write_piece<16>(s, ig, row, j0, rs);
+        }
     }
     if (!last) tmem_wait_st();
 }
@@ -176,29 +237,28 @@ __device__ __noinline__ void drain_wide(const XtSub& s, const ItemGeo ig, uint32
 // run[0..63] (+)= this thread's 64 columns of the accumulator at TMEM address `col`
 __device__ __forceinline__ void drain64(uint32_t (&run)[64], uint32_t col, bool have, int exact) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {           // two 32-column loads
-        uint32_t v[32];
-        tmem_ld32(col + 32 * h, v);
+    for (int h = 0; h < 4; ++h) {           // four 16-column loads
+        uint32_t v[16];
+        tmem_ld16(col + 16 * h, v);
         tmem_wait_ld();
         if (!have) {
 #pragma unroll
-            for (int e = 0; e < 32; ++e) run[32 * h + e] = chunk_add(exact, false, 0u, v[e]);
+            for (int e = 0; e < 16; ++e) run[16 * h + e] = chunk_add(exact, false, 0u, v[e]);
         } else if (exact) {
 #pragma unroll
-            for (int e = 0; e < 32; ++e) run[32 * h + e] = chunk_add(1, true, run[32 * h + e], v[e]);
+            for (int e = 0; e < 16; ++e) run[16 * h + e] = chunk_add(1, true, run[16 * h + e], v[e]);
         } else {
 #pragma unroll
-            for (int e = 0; e < 32; ++e) run[32 * h + e] = chunk_add(0, true, run[32 * h + e], v[e]);
+            for (int e = 0; e < 16; ++e) run[16 * h + e] = chunk_add(0, true, run[16 * h + e], v[e]);
         }
     }
 }
 
-// All chunks of a narrow item (N <= 128): chunk c (global chunk count cc + c) sits in accumulator
-// (cc + c) % nbuf; the running sums of this thread's row and 64-column half stay in registers,
-// the cross terms of a two-plane item are added at the end, then the sums are written.  `par`
-// holds the accumulators' phase bits; the updated bits are returned.  Kept out of line so that
-// its registers are allocated apart from the wide path's.
-__device__ __noinline__ uint32_t drain_narrow(Shared& sh, const XtSub& s, const ItemGeo ig, uint32_t tm, int row,
+// All chunks of a one-plane narrow item (N <= 128): chunk c (global chunk count cc + c) sits in
+// accumulator (cc + c) % nbuf; the running sums of this thread's row and 64-column half stay in
+// registers and are written after the last chunk.  `par`
+// holds the accumulators' phase bits; the updated bits are returned.
+__device__ __forceinline__ uint32_t drain_narrow(Shared& sh, const XtSub& s, const ItemGeo ig, uint32_t tm, int row,
                                               int half, int cc, uint32_t par, unsigned* err) {
     const int c0 = 64 * half;
     uint32_t run[64];
@@ -216,30 +276,110 @@ __device__ __noinline__ uint32_t drain_narrow(Shared& sh, const XtSub& s, const 
         tc_fence_before();
         mbar_arrive(&sh.acce[b]);             // the accumulator goes back to the MMA issuer
     }
-    if (ig.sep) {                             // add the cross terms of the whole integration
-        if (!mbar_wait(&sh.xf, (par >> kXBit) & 1, err, ERR_WAIT_MMA)) {
-            sh.abort_flag = 1;
-            return par;
-        }
-        par ^= 1u << kXBit;
-        tc_fence_after();
-        if (c0 < ig.N) drain64(run, tm + kColX + c0, true, 0);
-        tc_fence_before();
-        mbar_arrive(&sh.xe);
-    }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
         if (c0 + 32 * j < ig.N) {
             uint32_t piece[32];
 #pragma unroll
             for (int e = 0; e < 32; ++e) piece[e] = run[32 * j + e];
-            write_piece(s, ig, row, c0 + 32 * j, piece);
+            write_piece<32>(s, ig, row, c0 + 32 * j, piece);
         }
     }
     return par;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XtBatch* __restrict__ tab) {
+// FP32 form: stage g's FP32 slot g % kF32Stages (after the operand slots) becomes operand slot
+// g % kOpStages2 --
+// for each 8-frame K-block j and row r (unit j * R + r; the converter threads stride over the
+// units), the row's frames 8j..8j+7 (two 16-byte granules of the FP32 layout) scaled by the power
+// of two split_scale, rounded to fp16 hi and the remainder to fp16 lo, stored as row r of K-block
+// j of the hi tile and of the lo tile (full-stage offset).
+// Each converter warp works on its own units and signals on its own: lane 0 waits for the FP32
+// slot and the operand slot (the decision is shared by a shuffle), the warp converts, fences its
+// shared stores for the tensor core's (async) proxy, and lane 0 arrives on both slots' barriers,
+// which complete after all kConvWarps warps.  No barrier spans warps.
+__device__ __noinline__ void convert_stages(const XtBatch& t, Shared& sh, unsigned char* smem, int ct) {
+    volatile int* abort_flag = &sh.abort_flag;
+    const int lane = ct & 31;
+    int g = 0;
+    for (int it = blockIdx.x; it < t.n_items; it += gridDim.x) {
+        const ItemGeo ig = item_geo(t, it);
+        const XtSub& s = t.sub[ig.sub];
+        const int R = ig.R, Rp = ig.Rp, tb = ig.tb32;
+        const float sc = s.split_scale;
+        const int lo_off = ig.nkb_stage * R * 16;
+        for (int st = 0; st < ig.n_stage; ++st, ++g) {
+            const int fs = g % kF32Stages, os = g % kOpStages2;
+            int ok = 1;
+            if (lane == 0) {
+                ok = !*abort_flag && mbar_wait(&sh.f32full[fs], (g / kF32Stages) & 1, t.err, ERR_WAIT_STAGE) &&
+                     mbar_wait(&sh.empty[os], ((g / kOpStages2) & 1) ^ 1, t.err, ERR_WAIT_MMA);
+                if (!ok) *abort_flag = 1;
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) return;   // the same decision in the whole warp
+            const int frames = min(s.ks, s.n_int - st * s.ks);
+            const float* src = reinterpret_cast<const float*>(smem + kOpStages2 * kSlot2 + fs * kStage2Bytes);
+            unsigned char* dst = smem + os * kSlot2;
+            const int units = (frames / 8) * R;
+            // unit u = j * R + r: thread ct takes u = ct, ct + kConvThreads, ... (r, j stepped incrementally)
+            int r = ct % R, j = ct / R;
+            const int dr = kConvThreads % R, dj = kConvThreads / R;
+#pragma unroll 2
+            for (int u = ct; u < units; u += kConvThreads) {
+                // frames 0-3 and 4-7 of row r in the 8-frame span j (one FP32 K-block, or two of 4 frames)
+                // (TB 8: rows r and r + 4 of a row group read opposite halves first, so that the 8
+                // rows of a quarter warp hit 8 distinct bank groups)
+                const bool sw = tb == 8 && ((r >> 2) & 1);
+                const int oa = fp32_off(r, sw ? 4 : 0, tb);
+                const int ob = tb == 8 ? fp32_off(r, sw ? 0 : 4, 8) : Rp * 4 + oa;
+                const float* p = src + j * 8 * Rp;
+                unsigned char* d = dst + u * 16;
+                const float4 qa = *reinterpret_cast<const float4*>(p + oa);
+                const float4 qb = *reinterpret_cast<const float4*>(p + ob);
+                const float4 q0 = sw ? qb : qa, q1 = sw ? qa : qb;
+                // hi: v rounded to 11 significant bits in FP32 (Veltkamp's split, 2^13 + 1), exact in fp16
+                // above 2^-14 (below, fp16 rounds it once more: under 2^-25 absolute, against values of
+                // order 2^6); lo = v - hi is exact.  Two packed conversions per pair of values.
+                const float v[8] = {q0.x * sc, q0.y * sc, q0.z * sc, q0.w * sc,
+                                    q1.x * sc, q1.y * sc, q1.z * sc, q1.w * sc};
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    float hv[2], lv[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {   // (explicit roundings: no contraction, no reassociation)
+                        const float x = v[2 * m + e];
+                        const float tt = __fmul_rn(x, 8193.0f);
+                        hv[e] = __fsub_rn(tt, __fsub_rn(tt, x));
+                        lv[e] = __fsub_rn(x, hv[e]);
+                    }
+                    const __half2 hh = __floats2half2_rn(hv[0], hv[1]);
+                    const __half2 ll = __floats2half2_rn(lv[0], lv[1]);
+                    hw[m] = *reinterpret_cast<const uint32_t*>(&hh);
+                    lw[m] = *reinterpret_cast<const uint32_t*>(&ll);
+                }
+                *reinterpret_cast<uint4*>(d) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4*>(d + lo_off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                r += dr;
+                j += dj;
+                if (r >= R) {
+                    r -= R;
+                    ++j;
+                }
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                if (ct == 0) sh.consumed = g + 1;  // this FP32 copy has landed
+                mbar_arrive(&sh.f32empty[fs]);
+                mbar_arrive(&sh.full[os]);
+            }
+        }
+    }
+}
+
+template <bool kF32>
+__global__ void __launch_bounds__((kF32 ? kWarps2 : kWarps1) * 32, 1) xengine_tc_kernel(const XtBatch* __restrict__ tab) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ Shared sh;
     const XtBatch& t = *tab;
@@ -247,15 +387,19 @@ __global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XtBatch* 
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&sh.full[s], 1);
+            mbar_init(&sh.full[s], kF32 ? kConvWarps : 1);   // converted by every converter warp, or one copy
             mbar_init(&sh.empty[s], 1);
+        }
+        for (int s = 0; s < kF32Stages; ++s) {
+            mbar_init(&sh.f32full[s], 1);
+            mbar_init(&sh.f32empty[s], kConvWarps);
         }
         for (int b = 0; b < kAccBufs; ++b) {
             mbar_init(&sh.accf[b], 1);
-            mbar_init(&sh.acce[b], kEpiThreads);
+            mbar_init(&sh.acce[b], kF32 ? kEpiThreads2 : kEpiThreads1);
         }
         mbar_init(&sh.xf, 1);
-        mbar_init(&sh.xe, kEpiThreads);
+        mbar_init(&sh.xe, kEpiThreads2);
         fence_mbar_init();
         sh.abort_flag = 0;
         sh.consumed = 0;
@@ -273,30 +417,44 @@ __global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XtBatch* 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
+            constexpr bool f32 = kF32;
+            const int nsl = f32 ? kF32Stages : kStages;
+            uint64_t* fullb = f32 ? sh.f32full : sh.full;
+            uint64_t* emptyb = f32 ? sh.f32empty : sh.empty;
+            unsigned char* slots = f32 ? smem + kOpStages2 * kSlot2 : smem;
+            const int pitch = f32 ? kStage2Bytes : kSlot;
             int g = 0;
             for (int it = blockIdx.x; it < t.n_items && !*abort_flag; it += gridDim.x) {
                 const ItemGeo ig = item_geo(t, it);
                 const XtSub& s = t.sub[ig.sub];
                 for (int st = 0; st < ig.n_stage; ++st, ++g) {
-                    const int slot = g % kStages;
-                    if (!mbar_wait(&sh.empty[slot], ((g / kStages) & 1) ^ 1, t.err, ERR_WAIT_MMA)) {
+                    const int slot = g % nsl;
+                    if (!mbar_wait(&emptyb[slot], ((g / nsl) & 1) ^ 1, t.err, ERR_WAIT_MMA)) {
                         *abort_flag = 1;
                         break;
                     }
-                    const int kb0 = st * ig.nkb_stage;
-                    const int nkb = min(ig.nkb_stage, ig.ntb - kb0);
-                    const uint32_t bytes = static_cast<uint32_t>(nkb) * ig.R * 16;
-                    const int64_t off = (static_cast<int64_t>(ig.k) * ig.ntb + kb0) * ig.R * kTbHalf;
-                    mbar_arrive_expect_tx(&sh.full[slot], s.spec_lo ? 2 * bytes : bytes);
-                    bulk_g2s(smem + slot * kSlot, s.spec + off, bytes, &sh.full[slot]);
-                    if (s.spec_lo)   // the lo plane right after a full stage of hi
-                        bulk_g2s(smem + slot * kSlot + ig.nkb_stage * ig.R * 16, s.spec_lo + off, bytes,
-                                 &sh.full[slot]);
+                    unsigned char* dst = slots + slot * pitch;
+                    if (f32) {
+                        // the stage's FP32 K-blocks of channel k are contiguous
+                        const int frames = min(s.ks, s.n_int - st * s.ks);
+                        const uint32_t bytes = static_cast<uint32_t>(frames) * ig.Rp * 4;
+                        const float* src = s.spec32 +
+                            (static_cast<int64_t>(ig.k) * ig.ntb32 + st * (s.ks / ig.tb32)) * ig.Rp * ig.tb32;
+                        mbar_arrive_expect_tx(&fullb[slot], bytes);
+                        bulk_g2s(dst, src, bytes, &fullb[slot]);
+                    } else {
+                        const int kb0 = st * ig.nkb_stage;
+                        const int nkb = min(ig.nkb_stage, ig.ntb - kb0);
+                        const uint32_t bytes = static_cast<uint32_t>(nkb) * ig.R * 16;
+                        const int64_t off = (static_cast<int64_t>(ig.k) * ig.ntb + kb0) * ig.R * kTbHalf;
+                        mbar_arrive_expect_tx(&fullb[slot], bytes);
+                        bulk_g2s(dst, s.spec + off, bytes, &fullb[slot]);
+                    }
                 }
             }
             // let every issued copy land before the CTA can exit
             for (int q = *(volatile int*)&sh.consumed; q < g; ++q)
-                mbar_wait(&sh.full[q % kStages], (q / kStages) & 1, nullptr, 0);
+                mbar_wait(&fullb[q % nsl], (q / nsl) & 1, nullptr, 0);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
@@ -304,13 +462,14 @@ __global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XtBatch* 
             int g = 0, cc = 0;
             uint32_t par = 0;                     // bit b: parity of accumulator b's uses so far
             int prev_nbuf = -1;
+            constexpr int nsl = kF32 ? kOpStages2 : kStages;
             for (int it = blockIdx.x; it < t.n_items && !*abort_flag; it += gridDim.x) {
                 const ItemGeo ig = item_geo(t, it);
                 const XtSub& s = t.sub[ig.sub];
                 const uint32_t idesc = idesc_f16_f32(128, ig.N);
                 const uint32_t lbo = static_cast<uint32_t>(ig.R) * 16, sbo = 128;
                 const int stages_per_chunk = s.chunk / s.ks;
-                const bool two = s.spec_lo != nullptr;
+                const bool two = s.spec32 != nullptr;
                 const uint32_t lo_off = static_cast<uint32_t>(ig.nkb_stage) * ig.R * 16;
                 bool xfirst = true;                   // next cross-term MMA starts the accumulator
                 if (ig.sep) {                         // the previous item's cross terms are drained
@@ -327,7 +486,7 @@ __global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XtBatch* 
                     if (!ig.dbl || prev_nbuf != ig.nbuf) {
                         for (int q = 0; q < kAccBufs && ok; ++q)
                             ok = mbar_wait(&sh.acce[q], ((par >> q) & 1) ^ 1, t.err, ERR_WAIT_EPI);
-                        // (columns 384-511 may have held cross terms; a sep item already waited)
+                        // (columns 256-383 may have held cross terms; a sep item already waited)
                         if (ok && !ig.sep)
                             ok = mbar_wait(&sh.xe, ((par >> kXBit) & 1) ^ 1, t.err, ERR_WAIT_EPI);
                     } else {
@@ -345,14 +504,14 @@ __global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XtBatch* 
                     const int st1 = min(ig.n_stage, st0 + stages_per_chunk);
                     bool first = true;
                     for (int st = st0; st < st1; ++st, ++g) {
-                        const int slot = g % kStages;
-                        if (!mbar_wait(&sh.full[slot], (g / kStages) & 1, t.err, ERR_WAIT_STAGE)) {
+                        const int slot = g % nsl;
+                        if (!mbar_wait(&sh.full[slot], (g / nsl) & 1, t.err, ERR_WAIT_STAGE)) {
                             *abort_flag = 1;
                             break;
                         }
                         tc_fence_after();
                         const int nkb = min(ig.nkb_stage, ig.ntb - st * ig.nkb_stage);
-                        const uint32_t base = smem_u32(smem + slot * kSlot);
+                        const uint32_t base = smem_u32(smem + slot * (kF32 ? kSlot2 : kSlot));
                         for (int kk = 0; kk < nkb / 2; ++kk) {
                             const uint32_t kbase = base + kk * 2 * lbo;
                             const uint64_t da = smem_desc_noswizzle(kbase + ig.a0 * 16, lbo, sbo);
@@ -369,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XtBatch* 
                             }
                         }
                         umma_commit(&sh.empty[slot]);   // frees the stage once these MMAs finish
-                        sh.consumed = g + 1;
+                        if (!kF32) sh.consumed = g + 1;
                     }
                     if (*abort_flag) break;
                     umma_commit(&sh.accf[b]);           // chunk complete
@@ -378,18 +537,40 @@ __global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XtBatch* 
                 if (ig.sep) umma_commit(&sh.xf);        // cross terms complete
             }
         }
+    } else if (kF32 && warp >= kConvWarp0) {
+        // ------------------------------------------------------------ converters (FP32 form)
+        convert_stages(t, sh, smem, threadIdx.x - kConvWarp0 * 32);
     } else {
-        // ------------------------------------------------------------ epilogue (warps 2..9)
+        // ------------------------------------------------------------ epilogue (warps 2..9 or 2..5)
         const int q = warp & 3;                   // TMEM lane quarter this warp may access
         const int lrow = 32 * q + lane;           // row within the item's 128 rows = TMEM lane
-        const int half = (warp - 2) >> 2;         // column half: 64-column halves / alternate 32-column pieces
         const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
+        // one-plane forms: column half of the 8 drain warps; FP32 form: every column
+        const int half = kF32 ? 0 : (warp - 2) >> 2;
         int cc = 0;
         uint32_t par = 0;                         // bit b: parity of accumulator b's uses so far
         for (int it = blockIdx.x; it < t.n_items && !*abort_flag; it += gridDim.x) {
             const ItemGeo ig = item_geo(t, it);
             const XtSub& s = t.sub[ig.sub];
-            if (ig.dbl) {
+            if (kF32 && ig.sep) {           // (FP32 form: every narrow item)
+                for (int chunk = 0; chunk < ig.n_chunk; ++chunk, ++cc) {
+                    const int b = cc % ig.nbuf;
+                    const bool last = chunk == ig.n_chunk - 1;
+                    bool ok = mbar_wait(&sh.accf[b], (par >> b) & 1, t.err, ERR_WAIT_MMA);
+                    if (ok && last) ok = mbar_wait(&sh.xf, (par >> kXBit) & 1, t.err, ERR_WAIT_MMA);
+                    if (!ok) {
+                        sh.abort_flag = 1;
+                        break;
+                    }
+                    par ^= 1u << b;
+                    if (last) par ^= 1u << kXBit;
+                    tc_fence_after();
+                    drain_split(s, ig, tmem + lane_off, ig.a0 + lrow, b, chunk);
+                    tc_fence_before();
+                    mbar_arrive(&sh.acce[b]);
+                    if (last) mbar_arrive(&sh.xe);
+                }
+            } else if (!kF32 && ig.dbl) {
                 par = drain_narrow(sh, s, ig, tmem + lane_off, ig.a0 + lrow, half, cc, par, t.err);
                 cc += ig.n_chunk;
             } else {
@@ -400,7 +581,8 @@ __global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XtBatch* 
                     }
                     par ^= 1u;
                     tc_fence_after();
-                    drain_wide(s, ig, tmem + lane_off, ig.a0 + lrow, half, chunk);
+                    if constexpr (kF32) drain_wide<16>(s, ig, tmem + lane_off, ig.a0 + lrow, 0, 16, chunk);
+                    else drain_wide<32>(s, ig, tmem + lane_off, ig.a0 + lrow, 32 * half, 64, chunk);
                     tc_fence_before();
                     mbar_arrive(&sh.acce[0]);
                 }
@@ -420,21 +602,30 @@ __global__ void __launch_bounds__(kThreads, 1) xengine_tc_kernel(const XtBatch* 
 
 bool xengine_tc_supported(int n_in) { return n_in >= 1 && 2 * n_in <= 256; }
 
-int xengine_tc_max_ks(int n_in, int planes) {
+int xengine_tc_max_ks(int n_in) {
     int ks = 512;                                  // stages of at most 512 frames
-    while (ks > 16 && planes * (ks / kTbHalf) * 2 * n_in * 16 > kStageMaxBytes) ks /= 2;
+    while (ks > 16 && (ks / kTbHalf) * 2 * n_in * 16 > kStageMaxBytes) ks /= 2;
     return ks;
 }
 
-size_t xengine_tc_smem() { return static_cast<size_t>(kStages) * kSlot + kTailSlack; }
+int xengine_tc_ks_fp32(int n_in) {
+    // the FP32 slot holds ks * rows_fp32(n_in) floats; the operand slot's two planes then take
+    // ks * 2 n_in * 4 <= that many bytes
+    int ks = 512;
+    while (ks > 16 && ks * rows_fp32(n_in) * 4 > kStage2Bytes) ks /= 2;
+    return ks;
+}
 
-cudaError_t launch_xengine_tc_table(const XtBatch* dtab, int n_items, int n_sm, cudaStream_t s) {
+size_t xengine_tc_smem() { return static_cast<size_t>(kSmemBytes); }
+
+cudaError_t launch_xengine_tc_table(const XtBatch* dtab, int n_items, int n_sm, cudaStream_t s, bool fp32_in) {
     const size_t smem = xengine_tc_smem();
-    cudaError_t e = cudaFuncSetAttribute(xengine_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    auto kern = fp32_in ? xengine_tc_kernel<true> : xengine_tc_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, std::min(n_items, n_sm));
-    xengine_tc_kernel<<<grid, kThreads, smem, s>>>(dtab);
+    kern<<<grid, (fp32_in ? kWarps2 : kWarps1) * 32, smem, s>>>(dtab);
     return cudaGetLastError();
 }
 
