@@ -189,12 +189,31 @@ def stage_roofline(stage, mode, ms, pk):
     if stage == "xengine" and mode == "fp32":
         # useful FP32 work: n_in(n_in+1)/2 complex MACs (8 flop) per channel and frame
         alg = 8.0 * N_CHAN * N_INT * N_IN * (N_IN + 1) / 2
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+        peak = fp32_peak_tflops(pk)
         return "alu", alg / (ms * 1e-3) / 1e12, peak, "TFLOP/s", alg
-    # tensor-core X-engine: the fp16 operand planes read from HBM bound it (two for fp32tc)
+    # tensor-core X-engine: its operand read from HBM bounds it (fp16 spectra, or the FP32
+    # spectra for fp32tc -- the same bytes as two fp16 planes)
     planes = 2 if mode == "fp32tc" else 1
     alg = N_CHAN * N_INT * 2 * N_IN * 2 * planes + N_CHAN * N_BL * 4 * 8
     return "hbm", alg / (ms * 1e-3) / 1e9, pk["hbm_gbs"], "GB/s", alg
+
+
+def fp32_peak_tflops(pk):
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+
+
+def fengine_alu(ms, pk):
+    """The F-engine against the FP32 ALU roofline: 2.5 log2 N (real FFT) + 3 (Eq. 2 phasor) + 6 (beams)
+    flop per input sample, the second bound its intermediate spectra leave it (HBM is the first)."""
+    alg = (2.5 * math.log2(N_FFT) + 3 + 6) * step_samples()
+    ach = alg / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": fp32_peak_tflops(pk), "unit": "TFLOP/s",
+            "frac": ach / fp32_peak_tflops(pk), "flop_per_sample": alg / step_samples()}
+
+
+def useful_tflops(ms):
+    """Useful X-engine work: n_in (n_in + 1) / 2 complex MACs (8 flop) per channel and frame."""
+    return 8.0 * N_CHAN * N_INT * N_IN * (N_IN + 1) / 2 / (ms * 1e-3) / 1e12
 
 
 def tensor_fraction(ms, pk, mmas=1):
@@ -229,6 +248,28 @@ def oracle_sample(x, s, n_frames):
     oracle.beams(Y, s.n_ant, s.n_pol, s.n_fft, coh_mask=(np.arange(s.n_ant) < COH_ANTENNAS).astype(np.uint8))
     oracle.xengine(Y, s.n_ant, s.n_pol)
     return time.perf_counter() - t0
+
+
+def fft_sample(x, s, n_frames):
+    """CPU FFT baseline (FP32 radix-2 FFT F-engine, FP64 oracle beams and X-stage) on n_frames; seconds."""
+    import oracle
+    t0 = time.perf_counter()
+    Y = oracle.fft_fengine(x, s.n_ant, s.n_pol, s.n_fft, n_frames, s.delay, s.phi0, s.rate)
+    oracle.beams(Y, s.n_ant, s.n_pol, s.n_fft, coh_mask=(np.arange(s.n_ant) < COH_ANTENNAS).astype(np.uint8))
+    oracle.xengine(Y, s.n_ant, s.n_pol)
+    return time.perf_counter() - t0
+
+
+def cpu_fft_baseline_auto(x, s, target_s=8.0):
+    import oracle
+    t1 = fft_sample(x, s, 16)
+    n_frames = int(max(16, min(s.n_int, round(16 * target_s / max(t1, 1e-3)))))
+    n_frames -= n_frames % 16
+    dt = fft_sample(x, s, n_frames)
+    return {"value": N_IN * n_frames * N_FFT / dt, "unit": UNIT, "cores": oracle.threads(),
+            "kind": "cpu FFT baseline",
+            "sample": f"FP32 radix-2 FFT F-engine (own C, OpenMP) + FP64 oracle beams and X-stage on {n_frames} "
+                      f"of the 8192 spectra of all 64 inputs, all 1024 channels ({dt:.1f} s)"}
 
 
 def cpu_baseline_auto(x, s, target_s=15.0):
@@ -551,6 +592,7 @@ def run_ours(args, world, rank, local_rank):
             d["step_speedup_vs_fp32"] = runs["fp32"][0] / step_ms
         if name != "fp32":
             d["xengine_tensor_frac_of_sustained_peak"] = tensor_fraction(st2[2], pk, 3 if name == "fp32tc" else 1)
+        d["xengine_useful_tflops"] = useful_tflops(st2[2])
         bound, ach, peak, unit, _ = stage_roofline("xengine", name, st2[2], pk)
         d["xengine_roofline"] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak}
         d["form"] = FORMS[name]
@@ -574,11 +616,14 @@ def run_ours(args, world, rank, local_rank):
     for i, nme in ((1, "fengine"), (2, "xengine")):
         b, a, p, u, _ = stage_roofline(nme, args.xmode, st[i], pk)
         stages[nme] = {"ms": st[i], "bound": b, "achieved": a, "peak": p, "unit": u, "frac": a / p}
+    stages["fengine"]["alu_roofline"] = fengine_alu(st[1], pk)
+    stages["xengine"]["useful_tflops"] = useful_tflops(st[2])
     stages["phasor_setup"] = {"ms": st[0]}
 
-    cpu = None
+    cpu = cpu_fft = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline_auto(s.x, s)
+        cpu_fft = cpu_fft_baseline_auto(s.x, s)
 
     corr.corr_destroy(h)
     del xt
@@ -601,6 +646,7 @@ def run_ours(args, world, rank, local_rank):
             "roofline": roofline, "stages": stages, "precision_forms": modes,
             "batched_subarrays": batch, "learned_rfi": rfi,
             "e2e": e2e, "gpu_launches": 3 * K, "clocks": clocks, "cpu_baseline": cpu,
+            "cpu_fft_baseline": cpu_fft,
         }
     emit(line, rank)
     if dist:

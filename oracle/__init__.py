@@ -13,6 +13,8 @@ Functions and the passage each follows (Roy et al., arXiv:0910.1517):
   requant   -- 8-bit requantisation of spectra (precision form; Sec. 4.1 analogue)
   xint      -- exact integer MAC on requantised spectra (Sec. 4.1)
   mad_flag  -- median-absolute-deviation flagger (Sec. 5, Eq. 3-4)
+  fft_fengine (cpu_fft_baseline.c) -- not an oracle: the bench's second CPU baseline,
+            the same F-engine with an FP32 radix-2 FFT (pinned to ``fengine``)
   power_dumps, patch_stats, rfi_forward, rfi_loss_grad (rfi_oracle.c) -- the RFI
             stage: 1 ms auto-power dumps, per-patch Eq. 3-4 statistics and flags,
             and the learned flagger's forward pass, BCE loss and exact gradient
@@ -27,7 +29,8 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "fx_oracle.c"), os.path.join(_HERE, "rfi_oracle.c")]
+_SRCS = [os.path.join(_HERE, "fx_oracle.c"), os.path.join(_HERE, "rfi_oracle.c"),
+         os.path.join(_HERE, "cpu_fft_baseline.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -64,6 +67,7 @@ def lib():
         L.oracle_patch_stats.argtypes = [i32, i32, P, f64, P, P, P, P]
         L.oracle_rfi_forward.argtypes = [i32, i32, i32, P, P, P]
         L.oracle_rfi_loss_grad.argtypes = [i32, i32, i32, P, P, P, P, P]
+        L.cpu_fft_fengine.argtypes = [i32, i32, i32, i32, P, i64, i64, P, P, P, i64, P]
         _lib = L
     return _lib
 
@@ -107,6 +111,23 @@ def fengine(x, n_ant, n_pol, n_fft, n_frames, delay, phi0, rate, g0=0, chans=Non
     rc = lib().oracle_fengine(n_ant, n_pol, n_fft, n_frames, _p(x), x.strides[0], x.shape[1],
                               _p(d), _p(f0), _p(w), int(g0), chp, nch, _p(Y))
     _check(rc, "fengine")
+    return Y[..., 0] + 1j * Y[..., 1]
+
+
+def fft_fengine(x, n_ant, n_pol, n_fft, n_frames, delay, phi0, rate, g0=0):
+    """The bench's CPU FFT baseline (cpu_fft_baseline.c): the F-engine of ``fengine`` with
+    an FP32 radix-2 FFT in place of the FP64 DFT; spectra Y[i][t][k] (complex128), all k."""
+    x = np.asarray(x)
+    assert x.dtype == np.int8 and x.ndim == 2 and x.shape[0] == n_ant * n_pol
+    if x.strides[1] != 1:
+        x = np.ascontiguousarray(x)
+    d = np.ascontiguousarray(delay, dtype=np.float64)
+    f0 = np.ascontiguousarray(phi0, dtype=np.float64)
+    w = np.ascontiguousarray(rate, dtype=np.float64)
+    Y = np.zeros((n_ant * n_pol, n_frames, n_fft // 2, 2), dtype=np.float64)
+    rc = lib().cpu_fft_fengine(n_ant, n_pol, n_fft, n_frames, _p(x), x.strides[0], x.shape[1],
+                               _p(d), _p(f0), _p(w), int(g0), _p(Y))
+    _check(rc, "fft_fengine")
     return Y[..., 0] + 1j * Y[..., 1]
 
 

@@ -124,8 +124,14 @@ __device__ __forceinline__ void pass_load(const float2* __restrict__ src, const 
 #pragma unroll
     for (int m = 0; m < PER; ++m) {
         const int b = t + m * T;
+        if constexpr (NB % 16 == 0) {            // pad16(b + r NB) = pad16(b) + r (NB + NB / 16)
+            const float2* s0 = src + pad16(b);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[m * R + r] = src[pad16(b + r * NB)];
+            for (int r = 0; r < R; ++r) v[m * R + r] = s0[r * (NB + NB / 16)];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[m * R + r] = src[pad16(b + r * NB)];
+        }
         const int j = b % Ns;
 #pragma unroll
         for (int r = 1; r < R; ++r) v[m * R + r] = cmul(tw[r * Ns + j], v[m * R + r]);
@@ -140,8 +146,17 @@ __device__ __forceinline__ void pass_store(float2* __restrict__ dst, int t, cons
     for (int m = 0; m < PER; ++m) {
         const int b = t + m * T;
         const int base = (b / Ns) * Ns * R + (b % Ns);
+        if constexpr (Ns % 16 == 0 || (Ns == 1 && R == 16)) {
+            // Ns % 16 == 0: pad16(base + r Ns) = pad16(base) + r (Ns + Ns / 16);
+            // Ns == 1, R == 16: base = 16 b, so pad16(base + r) = pad16(base) + r
+            float2* d0 = dst + pad16(base);
+            constexpr int step = (Ns % 16 == 0) ? Ns + Ns / 16 : 1;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[pad16(base + r * Ns)] = v[m * R + r];
+            for (int r = 0; r < R; ++r) d0[r * step] = v[m * R + r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[pad16(base + r * Ns)] = v[m * R + r];
+        }
     }
 }
 

@@ -435,3 +435,14 @@ def test_mad_flag_tiny_and_gaussian(orc):
     f, med, mad = orc.mad_flag(g, 3.0)
     assert abs(mad / 0.6745 - 7.0) < 0.05               # MAD / 0.6745 estimates sigma
     assert abs(f.mean() - 2 * (1 - 0.99865)) < 5e-4    # P(|z| > 3) = 0.0027
+
+
+def test_cpu_fft_baseline_matches_the_dft_oracle(orc):
+    """The bench's second CPU baseline (FP32 radix-2 FFT in place of the FP64 DFT) computes
+    the oracle's spectra to FP32 accuracy, delays and fringes included."""
+    for cfg, kw in ((1, {}), (2, dict(n_ant=4, n_fft=256, n_int=8, seed=77))):
+        s = make_config(cfg, **kw)
+        Y = orc.fengine(s.x, s.n_ant, s.n_pol, s.n_fft, s.n_int, s.delay, s.phi0, s.rate, g0=5)
+        Yf = orc.fft_fengine(s.x, s.n_ant, s.n_pol, s.n_fft, s.n_int, s.delay, s.phi0, s.rate, g0=5)
+        for i in range(s.n_in):
+            assert np.abs(Yf[i] - Y[i]).max() <= 1e-5 * np.abs(Y[i]).max(), (cfg, i)
