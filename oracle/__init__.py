@@ -13,6 +13,8 @@ Functions and the passage each follows (Roy et al., arXiv:0910.1517):
   requant   -- 8-bit requantisation of spectra (precision form; Sec. 4.1 analogue)
   xint      -- exact integer MAC on requantised spectra (Sec. 4.1)
   mad_flag  -- median-absolute-deviation flagger (Sec. 5, Eq. 3-4)
+  mad_blank -- the time-domain voltage blanker built on it (Sec. 5): flagged raw samples
+            replaced by pre-computed Gaussian noise scaled by the block's MAD / 0.6745
   fft_fengine (cpu_fft_baseline.c) -- not an oracle: the bench's second CPU baseline,
             the same F-engine with an FP32 radix-2 FFT (pinned to ``fengine``)
   power_dumps, patch_stats, rfi_forward, rfi_loss_grad (rfi_oracle.c) -- the RFI
@@ -67,6 +69,7 @@ def lib():
         L.oracle_patch_stats.argtypes = [i32, i32, P, f64, P, P, P, P]
         L.oracle_rfi_forward.argtypes = [i32, i32, i32, P, P, P]
         L.oracle_rfi_loss_grad.argtypes = [i32, i32, i32, P, P, P, P, P]
+        L.oracle_mad_blank.argtypes = [i32, i64, P, i64, i32, f64, P, i32, P, P]
         L.cpu_fft_fengine.argtypes = [i32, i32, i32, i32, P, i64, i64, P, P, P, i64, P]
         _lib = L
     return _lib
@@ -202,6 +205,24 @@ def mad_flag(x, M):
     rc = lib().oracle_mad_flag(x.size, _p(x), float(M), _p(f), ctypes.byref(med), ctypes.byref(mad))
     _check(rc, "mad_flag")
     return f, med.value, mad.value
+
+
+def mad_blank(x, block, M, noise):
+    """Time-domain voltage blanker (Sec. 5, Eq. 3-4) on int8 rows x [n_in][n]: (blanked rows,
+    stats int32 [n_in][n_blocks][4] = 2 med, 4 MAD, floor(2 M MAD / 0.6745), samples replaced)."""
+    x = np.asarray(x)
+    assert x.dtype == np.int8 and x.ndim == 2
+    if x.strides[1] != 1:
+        x = np.ascontiguousarray(x)
+    g = np.ascontiguousarray(noise, dtype=np.float32)
+    n_in, n = x.shape
+    assert g.ndim == 2 and g.shape[0] == n_in
+    nb = (n + block - 1) // block
+    out = np.zeros((n_in, n), dtype=np.int8)
+    st = np.zeros((n_in, nb, 4), dtype=np.int32)
+    _check(lib().oracle_mad_blank(n_in, n, _p(x), x.strides[0], int(block), float(M), _p(g), g.shape[1],
+                                  _p(out), _p(st)), "mad_blank")
+    return out, st
 
 
 # ------------------------------------------------------------------ RFI stage

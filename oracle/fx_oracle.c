@@ -21,7 +21,8 @@
  *   visibilities     V[k][b=(a<=a')][p*n_pol+q] = sum_t Y_{a,p} conj(Y_{a',q})   (Sec. 2.1)
  *   beams (Sec. 2.2) B_inc = sum_{a in inc} g_a^2 sum_p |Y_{a,p}|^2
  *                    B_coh = sum_p | sum_{a in coh} g_a exp(i theta_{a,k}) Y_{a,p} |^2
- *   MAD (Eq. 3, 4)   flag |x - med| > M * MAD / 0.6745
+ *   MAD (Eq. 3, 4)   flag |x - med| > M * MAD / 0.6745; the voltage blanker replaces
+ *                    flagged raw samples by scaled table noise (oracle_mad_blank)
  *
  * Every function returns 0 on success and a negative value on bad arguments.
  */
@@ -290,6 +291,64 @@ int oracle_mad_flag(int n, const double* x, double M, uint8_t* flags,
     if (mad_out) *mad_out = mad;
     free(w);
     return OR_OK;
+}
+
+/*
+ * Time-domain voltage blanker (Sec. 5, Eq. 3-4): each input row is cut into blocks of
+ * `block` samples (the last one may be shorter); within a block, samples with
+ * |x - med| > M MAD / 0.6745 (oracle_mad_flag on the block) are replaced by pre-computed
+ * Gaussian noise, independent per input: the standard-normal table value g[i][pos mod L]
+ * (pos = sample position in the row, L a power of two) scaled by the block's robust sigma
+ * MAD / 0.6745 rounded to FP32, the product rounded to FP32 and to the nearest integer
+ * (ties to even), clamped to +-127.
+ * x [n_in] rows of ld bytes, n samples each; out the same shape (contiguous rows of n);
+ * stats [n_in][n_blocks][4] int32: 2 med, 4 MAD, floor(2 M MAD / 0.6745) (the largest
+ * 2 |x - med| that is kept; clamped to [-1, 1024]) and the number of samples replaced.
+ */
+int oracle_mad_blank(int n_in, int64_t n, const int8_t* x, int64_t ld, int block, double M,
+                     const float* noise, int L, int8_t* out, int32_t* stats) {
+    if (n_in < 1 || n < 1 || block < 2 || L < 1 || (L & (L - 1))) return OR_EINVAL;
+    const int64_t n_blocks = (n + block - 1) / block;
+    int rc = OR_OK;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long q = 0; q < (long long)n_in * n_blocks; ++q) {
+        const int i = (int)(q / n_blocks);
+        const int64_t b = q % n_blocks, p0 = b * block;
+        const int len = (int)(p0 + block <= n ? block : n - p0);
+        double* v = (double*)malloc(sizeof(double) * (size_t)len);
+        uint8_t* f = (uint8_t*)malloc((size_t)len);
+        if (!v || !f) {
+            free(v);
+            free(f);
+#pragma omp atomic write
+            rc = OR_ENOMEM;
+            continue;
+        }
+        for (int j = 0; j < len; ++j) v[j] = (double)x[(int64_t)i * ld + p0 + j];
+        double med = 0.0, mad = 0.0;
+        oracle_mad_flag(len, v, M, f, &med, &mad);
+        const float sig = (float)(mad / 0.6745);
+        double t2 = floor(2.0 * (M * mad / 0.6745));
+        if (t2 > 1024.0) t2 = 1024.0;
+        int count = 0;
+        for (int j = 0; j < len; ++j) {
+            int8_t y = x[(int64_t)i * ld + p0 + j];
+            if (f[j]) {
+                const float r = rintf(sig * noise[(size_t)i * L + (size_t)((p0 + j) & (L - 1))]);
+                y = (int8_t)(r > 127.0f ? 127.0f : (r < -127.0f ? -127.0f : r));
+                ++count;
+            }
+            out[(int64_t)i * n + p0 + j] = y;
+        }
+        int32_t* st = stats + 4 * q;
+        st[0] = (int32_t)(2.0 * med);
+        st[1] = (int32_t)(4.0 * mad);
+        st[2] = (int32_t)t2;
+        st[3] = count;
+        free(v);
+        free(f);
+    }
+    return rc;
 }
 
 /* Threads the OpenMP runtime will use (1 without OpenMP). */

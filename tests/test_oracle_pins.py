@@ -446,3 +446,66 @@ def test_cpu_fft_baseline_matches_the_dft_oracle(orc):
         Yf = orc.fft_fengine(s.x, s.n_ant, s.n_pol, s.n_fft, s.n_int, s.delay, s.phi0, s.rate, g0=5)
         for i in range(s.n_in):
             assert np.abs(Yf[i] - Y[i]).max() <= 1e-5 * np.abs(Y[i]).max(), (cfg, i)
+
+
+# ------------------------------------------------ time-domain voltage blanker (Sec. 5, Eq. 3-4)
+
+def _noise_rows(n_in, L, seed):
+    return np.random.default_rng(seed).standard_normal((n_in, L)).astype(np.float32)
+
+
+def test_mad_blank_blocks_follow_eq3_eq4_per_block(orc):
+    """Each block's median, MAD and flag count are those of the Eq. 3-4 flagger on that block
+    (the ragged last block included); an impulse far above M sigma is always replaced."""
+    rng = np.random.default_rng(11)
+    n, block, M = 5000, 2048, 3.0
+    x = np.clip(np.rint(rng.normal(0, 20, (3, n))), -127, 127).astype(np.int8)
+    x[0, 100] = 120
+    x[2, 4500:4510] = -127
+    out, st = orc.mad_blank(x, block, M, _noise_rows(3, 1024, 5))
+    for i in range(3):
+        for b in range(3):
+            seg = x[i, b * block:(b + 1) * block].astype(np.float64)
+            f, med, mad = orc.mad_flag(seg, M)
+            assert st[i, b, 0] == 2 * med and st[i, b, 1] == 4 * mad and st[i, b, 3] == f.sum()
+            assert st[i, b, 2] == math.floor(2 * (M * mad / 0.6745))
+            kept = f == 0
+            assert np.array_equal(out[i, b * block:(b + 1) * block][kept], x[i, b * block:(b + 1) * block][kept])
+    assert out[0, 100] != 120 and np.all(out[2, 4500:4510] != -127)
+    assert st[2, 2, 3] >= 10                       # the last (904-sample) block holds the burst
+
+
+def test_mad_blank_clean_gaussian_is_left_alone_at_large_M(orc):
+    x = np.clip(np.rint(np.random.default_rng(3).normal(0, 20, (2, 8192))), -127, 127).astype(np.int8)
+    out, st = orc.mad_blank(x, 4096, 50.0, _noise_rows(2, 256, 1))
+    assert np.array_equal(out, x) and st[..., 3].sum() == 0
+
+
+def test_mad_blank_replacement_noise_statistics_and_independence(orc):
+    """Replaced samples are robust-sigma Gaussian noise (mean ~0, std ~ MAD/0.6745), drawn from
+    each input's own table row: identical inputs with different rows get different noise."""
+    rng = np.random.default_rng(21)
+    n, block = 1 << 16, 4096
+    row = np.clip(np.rint(rng.normal(0, 20, n)), -127, 127).astype(np.int8)
+    row[::16] = 127                                 # 1 in 16 samples is an outlier
+    x = np.stack([row, row])
+    out, st = orc.mad_blank(x, block, 2.5, _noise_rows(2, 1 << 16, 9))
+    rep0 = out[0, ::16].astype(np.float64)
+    sigma = (st[0, :, 1] / 4.0 / 0.6745).mean()
+    assert abs(rep0.mean()) < 0.1 * sigma and abs(rep0.std() / sigma - 1) < 0.05
+    assert np.mean(out[0, ::16] != out[1, ::16]) > 0.9
+
+
+def test_mad_blank_noise_index_is_the_row_position_mod_L(orc):
+    """Replacement noise for row position p comes from table entry p mod L."""
+    n, L = 3000, 64
+    x = np.clip(np.rint(np.random.default_rng(8).normal(0, 20, (1, n))), -127, 127).astype(np.int8)
+    hits = [5, 69, 133, 1029, 6, 70]                # 5 mod 64 (blocks 0 and 1), and 6 mod 64
+    x[0, hits] = 127
+    g = np.zeros((1, L), np.float32)
+    g[0, 5] = 1.0                                   # only table entry 5 is non-zero
+    out, st = orc.mad_blank(x, 1024, 3.0, g)
+    sig0, sig1 = st[0, 0, 1] / 4.0 / 0.6745, st[0, 1, 1] / 4.0 / 0.6745
+    assert out[0, 5] == out[0, 69] == out[0, 133] == round(sig0) != 0
+    assert out[0, 1029] == round(sig1)
+    assert out[0, 6] == out[0, 70] == 0
