@@ -54,6 +54,8 @@ SIGNATURES = {
     "corr_batch_integrate_device": ([_P, _P, _P, _P, _P, _P], _I),
     "corr_batch_tune": ([_P, _P, _P], _I),
     "corr_read_power": ([_P, _P, ctypes.POINTER(ctypes.c_void_p)], _I),
+    "corr_set_blanker": ([_P, ctypes.c_double, _I, _P, _I], _I),
+    "corr_read_blank_stats": ([_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], _I),
     # include/rfi.h
     "rfi_n_params": ([], _I),
     "rfi_create": ([ctypes.POINTER(ctypes.c_void_p), _I], _I),
@@ -289,6 +291,23 @@ def corr_power_device(h):
     dev = ctypes.c_void_p()
     _ok(load().corr_read_power(h, None, ctypes.byref(dev)))
     return dev.value
+
+
+def corr_set_blanker(h, M: float, block: int = 0, noise=None):
+    """Time-domain voltage blanker (M = 0: off); noise float32 [n_in][L] standard normal."""
+    if M == 0:
+        return _ok(load().corr_set_blanker(h, 0.0, 0, None, 0))
+    g = np.ascontiguousarray(noise, dtype=np.float32)
+    return _ok(load().corr_set_blanker(h, float(M), int(block), _ptr(g), g.shape[1]))
+
+
+def corr_read_blank_stats(h):
+    """(stats int32 [n_in][n_blocks][4] = 2 med, 4 MAD, T2, replaced; samples covered per row)."""
+    nb, ns = ctypes.c_int64(), ctypes.c_int64()
+    _ok(load().corr_read_blank_stats(h, None, ctypes.byref(nb), ctypes.byref(ns)))
+    out = np.empty((corr_info(h)["n_in"], nb.value, 4), dtype=np.int32)
+    _ok(load().corr_read_blank_stats(h, _ptr(out), None, None))
+    return out, int(ns.value)
 
 
 def corr_read_power_host(h, n_dump: int):

@@ -173,6 +173,7 @@ int corr_batch_create(corr_batch_t** out, int n_sub, corr_t* const* subs) {
         if (!subs[s]) return bfail(CORR_E_INVAL, "null sub-array handle");
         if (subs[s]->xmode != subs[0]->xmode) return bfail(CORR_E_INVAL, "sub-arrays must share one precision mode");
         if (subs[s]->xmode == CORR_FP32TC) return bfail(CORR_E_INVAL, "CORR_FP32TC runs per handle, not in batches");
+        if (subs[s]->blank_M > 0.0) return bfail(CORR_E_INVAL, "the voltage blanker runs per handle, not in batches");
         if (subs[s]->out_vis) return bfail(CORR_E_STATE, "a sub-array handle has an output ring (double-buffered outputs)");
         for (int q = 0; q < s; ++q)
             if (subs[q] == subs[s]) return bfail(CORR_E_INVAL, "a handle appears twice");

@@ -173,6 +173,19 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
     fp.err = h->d_err;
     const int fmode = fe_mode(h->xmode);
     if (int rc = mark(h, 1, s)) return rc;
+    if (h->blank_M > 0.0) {   // voltage blanker: per-block statistics of every sample the F-engine reads
+        const int64_t need = static_cast<int64_t>(h->n_int) * h->n_fft + max_int_delay(h);
+        const int64_t nb = (need + (int64_t(1) << h->blank_log2) - 1) >> h->blank_log2;
+        if (nb > h->blank_cap) return fail(CORR_E_STATE, "max_delay grew after corr_set_blanker: set the blanker again");
+        CU(launch_blank_stats(x, ld, h->n_in, need, 1 << h->blank_log2, h->blank_M, h->d_blank, s));
+        fp.blank = h->d_blank;
+        fp.blank_log2 = h->blank_log2;
+        fp.blank_nb = nb;
+        fp.noise = h->d_noise;
+        fp.noise_mask = h->noise_L - 1;
+        h->blank_nb = nb;
+        h->blank_n = need;
+    }
     CU(launch_fengine(fp, fmode, s));
     if (int rc = mark(h, 2, s)) return rc;
     XParams xp{};
@@ -481,6 +494,8 @@ int corr_destroy(corr_t* h) {
     cudaSetDevice(h->dev);
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->d_power) cudaFree(h->d_power);
+    if (h->d_noise) cudaFree(h->d_noise);
+    if (h->d_blank) cudaFree(h->d_blank);
     if (h->d_xtab) cudaFree(h->d_xtab);
     if (h->d_items) cudaFree(h->d_items);
     if (h->cstream) cudaStreamSynchronize(h->cstream);
@@ -824,6 +839,47 @@ int corr_set_power_dump(corr_t* h, int dump) {
         CU(dalloc(&h->d_power, static_cast<size_t>(h->n_in) * (h->n_int / dump) * h->n_chan));
         CU(cudaMemset(h->d_power, 0, sizeof(float) * h->n_in * (h->n_int / dump) * h->n_chan));
     }
+    return CORR_OK;
+}
+
+int corr_set_blanker(corr_t* h, double M, int block, const float* noise, int L) {
+    if (int rc = check_handle(h)) return rc;
+    if (!(M >= 0.0) || !std::isfinite(M)) return fail(CORR_E_INVAL, "M must be finite and >= 0");
+    if (h->batch_refs > 0) return fail(CORR_E_STATE, "the voltage blanker runs per handle, not in batches");
+    CU(cudaStreamSynchronize(h->stream));
+    if (h->d_noise) cudaFree(h->d_noise);
+    if (h->d_blank) cudaFree(h->d_blank);
+    h->d_noise = nullptr;
+    h->d_blank = nullptr;
+    h->blank_M = 0.0;
+    h->blank_cap = h->blank_nb = h->blank_n = 0;
+    if (M == 0.0) return CORR_OK;
+    int lg = 0;
+    while ((1 << lg) < block && lg < 30) ++lg;
+    if (block < h->n_fft || block > 32768 || (1 << lg) != block)
+        return fail(CORR_E_INVAL, "block must be a power of two in [n_fft, 32768]");
+    if (!noise || L < 1 || L > (1 << 24) || (L & (L - 1))) return fail(CORR_E_INVAL, "noise table: L a power of two in [1, 2^24]");
+    const size_t nn = static_cast<size_t>(h->n_in) * L;
+    CU(dalloc(&h->d_noise, nn));
+    CU(cudaMemcpy(h->d_noise, noise, nn * sizeof(float), cudaMemcpyHostToDevice));
+    h->blank_cap = (static_cast<int64_t>(h->n_int) * h->n_fft + h->max_delay + block - 1) / block;
+    CU(cudaMalloc(&h->d_blank, sizeof(int32_t) * 4 * static_cast<size_t>(h->n_in) * h->blank_cap));
+    h->blank_M = M;
+    h->blank_log2 = lg;
+    h->noise_L = L;
+    return CORR_OK;
+}
+
+int corr_read_blank_stats(corr_t* h, int32_t* out, int64_t* n_blocks, int64_t* n_samples) {
+    if (int rc = check_handle(h)) return rc;
+    if (h->blank_M == 0.0) return fail(CORR_E_STATE, "the voltage blanker is off (corr_set_blanker)");
+    if (h->blank_nb == 0) return fail(CORR_E_STATE, "no integration with the blanker yet");
+    if (int rc = settle(h, 1)) return rc;
+    if (n_blocks) *n_blocks = h->blank_nb;
+    if (n_samples) *n_samples = h->blank_n;
+    if (out)
+        CU(cudaMemcpy(out, h->d_blank, sizeof(int32_t) * 4 * static_cast<size_t>(h->n_in) * h->blank_nb,
+                      cudaMemcpyDeviceToHost));
     return CORR_OK;
 }
 

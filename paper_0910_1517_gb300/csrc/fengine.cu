@@ -1,690 +1,13 @@
-// fengine.cu -- F-engine of the FX correlator for sm_103a.
-//
-// One CTA owns a block of F consecutive frames (F * n_chan = 8192 complex
-// channel-frames) and walks over every input (antenna x polarisation) in turn:
-//   1. the F frames of input i, offset by its integer delay D_a (Sec. 2.1,
-//      Sec. 2.3.2: the read pointer is moved, no data is shifted), arrive in
-//      shared memory through one TMA-engine bulk copy, double-buffered so the
-//      next input streams in while this one is transformed;
-//   2. each frame is an n_fft-point real FFT computed as an M = n_fft/2-point
-//      complex FFT of (x[2n] + i x[2n+1]) -- Stockham radix-16/16/R passes, 16
-//      points per thread in registers, shared memory between passes -- followed
-//      by the even/odd real split; channels 0..M-1 are kept (Nyquist dropped);
-//   3. every channel is multiplied by the post-FFT phasor of Eq. 2, the FSTC
-//      term exp(+2 pi i k tau_f / N) times the fringe term exp(-i phi_a(g));
-//   4. the incoherent beam (sum of g_a^2 |Y|^2) and the coherent voltage sum
-//      (sum of g_a e^{i theta} Y, detected once per polarisation) accumulate
-//      in shared memory, since this CTA sees every antenna of its frames
-//      (Sec. 2.2) -- no atomics, no second pass over the spectra;
-//   5. the spectra are transposed in shared memory and written in the K-block
-//      layout the X-engines read (FP32, or requantised int8-valued / FP16
-//      values for the tensor-core X-engine), 32-byte runs per (channel, input).
+// fengine.cu -- F-engine of the FX correlator for sm_103a: launches of the kernel in
+// fengine_impl.cuh (single integrations and the batched form), the per-integration phasor
+// set-up, the RFI stage's power dumps and the beam averaging.
 #include <cmath>
 #include <vector>
 
-#include "common.cuh"
-#include "fengine.cuh"
+#include "fengine_impl.cuh"
 
 namespace gbx {
-
 namespace {
-
-constexpr int kThreads = 512;
-constexpr int kE = 16;                      // complex points per thread per FFT
-constexpr int kChanFrames = 8192;           // F * M per CTA
-constexpr int kMaxAnt = 128;
-
-template <int M>
-struct Plan {
-    static constexpr int T = M / kE;                           // threads per FFT
-    static constexpr int F = kThreads / T;                     // frames per CTA
-    static constexpr int N = 2 * M;                            // real FFT size
-    static constexpr int R1 = 16;
-    static constexpr int R2 = (M / 16 >= 16) ? 16 : M / 16;
-    static constexpr int R3 = M / (R1 * R2);                   // 1 when two passes suffice
-    static constexpr int PADM = M + M / 16;                    // padded frame length (float2)
-    static constexpr int STAGE = F * N + 32;                   // staging bytes per buffer
-    static_assert(F * M == kChanFrames, "CTA covers 8192 channel-frames");
-};
-
-// one pad element per 16: every Stockham exchange of 8-byte points is free of bank conflicts
-__host__ __device__ constexpr int pad16(int i) { return i + (i >> 4); }
-
-// cos / sin of 2 pi m / 16
-__device__ __forceinline__ constexpr float c16(int m) {
-    return m == 0 ? 1.0f : m == 1 ? 0.92387953251128674f : m == 2 ? 0.70710678118654752f
-         : m == 3 ? 0.38268343236508977f : m == 4 ? 0.0f : m == 5 ? -0.38268343236508977f
-         : m == 6 ? -0.70710678118654752f : m == 7 ? -0.92387953251128674f : -1.0f;
-}
-
-// o * exp(-2 pi i k / R) with the trivial cases spelled out
-template <int R, int K>
-__device__ __forceinline__ float2 twiddle_const(float2 o) {
-    constexpr int m = K * (16 / R);              // position on the 16-point circle, 0..7
-    if constexpr (m == 0) {
-        return o;
-    } else if constexpr (m == 4) {               // -i
-        return make_float2(o.y, -o.x);
-    } else if constexpr (m == 2) {               // (1 - i) / sqrt2
-        constexpr float h = 0.70710678118654752f;
-        return make_float2(h * (o.x + o.y), h * (o.y - o.x));
-    } else if constexpr (m == 6) {               // (-1 - i) / sqrt2
-        constexpr float h = 0.70710678118654752f;
-        return make_float2(h * (o.y - o.x), -h * (o.x + o.y));
-    } else {
-        constexpr float c = c16(m);
-        constexpr float s = (m <= 4) ? c16(4 - m) : c16(m - 4);  // sin(2 pi m / 16), m = 1..7
-        // w = c - i s
-        return make_float2(c * o.x + s * o.y, c * o.y - s * o.x);
-    }
-}
-
-// In-register forward DFT of R points (radix-2 recursion, natural-order output).
-template <int R>
-struct Dft {
-    template <int S>
-    __device__ __forceinline__ static void run(float2* v) {
-        // v[0], v[S], v[2S], ... hold the R inputs; transform in place
-        Dft<R / 2>::template run<2 * S>(v);      // evens
-        Dft<R / 2>::template run<2 * S>(v + S);  // odds
-        float2 out[R];
-#pragma unroll
-        for (int k = 0; k < R / 2; ++k) {
-            out[k] = v[2 * S * k];
-            out[k + R / 2] = v[2 * S * k + S];
-        }
-        apply<0>(out);
-#pragma unroll
-        for (int k = 0; k < R; ++k) v[S * k] = out[k];
-    }
-    template <int K>
-    __device__ __forceinline__ static void apply(float2* out) {
-        if constexpr (K < R / 2) {
-            const float2 e = out[K];
-            const float2 t = twiddle_const<R, K>(out[K + R / 2]);
-            out[K] = cadd(e, t);
-            out[K + R / 2] = csub(e, t);
-            apply<K + 1>(out);
-        }
-    }
-};
-template <>
-struct Dft<1> {
-    template <int S>
-    __device__ __forceinline__ static void run(float2*) {}
-};
-
-// Stockham pass of radix R over span Ns for one frame: read X[b + r*M/R], twiddle by
-// W_{Ns R}^{(b mod Ns) r}, DFT, write X[(b/Ns)*Ns*R + b%Ns + r*Ns].  The pass's twiddles are
-// tabulated as tw[r*Ns + j] so that a warp's consecutive j read consecutive words.
-template <int M, int R, int Ns>
-__device__ __forceinline__ void pass_load(const float2* __restrict__ src, const float2* __restrict__ tw, int t,
-                                          float2 (&v)[kE]) {
-    constexpr int T = M / kE, NB = M / R, PER = kE / R;
-#pragma unroll
-    for (int m = 0; m < PER; ++m) {
-        const int b = t + m * T;
-        if constexpr (NB % 16 == 0) {            // pad16(b + r NB) = pad16(b) + r (NB + NB / 16)
-            const float2* s0 = src + pad16(b);
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[m * R + r] = s0[r * (NB + NB / 16)];
-        } else {
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[m * R + r] = src[pad16(b + r * NB)];
-        }
-        const int j = b % Ns;
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[m * R + r] = cmul(tw[r * Ns + j], v[m * R + r]);
-        Dft<R>::template run<1>(v + m * R);
-    }
-}
-
-template <int M, int R, int Ns>
-__device__ __forceinline__ void pass_store(float2* __restrict__ dst, int t, const float2 (&v)[kE]) {
-    constexpr int T = M / kE, PER = kE / R;
-#pragma unroll
-    for (int m = 0; m < PER; ++m) {
-        const int b = t + m * T;
-        const int base = (b / Ns) * Ns * R + (b % Ns);
-        if constexpr (Ns % 16 == 0 || (Ns == 1 && R == 16)) {
-            // Ns % 16 == 0: pad16(base + r Ns) = pad16(base) + r (Ns + Ns / 16);
-            // Ns == 1, R == 16: base = 16 b, so pad16(base + r) = pad16(base) + r
-            float2* d0 = dst + pad16(base);
-            constexpr int step = (Ns % 16 == 0) ? Ns + Ns / 16 : 1;
-#pragma unroll
-            for (int r = 0; r < R; ++r) d0[r * step] = v[m * R + r];
-        } else {
-#pragma unroll
-            for (int r = 0; r < R; ++r) dst[pad16(base + r * Ns)] = v[m * R + r];
-        }
-    }
-}
-
-// barrier among the T threads of one FFT group (group g); a warp when T <= 32
-template <int T>
-__device__ __forceinline__ void group_sync(int g) {
-    if constexpr (T <= 32) {
-        __syncwarp();
-    } else {
-        asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(T) : "memory");
-    }
-}
-
-// Split / epilogue geometry: after the FFT every thread takes L consecutive frames (8, or all
-// F when fewer) of NP channel pairs (k, M - k), a whole number of K-block runs (TB frames per
-// 16-byte row), so that it holds whole (channel, input) pieces of the K-block layout and
-// writes each run as one 32-byte sector straight from registers -- no transposition buffer.
-// The TPG = L * T threads of a frame group are exactly the FFT groups of its L frames.
-template <int M, int MODE>
-struct Epi {
-    using P = Plan<M>;
-    static constexpr int TB = (MODE == OUT_FP32) ? tb_fp32(M) : kTbHalf;
-    static constexpr int L = (P::F < 8) ? P::F : 8;      // frames per thread
-    // fp16 runs of 8 frames from 4-frame CTAs (n_chan 2048): the two CTAs of a cluster (consecutive
-    // frame blocks) trade halves of their channels through distributed shared memory, so that each
-    // writes whole 32-byte pieces (8 frames x re, im) of its half of the channels
-    static constexpr bool kPair = (M == 2048 && MODE != OUT_FP32);
-    static_assert(L % TB == 0 || L < TB, "whole K-block runs, or part of one when F < TB");
-    static constexpr int NP = kE / (2 * L);                // channel pairs per thread
-    static constexpr int TPG = L * P::T;                   // threads per frame group
-    static_assert(2 * NP * L == kE && NP * TPG == M / 2, "split covers every channel of every frame once");
-};
-
-template <int M>
-struct Smem {
-    using P = Plan<M>;
-    static constexpr int kTw = P::R2 * 16 + (P::R3 > 1 ? P::R3 * 16 * P::R2 : 0) + M / 2 + 1;
-    static constexpr int kTab = 2 * M + P::F;                          // [pf M | wcoh M | ff F] of one antenna
-    static constexpr size_t stage = 0;
-    static constexpr size_t X = stage + 2 * static_cast<size_t>(P::STAGE);
-    static constexpr size_t tw = X + sizeof(float2) * P::F * P::PADM;
-    static constexpr size_t tab = ((tw + sizeof(float2) * kTw + 127) / 128) * 128;   // 2 bulk-copy targets
-    // cluster-pair exchange buffer (n_chan 2048): [4 slots (re, im) x (rank 0, 1)][M/2 channels] of 4
-    // fp16 frames (8 bytes): a warp's writes and reads of consecutive channels are conflict-free
-    static constexpr size_t xch = ((tab + 2 * sizeof(float2) * kTab + 127) / 128) * 128;
-    static constexpr size_t total = xch + (M == 2048 ? static_cast<size_t>(M / 2) * 32 : 0);
-    static_assert(total <= 232448, "F-engine shared memory exceeds 227 KB");
-    static_assert(X % 16 == 0 && tab % 16 == 0 && (sizeof(float2) * kTab) % 16 == 0 && P::STAGE % 16 == 0,
-                  "bulk-copy targets are 16-byte aligned");
-};
-
-// Per-CTA control words kept in static shared memory by the kernel that runs the body.
-struct FeCtl {
-    uint64_t bar[2];
-    uint64_t tbar[2];
-    int abort_flag;
-    uint64_t xfull;            // paired CTAs: the partner's half of this input's exchange has landed
-    uint64_t xempty;           // paired CTAs: the partner has read its exchange buffer (we may write it)
-    int Ds[kMaxAnt];           // integer delays, read every iteration
-};
-
-__device__ __forceinline__ uint32_t pack_half2(__half lo, __half hi) {
-    return static_cast<uint32_t>(__half_as_ushort(lo)) | (static_cast<uint32_t>(__half_as_ushort(hi)) << 16);
-}
-
-// The F-engine work of one CTA: frame block `block` of the integration described by p.
-template <int M, int MODE>
-__device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl& ctl) {
-    using P = Plan<M>;
-    using S = Smem<M>;
-    using E = Epi<M, MODE>;
-    constexpr int T = P::T, F = P::F, N = P::N;
-    constexpr int Ns3 = P::R1 * P::R2;
-    constexpr int TB = E::TB, L = E::L, NP = E::NP, TPG = E::TPG;
-    extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char* stage0 = smem + S::stage;
-    float2* X = reinterpret_cast<float2*>(smem + S::X);           // F * PADM
-    float2* tw2 = reinterpret_cast<float2*>(smem + S::tw);       // [R2][16]
-    float2* tw3 = tw2 + P::R2 * 16;                               // [R3][Ns3]
-    float2* twN = tw3 + (P::R3 > 1 ? P::R3 * Ns3 : 0);            // [M/2 + 1]
-    float2* tab = reinterpret_cast<float2*>(smem + S::tab);      // 2 x [pf | wcoh | ff] of one antenna
-    uint64_t* bar = ctl.bar;
-    uint64_t* tbar = ctl.tbar;
-    int& abort_flag = ctl.abort_flag;
-    int* Ds = ctl.Ds;
-
-    const int tid = threadIdx.x;
-    const int f = tid / T;            // frame of this thread's FFT group
-    const int t = tid % T;            // thread within the FFT group
-    const int fg = tid / TPG;         // frame group of the split: frames fg*L .. fg*L + L - 1
-    const int kk = tid % TPG;         // channel pairs kk + q*TPG, q < NP
-    const int t0 = block * F;
-    if (t0 >= p.n_int) return;        // padding CTA of a batched launch (never a cluster-paired one)
-    const int n_fr = min(F, p.n_int - t0);
-    const bool live = fg * L < n_fr;  // n_fr is a multiple of L: whole frame groups are live or not
-    constexpr bool kPair = E::kPair;
-    unsigned char* xch = smem + S::xch;
-    const uint32_t rank = kPair ? cluster_ctarank() : 0;   // frames 4 rank .. of the pair's 8
-    const int R = 2 * p.n_in;
-    const int64_t ntb = p.n_int / TB;
-
-    // this thread's channels, fixed for the CTA; the K-block of its frames starts at element
-    // (ch * ntb + kb) * rows * TB of the spectra
-    int chs[2 * NP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        const int k = kk + q * TPG;
-        chs[2 * q] = k;
-        chs[2 * q + 1] = (k == 0) ? M / 2 : M - k;
-    }
-    const int kb_run = (t0 + fg * L) / TB;
-    const int64_t blk_elems = static_cast<int64_t>((MODE == OUT_FP32) ? rows_fp32(p.n_in) : R) * TB;
-
-    // beam accumulators of this thread's L x 2 NP points: the incoherent sum over every input,
-    // and the coherent voltage sum of the current polarisation
-    float incr[L][2 * NP];
-    float2 cohr[L][2 * NP];
-#pragma unroll
-    for (int l = 0; l < L; ++l)
-#pragma unroll
-        for (int c = 0; c < 2 * NP; ++c) {
-            incr[l][c] = 0.0f;
-            cohr[l][c] = make_float2(0.0f, 0.0f);
-        }
-
-    for (int m = tid; m < S::kTw; m += kThreads) tw2[m] = p.tw[m];
-    for (int m = tid; m < p.n_ant; m += kThreads) Ds[m] = p.D[m];
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_init(&tbar[0], 1);
-        mbar_init(&tbar[1], 1);
-        if constexpr (kPair) {
-            mbar_init(&ctl.xfull, 1);
-            mbar_init(&ctl.xempty, 1);
-        }
-        fence_mbar_init();
-        abort_flag = 0;
-    }
-    __syncthreads();
-    // Paired CTAs trade channel halves each input: the partner's 4-frame halves of the channels
-    // this CTA writes arrive by st.async, completing bytes on xfull; before writing into the
-    // partner's buffer a CTA waits on xempty, which the partner's arrive completes once it has
-    // read that buffer.  All waits are bounded; one cluster barrier at exit keeps both CTAs
-    // resident while the other may still write into them.
-    constexpr uint32_t kXBytes = (M / 2) * 16;           // partner's re + im halves of our channels
-    uint32_t peer_xfull = 0, peer_xempty = 0;
-    if constexpr (kPair) {
-        cluster_sync();                                  // both CTAs and their barriers exist
-        peer_xfull = cluster_map(&ctl.xfull, rank ^ 1u);
-        peer_xempty = cluster_map(&ctl.xempty, rank ^ 1u);
-        if (tid == 0) {
-            mbar_arrive_expect_tx(&ctl.xfull, kXBytes);  // input 0's exchange
-            mbar_arrive_remote(peer_xempty);             // the partner may write into our buffer
-        }
-    }
-
-    const int n_iter = p.n_in;  // polarisation-major order: it = pol * n_ant + a
-    // Called by all of warp 0: lane 0 issues the bulk copy of the F frames of input `it`
-    // (offset by its integer delay); bytes past the last 16-byte boundary are copied by the
-    // lanes only when rounding the copy up would read past the row's readable samples.
-    auto issue = [&](int it) {
-        const int pol = it / p.n_ant, a = it % p.n_ant;
-        const int i = a * p.n_pol + pol;
-        unsigned char* dst = stage0 + (it & 1) * P::STAGE;
-        const int64_t s0 = static_cast<int64_t>(t0) * N + Ds[a];
-        const int64_t aligned = s0 & ~static_cast<int64_t>(15);
-        const int64_t end = s0 + static_cast<int64_t>(n_fr) * N;
-        const int64_t up = (end + 15) & ~static_cast<int64_t>(15);
-        const int64_t bulk_end = up <= p.n_avail ? up : (end & ~static_cast<int64_t>(15));
-        const uint32_t bulk = static_cast<uint32_t>(bulk_end - aligned);
-        const int8_t* row = p.x + static_cast<int64_t>(i) * p.ld;
-        const int lane = tid & 31;
-        if (lane == 0) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bar[it & 1], bulk);
-            bulk_g2s(dst, row + aligned, bulk, &bar[it & 1]);
-        }
-        const int64_t q = bulk_end + lane;
-        if (q < end) dst[q - aligned] = static_cast<unsigned char>(row[q]);
-    };
-    // phasor, beam-weight and fringe rows of the antenna of input `it` (n_fr fringe phasors:
-    // n_fr * 8 bytes is a multiple of 16 since n_fr is F or a multiple of 16)
-    auto issue_tab = [&](int it) {
-        const int a = it % p.n_ant;
-        float2* dst = tab + (it & 1) * S::kTab;
-        uint64_t* tb = &tbar[it & 1];
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(tb, (2 * M + n_fr) * sizeof(float2));
-        bulk_g2s(dst, p.pf + static_cast<int64_t>(a) * M, M * sizeof(float2), tb);
-        bulk_g2s(dst + M, p.wcoh + static_cast<int64_t>(a) * M, M * sizeof(float2), tb);
-        bulk_g2s(dst + 2 * M, p.ff + static_cast<int64_t>(a) * p.n_int + t0, n_fr * sizeof(float2), tb);
-    };
-    __syncthreads();                 // Ds visible to warp 0
-    if (tid < 32) issue(0);
-    if (tid == 0) issue_tab(0);
-
-    int it = 0;
-    for (; it < n_iter; ++it) {
-        const int pol = it / p.n_ant, a = it % p.n_ant;
-        const int i = a * p.n_pol + pol;
-        if (tid < 32 && it + 1 < n_iter) issue(it + 1);
-        const float g2 = p.ginc[a];
-        float scv[2 * NP];           // requantisation scales of this thread's channels
-        if constexpr (MODE != OUT_FP32) {
-#pragma unroll
-            for (int c = 0; c < 2 * NP; ++c) scv[c] = p.scale[static_cast<int64_t>(i) * M + chs[c]];
-        }
-        if (!mbar_wait(&bar[it & 1], (it >> 1) & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
-        const int64_t s0 = static_cast<int64_t>(t0) * N + Ds[a];
-        const unsigned char* st = stage0 + (it & 1) * P::STAGE + (s0 & 15) + f * N;
-        float2* Xf = X + f * P::PADM;
-
-        // ---- pass 1: radix-16 straight from the int8 staging buffer (z[n] = x[2n] + i x[2n+1])
-        float2 v[kE];
-        {
-            constexpr int NB = M / P::R1;
-            if ((s0 & 1) == 0) {                       // pairs are 2-byte aligned: one load each
-                const uint16_t* st16 = reinterpret_cast<const uint16_t*>(st);
-#pragma unroll
-                for (int r = 0; r < kE; ++r) {
-                    const uint16_t w = st16[t + r * NB];
-                    v[r] = make_float2(static_cast<float>(static_cast<signed char>(w & 0xff)),
-                                       static_cast<float>(static_cast<signed char>(w >> 8)));
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < kE; ++r) {
-                    const int n = t + r * NB;
-                    v[r] = make_float2(static_cast<float>(static_cast<signed char>(st[2 * n])),
-                                       static_cast<float>(static_cast<signed char>(st[2 * n + 1])));
-                }
-            }
-            Dft<16>::template run<1>(v);
-        }
-        __syncthreads();  // the previous iteration's split has finished reading X and its antenna tables
-        if (abort_flag) break;
-        if (kPair && tid == 0 && it > 0) {               // every thread has read the last exchange
-            mbar_arrive_expect_tx(&ctl.xfull, kXBytes);
-            mbar_arrive_remote(peer_xempty);
-        }
-        if (tid == 0 && it + 1 < n_iter) issue_tab(it + 1);   // into the buffer that split just released
-        pass_store<M, P::R1, 1>(Xf, t, v);
-        group_sync<T>(f);
-        // ---- pass 2
-        pass_load<M, P::R2, P::R1>(Xf, tw2, t, v);
-        group_sync<T>(f);
-        pass_store<M, P::R2, P::R1>(Xf, t, v);
-        // ---- pass 3
-        if constexpr (P::R3 > 1) {
-            group_sync<T>(f);
-            pass_load<M, P::R3, Ns3>(Xf, tw3, t, v);
-            group_sync<T>(f);
-            pass_store<M, P::R3, Ns3>(Xf, t, v);
-        }
-        __syncthreads();  // every frame's FFT is in X: the split reads the frames of its group
-
-        // ---- real split, Eq. 2 phasor (fractional delay x fringe), beams, K-block stores
-        if (!mbar_wait(&tbar[it & 1], (it >> 1) & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
-        const float2* pfa = tab + (it & 1) * S::kTab;
-        const float2* wa = pfa + M;
-        const float2* fra = pfa + 2 * M;   // fringe phasors of the CTA's frames
-        if constexpr (kPair) {   // the partner has read its exchange buffer: this input's halves may go in
-            if (!mbar_wait_cluster(&ctl.xempty, it & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
-        }
-        if (live) {
-        // FP32 piece of input i in a K-block: granules m*PG .. m*PG + PG - 1 of row group G (PG = TB/2:
-        // the re row's TB/4 granules, then the im row's), XOR-placed by s = G & 7
-        constexpr int PG = TB / 2;
-        const int G = (2 * i) >> 3, s = G & 7;
-        const int pstart = G * 8 * TB + ((((i & 3) ^ (s / PG)) * PG) << 2);   // floats from the block start
-        // beams and the K-block store of channel c from its L frames
-        auto emit = [&](int c, const float2 (&yc)[L]) {
-            const float2 w = wa[chs[c]];
-#pragma unroll
-            for (int l = 0; l < L; ++l) {
-                incr[l][c] += g2 * (yc[l].x * yc[l].x + yc[l].y * yc[l].y);
-                const float2 prev = (a == 0) ? make_float2(0.0f, 0.0f) : cohr[l][c];
-                cohr[l][c] = cadd(prev, cmul(w, yc[l]));
-                if (a == p.n_ant - 1) {  // this polarisation's coherent sum is complete: detect
-                    float* bc = p.beams + (static_cast<int64_t>(p.n_int) + t0 + fg * L + l) * M + chs[c];
-                    const float pw = cohr[l][c].x * cohr[l][c].x + cohr[l][c].y * cohr[l][c].y;
-                    *bc = (pol == 0) ? pw : *bc + pw;
-                }
-            }
-            // one 32-byte sector per (channel, input): rows 2i and 2i+1 over the L frames
-            const int64_t blk = (static_cast<int64_t>(chs[c]) * ntb + kb_run) * blk_elems;
-            if constexpr (MODE == OUT_FP32) {
-                float* spec = static_cast<float*>(p.spec);
-                if constexpr (TB == 4) {
-                    // 32-byte piece: granule slot j' = c ^ (s & 1) holds component c (0 re, 1 im)
-                    const bool flip = s & 1;
-                    uint32_t u[8];
-#pragma unroll
-                    for (int l = 0; l < 4; ++l) {
-                        u[l] = __float_as_uint(flip ? yc[l].y : yc[l].x);
-                        u[4 + l] = __float_as_uint(flip ? yc[l].x : yc[l].y);
-                    }
-                    st_global_v8(spec + blk + pstart, u);
-                } else {
-                    // 64-byte piece: slot j' = (2 c + h) ^ (s & 3), h = frames 0-3 / 4-7.  Each lane pair
-                    // writes one piece per instruction (a full 64-byte request): the even lane slots 0-1
-                    // (component cA), the odd lane slots 2-3 (component 1 - cA); first the even lane's
-                    // channel, then the odd lane's, trading the component each needs by a shuffle.
-                    static_assert(TB == 8 && L == 8, "FP32 runs of 8 frames");
-                    const bool odd = kk & 1;
-                    const int cA = (s >> 1) & 1;
-                    const bool hswap = s & 1;
-                    const int chp = __shfl_xor_sync(0xffffffffu, chs[c], 1);
-                    const int csend = odd ? cA : 1 - cA;
-                    float mine[8], recv[8];
-#pragma unroll
-                    for (int l = 0; l < 8; ++l) {
-                        const float own_keep = (odd ? 1 - cA : cA) ? yc[l].y : yc[l].x;
-                        const float own_send = csend ? yc[l].y : yc[l].x;
-                        mine[l] = own_keep;
-                        recv[l] = __shfl_xor_sync(0xffffffffu, own_send, 1);
-                    }
-                    auto put = [&](int ch, const float (&v)[8]) {
-                        uint32_t u[8];
-#pragma unroll
-                        for (int l = 0; l < 4; ++l) {   // static indices: v stays in registers
-                            u[l] = __float_as_uint(hswap ? v[4 + l] : v[l]);
-                            u[4 + l] = __float_as_uint(hswap ? v[l] : v[4 + l]);
-                        }
-                        st_global_v8(spec + (static_cast<int64_t>(ch) * ntb + kb_run) * blk_elems + pstart + (odd ? 8 : 0), u);
-                    };
-                    // piece of the even lane's channel, then of the odd lane's: both lanes of a pair
-                    // issue the same two stores (selects, no divergence)
-                    float d0[8], d1[8];
-#pragma unroll
-                    for (int l = 0; l < 8; ++l) {
-                        d0[l] = odd ? recv[l] : mine[l];
-                        d1[l] = odd ? mine[l] : recv[l];
-                    }
-                    put(odd ? chp : chs[c], d0);
-                    put(odd ? chs[c] : chp, d1);
-                }
-            } else {
-                __half hr[L], hi[L];
-#pragma unroll
-                for (int l = 0; l < L; ++l) {
-                    const float xr = yc[l].x * scv[c], xi = yc[l].y * scv[c];
-                    if constexpr (MODE == OUT_I8) {
-                        hr[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xr))));
-                        hi[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xi))));
-                    } else {
-                        hr[l] = __float2half_rn(xr);
-                        hi[l] = __float2half_rn(xi);
-                    }
-                }
-                __half* o = static_cast<__half*>(p.spec) + blk + 2 * i * TB + (t0 + fg * L) % TB;
-                if constexpr (L == 8) {
-                    uint32_t u[8];
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        u[m] = pack_half2(hr[2 * m], hr[2 * m + 1]);
-                        u[4 + m] = pack_half2(hi[2 * m], hi[2 * m + 1]);
-                    }
-                    st_global_v8(o, u);
-                } else {
-                    // 4-frame halves of the 8-frame run: into the exchange buffer of the CTA of the
-                    // pair that writes this channel (rank 0: channels < M/2), at frame offset 4 rank
-                    static_assert(L == 4 && kPair, "fp16 runs of 4 frames only in cluster pairs");
-                    (void)o;
-                    const int ch = chs[c];
-                    const uint32_t owner = ch < M / 2 ? 0u : 1u;
-                    // slot 2c + rank (c = 0 re, 1 im), word ch % (M/2)
-                    unsigned char* dre = xch + (static_cast<size_t>(rank) * (M / 2) + ch % (M / 2)) * 8;
-                    unsigned char* dim = dre + static_cast<size_t>(M) * 8;
-                    const uint2 vr = make_uint2(pack_half2(hr[0], hr[1]), pack_half2(hr[2], hr[3]));
-                    const uint2 vi = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
-                    if (owner == rank) {
-                        *reinterpret_cast<uint2*>(dre) = vr;
-                        *reinterpret_cast<uint2*>(dim) = vi;
-                    } else {
-                        st_async_v2(cluster_map(dre, owner), vr.x, vr.y, peer_xfull);
-                        st_async_v2(cluster_map(dim, owner), vi.x, vi.y, peer_xfull);
-                    }
-                }
-            }
-        };
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            const int k = chs[2 * q], kc = chs[2 * q + 1];
-            const float2 wk = twN[k];
-            const float2 pk = pfa[k], pm = pfa[kc];
-            float2 yk[L], ym[L];
-#pragma unroll
-            for (int l = 0; l < L; ++l) {
-                const int fl = fg * L + l;
-                const float2* Xl = X + fl * P::PADM;
-                const float2 zk = Xl[pad16(k)];
-                const float2 zm = Xl[pad16(kc)];
-                float2 xk, xmk;
-                if (k == 0) {
-                    xk = make_float2(zk.x + zk.y, 0.0f);       // DC
-                    xmk = make_float2(zm.x, -zm.y);            // channel M/2 (zm = z[M/2])
-                } else {
-                    const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-                    const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-                    const float2 wo = cmul(wk, o);
-                    xk = cadd(e, wo);
-                    const float2 d = csub(e, wo);
-                    xmk = make_float2(d.x, -d.y);
-                }
-                const float2 fr = fra[fl];
-                yk[l] = cmul(xk, cmul(pk, fr));
-                ym[l] = cmul(xmk, cmul(pm, fr));
-            }
-            emit(2 * q, yk);
-            emit(2 * q + 1, ym);
-        }
-        }  // live
-        if constexpr (kPair) {
-            // our halves are in (local stores, barrier) and the partner's have landed (xfull): write
-            // this CTA's half of the channels as whole 8-frame pieces (rows 2i, 2i+1: 32 bytes)
-            __syncthreads();
-            if (!mbar_wait_cluster(&ctl.xfull, it & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
-            const int64_t kb8 = (t0 - 4 * static_cast<int>(rank)) / TB;
-            __half* spec = static_cast<__half*>(p.spec);
-            const uint2* xw = reinterpret_cast<const uint2*>(xch);   // [slot][M/2]
-            for (int j = tid; j < M / 2; j += kThreads) {
-                const int ch = static_cast<int>(rank) * (M / 2) + j;
-                const uint2 r0 = xw[j], r1 = xw[M / 2 + j], i0 = xw[M + j], i1 = xw[3 * (M / 2) + j];
-                const uint32_t u[8] = {r0.x, r0.y, r1.x, r1.y, i0.x, i0.y, i1.x, i1.y};
-                st_global_v8(spec + (static_cast<int64_t>(ch) * ntb + kb8) * blk_elems + 2 * i * TB, u);
-            }
-        }
-    }
-
-    // incoherent beam of this thread's points
-    __syncthreads();
-    if (!abort_flag) {
-        if (live) {
-#pragma unroll
-            for (int l = 0; l < L; ++l)
-#pragma unroll
-                for (int c = 0; c < 2 * NP; ++c)
-                    p.beams[static_cast<int64_t>(t0 + fg * L + l) * M + chs[c]] = incr[l][c];
-        }
-    } else if (tid == 0) {
-        // copies issued ahead of an aborted iteration must land before the CTA exits: the
-        // stages of iterations it and it + 1, and the antenna tables of iterations it - 1 and it
-        mbar_wait(&bar[it & 1], (it >> 1) & 1, nullptr, 0);
-        if (it + 1 < n_iter) mbar_wait(&bar[(it + 1) & 1], ((it + 1) >> 1) & 1, nullptr, 0);
-        if (it > 0) mbar_wait(&tbar[(it - 1) & 1], ((it - 1) >> 1) & 1, nullptr, 0);
-        mbar_wait(&tbar[it & 1], (it >> 1) & 1, nullptr, 0);
-    }
-    if constexpr (kPair) cluster_sync();   // neither CTA leaves while the other may still write into it
-}
-
-template <int M, int MODE>
-__global__ void __launch_bounds__(kThreads, 1) fengine_kernel(const FeParams p) {
-    __shared__ __align__(8) FeCtl ctl;
-    fengine_cta<M, MODE>(p, blockIdx.x, ctl);
-}
-
-// Several integrations (sub-arrays of any supported FFT size) in one launch: CTA b runs
-// frame block b - first[s] of sub-array s, first[s] <= b < first[s + 1].
-template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1) fengine_batched_kernel(const FeBatch* __restrict__ tab) {
-    __shared__ __align__(8) FeCtl ctl;
-    __shared__ int sub;
-    if (threadIdx.x == 0) {
-        int q = 0;
-        while (q + 1 < tab->n_sub && static_cast<int>(blockIdx.x) >= tab->first[q + 1]) ++q;
-        sub = q;
-    }
-    __syncthreads();
-    const FeParams& p = tab->p[sub];
-    const int block = blockIdx.x - tab->first[sub];
-    switch (p.n_chan) {
-        case 32: fengine_cta<32, MODE>(p, block, ctl); break;
-        case 64: fengine_cta<64, MODE>(p, block, ctl); break;
-        case 128: fengine_cta<128, MODE>(p, block, ctl); break;
-        case 256: fengine_cta<256, MODE>(p, block, ctl); break;
-        case 512: fengine_cta<512, MODE>(p, block, ctl); break;
-        case 1024: fengine_cta<1024, MODE>(p, block, ctl); break;
-        case 2048: fengine_cta<2048, MODE>(p, block, ctl); break;
-        default: break;
-    }
-}
-
-template <int M, int MODE>
-cudaError_t launch_t(const FeParams& p, cudaStream_t s) {
-    using P = Plan<M>;
-    const size_t smem = Smem<M>::total;
-    cudaError_t e = cudaFuncSetAttribute(fengine_kernel<M, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    const int grid = (p.n_int + P::F - 1) / P::F;
-    if constexpr (Epi<M, MODE>::kPair) {
-        // clusters of two consecutive frame blocks (grid is even: n_int is a multiple of 16)
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(grid);
-        cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, fengine_kernel<M, MODE>, p);
-        if (e != cudaSuccess) return e;
-        return cudaGetLastError();
-    }
-    fengine_kernel<M, MODE><<<grid, kThreads, smem, s>>>(p);
-    return cudaGetLastError();
-}
-
-template <int MODE>
-cudaError_t launch_mode(const FeParams& p, cudaStream_t s) {
-    switch (p.n_chan) {
-        case 32: return launch_t<32, MODE>(p, s);
-        case 64: return launch_t<64, MODE>(p, s);
-        case 128: return launch_t<128, MODE>(p, s);
-        case 256: return launch_t<256, MODE>(p, s);
-        case 512: return launch_t<512, MODE>(p, s);
-        case 1024: return launch_t<1024, MODE>(p, s);
-        case 2048: return launch_t<2048, MODE>(p, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 __global__ void phasor_setup_kernel(int n_ant, int n_chan, int n_fft, int n_int, int64_t g0_val,
                                     const int64_t* __restrict__ g0_ptr,
                                     const double* __restrict__ tau, const double* __restrict__ phi0,
@@ -794,10 +117,11 @@ int fengine_frames_per_cta(int n_fft) { return kChanFrames / (n_fft / 2); }
 
 cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s) {
     if (p.n_chan * 2 != p.n_fft) return cudaErrorInvalidValue;
+    if (p.blank) return launch_fengine_blank(p, mode, s);   // fengine_blank.cu
     switch (mode) {
-        case OUT_FP32: return launch_mode<OUT_FP32>(p, s);
-        case OUT_I8: return launch_mode<OUT_I8>(p, s);
-        case OUT_F16: return launch_mode<OUT_F16>(p, s);
+        case OUT_FP32: return launch_mode<OUT_FP32, false>(p, s);
+        case OUT_I8: return launch_mode<OUT_I8, false>(p, s);
+        case OUT_F16: return launch_mode<OUT_F16, false>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -80,6 +80,15 @@ struct corr {
     // auto-power dumps for the RFI stage (0 = off)
     int dump = 0;
     float* d_power = nullptr;
+    // time-domain voltage blanker (Sec. 5, Eq. 3-4; blank_M = 0: off): blocks of 2^blank_log2 samples,
+    // noise table [n_in][noise_L], per-block statistics [n_in][blank_nb][4] of the last integration
+    // (blank_cap blocks per input allocated), covering blank_n samples of each row
+    double blank_M = 0.0;
+    int blank_log2 = 0;
+    float* d_noise = nullptr;
+    int noise_L = 0;
+    int32_t* d_blank = nullptr;
+    int64_t blank_cap = 0, blank_nb = 0, blank_n = 0;
     // per-stage timing: kTimedMax integrations x 5 events (before set-up and after each stage)
     bool timing = false;
     std::vector<cudaEvent_t> tev;
