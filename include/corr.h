@@ -199,13 +199,14 @@ int corr_read_power(corr_t* h, float* out, void** device_ptr);
 
 /* Time-domain voltage blanker (Sec. 5, Eq. 3-4) on the raw samples of every later
  * integration, before the FFT: each input row is cut into blocks of `block` samples (a
- * power of two in [n_fft, 32768], counted from the integration's first sample); in each
+ * power of two in [4096, 32768], counted from the integration's first sample); in each
  * block the median med and MAD = median |x - med| are found, and samples with
  * |x - med| > M MAD / 0.6745 are replaced by rint(sigma g[i][pos mod L]) clamped to +-127,
  * sigma = MAD / 0.6745 rounded to FP32, g the caller's table `noise` [n_in][L] of
  * standard-normal values (L a power of two <= 2^24; pos = sample position in the row), so
  * the noise is independent between inputs.  M = 0 turns the blanker off (block, noise
- * ignored); the paper uses M = 2.5-3.  Not available to batch members. */
+ * ignored); the paper uses M = 2.5-3.  The blanked copy of the samples lives in a device
+ * buffer of the handle (n_in x (n_int n_fft + max_delay) bytes).  Not available to batch members. */
 int corr_set_blanker(corr_t* h, double M, int block, const float* noise, int L);
 /* The blanker's statistics of the last integration: out [n_in][*n_blocks][4] int32 =
  * 2 med, 4 MAD, T2 = floor(2 M MAD / 0.6745) (a sample is replaced iff |2x - 2 med| > T2)

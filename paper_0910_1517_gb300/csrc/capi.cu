@@ -177,12 +177,11 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
         const int64_t need = static_cast<int64_t>(h->n_int) * h->n_fft + max_int_delay(h);
         const int64_t nb = (need + (int64_t(1) << h->blank_log2) - 1) >> h->blank_log2;
         if (nb > h->blank_cap) return fail(CORR_E_STATE, "max_delay grew after corr_set_blanker: set the blanker again");
-        CU(launch_blank_stats(x, ld, h->n_in, need, 1 << h->blank_log2, h->blank_M, h->d_blank, s));
-        fp.blank = h->d_blank;
-        fp.blank_log2 = h->blank_log2;
-        fp.blank_nb = nb;
-        fp.noise = h->d_noise;
-        fp.noise_mask = h->noise_L - 1;
+        CU(launch_blank(x, ld, h->n_in, need, 1 << h->blank_log2, h->blank_M, h->d_noise, h->noise_L - 1,
+                        h->d_blank, h->d_blanked, h->blanked_ld, s));
+        fp.x = h->d_blanked;            // the F-engine reads the blanked rows
+        fp.ld = h->blanked_ld;
+        fp.n_avail = need;
         h->blank_nb = nb;
         h->blank_n = need;
     }
@@ -496,6 +495,7 @@ int corr_destroy(corr_t* h) {
     if (h->d_power) cudaFree(h->d_power);
     if (h->d_noise) cudaFree(h->d_noise);
     if (h->d_blank) cudaFree(h->d_blank);
+    if (h->d_blanked) cudaFree(h->d_blanked);
     if (h->d_xtab) cudaFree(h->d_xtab);
     if (h->d_items) cudaFree(h->d_items);
     if (h->cstream) cudaStreamSynchronize(h->cstream);
@@ -849,21 +849,25 @@ int corr_set_blanker(corr_t* h, double M, int block, const float* noise, int L) 
     CU(cudaStreamSynchronize(h->stream));
     if (h->d_noise) cudaFree(h->d_noise);
     if (h->d_blank) cudaFree(h->d_blank);
+    if (h->d_blanked) cudaFree(h->d_blanked);
     h->d_noise = nullptr;
     h->d_blank = nullptr;
+    h->d_blanked = nullptr;
     h->blank_M = 0.0;
     h->blank_cap = h->blank_nb = h->blank_n = 0;
     if (M == 0.0) return CORR_OK;
     int lg = 0;
     while ((1 << lg) < block && lg < 30) ++lg;
-    if (block < h->n_fft || block > 32768 || (1 << lg) != block)
-        return fail(CORR_E_INVAL, "block must be a power of two in [n_fft, 32768]");
+    if (block < 4096 || block > 32768 || (1 << lg) != block)
+        return fail(CORR_E_INVAL, "block must be a power of two in [4096, 32768]");
     if (!noise || L < 1 || L > (1 << 24) || (L & (L - 1))) return fail(CORR_E_INVAL, "noise table: L a power of two in [1, 2^24]");
     const size_t nn = static_cast<size_t>(h->n_in) * L;
     CU(dalloc(&h->d_noise, nn));
     CU(cudaMemcpy(h->d_noise, noise, nn * sizeof(float), cudaMemcpyHostToDevice));
     h->blank_cap = (static_cast<int64_t>(h->n_int) * h->n_fft + h->max_delay + block - 1) / block;
     CU(cudaMalloc(&h->d_blank, sizeof(int32_t) * 4 * static_cast<size_t>(h->n_in) * h->blank_cap));
+    h->blanked_ld = h->blank_cap * block;   // block: a power of two >= 4096, so a multiple of 16
+    CU(cudaMalloc(&h->d_blanked, static_cast<size_t>(h->n_in) * h->blanked_ld));
     h->blank_M = M;
     h->blank_log2 = lg;
     h->noise_L = L;

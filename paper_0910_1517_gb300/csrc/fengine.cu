@@ -117,11 +117,10 @@ int fengine_frames_per_cta(int n_fft) { return kChanFrames / (n_fft / 2); }
 
 cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s) {
     if (p.n_chan * 2 != p.n_fft) return cudaErrorInvalidValue;
-    if (p.blank) return launch_fengine_blank(p, mode, s);   // fengine_blank.cu
     switch (mode) {
-        case OUT_FP32: return launch_mode<OUT_FP32, false>(p, s);
-        case OUT_I8: return launch_mode<OUT_I8, false>(p, s);
-        case OUT_F16: return launch_mode<OUT_F16, false>(p, s);
+        case OUT_FP32: return launch_mode<OUT_FP32>(p, s);
+        case OUT_I8: return launch_mode<OUT_I8>(p, s);
+        case OUT_F16: return launch_mode<OUT_F16>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }

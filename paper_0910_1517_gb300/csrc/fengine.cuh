@@ -46,14 +46,6 @@ struct FeParams {
     const float* scale;    // [n_in][n_chan] requantisation scales (I8 / F16)
     void* spec;            // spectra in the K-block layout
     float* beams;          // [2][n_int][n_chan] raw-resolution beams (0 inc, 1 coh)
-    // time-domain voltage blanker (nullptr: off): per (input, block) statistics [n_in][blank_nb][4]
-    // (2 med, 4 MAD, T2, count) of blocks of 2^blank_log2 >= n_fft samples, and the noise table
-    // [n_in][noise_mask + 1] of standard-normal values
-    const int32_t* blank;
-    int blank_log2;
-    int64_t blank_nb;
-    const float* noise;
-    int noise_mask;
     const float2* tw;      // FFT twiddles laid out by fengine_twiddles()
     unsigned* err;
 };
@@ -75,8 +67,6 @@ int fengine_frames_per_cta(int n_fft);
 // Twiddle tables of the F-engine's FFT plan for n_fft, computed in FP64 and rounded once.
 std::vector<float2> fengine_twiddles(int n_fft);
 cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s);
-// The same with the voltage blanker compiled in (p.blank set; block >= n_fft).
-cudaError_t launch_fengine_blank(const FeParams& p, int mode, cudaStream_t s);
 
 // pf, ff and D for one integration from the FP64 delay / fringe model.
 // g0_dev, when given, is read on the device instead of g0 (graph-captured launches).
@@ -89,11 +79,14 @@ cudaError_t launch_phasor_setup(int n_ant, int n_chan, int n_fft, int n_int, int
 cudaError_t launch_power_dumps(const float* spec, int n_in, int n_chan, int n_int, int dump, float* P,
                                cudaStream_t s);
 
-// Voltage-blanker statistics (blank.cu) of rows x[i][0..n) cut into blocks of `block` samples
-// (a multiple of 16): stats [n_in][ceil(n / block)][4] = 2 med, 4 MAD, T2 = floor(2 M MAD / 0.6745),
-// samples with |2x - 2 med| > T2.
-cudaError_t launch_blank_stats(const int8_t* x, int64_t ld, int n_in, int64_t n, int block, double M,
-                               int32_t* stats, cudaStream_t s);
+// Time-domain voltage blanker (blank.cu, Sec. 5, Eq. 3-4) on rows x[i][0..n) cut into blocks of
+// `block` samples (a multiple of 16): per block, stats [n_in][ceil(n / block)][4] = 2 med, 4 MAD,
+// T2 = floor(2 M MAD / 0.6745) and the number of samples with |2x - 2 med| > T2, and the blanked
+// rows y[i][0..n) (stride ldy): flagged samples replaced by rint(sigma g[i][pos & noise_mask])
+// clamped to +-127, sigma = MAD / 0.6745 rounded to FP32; the rest copied.
+cudaError_t launch_blank(const int8_t* x, int64_t ld, int n_in, int64_t n, int block, double M,
+                         const float* noise, int noise_mask, int32_t* stats, int8_t* y, int64_t ldy,
+                         cudaStream_t s);
 
 // beams_out[b][to][k] = mean over beam_avg frames of beams_raw[b][to*beam_avg + j][k]
 cudaError_t launch_beam_average(const float* raw, float* out, int n_int, int n_chan, int beam_avg,

@@ -1,14 +1,12 @@
-// fengine_impl.cuh -- the F-engine kernel body (templates), shared by fengine.cu (plain
-// launches and the batched kernel) and fengine_blank.cu (launches with the time-domain voltage
-// blanker compiled in).  Each including translation unit gets its own copy (internal linkage).
+// fengine_impl.cuh -- the F-engine kernel body (templates) and its launchers, included by
+// fengine.cu.
 //
 // One CTA owns a block of F consecutive frames (F * n_chan = 8192 complex
 // channel-frames) and walks over every input (antenna x polarisation) in turn:
 //   1. the F frames of input i, offset by its integer delay D_a (Sec. 2.1,
 //      Sec. 2.3.2: the read pointer is moved, no data is shifted), arrive in
 //      shared memory through one TMA-engine bulk copy, double-buffered so the
-//      next input streams in while this one is transformed; with the blanker on
-//      (Sec. 5, Eq. 3-4), outlying samples are replaced as they are converted;
+//      next input streams in while this one is transformed;
 //   2. each frame is an n_fft-point real FFT computed as an M = n_fft/2-point
 //      complex FFT of (x[2n] + i x[2n+1]) -- Stockham radix-16/16/R passes, 16
 //      points per thread in registers, shared memory between passes -- followed
@@ -227,40 +225,8 @@ __device__ __forceinline__ uint32_t pack_half2(__half lo, __half hi) {
     return static_cast<uint32_t>(__half_as_ushort(lo)) | (static_cast<uint32_t>(__half_as_ushort(hi)) << 16);
 }
 
-// Time-domain voltage blanker (Sec. 5, Eq. 3-4), applied to this thread's samples of one frame
-// while they enter the FFT: sample position pos of input i (the frame starts at fpos) lies in
-// block pos >> blank_log2, whose statistics (blank.cu) give 2 med and T2; the sample is replaced
-// iff |2x - 2 med| > T2, by rint(sigma * g[i][pos mod L]) clamped to +-127, sigma = MAD / 0.6745
-// rounded to FP32.  A frame spans at most two blocks (block >= n_fft).
-template <int NB>
-__device__ __forceinline__ void blank_samples(const FeParams& p, int i, int64_t fpos, int t, float2 (&v)[kE]) {
-    const int64_t b0 = fpos >> p.blank_log2;
-    const int32_t* sa = p.blank + (static_cast<int64_t>(i) * p.blank_nb + b0) * 4;
-    const bool has_b = b0 + 1 < p.blank_nb;
-    const int med_a = sa[0], t_a = sa[2];
-    const int med_b = has_b ? sa[4] : med_a, t_b = has_b ? sa[6] : t_a;
-    const int cut = static_cast<int>(((b0 + 1) << p.blank_log2) - fpos);   // first offset in block b0 + 1
-    auto one = [&](float& xv, int rel) {
-        const bool nb = rel >= cut;
-        const int x = static_cast<int>(xv);
-        if (abs(2 * x - (nb ? med_b : med_a)) > (nb ? t_b : t_a)) {
-            const int mad4 = sa[nb ? 5 : 1];
-            const float sig = static_cast<float>(mad4 / 4.0 / 0.6745);
-            const int64_t pos = fpos + rel;
-            const float g = p.noise[static_cast<int64_t>(i) * (p.noise_mask + 1) + (pos & p.noise_mask)];
-            xv = fminf(127.0f, fmaxf(-127.0f, rintf(__fmul_rn(sig, g))));
-        }
-    };
-#pragma unroll
-    for (int r = 0; r < kE; ++r) {
-        const int n = t + r * NB;
-        one(v[r].x, 2 * n);
-        one(v[r].y, 2 * n + 1);
-    }
-}
-
 // The F-engine work of one CTA: frame block `block` of the integration described by p.
-template <int M, int MODE, bool BLANK = false>
+template <int M, int MODE>
 __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl& ctl) {
     using P = Plan<M>;
     using S = Smem<M>;
@@ -427,7 +393,6 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
                                        static_cast<float>(static_cast<signed char>(st[2 * n + 1])));
                 }
             }
-            if constexpr (BLANK) blank_samples<NB>(p, i, s0 + static_cast<int64_t>(f) * N, t, v);
             Dft<16>::template run<1>(v);
         }
         __syncthreads();  // the previous iteration's split has finished reading X and its antenna tables
@@ -647,10 +612,10 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
     if constexpr (kPair) cluster_sync();   // neither CTA leaves while the other may still write into it
 }
 
-template <int M, int MODE, bool BLANK>
+template <int M, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) fengine_kernel(const FeParams p) {
     __shared__ __align__(8) FeCtl ctl;
-    fengine_cta<M, MODE, BLANK>(p, blockIdx.x, ctl);
+    fengine_cta<M, MODE>(p, blockIdx.x, ctl);
 }
 
 // Several integrations (sub-arrays of any supported FFT size) in one launch: CTA b runs
@@ -679,11 +644,11 @@ __global__ void __launch_bounds__(kThreads, 1) fengine_batched_kernel(const FeBa
     }
 }
 
-template <int M, int MODE, bool BLANK>
+template <int M, int MODE>
 cudaError_t launch_t(const FeParams& p, cudaStream_t s) {
     using P = Plan<M>;
     const size_t smem = Smem<M>::total;
-    cudaError_t e = cudaFuncSetAttribute(fengine_kernel<M, MODE, BLANK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(fengine_kernel<M, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const int grid = (p.n_int + P::F - 1) / P::F;
@@ -701,24 +666,24 @@ cudaError_t launch_t(const FeParams& p, cudaStream_t s) {
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, fengine_kernel<M, MODE, BLANK>, p);
+        e = cudaLaunchKernelEx(&cfg, fengine_kernel<M, MODE>, p);
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
-    fengine_kernel<M, MODE, BLANK><<<grid, kThreads, smem, s>>>(p);
+    fengine_kernel<M, MODE><<<grid, kThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-template <int MODE, bool BLANK>
+template <int MODE>
 cudaError_t launch_mode(const FeParams& p, cudaStream_t s) {
     switch (p.n_chan) {
-        case 32: return launch_t<32, MODE, BLANK>(p, s);
-        case 64: return launch_t<64, MODE, BLANK>(p, s);
-        case 128: return launch_t<128, MODE, BLANK>(p, s);
-        case 256: return launch_t<256, MODE, BLANK>(p, s);
-        case 512: return launch_t<512, MODE, BLANK>(p, s);
-        case 1024: return launch_t<1024, MODE, BLANK>(p, s);
-        case 2048: return launch_t<2048, MODE, BLANK>(p, s);
+        case 32: return launch_t<32, MODE>(p, s);
+        case 64: return launch_t<64, MODE>(p, s);
+        case 128: return launch_t<128, MODE>(p, s);
+        case 256: return launch_t<256, MODE>(p, s);
+        case 512: return launch_t<512, MODE>(p, s);
+        case 1024: return launch_t<1024, MODE>(p, s);
+        case 2048: return launch_t<2048, MODE>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }

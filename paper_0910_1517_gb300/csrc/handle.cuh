@@ -88,6 +88,8 @@ struct corr {
     float* d_noise = nullptr;
     int noise_L = 0;
     int32_t* d_blank = nullptr;
+    int8_t* d_blanked = nullptr;        // the blanked rows the F-engine reads, stride blanked_ld
+    int64_t blanked_ld = 0;
     int64_t blank_cap = 0, blank_nb = 0, blank_n = 0;
     // per-stage timing: kTimedMax integrations x 5 events (before set-up and after each stage)
     bool timing = false;

@@ -11,7 +11,7 @@ from synth import make_config
 pytestmark = pytest.mark.gpu
 
 N_ANT, N_POL, N_FFT, N_INT = 8, 2, 1024, 64
-BLOCK, M, L = 2048, 3.0, 4096
+BLOCK, M, L = 4096, 3.0, 4096
 
 
 @pytest.fixture(scope="module")
@@ -121,14 +121,14 @@ def test_blanker_arguments(env):
     h = corr.corr_create(4, 2, 1024, 16)
     g = np.zeros((8, 64), np.float32)
     try:
-        for block, gg in ((512, g), (3000, g), (65536, g), (2048, np.zeros((8, 48), np.float32))):
+        for block, gg in ((512, g), (2048, g), (3000, g), (65536, g), (4096, np.zeros((8, 48), np.float32))):
             with pytest.raises(corr.CorrError) as ei:
                 corr.corr_set_blanker(h, 3.0, block, gg)
             assert ei.value.code == -1
         with pytest.raises(corr.CorrError) as ei:
             corr.corr_read_blank_stats(h)
         assert ei.value.code == -7                     # off
-        corr.corr_set_blanker(h, 3.0, 2048, g)
+        corr.corr_set_blanker(h, 3.0, 4096, g)
         with pytest.raises(corr.CorrError) as ei:
             corr.corr_read_blank_stats(h)
         assert ei.value.code == -7                     # not run yet
@@ -139,7 +139,7 @@ def test_blanker_arguments(env):
         b = corr.corr_batch_create([h])
         try:
             with pytest.raises(corr.CorrError) as ei:
-                corr.corr_set_blanker(h, 3.0, 2048, g)
+                corr.corr_set_blanker(h, 3.0, 4096, g)
             assert ei.value.code == -7
         finally:
             corr.corr_batch_destroy(b)
