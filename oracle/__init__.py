@@ -10,6 +10,7 @@ Functions and the passage each follows (Roy et al., arXiv:0910.1517):
   fengine   -- integer delay, real DFT, FSTC + fringe phasor (Sec. 2.1, Eq. 2)
   xengine   -- MAC over N(N+1)/2 baselines x n_pol^2 products (Sec. 2.1)
   beams     -- incoherent and coherent array beams (Sec. 2.2, 4.3)
+  multibeam -- several phased beams with full-polar products or voltages (Sec. 2.2, 5)
   requant   -- 8-bit requantisation of spectra (precision form; Sec. 4.1 analogue)
   xint      -- exact integer MAC on requantised spectra (Sec. 4.1)
   mad_flag  -- median-absolute-deviation flagger (Sec. 5, Eq. 3-4)
@@ -69,6 +70,7 @@ def lib():
         L.oracle_patch_stats.argtypes = [i32, i32, P, f64, P, P, P, P]
         L.oracle_rfi_forward.argtypes = [i32, i32, i32, P, P, P]
         L.oracle_rfi_loss_grad.argtypes = [i32, i32, i32, P, P, P, P, P]
+        L.oracle_multibeam.argtypes = [i32, i32, i32, i32, P, i32, P, i32, i32, P]
         L.oracle_mad_blank.argtypes = [i32, i64, P, i64, i32, f64, P, i32, P, P]
         L.cpu_fft_fengine.argtypes = [i32, i32, i32, i32, P, i64, i64, P, P, P, i64, P]
         _lib = L
@@ -171,6 +173,20 @@ def beams(Y, n_ant, n_pol, n_fft, gain=None, theta=None, inc_mask=None, coh_mask
                             None if th is None else _p(th), _p(im), _p(cm), beam_avg, _p(B))
     _check(rc, "beams")
     return B[0], B[1]
+
+
+def multibeam(Y, n_ant, n_pol, w, products=0, avg=1):
+    """Phased beams [n_beams][n_frames/avg][n_chans][4] (float64) from spectra Y [n_in][t][c] and
+    complex weights w [n_beams][n_ant][n_chans]: full-polar products (0) or voltages (1)."""
+    n_in, n_frames, nch = Y.shape
+    w = np.asarray(w)
+    nb = w.shape[0]
+    assert n_in == n_ant * n_pol and w.shape == (nb, n_ant, nch)
+    wr = _as_ri(w.astype(np.complex128))
+    out = np.zeros((nb, n_frames // avg, nch, 4), dtype=np.float64)
+    _check(lib().oracle_multibeam(n_ant, n_pol, nch, n_frames, _p(_as_ri(Y)), nb, _p(wr), products, avg, _p(out)),
+           "multibeam")
+    return out
 
 
 def requant(Y, scale):

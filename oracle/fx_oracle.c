@@ -201,6 +201,57 @@ int oracle_beams(int n_ant, int n_pol, int n_fft, int n_chans, int n_frames,
 }
 
 /*
+ * Multiple phased-array beams with full-polar products (Sec. 2.2: the coherent beamformer
+ * gives the voltage cross products for the Stokes parameters; Sec. 5: several phased beams
+ * covering different directions).  Beam b's voltage in polarisation p is
+ *   U_bp[t][k] = sum_a w[b][a][k] Y_{a,p}[t][k]   (complex weights, FP64 here),
+ * and each output point carries four numbers averaged over `avg` frames:
+ *   products = 0 (full polar):  |U_b0|^2, |U_b1|^2, Re(U_b0 conj U_b1), Im(U_b0 conj U_b1)
+ *   products = 1 (voltages, avg = 1): Re U_b0, Im U_b0, Re U_b1, Im U_b1
+ * (the entries of polarisation 1 are 0 when n_pol = 1).
+ * Y [n_in][n_frames][n_chans][2]; w [n_beams][n_ant][n_chans][2] (the channels of Y);
+ * out [n_beams][n_frames / avg][n_chans][4].
+ */
+int oracle_multibeam(int n_ant, int n_pol, int n_chans, int n_frames, const double* Y, int n_beams,
+                     const double* w, int products, int avg, double* out) {
+    if (n_ant < 1 || (n_pol != 1 && n_pol != 2) || n_beams < 1 || avg < 1 || n_frames % avg ||
+        (products != 0 && products != 1) || (products == 1 && avg != 1))
+        return OR_EINVAL;
+    const int n_out = n_frames / avg;
+#pragma omp parallel for schedule(static)
+    for (int b = 0; b < n_beams; ++b)
+        for (int c = 0; c < n_chans; ++c)
+            for (int to = 0; to < n_out; ++to) {
+                double acc[4] = {0.0, 0.0, 0.0, 0.0};
+                for (int tt = 0; tt < avg; ++tt) {
+                    const int t = to * avg + tt;
+                    double ur[2] = {0.0, 0.0}, ui[2] = {0.0, 0.0};
+                    for (int p = 0; p < n_pol; ++p)
+                        for (int a = 0; a < n_ant; ++a) {
+                            const double* y = Y + (((size_t)(a * n_pol + p) * n_frames + t) * n_chans + c) * 2;
+                            const double* wa = w + (((size_t)b * n_ant + a) * n_chans + c) * 2;
+                            ur[p] += wa[0] * y[0] - wa[1] * y[1];
+                            ui[p] += wa[0] * y[1] + wa[1] * y[0];
+                        }
+                    if (products == 0) {
+                        acc[0] += ur[0] * ur[0] + ui[0] * ui[0];
+                        acc[1] += ur[1] * ur[1] + ui[1] * ui[1];
+                        acc[2] += ur[0] * ur[1] + ui[0] * ui[1];    /* Re(U0 conj U1) */
+                        acc[3] += ui[0] * ur[1] - ur[0] * ui[1];    /* Im(U0 conj U1) */
+                    } else {
+                        acc[0] = ur[0];
+                        acc[1] = ui[0];
+                        acc[2] = ur[1];
+                        acc[3] = ui[1];
+                    }
+                }
+                double* o = out + (((size_t)b * n_out + to) * n_chans + c) * 4;
+                for (int q = 0; q < 4; ++q) o[q] = products == 0 ? acc[q] / avg : acc[q];
+            }
+    return OR_OK;
+}
+
+/*
  * Requantisation of spectra to 8-bit integers with per-(input, channel)
  * scales: q = clamp(rint(y * s), -127, 127), round half to even.  This is
  * the FP64 reading of the requantiser; the bit-exact X-engine check uses the

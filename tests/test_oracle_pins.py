@@ -509,3 +509,51 @@ def test_mad_blank_noise_index_is_the_row_position_mod_L(orc):
     assert out[0, 5] == out[0, 69] == out[0, 133] == round(sig0) != 0
     assert out[0, 1029] == round(sig1)
     assert out[0, 6] == out[0, 70] == 0
+
+
+# ------------------------------------------------ multiple phased beams, full polar (Sec. 2.2, 5)
+
+def test_multibeam_reduces_to_the_coherent_beam_and_to_autocorrelations(orc):
+    """A beam with the coherent beam's weights has RR* + LL* equal to the (pinned) coherent beam;
+    a beam with one unit weight has the per-frame autocorrelation products of that antenna; the
+    voltage form is the weighted sum itself and its products are the full-polar form."""
+    s = make_config(1, n_int=16)
+    nch = s.n_fft // 2
+    Y = orc.fengine(s.x, s.n_ant, s.n_pol, s.n_fft, s.n_int, s.delay, s.phi0, s.rate)
+    rng = np.random.default_rng(5)
+    gain = rng.uniform(0.5, 1.5, s.n_ant)
+    theta = rng.uniform(-np.pi, np.pi, (s.n_ant, nch))
+    coh = np.array([1, 0, 1, 1], np.uint8)
+    w0 = (gain * coh)[:, None] * np.exp(1j * theta)
+    w1 = np.zeros((s.n_ant, nch), complex)
+    w1[2] = 1.0
+    W = np.stack([w0, w1])
+    B = orc.multibeam(Y, s.n_ant, s.n_pol, W, 0, 4)
+    _, Bc = orc.beams(Y, s.n_ant, s.n_pol, s.n_fft, gain=gain, theta=theta, coh_mask=coh, beam_avg=4)
+    assert np.allclose(B[0, ..., 0] + B[0, ..., 1], Bc, rtol=1e-12)
+    V1 = np.stack([orc.xengine(Y[:, t:t + 1], s.n_ant, s.n_pol) for t in range(s.n_int)])  # per-frame V
+    b = 2 * s.n_ant - 2 * (2 - 1) // 2                  # baseline (2, 2), row-major over a <= a'
+    auto = V1[:, :, b]                                  # [t][c][pq]
+    avg = auto.reshape(4, 4, nch, 4).mean(axis=1)
+    assert np.allclose(B[1, ..., 0], avg[..., 0].real) and np.allclose(B[1, ..., 1], avg[..., 3].real)
+    assert np.allclose(B[1, ..., 2], avg[..., 1].real) and np.allclose(B[1, ..., 3], avg[..., 1].imag)
+    U = orc.multibeam(Y, s.n_ant, s.n_pol, W, 1, 1)
+    u0, u1 = U[..., 0] + 1j * U[..., 1], U[..., 2] + 1j * U[..., 3]
+    assert np.allclose(u0[1], Y[2 * 2 + 0]) and np.allclose(u1[1], Y[2 * 2 + 1])
+    F = orc.multibeam(Y, s.n_ant, s.n_pol, W, 0, 1)
+    assert np.allclose(F[..., 0], np.abs(u0) ** 2) and np.allclose(F[..., 2] + 1j * F[..., 3], u0 * np.conj(u1))
+
+
+def test_multibeam_linearity_and_single_polarisation(orc):
+    s = make_config(2, n_ant=3, n_fft=64, n_int=8, seed=9)
+    Y = orc.fengine(s.x, s.n_ant, s.n_pol, s.n_fft, s.n_int, s.delay, s.phi0, s.rate)
+    rng = np.random.default_rng(2)
+    w = rng.standard_normal((2, s.n_ant, 32)) + 1j * rng.standard_normal((2, s.n_ant, 32))
+    U = orc.multibeam(Y, s.n_ant, s.n_pol, w, 1, 1)
+    U2 = orc.multibeam(Y, s.n_ant, s.n_pol, 2.5j * w, 1, 1)
+    z, z2 = U[..., 0] + 1j * U[..., 1], U2[..., 0] + 1j * U2[..., 1]
+    assert np.allclose(z2, 2.5j * z)
+    Y1 = Y[0::2]                                        # pol 0 only: a single-polarisation array
+    F = orc.multibeam(Y1, s.n_ant, 1, w, 0, 2)
+    assert np.all(F[..., 1] == 0) and np.all(F[..., 2] == 0) and np.all(F[..., 3] == 0)
+    assert np.allclose(F[..., 0], orc.multibeam(Y, s.n_ant, s.n_pol, w, 0, 2)[..., 0])
