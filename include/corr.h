@@ -197,6 +197,21 @@ int corr_info(corr_t* h, int64_t* out6);
 int corr_set_power_dump(corr_t* h, int dump);
 int corr_read_power(corr_t* h, float* out, void** device_ptr);
 
+/* Multiple phased-array beams (Sec. 2.2: the coherent beamformer's voltage cross products
+ * for the Stokes parameters; Sec. 5: several phased beams covering different directions),
+ * formed after every later CORR_FP32 / CORR_FP32TC integration from its FP32 spectra:
+ * U_bp[t][k] = sum_a w[b][a][k] Y_{a,p}[t][k], weights [n_beams][n_ant][n_fft/2] complex
+ * (re, im pairs, host, copied).  CORR_BEAM_FULLPOL: per beam, window of avg frames and channel,
+ * the window means of |U_b0|^2, |U_b1|^2, Re U_b0 conj U_b1, Im U_b0 conj U_b1 (polarisation-1
+ * entries 0 when n_pol = 1); CORR_BEAM_VOLTAGE (avg = 1): Re U_b0, Im U_b0, Re U_b1, Im U_b1.
+ * n_beams in [0, 64] (0: off); avg a power of two with max(64, avg) dividing n_int.  The
+ * integration fails with CORR_E_STATE in the int8 / FP16 modes (no FP32 spectra). */
+enum { CORR_BEAM_FULLPOL = 0, CORR_BEAM_VOLTAGE = 1 };
+int corr_set_multibeam(corr_t* h, int n_beams, const float* weights, int products, int avg);
+/* The last integration's beams, out [n_beams][n_int/avg][n_fft/2][4] float32; blocking as in
+ * corr_read_visibilities. */
+int corr_read_multibeam(corr_t* h, float* out, int blocking);
+
 /* Time-domain voltage blanker (Sec. 5, Eq. 3-4) on the raw samples of every later
  * integration, before the FFT: each input row is cut into blocks of `block` samples (a
  * power of two in [4096, 32768], counted from the integration's first sample); in each

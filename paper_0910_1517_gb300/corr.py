@@ -55,6 +55,8 @@ SIGNATURES = {
     "corr_batch_tune": ([_P, _P, _P], _I),
     "corr_read_power": ([_P, _P, ctypes.POINTER(ctypes.c_void_p)], _I),
     "corr_set_blanker": ([_P, ctypes.c_double, _I, _P, _I], _I),
+    "corr_set_multibeam": ([_P, _I, _P, _I, _I], _I),
+    "corr_read_multibeam": ([_P, _P, _I], _I),
     "corr_read_blank_stats": ([_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], _I),
     # include/rfi.h
     "rfi_n_params": ([], _I),
@@ -291,6 +293,26 @@ def corr_power_device(h):
     dev = ctypes.c_void_p()
     _ok(load().corr_read_power(h, None, ctypes.byref(dev)))
     return dev.value
+
+
+CORR_BEAM_FULLPOL, CORR_BEAM_VOLTAGE = 0, 1
+
+
+def corr_set_multibeam(h, weights=None, products: int = 0, avg: int = 1):
+    """Phased beams from complex weights [n_beams][n_ant][n_chan] (None: off)."""
+    if weights is None:
+        return _ok(load().corr_set_multibeam(h, 0, None, 0, 1))
+    w = np.asarray(weights)
+    wr = np.ascontiguousarray(np.stack([w.real, w.imag], axis=-1), dtype=np.float32)
+    return _ok(load().corr_set_multibeam(h, w.shape[0], _ptr(wr), int(products), int(avg)))
+
+
+def corr_read_multibeam(h, n_beams: int, n_out: int, blocking: int = 1):
+    """The last integration's beams [n_beams][n_out = n_int/avg][n_chan][4] float32."""
+    i = corr_info(h)
+    out = np.empty((n_beams, n_out, i["n_chan"], 4), dtype=np.float32)
+    _ok(load().corr_read_multibeam(h, _ptr(out), blocking))
+    return out
 
 
 def corr_set_blanker(h, M: float, block: int = 0, noise=None):

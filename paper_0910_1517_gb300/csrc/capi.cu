@@ -136,6 +136,8 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
         return fail(CORR_E_STATE, "CORR_I8 / CORR_F16 need requantisation scales (corr_set_scales)");
     if (h->dump > 0 && h->xmode != CORR_FP32 && h->xmode != CORR_FP32TC)
         return fail(CORR_E_STATE, "power dumps need the FP32 spectra (CORR_FP32 or CORR_FP32TC)");
+    if (h->n_mb > 0 && h->xmode != CORR_FP32 && h->xmode != CORR_FP32TC)
+        return fail(CORR_E_STATE, "multiple beams need the FP32 spectra (CORR_FP32 or CORR_FP32TC)");
     const int nd = h->n_ant;
     // stage the model in a pinned slot no queued copy still reads (integrations may be queued
     // back to back while earlier ones run)
@@ -212,6 +214,9 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
     }
     if (int rc = mark(h, 3, s)) return rc;
     if (h->beam_avg > 1) CU(launch_beam_average(h->d_beams_raw, h->d_beams, h->n_int, h->n_chan, h->beam_avg, s));
+    if (h->n_mb > 0)
+        CU(launch_multibeam(static_cast<const float*>(h->d_spec), h->n_ant, h->n_pol, h->n_chan, h->n_int, h->d_mbw,
+                            h->n_mb, h->mb_products, h->mb_avg, h->d_mb, h->d_err, s));
     if (int rc = mark(h, 4, s)) return rc;
     if (h->timing && h->t_count < kTimedMax) h->t_count += 1;
     CU(cudaEventRecord(h->ev_done, s));
@@ -496,6 +501,8 @@ int corr_destroy(corr_t* h) {
     if (h->d_noise) cudaFree(h->d_noise);
     if (h->d_blank) cudaFree(h->d_blank);
     if (h->d_blanked) cudaFree(h->d_blanked);
+    if (h->d_mbw) cudaFree(h->d_mbw);
+    if (h->d_mb) cudaFree(h->d_mb);
     if (h->d_xtab) cudaFree(h->d_xtab);
     if (h->d_items) cudaFree(h->d_items);
     if (h->cstream) cudaStreamSynchronize(h->cstream);
@@ -871,6 +878,55 @@ int corr_set_blanker(corr_t* h, double M, int block, const float* noise, int L) 
     h->blank_M = M;
     h->blank_log2 = lg;
     h->noise_L = L;
+    return CORR_OK;
+}
+
+int corr_set_multibeam(corr_t* h, int n_beams, const float* weights, int products, int avg) {
+    if (int rc = check_handle(h)) return rc;
+    if (n_beams < 0 || n_beams > multibeam_max_beams())
+        return fail(CORR_E_INVAL, "n_beams must be in [0, %d]", multibeam_max_beams());
+    if (n_beams > 0) {
+        const int fcta = avg > 64 ? avg : 64;
+        if (avg < 1 || (avg & (avg - 1)) || h->n_int % fcta)
+            return fail(CORR_E_INVAL, "avg must be a power of two with max(64, avg) dividing n_int");
+        if (products != CORR_BEAM_FULLPOL && products != CORR_BEAM_VOLTAGE) return fail(CORR_E_INVAL, "unknown products");
+        if (products == CORR_BEAM_VOLTAGE && avg != 1) return fail(CORR_E_INVAL, "beam voltages need avg = 1");
+        if (!weights) return fail(CORR_E_INVAL, "weights required");
+    }
+    CU(cudaStreamSynchronize(h->stream));
+    if (h->d_mbw) cudaFree(h->d_mbw);
+    if (h->d_mb) cudaFree(h->d_mb);
+    h->d_mbw = nullptr;
+    h->d_mb = nullptr;
+    h->n_mb = 0;
+    if (n_beams == 0) return CORR_OK;
+    // weights [beam][antenna][channel] -> [channel][beam * n_ant + antenna] (padded to even)
+    const int ws = multibeam_wstride(n_beams, h->n_ant);
+    std::vector<float2> w(static_cast<size_t>(h->n_chan) * ws, make_float2(0.0f, 0.0f));
+    for (int b = 0; b < n_beams; ++b)
+        for (int a = 0; a < h->n_ant; ++a)
+            for (int k = 0; k < h->n_chan; ++k) {
+                const float* src = weights + 2 * ((static_cast<size_t>(b) * h->n_ant + a) * h->n_chan + k);
+                w[static_cast<size_t>(k) * ws + b * h->n_ant + a] = make_float2(src[0], src[1]);
+            }
+    CU(dalloc(&h->d_mbw, w.size()));
+    CU(cudaMemcpy(h->d_mbw, w.data(), w.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    const size_t n_out = static_cast<size_t>(n_beams) * (h->n_int / avg) * h->n_chan;
+    CU(dalloc(&h->d_mb, n_out));
+    CU(cudaMemset(h->d_mb, 0, n_out * sizeof(float4)));
+    h->n_mb = n_beams;
+    h->mb_products = products;
+    h->mb_avg = avg;
+    return CORR_OK;
+}
+
+int corr_read_multibeam(corr_t* h, float* out, int blocking) {
+    if (int rc = check_handle(h)) return rc;
+    if (h->n_mb == 0) return fail(CORR_E_STATE, "multiple beams are off (corr_set_multibeam)");
+    if (!out) return fail(CORR_E_INVAL, "out required");
+    if (int rc = settle(h, blocking)) return rc;
+    CU(cudaMemcpy(out, h->d_mb, sizeof(float4) * static_cast<size_t>(h->n_mb) * (h->n_int / h->mb_avg) * h->n_chan,
+                  cudaMemcpyDeviceToHost));
     return CORR_OK;
 }
 

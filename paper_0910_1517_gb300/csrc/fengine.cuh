@@ -88,6 +88,15 @@ cudaError_t launch_blank(const int8_t* x, int64_t ld, int n_in, int64_t n, int b
                          const float* noise, int noise_mask, int32_t* stats, int8_t* y, int64_t ldy,
                          cudaStream_t s);
 
+// Phased beams with full-polar products or voltages (multibeam.cu) from the FP32 spectra:
+// w [n_chan][wstride] float2, entry b * n_ant + a the weight of antenna a in beam b for the channel
+// (wstride = multibeam_wstride(): n_beams * n_ant rounded up to even); out [n_beams][n_int/avg][n_chan]
+// float4.  avg a power of two, max(64, avg) dividing n_int; products 1 (voltages) needs avg = 1.
+int multibeam_max_beams();
+int multibeam_wstride(int n_beams, int n_ant);
+cudaError_t launch_multibeam(const float* spec, int n_ant, int n_pol, int n_chan, int n_int, const float2* w,
+                             int n_beams, int products, int avg, float4* out, unsigned* err, cudaStream_t s);
+
 // beams_out[b][to][k] = mean over beam_avg frames of beams_raw[b][to*beam_avg + j][k]
 cudaError_t launch_beam_average(const float* raw, float* out, int n_int, int n_chan, int beam_avg,
                                 cudaStream_t s);

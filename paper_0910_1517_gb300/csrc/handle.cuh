@@ -87,6 +87,11 @@ struct corr {
     int blank_log2 = 0;
     float* d_noise = nullptr;
     int noise_L = 0;
+    // multiple phased beams (n_mb = 0: off): weights [n_chan][multibeam_wstride] float2, output
+    // [n_mb][n_int / mb_avg][n_chan] float4 of the last integration
+    int n_mb = 0, mb_products = 0, mb_avg = 1;
+    float2* d_mbw = nullptr;
+    float4* d_mb = nullptr;
     int32_t* d_blank = nullptr;
     int8_t* d_blanked = nullptr;        // the blanked rows the F-engine reads, stride blanked_ld
     int64_t blanked_ld = 0;
