@@ -366,6 +366,49 @@ def run_e2e(args, corr, torch, dist, s, coh, world, xmode):
     return e2e
 
 
+def run_multibeam_leg(corr, torch, s, xt, ld, coh, xmode, k, st_plain, pk, n_beams=16, avg=32):
+    """Multiple phased beams (Sec. 2.2, 5) on the GMRT-scale step: 16 beams with per-antenna phase
+    gradients across the band (different pointings), full-polar products in 32-frame (~1 ms)
+    windows, read from the FP32 spectra after the X-engine.  Reports the beam kernel's time (the
+    last stage of the step) against its rooflines: the FP32 spectra read once from HBM, and the
+    useful FP32 work n_beams x n_in complex MACs per channel-frame."""
+    rng = np.random.default_rng(31)
+    delays = rng.uniform(-20, 20, (n_beams, N_ANT, 1))          # samples of geometric delay per beam
+    W = np.exp(2j * np.pi * delays * np.arange(N_CHAN)[None, None, :] / N_FFT)
+    h2 = corr.corr_create(N_ANT, N_POL, N_FFT, N_INT)
+    try:
+        corr.corr_set_delays(h2, s.delay, s.phi0, s.rate)
+        corr.corr_set_beam_weights(h2, None, None, None, coh)
+        corr.corr_set_mode(h2, xmode, 0, 1)
+        corr.corr_set_multibeam(h2, W, 0, avg)
+        stream = torch.cuda.current_stream()
+        for j in range(3):
+            corr.corr_integrate_device(h2, xt, n_avail=ld, g0=j * N_INT, stream=stream)
+        torch.cuda.synchronize()
+        corr.corr_set_timing(h2, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for j in range(k):
+            corr.corr_integrate_device(h2, xt, n_avail=ld, g0=(3 + j) * N_INT, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st, cnt = corr.corr_stage_times(h2)
+        corr.corr_set_timing(h2, 0)
+        ms = e0.elapsed_time(e1) / k
+        mb_ms = float(st[3] / max(cnt, 1))
+        flop = 8.0 * n_beams * N_IN * N_CHAN * N_INT
+        bytes_ = N_CHAN * N_INT * 2 * N_IN * 4 + n_beams * (N_INT // avg) * N_CHAN * 16
+        return {"workload": f"GMRT-scale step + {n_beams} phased beams, full-polar products in {avg}-frame windows",
+                "ms_per_step": ms, "value": step_samples() / (ms * 1e-3), "unit": UNIT,
+                "beam_kernel_ms": mb_ms,
+                "roofline_hbm": {"achieved": bytes_ / (mb_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                 "frac": bytes_ / (mb_ms * 1e-3) / 1e9 / pk["hbm_gbs"]},
+                "roofline_alu": {"achieved": flop / (mb_ms * 1e-3) / 1e12, "peak": fp32_peak_tflops(pk),
+                                 "unit": "TFLOP/s", "frac": flop / (mb_ms * 1e-3) / 1e12 / fp32_peak_tflops(pk)}}
+    finally:
+        corr.corr_destroy(h2)
+
+
 def run_blank_leg(corr, torch, s, xt, ld, coh, xmode, k, st_plain):
     """The time-domain MAD voltage blanker (Sec. 5, Eq. 3-4) on the GMRT-scale step: broadband
     bursts (+-90 counts, 100 samples each, independent signs per input) cover ~2.5 % of a copy of
@@ -648,6 +691,10 @@ def run_ours(args, world, rank, local_rank):
     blank = None if args.no_extras else run_blank_leg(corr, torch, s, xt, ld, coh, all_forms[args.xmode],
                                                       max(10, min(K, 50)), st)
 
+    # multiple phased beams (16 beams, full polar, 32-frame windows) on the same samples
+    multibeam = None if args.no_extras else run_multibeam_leg(corr, torch, s, xt, ld, coh, all_forms[args.xmode],
+                                                              max(10, min(K, 50)), st, pk)
+
     # end to end through the public API: pinned host samples in, visibilities + beams out
     e2e = None if args.no_extras else run_e2e(args, corr, torch, dist, s, coh, world, all_forms[args.xmode])
 
@@ -695,7 +742,7 @@ def run_ours(args, world, rank, local_rank):
             "roofline": roofline, "stages": stages, "precision_forms": modes,
             "batched_subarrays": batch, "learned_rfi": rfi,
             "e2e": e2e, "gpu_launches": 3 * K, "clocks": clocks, "cpu_baseline": cpu,
-            "cpu_fft_baseline": cpu_fft, "voltage_blanker": blank,
+            "cpu_fft_baseline": cpu_fft, "voltage_blanker": blank, "multibeam": multibeam,
         }
     emit(line, rank)
     if dist:
