@@ -14,6 +14,8 @@ Functions and the passage each follows (Roy et al., arXiv:0910.1517):
   requant   -- 8-bit requantisation of spectra (precision form; Sec. 4.1 analogue)
   xint      -- exact integer MAC on requantised spectra (Sec. 4.1)
   mad_flag  -- median-absolute-deviation flagger (Sec. 5, Eq. 3-4)
+  unpack4   -- ADC-format ingest of the 4-bit, 33 MHz mode: demultiplex 4 inputs per card and
+            sign-extend each 4-bit sample to 8 bits (Sec. 2.3.1, 2.3.2)
   mad_blank -- the time-domain voltage blanker built on it (Sec. 5): flagged raw samples
             replaced by pre-computed Gaussian noise scaled by the block's MAD / 0.6745
   fft_fengine (cpu_fft_baseline.c) -- not an oracle: the bench's second CPU baseline,
@@ -70,6 +72,7 @@ def lib():
         L.oracle_patch_stats.argtypes = [i32, i32, P, f64, P, P, P, P]
         L.oracle_rfi_forward.argtypes = [i32, i32, i32, P, P, P]
         L.oracle_rfi_loss_grad.argtypes = [i32, i32, i32, P, P, P, P, P]
+        L.oracle_unpack4.argtypes = [i32, i64, P, i64, P]
         L.oracle_multibeam.argtypes = [i32, i32, i32, i32, P, i32, P, i32, i32, P]
         L.oracle_mad_blank.argtypes = [i32, i64, P, i64, i32, f64, P, i32, P, P]
         L.cpu_fft_fengine.argtypes = [i32, i32, i32, i32, P, i64, i64, P, P, P, i64, P]
@@ -173,6 +176,17 @@ def beams(Y, n_ant, n_pol, n_fft, gain=None, theta=None, inc_mask=None, coh_mask
                             None if th is None else _p(th), _p(im), _p(cm), beam_avg, _p(B))
     _check(rc, "beams")
     return B[0], B[1]
+
+
+def unpack4(packed, n):
+    """ADC-format 4-bit ingest: card rows packed uint8 [n_cards][>= 2n] -> int8 rows [4 n_cards][n]."""
+    packed = np.asarray(packed)
+    assert packed.dtype == np.uint8 and packed.ndim == 2
+    if packed.strides[1] != 1:
+        packed = np.ascontiguousarray(packed)
+    out = np.zeros((4 * packed.shape[0], n), dtype=np.int8)
+    _check(lib().oracle_unpack4(packed.shape[0], n, _p(packed), packed.strides[0], _p(out)), "unpack4")
+    return out
 
 
 def multibeam(Y, n_ant, n_pol, w, products=0, avg=1):

@@ -402,6 +402,26 @@ int oracle_mad_blank(int n_in, int64_t n, const int8_t* x, int64_t ld, int block
     return rc;
 }
 
+/*
+ * ADC-format ingest of the paper's 33 MHz, 4-bit mode (Sec. 2.3.1, 2.3.2): each ADC card
+ * digitises 4 analog inputs and its stream interleaves them sample by sample, 4 bits each;
+ * the pipeline demultiplexes the 4 streams and unpacks every sample to 8 bits.  Reading: for
+ * sample s of card c, byte 2s holds input 4c (bits 0-3) and input 4c+1 (bits 4-7), byte 2s+1
+ * inputs 4c+2 and 4c+3; a 4-bit sample is two's complement (-8..7), sign-extended to 8 bits.
+ * packed [n_cards] rows of ld bytes (2 n used); out [4 n_cards][n] int8.
+ */
+int oracle_unpack4(int n_cards, int64_t n, const uint8_t* packed, int64_t ld, int8_t* out) {
+    if (n_cards < 1 || n < 0 || ld < 2 * n) return OR_EINVAL;
+    for (int c = 0; c < n_cards; ++c)
+        for (int64_t s = 0; s < n; ++s)
+            for (int j = 0; j < 4; ++j) {
+                const uint8_t byte = packed[(int64_t)c * ld + 2 * s + j / 2];
+                const int nib = (j % 2) ? (byte >> 4) & 0xF : byte & 0xF;
+                out[(int64_t)(4 * c + j) * n + s] = (int8_t)(nib >= 8 ? nib - 16 : nib);
+            }
+    return OR_OK;
+}
+
 /* Threads the OpenMP runtime will use (1 without OpenMP). */
 int oracle_threads(void) {
 #ifdef _OPENMP

@@ -557,3 +557,24 @@ def test_multibeam_linearity_and_single_polarisation(orc):
     F = orc.multibeam(Y1, s.n_ant, 1, w, 0, 2)
     assert np.all(F[..., 1] == 0) and np.all(F[..., 2] == 0) and np.all(F[..., 3] == 0)
     assert np.allclose(F[..., 0], orc.multibeam(Y, s.n_ant, s.n_pol, w, 0, 2)[..., 0])
+
+
+# ------------------------------------------------ ADC-format 4-bit ingest (Sec. 2.3.1, 2.3.2)
+
+def test_unpack4_hand_worked_bytes(orc):
+    # card 0, sample 0: 0x7F -> input 0 = -1 (0xF), input 1 = 7; 0x80 -> input 2 = 0, input 3 = -8
+    # sample 1: 0x21 -> 1, 2; 0xE9 -> -7 (0x9), -2 (0xE)
+    p = np.array([[0x7F, 0x80, 0x21, 0xE9]], np.uint8)
+    out = orc.unpack4(p, 2)
+    assert out.tolist() == [[-1, 1], [7, 2], [0, -7], [-8, -2]]
+
+
+def test_unpack4_round_trip_and_card_demux(orc):
+    rng = np.random.default_rng(4)
+    x = rng.integers(-8, 8, (12, 1001)).astype(np.int8)     # 3 cards of 4 inputs
+    nib = (x.astype(np.int16) & 0xF).astype(np.uint8)
+    packed = np.zeros((3, 2 * 1001 + 6), np.uint8)            # rows with slack: ld > 2n
+    for c in range(3):
+        packed[c, 0:2002:2] = nib[4 * c] | (nib[4 * c + 1] << 4)
+        packed[c, 1:2002:2] = nib[4 * c + 2] | (nib[4 * c + 3] << 4)
+    assert np.array_equal(orc.unpack4(packed, 1001), x)
