@@ -197,6 +197,18 @@ int corr_info(corr_t* h, int64_t* out6);
 int corr_set_power_dump(corr_t* h, int dump);
 int corr_read_power(corr_t* h, float* out, void** device_ptr);
 
+/* ADC-format ingest of the 33 MHz, 4-bit mode (Sec. 2.3.1, 2.3.2): each ADC card interleaves 4
+ * inputs sample by sample, 4 bits (two's complement) each -- byte 2s of card c holds inputs 4c
+ * (bits 0-3) and 4c+1 (bits 4-7) of sample s, byte 2s+1 inputs 4c+2 and 4c+3; card c carries
+ * inputs 4c .. 4c+3 (n_in a multiple of 4).  The library demultiplexes and sign-extends to the
+ * int8 rows the F-engine reads.  corr_push_samples_4bit: host packed [n_in/4][ld] (ld even,
+ * >= 2 n), streaming as corr_push_samples (half the host-to-device bytes).
+ * corr_integrate_4bit_device: one integration from device packed rows (2-byte aligned, ld even,
+ * >= 2 n_avail), as corr_integrate_device. */
+int corr_push_samples_4bit(corr_t* h, const uint8_t* packed, int64_t ld, int64_t n, int64_t seq);
+int corr_integrate_4bit_device(corr_t* h, const uint8_t* packed, int64_t ld, int64_t n_avail, int64_t g0,
+                               void* stream);
+
 /* Multiple phased-array beams (Sec. 2.2: the coherent beamformer's voltage cross products
  * for the Stokes parameters; Sec. 5: several phased beams covering different directions),
  * formed after every later CORR_FP32 / CORR_FP32TC integration from its FP32 spectra:

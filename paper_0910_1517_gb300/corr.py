@@ -56,6 +56,8 @@ SIGNATURES = {
     "corr_read_power": ([_P, _P, ctypes.POINTER(ctypes.c_void_p)], _I),
     "corr_set_blanker": ([_P, ctypes.c_double, _I, _P, _I], _I),
     "corr_set_multibeam": ([_P, _I, _P, _I, _I], _I),
+    "corr_push_samples_4bit": ([_P, _P, _L, _L, _L], _I),
+    "corr_integrate_4bit_device": ([_P, _P, _L, _L, _L, _P], _I),
     "corr_read_multibeam": ([_P, _P, _I], _I),
     "corr_read_blank_stats": ([_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], _I),
     # include/rfi.h
@@ -171,6 +173,18 @@ def corr_push_samples(h, x, seq: int, allow_dataloss: bool = False):
     n = x.shape[1]
     allow = (-4,) if allow_dataloss else ()
     return _ok(load().corr_push_samples(h, _ptr(x), n, seq), allow)
+
+
+def corr_push_samples_4bit(h, packed, n: int, seq: int, allow_dataloss: bool = False):
+    """packed: host uint8 [n_in/4][ld] ADC card rows (4 inputs x 4 bits per 2 bytes), n samples."""
+    ld = packed.strides[0] if isinstance(packed, np.ndarray) else packed.stride(0)
+    allow = (-4,) if allow_dataloss else ()
+    return _ok(load().corr_push_samples_4bit(h, _ptr(packed), ld, n, seq), allow)
+
+
+def corr_integrate_4bit_device(h, packed, n_avail: int, g0: int = 0, stream=None):
+    """packed: device uint8 tensor [n_in/4][ld] of ADC card rows; n_avail samples per input."""
+    return _ok(load().corr_integrate_4bit_device(h, _ptr(packed), packed.stride(0), n_avail, g0, _stream(stream)))
 
 
 def corr_push_samples_device(h, x, seq: int, stream=None):

@@ -337,7 +337,10 @@ int enqueue_output(corr* h, int64_t index) {
 // stream into the current ring; a full ring launches its integration on h->stream (after the
 // copies) and the next integration fills the other ring, once the integration before that is
 // done with it.  Returns when x has been read (host sources; device sources stay stream-ordered).
-int ingest(corr* h, const int8_t* x, int64_t spitch, int64_t n, int64_t seq, cudaMemcpyKind kind) {
+// Streaming ingest of n samples per input: put(dst, take, done) queues on h->cstream the copy of
+// samples done .. done + take - 1 of every input into the ring rows at dst (stride ring_ld).
+template <typename Put>
+int ingest(corr* h, Put&& put, int64_t n, int64_t seq, bool from_host) {
     int rc = CORR_OK;
     if (!h->ring_started) {
         h->ring_started = true;
@@ -360,7 +363,7 @@ int ingest(corr* h, const int8_t* x, int64_t spitch, int64_t n, int64_t seq, cud
     while (done < n) {
         int8_t* ring = h->cur_ring ? h->d_ring2 : h->d_ring;
         const int64_t take = std::min(n - done, need - h->fill);
-        CU(cudaMemcpy2DAsync(ring + h->fill, h->ring_ld, x + done, spitch, take, h->n_in, kind, h->cstream));
+        if (int e = put(ring + h->fill, take, done)) return e;
         h->fill += take;
         done += take;
         if (h->fill == need) {
@@ -391,7 +394,7 @@ int ingest(corr* h, const int8_t* x, int64_t spitch, int64_t n, int64_t seq, cud
         }
     }
     h->seq_next += n;
-    if (kind == cudaMemcpyHostToDevice) {   // the caller may reuse x
+    if (from_host) {   // the caller may reuse its buffer
         CU(cudaEventRecord(h->ev_copied, h->cstream));
         CU(cudaEventSynchronize(h->ev_copied));
     }
@@ -503,6 +506,8 @@ int corr_destroy(corr_t* h) {
     if (h->d_blanked) cudaFree(h->d_blanked);
     if (h->d_mbw) cudaFree(h->d_mbw);
     if (h->d_mb) cudaFree(h->d_mb);
+    if (h->d_stage4) cudaFree(h->d_stage4);
+    if (h->d_unpack) cudaFree(h->d_unpack);
     if (h->d_xtab) cudaFree(h->d_xtab);
     if (h->d_items) cudaFree(h->d_items);
     if (h->cstream) cudaStreamSynchronize(h->cstream);
@@ -648,7 +653,32 @@ int corr_push_samples(corr_t* h, const int8_t* x, int64_t n, int64_t seq) {
     if (n == 0) return CORR_OK;
     if (!h->d_ring)
         if (int rc = alloc_ring(h)) return rc;
-    return ingest(h, x, n, n, seq, cudaMemcpyHostToDevice);
+    auto put = [&](int8_t* dst, int64_t take, int64_t done) -> int {
+        CU(cudaMemcpy2DAsync(dst, h->ring_ld, x + done, n, take, h->n_in, cudaMemcpyHostToDevice, h->cstream));
+        return CORR_OK;
+    };
+    return ingest(h, put, n, seq, true);
+}
+
+int corr_push_samples_4bit(corr_t* h, const uint8_t* packed, int64_t ld, int64_t n, int64_t seq) {
+    if (int rc = check_handle(h)) return rc;
+    if (h->n_in % 4) return fail(CORR_E_INVAL, "4-bit ADC ingest needs n_in a multiple of 4 (4 inputs per card)");
+    if (!packed || n < 0 || (ld & 1) || ld < 2 * n) return fail(CORR_E_INVAL, "bad packed buffer (ld even, >= 2 n)");
+    if (n == 0) return CORR_OK;
+    if (!h->d_ring)
+        if (int rc = alloc_ring(h)) return rc;
+    const int n_cards = h->n_in / 4;
+    if (!h->d_stage4) CU(cudaMalloc(&h->d_stage4, static_cast<size_t>(n_cards) * 2 * corr::kStage4));
+    auto put = [&](int8_t* dst, int64_t take, int64_t done) -> int {
+        for (int64_t q = 0; q < take; q += corr::kStage4) {   // packed pieces through the staging rows
+            const int64_t len = std::min<int64_t>(corr::kStage4, take - q);
+            CU(cudaMemcpy2DAsync(h->d_stage4, 2 * corr::kStage4, packed + 2 * (done + q), ld, 2 * len, n_cards,
+                                 cudaMemcpyHostToDevice, h->cstream));
+            CU(launch_unpack4(h->d_stage4, 2 * corr::kStage4, n_cards, len, dst + q, h->ring_ld, h->n_sm, h->cstream));
+        }
+        return CORR_OK;
+    };
+    return ingest(h, put, n, seq, true);
 }
 
 int corr_set_output_ring(corr_t* h, float* vis, float* beams, int n_slots) {
@@ -734,7 +764,36 @@ int corr_push_samples_device(corr_t* h, const int8_t* x, int64_t n, int64_t seq,
     // order the copy after the caller's producer work
     CU(cudaEventRecord(h->ev_aux, static_cast<cudaStream_t>(stream)));
     CU(cudaStreamWaitEvent(h->cstream, h->ev_aux, 0));
-    return ingest(h, x, n, n, seq, cudaMemcpyDeviceToDevice);
+    auto put = [&](int8_t* dst, int64_t take, int64_t done) -> int {
+        CU(cudaMemcpy2DAsync(dst, h->ring_ld, x + done, n, take, h->n_in, cudaMemcpyDeviceToDevice, h->cstream));
+        return CORR_OK;
+    };
+    return ingest(h, put, n, seq, false);
+}
+
+int corr_integrate_4bit_device(corr_t* h, const uint8_t* packed, int64_t ld, int64_t n_avail, int64_t g0,
+                               void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (h->n_in % 4) return fail(CORR_E_INVAL, "4-bit ADC ingest needs n_in a multiple of 4 (4 inputs per card)");
+    if (!packed || (ld & 1) || ld < 2 * n_avail || (reinterpret_cast<uintptr_t>(packed) & 1))
+        return fail(CORR_E_INVAL, "packed must be 2-byte aligned with an even ld >= 2 n_avail");
+    const int64_t need = static_cast<int64_t>(h->n_int) * h->n_fft + max_int_delay(h);
+    if (n_avail < need)
+        return fail(CORR_E_RANGE, "n_avail = %lld < n_int * n_fft + max delay = %lld", (long long)n_avail,
+                    (long long)need);
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : h->stream;
+    const int64_t ldu = ((n_avail + 15) / 16) * 16 + 16;
+    if (ldu > h->unpack_ld) {   // grow the unpacked rows (the stream is drained first)
+        CU(cudaStreamSynchronize(s));
+        CU(cudaStreamSynchronize(h->stream));
+        if (h->d_unpack) cudaFree(h->d_unpack);
+        h->d_unpack = nullptr;
+        h->unpack_ld = 0;
+        CU(cudaMalloc(&h->d_unpack, static_cast<size_t>(h->n_in) * ldu));
+        h->unpack_ld = ldu;
+    }
+    CU(launch_unpack4(packed, ld, h->n_in / 4, n_avail, h->d_unpack, h->unpack_ld, h->n_sm, s));
+    return run_integration(h, h->d_unpack, h->unpack_ld, n_avail, g0, s);
 }
 
 int corr_integrate_device(corr_t* h, const int8_t* x, int64_t ld, int64_t n_avail, int64_t g0, void* stream) {

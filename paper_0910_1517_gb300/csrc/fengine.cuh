@@ -97,6 +97,11 @@ int multibeam_wstride(int n_beams, int n_ant);
 cudaError_t launch_multibeam(const float* spec, int n_ant, int n_pol, int n_chan, int n_int, const float2* w,
                              int n_beams, int products, int avg, float4* out, unsigned* err, cudaStream_t s);
 
+// ADC-format 4-bit ingest (ingest4.cu): card rows packed[c][0..2n) (stride ld, even) -> int8 rows
+// rows[4c + j][0..n) (stride ldr), the 4 interleaved inputs of each card demultiplexed and sign-extended.
+cudaError_t launch_unpack4(const uint8_t* packed, int64_t ld, int n_cards, int64_t n, int8_t* rows, int64_t ldr,
+                           int n_sm, cudaStream_t s);
+
 // beams_out[b][to][k] = mean over beam_avg frames of beams_raw[b][to*beam_avg + j][k]
 cudaError_t launch_beam_average(const float* raw, float* out, int n_int, int n_chan, int beam_avg,
                                 cudaStream_t s);

@@ -92,6 +92,12 @@ struct corr {
     int n_mb = 0, mb_products = 0, mb_avg = 1;
     float2* d_mbw = nullptr;
     float4* d_mb = nullptr;
+    // 4-bit ADC-format ingest: packed staging rows (kStage4 samples per card row) for pushes, and
+    // the unpacked int8 rows of device integrations
+    static constexpr int64_t kStage4 = int64_t(1) << 22;
+    uint8_t* d_stage4 = nullptr;
+    int8_t* d_unpack = nullptr;
+    int64_t unpack_ld = 0;
     int32_t* d_blank = nullptr;
     int8_t* d_blanked = nullptr;        // the blanked rows the F-engine reads, stride blanked_ld
     int64_t blanked_ld = 0;
