@@ -317,7 +317,19 @@ def run_reference(args, world, rank):
 
 # -------------------------------------------------------------------- ours
 
-def run_e2e(args, corr, torch, dist, s, coh, world, xmode):
+def pack4(x):
+    """4-bit ADC card rows (4 inputs x 4 bits per 2 bytes) of the int8 stream x scaled by 1/5."""
+    n_cards, n = x.shape[0] // 4, x.shape[1]
+    out = np.empty((n_cards, 2 * n), np.uint8)
+    for c in range(n_cards):                   # one card (4 rows) at a time
+        nib = (np.clip(np.rint(x[4 * c:4 * c + 4].astype(np.float32) / 5.0), -8, 7).astype(np.int8)
+               .view(np.uint8) & 0xF)
+        out[c, 0::2] = nib[0] | (nib[1] << 4)
+        out[c, 1::2] = nib[2] | (nib[3] << 4)
+    return out
+
+
+def run_e2e(args, corr, torch, dist, s, coh, world, xmode, four_bit=False):
     """The public streaming path: samples pushed from pinned host memory (corr_push_samples,
     two sample rings so the copy of integration j + 1 overlaps the correlation of j) and every
     integration's visibilities and beams copied back into a ring of pinned host slots
@@ -325,8 +337,15 @@ def run_e2e(args, corr, torch, dist, s, coh, world, xmode):
     in host memory."""
     K = args.steps
     body = N_INT * N_FFT
-    hx0 = torch.from_numpy(np.ascontiguousarray(s.x[:, :body + 2048])).pin_memory()
-    hx = torch.from_numpy(np.ascontiguousarray(s.x[:, 2048:2048 + body])).pin_memory()
+    if four_bit:   # the paper's 33 MHz mode: 4-bit samples, 4 inputs per ADC card
+        p4 = pack4(s.x)
+        hx0 = torch.from_numpy(np.ascontiguousarray(p4[:, :2 * (body + 2048)])).pin_memory()
+        hx = torch.from_numpy(np.ascontiguousarray(p4[:, 2 * 2048:2 * (2048 + body)])).pin_memory()
+        push = lambda buf, n, q: corr.corr_push_samples_4bit(he, buf.numpy(), n, q)
+    else:
+        hx0 = torch.from_numpy(np.ascontiguousarray(s.x[:, :body + 2048])).pin_memory()
+        hx = torch.from_numpy(np.ascontiguousarray(s.x[:, 2048:2048 + body])).pin_memory()
+        push = lambda buf, n, q: corr.corr_push_samples(he, buf.numpy(), q)
     n_slots = 2
     hv = torch.empty((n_slots, N_CHAN, N_BL, 4, 2), dtype=torch.float32).pin_memory()
     hb = torch.empty((n_slots, 2, N_INT, N_CHAN), dtype=torch.float32).pin_memory()
@@ -336,12 +355,12 @@ def run_e2e(args, corr, torch, dist, s, coh, world, xmode):
     corr.corr_set_mode(he, xmode, 0, 1)
     corr.corr_set_output_ring(he, hv.numpy(), hb.numpy(), n_slots)
     seq = 0
-    corr.corr_push_samples(he, hx0.numpy(), seq)            # first integration + the delay overlap
+    push(hx0, body + 2048, seq)                            # first integration + the delay overlap
     seq += body + 2048
     corr.corr_wait_output(he, 0)
     j = 1
     for _ in range(2):                                     # warm the path
-        corr.corr_push_samples(he, hx.numpy(), seq)
+        push(hx, body, seq)
         seq += body
         corr.corr_wait_output(he, j)
         j += 1
@@ -350,18 +369,20 @@ def run_e2e(args, corr, torch, dist, s, coh, world, xmode):
         dist.barrier()
     t0 = time.perf_counter()
     for q in range(k3):
-        corr.corr_push_samples(he, hx.numpy(), seq)        # launches integration j + q
+        push(hx, body, seq)                                # launches integration j + q
         seq += body
         if q > 0:
             corr.corr_wait_output(he, j + q - 1)          # the previous one's results, in host memory
     corr.corr_wait_output(he, j + k3 - 1)
     dt = time.perf_counter() - t0
     dt = max_over_ranks(dt, dist, "cuda")
-    e2e = {"value": job_rate(world, k3 * step_samples(), dt), "unit": UNIT, "h2d_bytes_per_step": N_IN * body,
+    e2e = {"value": job_rate(world, k3 * step_samples(), dt), "unit": UNIT,
+           "h2d_bytes_per_step": N_IN * body // (2 if four_bit else 1),
            "d2h_bytes_per_step": (hv.numel() + hb.numel()) * 4 // n_slots, "steps": k3,
            "ms_per_step": 1e3 * dt / k3,
-           "path": "corr_push_samples (pinned host, two sample rings) + corr_wait_output (visibilities and "
-                   "beams of every integration in a ring of pinned host slots)"}
+           "path": ("corr_push_samples_4bit (pinned host ADC card rows, 4 bits per sample)" if four_bit else
+                    "corr_push_samples (pinned host, two sample rings)") +
+                   " + corr_wait_output (visibilities and beams of every integration in a ring of pinned host slots)"}
     corr.corr_destroy(he)
     return e2e
 
@@ -697,6 +718,8 @@ def run_ours(args, world, rank, local_rank):
 
     # end to end through the public API: pinned host samples in, visibilities + beams out
     e2e = None if args.no_extras else run_e2e(args, corr, torch, dist, s, coh, world, all_forms[args.xmode])
+    e2e_4bit = None if args.no_extras else run_e2e(args, corr, torch, dist, s, coh, world, all_forms[args.xmode],
+                                                   four_bit=True)
 
     # roofline of the dominant kernel of the timed step
     dom = 1 if st[1] >= st[2] else 2
@@ -743,6 +766,7 @@ def run_ours(args, world, rank, local_rank):
             "batched_subarrays": batch, "learned_rfi": rfi,
             "e2e": e2e, "gpu_launches": 3 * K, "clocks": clocks, "cpu_baseline": cpu,
             "cpu_fft_baseline": cpu_fft, "voltage_blanker": blank, "multibeam": multibeam,
+            "e2e_4bit_adc": e2e_4bit,
         }
     emit(line, rank)
     if dist:
