@@ -333,15 +333,20 @@ int enqueue_output(corr* h, int64_t index) {
     return CORR_OK;
 }
 
-// Streaming ingest of n samples per input from x (row pitch spitch).  Copies run on the copy
-// stream into the current ring; a full ring launches its integration on h->stream (after the
-// copies) and the next integration fills the other ring, once the integration before that is
-// done with it.  Returns when x has been read (host sources; device sources stay stream-ordered).
-// Streaming ingest of n samples per input: put(dst, take, done) queues on h->cstream the copy of
-// samples done .. done + take - 1 of every input into the ring rows at dst (stride ring_ld).
+// Streaming ingest of n samples per input: put(dst, take, done) queues the writes of samples
+// done .. done + take - 1 of every input into the ring rows at dst (stride ring_ld), the last of
+// them on ws (host copies run on the copy stream h->cstream).  A full ring launches its
+// integration on h->stream (after ws) and the next integration fills the other ring, once the
+// integration before that is done with it.  Returns when the host source has been read (host
+// sources; device sources stay stream-ordered).
 template <typename Put>
-int ingest(corr* h, Put&& put, int64_t n, int64_t seq, bool from_host) {
+int ingest(corr* h, Put&& put, int64_t n, int64_t seq, bool from_host, cudaStream_t ws) {
     int rc = CORR_OK;
+    if (h->wstream && h->wstream != ws) {   // ring writes switch streams: keep them in order
+        CU(cudaEventRecord(h->ev_ws, h->wstream));
+        CU(cudaStreamWaitEvent(ws, h->ev_ws, 0));
+    }
+    h->wstream = ws;
     if (!h->ring_started) {
         h->ring_started = true;
         h->seq_origin = seq;
@@ -370,7 +375,7 @@ int ingest(corr* h, Put&& put, int64_t n, int64_t seq, bool from_host) {
             if (max_int_delay(h) > h->max_delay)
                 return fail(CORR_E_RANGE, "a delay exceeds max_delay = %d", h->max_delay);
             const int r = h->cur_ring, nx = r ^ 1;
-            CU(cudaEventRecord(h->ev_ready[r], h->cstream));
+            CU(cudaEventRecord(h->ev_ready[r], ws));
             CU(cudaStreamWaitEvent(h->stream, h->ev_ready[r], 0));
             if (h->out_vis) {            // output buffer j % 2, once its copy to the host slot is done
                 const int b = static_cast<int>(h->n_streamed & 1);
@@ -383,10 +388,10 @@ int ingest(corr* h, Put&& put, int64_t n, int64_t seq, bool from_host) {
             // the next integration fills the other ring, once the integration two back is done
             // with it, beginning with this one's last max_delay samples (overlap, Sec. 2.3.2)
             int8_t* next = nx ? h->d_ring2 : h->d_ring;
-            CU(cudaStreamWaitEvent(h->cstream, h->ev_free[nx], 0));
+            CU(cudaStreamWaitEvent(ws, h->ev_free[nx], 0));
             if (h->max_delay > 0)
                 CU(cudaMemcpy2DAsync(next, h->ring_ld, ring + body, h->ring_ld, h->max_delay, h->n_in,
-                                     cudaMemcpyDeviceToDevice, h->cstream));
+                                     cudaMemcpyDeviceToDevice, ws));
             h->cur_ring = nx;
             h->fill = h->max_delay;
             h->g_next += h->n_int;
@@ -444,6 +449,7 @@ int corr_create(corr_t** out, int n_ant, int n_pol, int n_fft, int n_int) {
     CUB(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
     CUB(cudaEventCreateWithFlags(&h->ev_aux, cudaEventDisableTiming));
     CUB(cudaEventCreateWithFlags(&h->ev_copied, cudaEventDisableTiming));
+    CUB(cudaEventCreateWithFlags(&h->ev_ws, cudaEventDisableTiming));
     for (int r = 0; r < 2; ++r) {
         CUB(cudaEventCreateWithFlags(&h->ev_ready[r], cudaEventDisableTiming));
         CUB(cudaEventCreateWithFlags(&h->ev_free[r], cudaEventDisableTiming));
@@ -500,6 +506,9 @@ int corr_destroy(corr_t* h) {
     if (!h) return CORR_OK;
     cudaSetDevice(h->dev);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->cstream) cudaStreamSynchronize(h->cstream);
+    if (h->ustream) cudaStreamSynchronize(h->ustream);
+    if (h->ostream) cudaStreamSynchronize(h->ostream);
     if (h->d_power) cudaFree(h->d_power);
     if (h->d_noise) cudaFree(h->d_noise);
     if (h->d_blank) cudaFree(h->d_blank);
@@ -510,8 +519,6 @@ int corr_destroy(corr_t* h) {
     if (h->d_unpack) cudaFree(h->d_unpack);
     if (h->d_xtab) cudaFree(h->d_xtab);
     if (h->d_items) cudaFree(h->d_items);
-    if (h->cstream) cudaStreamSynchronize(h->cstream);
-    if (h->ostream) cudaStreamSynchronize(h->ostream);
     if (h->vis_b[1]) {                   // the second output buffers (the current may be either)
         select_outputs(h, 0);
         if (h->beams_b[1] != h->beams_raw_b[1]) cudaFree(h->beams_b[1]);
@@ -529,6 +536,11 @@ int corr_destroy(corr_t* h) {
     if (h->ev_done) cudaEventDestroy(h->ev_done);
     if (h->ev_aux) cudaEventDestroy(h->ev_aux);
     if (h->ev_copied) cudaEventDestroy(h->ev_copied);
+    if (h->ev_ws) cudaEventDestroy(h->ev_ws);
+    for (int k = 0; k < corr::kStage4Slots; ++k) {
+        if (h->ev_s4[k]) cudaEventDestroy(h->ev_s4[k]);
+        if (h->ev_s4_free[k]) cudaEventDestroy(h->ev_s4_free[k]);
+    }
     for (int r = 0; r < 2; ++r) {
         if (h->ev_ready[r]) cudaEventDestroy(h->ev_ready[r]);
         if (h->ev_free[r]) cudaEventDestroy(h->ev_free[r]);
@@ -541,6 +553,7 @@ int corr_destroy(corr_t* h) {
         if (e) cudaEventDestroy(e);
     if (h->ostream) cudaStreamDestroy(h->ostream);
     if (h->cstream) cudaStreamDestroy(h->cstream);
+    if (h->ustream) cudaStreamDestroy(h->ustream);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return CORR_OK;
@@ -560,6 +573,7 @@ int corr_set_mode(corr_t* h, int xmode, int polmode, int beam_avg) {
         return fail(CORR_E_INVAL, "tensor-core modes need n_in <= 128");
     if (xmode == CORR_I8 && h->n_int > 66571) return fail(CORR_E_INVAL, "CORR_I8 needs n_int <= 66571");
     CU(cudaStreamSynchronize(h->cstream));
+    if (h->ustream) CU(cudaStreamSynchronize(h->ustream));
     CU(cudaStreamSynchronize(h->stream));
     if (beam_avg != h->beam_avg) {
         if (h->d_beams != h->d_beams_raw) cudaFree(h->d_beams);
@@ -657,7 +671,7 @@ int corr_push_samples(corr_t* h, const int8_t* x, int64_t n, int64_t seq) {
         CU(cudaMemcpy2DAsync(dst, h->ring_ld, x + done, n, take, h->n_in, cudaMemcpyHostToDevice, h->cstream));
         return CORR_OK;
     };
-    return ingest(h, put, n, seq, true);
+    return ingest(h, put, n, seq, true, h->cstream);
 }
 
 int corr_push_samples_4bit(corr_t* h, const uint8_t* packed, int64_t ld, int64_t n, int64_t seq) {
@@ -668,17 +682,37 @@ int corr_push_samples_4bit(corr_t* h, const uint8_t* packed, int64_t ld, int64_t
     if (!h->d_ring)
         if (int rc = alloc_ring(h)) return rc;
     const int n_cards = h->n_in / 4;
-    if (!h->d_stage4) CU(cudaMalloc(&h->d_stage4, static_cast<size_t>(n_cards) * 2 * corr::kStage4));
+    constexpr int64_t kS = corr::kStage4, kP = corr::kStage4Pitch;
+    if (!h->d_stage4) {
+        int lo = 0, hi = 0;
+        CU(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        if (!h->ustream) CU(cudaStreamCreateWithPriority(&h->ustream, cudaStreamNonBlocking, hi));
+        for (int k = 0; k < corr::kStage4Slots; ++k) {
+            if (!h->ev_s4[k]) CU(cudaEventCreateWithFlags(&h->ev_s4[k], cudaEventDisableTiming));
+            if (!h->ev_s4_free[k]) CU(cudaEventCreateWithFlags(&h->ev_s4_free[k], cudaEventDisableTiming));
+        }
+        CU(cudaMalloc(&h->d_stage4, static_cast<size_t>(corr::kStage4Slots) * n_cards * kP));
+    }
     auto put = [&](int8_t* dst, int64_t take, int64_t done) -> int {
-        for (int64_t q = 0; q < take; q += corr::kStage4) {   // packed pieces through the staging rows
-            const int64_t len = std::min<int64_t>(corr::kStage4, take - q);
-            CU(cudaMemcpy2DAsync(h->d_stage4, 2 * corr::kStage4, packed + 2 * (done + q), ld, 2 * len, n_cards,
-                                 cudaMemcpyHostToDevice, h->cstream));
-            CU(launch_unpack4(h->d_stage4, 2 * corr::kStage4, n_cards, len, dst + q, h->ring_ld, h->n_sm, h->cstream));
+        for (int64_t q = 0; q < take; q += kS) {   // packed pieces through the staging slots
+            const int64_t len = std::min<int64_t>(kS, take - q);
+            const int k = h->s4_next;
+            h->s4_next = (k + 1) % corr::kStage4Slots;
+            // the copy lands at the offset that puts the input of the first 16-byte aligned
+            // output sample on a 16-byte boundary (the unpack's vector path)
+            const int64_t off = (2 * static_cast<int64_t>(reinterpret_cast<uintptr_t>(dst + q) & 15)) & 15;
+            uint8_t* slot = h->d_stage4 + static_cast<size_t>(k) * n_cards * kP + off;
+            CU(cudaStreamWaitEvent(h->cstream, h->ev_s4_free[k], 0));
+            CU(cudaMemcpy2DAsync(slot, kP, packed + 2 * (done + q), ld, 2 * len, n_cards, cudaMemcpyHostToDevice,
+                                 h->cstream));
+            CU(cudaEventRecord(h->ev_s4[k], h->cstream));
+            CU(cudaStreamWaitEvent(h->ustream, h->ev_s4[k], 0));
+            CU(launch_unpack4(slot, kP, n_cards, len, dst + q, h->ring_ld, h->n_sm, h->ustream));
+            CU(cudaEventRecord(h->ev_s4_free[k], h->ustream));
         }
         return CORR_OK;
     };
-    return ingest(h, put, n, seq, true);
+    return ingest(h, put, n, seq, true, h->ustream);
 }
 
 int corr_set_output_ring(corr_t* h, float* vis, float* beams, int n_slots) {
@@ -686,6 +720,7 @@ int corr_set_output_ring(corr_t* h, float* vis, float* beams, int n_slots) {
     if (vis && (n_slots < 1 || n_slots > 4096)) return fail(CORR_E_INVAL, "n_slots must be in [1, 4096]");
     if (vis && h->batch_refs > 0) return fail(CORR_E_STATE, "the handle belongs to a batch (captured graph)");
     CU(cudaStreamSynchronize(h->cstream));
+    if (h->ustream) CU(cudaStreamSynchronize(h->ustream));
     CU(cudaStreamSynchronize(h->stream));
     if (h->ostream) CU(cudaStreamSynchronize(h->ostream));
     for (cudaEvent_t e : h->ev_out) cudaEventDestroy(e);
@@ -768,7 +803,7 @@ int corr_push_samples_device(corr_t* h, const int8_t* x, int64_t n, int64_t seq,
         CU(cudaMemcpy2DAsync(dst, h->ring_ld, x + done, n, take, h->n_in, cudaMemcpyDeviceToDevice, h->cstream));
         return CORR_OK;
     };
-    return ingest(h, put, n, seq, false);
+    return ingest(h, put, n, seq, false, h->cstream);
 }
 
 int corr_integrate_4bit_device(corr_t* h, const uint8_t* packed, int64_t ld, int64_t n_avail, int64_t g0,

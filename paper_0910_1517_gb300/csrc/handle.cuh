@@ -92,10 +92,23 @@ struct corr {
     int n_mb = 0, mb_products = 0, mb_avg = 1;
     float2* d_mbw = nullptr;
     float4* d_mb = nullptr;
-    // 4-bit ADC-format ingest: packed staging rows (kStage4 samples per card row) for pushes, and
-    // the unpacked int8 rows of device integrations
-    static constexpr int64_t kStage4 = int64_t(1) << 22;
+    // 4-bit ADC-format ingest.  Pushes go through a ring of kStage4Slots packed staging slots
+    // (n_cards rows of up to kStage4 samples, pitch kStage4Pitch): host-to-device copies into a
+    // slot on cstream, the unpack into the sample ring on ustream, a high-priority stream so that
+    // unpacks take the next free SM slots ahead of queued correlator CTAs.  ev_s4[k]: slot k's
+    // copy has landed; ev_s4_free[k]: slot k has been unpacked.  Device integrations unpack into
+    // d_unpack.
+    static constexpr int64_t kStage4 = int64_t(1) << 21;
+    static constexpr int kStage4Slots = 8;
+    static constexpr int64_t kStage4Pitch = 2 * kStage4 + 16;
     uint8_t* d_stage4 = nullptr;
+    cudaStream_t ustream = nullptr;
+    cudaEvent_t ev_s4[kStage4Slots] = {}, ev_s4_free[kStage4Slots] = {};
+    int s4_next = 0;
+    // the stream of the last writes into the sample rings (cstream, or ustream for 4-bit pushes);
+    // a push from the other kind first waits for it through ev_ws
+    cudaStream_t wstream = nullptr;
+    cudaEvent_t ev_ws = nullptr;
     int8_t* d_unpack = nullptr;
     int64_t unpack_ld = 0;
     int32_t* d_blank = nullptr;

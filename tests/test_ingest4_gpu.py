@@ -88,6 +88,55 @@ def test_streaming_4bit_push_equals_the_int8_push(env):
     assert np.array_equal(got["4bit"][0], got["int8"][0]) and np.array_equal(got["4bit"][1], got["int8"][1])
 
 
+def test_device_4bit_from_a_pointer_off_16_byte_boundaries(env):
+    # packed rows starting 2 bytes past an aligned address with an odd row pitch (in 2-byte
+    # units): the unpack's 2-byte load path for every card, 16-byte loads for none
+    torch, corr, orc = env
+    s, packed, n = _packed(8810)
+    rows = orc.unpack4(packed, n)
+    h4, h8 = _handle(corr, s), _handle(corr, s)
+    try:
+        width = 2 * n + (2 if n % 2 == 0 else 4)          # = 2 (mod 4)
+        big = torch.zeros((packed.shape[0], width), dtype=torch.uint8, device="cuda")
+        big[:, 2:2 + 2 * n] = torch.from_numpy(packed).cuda()
+        view = big[:, 2:2 + 2 * n]
+        assert view.data_ptr() % 16 == 2 and view.stride(0) % 4 == 2
+        corr.corr_integrate_4bit_device(h4, view, n, stream=torch.cuda.current_stream())
+        xt = torch.zeros((s.n_in, ((n + 15) // 16) * 16 + 16), dtype=torch.int8, device="cuda")
+        xt[:, :n] = torch.from_numpy(rows).cuda()
+        corr.corr_integrate_device(h8, xt, n_avail=n, stream=torch.cuda.current_stream())
+        assert np.array_equal(corr.corr_read_visibilities(h4), corr.corr_read_visibilities(h8))
+        assert np.array_equal(corr.corr_read_beams(h4), corr.corr_read_beams(h8))
+    finally:
+        corr.corr_destroy(h4)
+        corr.corr_destroy(h8)
+
+
+def test_streaming_pushes_mixing_4bit_and_int8(env):
+    # 4-bit pushes (unpacked on their own stream) and int8 pushes (copied on the copy stream)
+    # interleaved on one handle, at cuts that leave every output alignment: the rings see the
+    # same samples in the same order as with int8 pushes alone
+    torch, corr, orc = env
+    s, packed, n = _packed(8950, n_int=3 * N_INT)
+    rows = orc.unpack4(packed, n)
+    body = N_INT * N_FFT
+    cuts = [0, 5, 4099, 4100, 17000, body - 3, body + 9, 2 * body + 1, 2 * body + 2048]
+    got = {}
+    for kind in ("mixed", "int8"):
+        h = corr.corr_create(s.n_ant, s.n_pol, s.n_fft, N_INT)
+        try:
+            corr.corr_set_delays(h, s.delay, s.phi0, s.rate)
+            for j, (a, b) in enumerate(zip(cuts[:-1], cuts[1:])):
+                if kind == "mixed" and j % 2 == 0:
+                    corr.corr_push_samples_4bit(h, np.ascontiguousarray(packed[:, 2 * a:2 * b]), b - a, seq=a)
+                else:
+                    corr.corr_push_samples(h, np.ascontiguousarray(rows[:, a:b]), seq=a)
+            got[kind] = (corr.corr_read_visibilities(h), corr.corr_read_beams(h))
+        finally:
+            corr.corr_destroy(h)
+    assert np.array_equal(got["mixed"][0], got["int8"][0]) and np.array_equal(got["mixed"][1], got["int8"][1])
+
+
 def test_4bit_arguments(env):
     torch, corr, orc = env
     h = corr.corr_create(3, 1, 256, 16)               # 3 inputs: not whole cards
