@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
 package; the product path (``paper_0910_1517_gb300``) never does.  The
 arithmetic lives in ``fx_oracle.c`` (plain C, double precision, direct DFT);
-this module only builds it with gcc and marshals numpy arrays through ctypes.
+this module only builds it with gcc and marshals numpy arrays through ctypes (the
+dedispersion stage, whose steps are FFTs, is numpy in ``dedisp.py``).
 
 Functions and the passage each follows (Roy et al., arXiv:0910.1517):
   fengine   -- integer delay, real DFT, FSTC + fringe phasor (Sec. 2.1, Eq. 2)
@@ -18,6 +19,9 @@ Functions and the passage each follows (Roy et al., arXiv:0910.1517):
             sign-extend each 4-bit sample to 8 bits (Sec. 2.3.1, 2.3.2)
   mad_blank -- the time-domain voltage blanker built on it (Sec. 5): flagged raw samples
             replaced by pre-computed Gaussian noise scaled by the block's MAD / 0.6745
+  coherent_dedisperse (dedisp.py, numpy FP64) -- coherent dedispersion of the phased-array
+            voltage beam (Sec. 5): per-frame inverse FFT to the baseband series, overlap-save
+            multiplication by the inverse ISM chirp, detection of both polarisations, averaging
   fft_fengine (cpu_fft_baseline.c) -- not an oracle: the bench's second CPU baseline,
             the same F-engine with an FP32 radix-2 FFT (pinned to ``fengine``)
   power_dumps, patch_stats, rfi_forward, rfi_loss_grad (rfi_oracle.c) -- the RFI
@@ -303,3 +307,6 @@ def rfi_loss_grad(params, x, mask):
     loss = ctypes.c_double()
     _check(lib().oracle_rfi_loss_grad(B, H, W, _p(p), _p(x), _p(m), ctypes.byref(loss), _p(g)), "rfi_loss_grad")
     return loss.value, g
+
+
+from .dedisp import coherent_dedisperse  # noqa: E402  (numpy oracle, Sec. 5)
