@@ -301,6 +301,43 @@ int corr_integrate_static(int n_ant, int n_pol, int n_fft, int n_int, const int8
                           int64_t n_avail, int64_t g0, const double* delay, const double* phi0,
                           const double* rate, float* vis, float* beams, void* stream, int blocking);
 
+/* Coherent dedispersion of the phased-array voltage beam (Sec. 5: the coherent array's
+ * pre-detected voltages per polarisation are inverse-FFT'd back to a broadband time series,
+ * deconvolved from the ISM dispersion by multiplying with the inverse transfer function in the
+ * Fourier domain, detected, the two polarisations added, and integrated in time).
+ * Input: voltage spectra of one beam, [n_frames][n_chan] of (X re, X im, Y re, Y im) float32 --
+ * the layout corr_read_multibeam gives per beam in CORR_BEAM_VOLTAGE mode; channel k of every
+ * frame lies at sky frequency f_lo + k bw / n_chan MHz (an upper-sideband band, bw > 0).
+ * Method (all on the GPU):
+ *   z[t n_chan + m] = inverse FFT over k of frame t (complex baseband at bw MHz);
+ *   blocks of M = fft_frames * n_chan samples stepping by S = (fft_frames - overlap) * n_chan
+ *   (overlap-save): y = IFFT(FFT(z_block) * C), C[j] = exp(-i Phi(nu_j)),
+ *   nu_j = f_lo + j bw / M, Phi(nu) = 2 pi 1e6 D DM (nu - nu_ref)^2 / (nu_ref^2 nu),
+ *   nu_ref = f_lo + bw, D = 4.148808e3 s MHz^2 pc^-1 cm^3; the first S samples of each block
+ *   are kept (output time = arrival time at the top of the band);
+ *   out[i] = mean over samples [i avg, (i + 1) avg) of |y_X|^2 + |y_Y|^2.
+ * corr_dd_create: n_chan and fft_frames powers of two in [64, 4096] and [256, 4096],
+ *   fft_frames * n_chan <= 2^24; 0 <= overlap < fft_frames with overlap * n_chan at least the
+ *   smear (corr_dd_smear_samples; else CORR_E_RANGE); avg a power of two in [2, 32 n_chan]
+ *   dividing S; max_push_frames bounds one push.  Device memory: a ring of fft_frames +
+ *   max_push_frames frames, (max_push_frames / (fft_frames - overlap) + 1) work blocks of
+ *   16 M bytes, and the 8 M-byte chirp table (computed in FP64 on the host at creation).
+ * corr_dd_push_device: appends n_frames frames (device pointer, 16-byte aligned) on `stream`
+ *   (cudaStream_t; NULL = legacy default stream; every push of one dedisperser on one stream)
+ *   and writes the outputs of every block they complete to out (device, room for out_cap
+ *   floats; CORR_E_INVAL when smaller), in time order, continuing where the previous push
+ *   stopped; *n_out gets their count (known at return, no synchronisation).  The first output
+ *   is the window starting at the first frame ever pushed (or pushed after corr_dd_reset).
+ * corr_dd_smear_samples: samples by which the bottom of the band lags the top, -1 on bad input. */
+typedef struct corr_dd corr_dd_t;
+double corr_dd_smear_samples(double dm, double f_lo, double bw);
+int corr_dd_create(corr_dd_t** out, int n_chan, int fft_frames, int overlap_frames, int max_push_frames, double dm,
+                   double f_lo, double bw, int avg);
+int corr_dd_push_device(corr_dd_t* d, const float* spec, int64_t n_frames, float* out, int64_t out_cap,
+                        int64_t* n_out, void* stream);
+int corr_dd_reset(corr_dd_t* d);
+int corr_dd_destroy(corr_dd_t* d);
+
 #if defined(__GNUC__)
 #pragma GCC visibility pop
 #endif

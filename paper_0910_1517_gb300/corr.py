@@ -60,6 +60,12 @@ SIGNATURES = {
     "corr_integrate_4bit_device": ([_P, _P, _L, _L, _L, _P], _I),
     "corr_read_multibeam": ([_P, _P, _I], _I),
     "corr_read_blank_stats": ([_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], _I),
+    "corr_dd_smear_samples": ([ctypes.c_double, ctypes.c_double, ctypes.c_double], ctypes.c_double),
+    "corr_dd_create": ([ctypes.POINTER(ctypes.c_void_p), _I, _I, _I, _I, ctypes.c_double, ctypes.c_double,
+                        ctypes.c_double, _I], _I),
+    "corr_dd_push_device": ([_P, _P, _L, _P, _L, ctypes.POINTER(ctypes.c_int64), _P], _I),
+    "corr_dd_reset": ([_P], _I),
+    "corr_dd_destroy": ([_P], _I),
     # include/rfi.h
     "rfi_n_params": ([], _I),
     "rfi_create": ([ctypes.POINTER(ctypes.c_void_p), _I], _I),
@@ -436,3 +442,33 @@ def corr_batch_tune(b, n_sub: int):
     ms = np.zeros(n_sub, dtype=np.float32)
     _ok(load().corr_batch_tune(b, _ptr(ks), _ptr(ms)))
     return ks, ms
+
+
+def corr_dd_smear_samples(dm: float, f_lo: float, bw: float) -> float:
+    return load().corr_dd_smear_samples(dm, f_lo, bw)
+
+
+def corr_dd_create(n_chan: int, fft_frames: int, overlap_frames: int, max_push_frames: int, dm: float, f_lo: float,
+                   bw: float, avg: int):
+    d = ctypes.c_void_p()
+    _ok(load().corr_dd_create(ctypes.byref(d), n_chan, fft_frames, overlap_frames, max_push_frames, dm, f_lo, bw,
+                              avg))
+    return d
+
+
+def corr_dd_push_device(d, spec, out, stream=None) -> int:
+    """spec: device float32 tensor [n_frames][n_chan][4] (X re, X im, Y re, Y im), contiguous;
+    out: device float32 tensor receiving the outputs of the blocks this push completes.
+    Returns their count."""
+    n = ctypes.c_int64(0)
+    _ok(load().corr_dd_push_device(d, _ptr(spec), spec.shape[0], _ptr(out), out.numel(), ctypes.byref(n),
+                                   _stream(stream)))
+    return n.value
+
+
+def corr_dd_reset(d):
+    return _ok(load().corr_dd_reset(d))
+
+
+def corr_dd_destroy(d):
+    return _ok(load().corr_dd_destroy(d))

@@ -28,6 +28,7 @@
 
 #include "common.cuh"
 #include "fengine.cuh"
+#include "fft_smem.cuh"
 
 namespace gbx {
 namespace {
@@ -48,73 +49,6 @@ struct Plan {
     static constexpr int PADM = M + M / 16;                    // padded frame length (float2)
     static constexpr int STAGE = F * N + 32;                   // staging bytes per buffer
     static_assert(F * M == kChanFrames, "CTA covers 8192 channel-frames");
-};
-
-// one pad element per 16: every Stockham exchange of 8-byte points is free of bank conflicts
-__host__ __device__ constexpr int pad16(int i) { return i + (i >> 4); }
-
-// cos / sin of 2 pi m / 16
-__device__ __forceinline__ constexpr float c16(int m) {
-    return m == 0 ? 1.0f : m == 1 ? 0.92387953251128674f : m == 2 ? 0.70710678118654752f
-         : m == 3 ? 0.38268343236508977f : m == 4 ? 0.0f : m == 5 ? -0.38268343236508977f
-         : m == 6 ? -0.70710678118654752f : m == 7 ? -0.92387953251128674f : -1.0f;
-}
-
-// o * exp(-2 pi i k / R) with the trivial cases spelled out
-template <int R, int K>
-__device__ __forceinline__ float2 twiddle_const(float2 o) {
-    constexpr int m = K * (16 / R);              // position on the 16-point circle, 0..7
-    if constexpr (m == 0) {
-        return o;
-    } else if constexpr (m == 4) {               // -i
-        return make_float2(o.y, -o.x);
-    } else if constexpr (m == 2) {               // (1 - i) / sqrt2
-        constexpr float h = 0.70710678118654752f;
-        return make_float2(h * (o.x + o.y), h * (o.y - o.x));
-    } else if constexpr (m == 6) {               // (-1 - i) / sqrt2
-        constexpr float h = 0.70710678118654752f;
-        return make_float2(h * (o.y - o.x), -h * (o.x + o.y));
-    } else {
-        constexpr float c = c16(m);
-        constexpr float s = (m <= 4) ? c16(4 - m) : c16(m - 4);  // sin(2 pi m / 16), m = 1..7
-        // w = c - i s
-        return make_float2(c * o.x + s * o.y, c * o.y - s * o.x);
-    }
-}
-
-// In-register forward DFT of R points (radix-2 recursion, natural-order output).
-template <int R>
-struct Dft {
-    template <int S>
-    __device__ __forceinline__ static void run(float2* v) {
-        // v[0], v[S], v[2S], ... hold the R inputs; transform in place
-        Dft<R / 2>::template run<2 * S>(v);      // evens
-        Dft<R / 2>::template run<2 * S>(v + S);  // odds
-        float2 out[R];
-#pragma unroll
-        for (int k = 0; k < R / 2; ++k) {
-            out[k] = v[2 * S * k];
-            out[k + R / 2] = v[2 * S * k + S];
-        }
-        apply<0>(out);
-#pragma unroll
-        for (int k = 0; k < R; ++k) v[S * k] = out[k];
-    }
-    template <int K>
-    __device__ __forceinline__ static void apply(float2* out) {
-        if constexpr (K < R / 2) {
-            const float2 e = out[K];
-            const float2 t = twiddle_const<R, K>(out[K + R / 2]);
-            out[K] = cadd(e, t);
-            out[K + R / 2] = csub(e, t);
-            apply<K + 1>(out);
-        }
-    }
-};
-template <>
-struct Dft<1> {
-    template <int S>
-    __device__ __forceinline__ static void run(float2*) {}
 };
 
 // Stockham pass of radix R over span Ns for one frame: read X[b + r*M/R], twiddle by
@@ -160,16 +94,6 @@ __device__ __forceinline__ void pass_store(float2* __restrict__ dst, int t, cons
 #pragma unroll
             for (int r = 0; r < R; ++r) dst[pad16(base + r * Ns)] = v[m * R + r];
         }
-    }
-}
-
-// barrier among the T threads of one FFT group (group g); a warp when T <= 32
-template <int T>
-__device__ __forceinline__ void group_sync(int g) {
-    if constexpr (T <= 32) {
-        __syncwarp();
-    } else {
-        asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(T) : "memory");
     }
 }
 
