@@ -222,6 +222,14 @@ def tensor_fraction(ms, pk, mmas=1):
     return executed / (ms * 1e-3) / 1e12 / pk["bf16_tflops_sustained"]
 
 
+def source_sha(files):
+    """First 16 hex digits of the SHA-256 over a kernel's source files (a name or a list), in order."""
+    h = hashlib.sha256()
+    for f in [files] if isinstance(files, str) else files:
+        h.update(open(os.path.join(ROOT, "paper_0910_1517_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_for(kernel):
     """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged since."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
@@ -229,9 +237,7 @@ def traffic_for(kernel):
         with open(path) as f:
             t = json.load(f)
         e = t[kernel]
-        src = os.path.join(ROOT, "paper_0910_1517_gb300", "csrc", e["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if h != e["source_sha"]:
+        if source_sha(e["source"]) != e["source_sha"]:
             return None
         return float(e["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -428,6 +434,64 @@ def run_multibeam_leg(corr, torch, s, xt, ld, coh, xmode, k, st_plain, pk, n_bea
                                  "unit": "TFLOP/s", "frac": flop / (mb_ms * 1e-3) / 1e12 / fp32_peak_tflops(pk)}}
     finally:
         corr.corr_destroy(h2)
+
+
+def run_dedisp_leg(corr, torch, pk, k=20, dm=30.0, f_lo=1780.0 / 3.0, bw=100.0 / 3.0):
+    """Coherent dedispersion of the phased-array voltage beam (Sec. 5) at GMRT scale: one beam's
+    voltage spectra (1024 channels over 33.3 MHz at 610 MHz, both polarisations), one
+    integration (8192 frames) per push, DM 30 pc/cc (1.22 M samples = 1192 frames of smear),
+    blocks of 4096 frames overlapping by 2048 (four blocks per push), one total-power sample per
+    frame.  Input
+    spectra (seeded Gaussian) are resident in HBM; each push copies them into the frame ring.
+    Reports the push time, per-stage times and each pass's HBM traffic of the design (A: read the
+    frames, write the work block; B: read it and the chirp, write it back; C: read it, write the
+    column sums) against the measured HBM peak, and the real-time factor."""
+    F, O, n_push = 4096, 2048, N_INT
+    d = corr.corr_dd_create(N_CHAN, F, O, n_push, dm, f_lo, bw, N_CHAN)
+    try:
+        g = torch.Generator(device="cuda").manual_seed(555)
+        v = torch.randn((n_push, N_CHAN, 4), generator=g, device="cuda") * 100.0
+        keep = F - O
+        out = torch.empty((n_push // keep + 1) * keep, dtype=torch.float32, device="cuda")
+        stream = torch.cuda.current_stream()
+        for _ in range(4):                                  # fill the ring, reach the steady state
+            corr.corr_dd_push_device(d, v, out, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n_out = 0
+        for _ in range(k):
+            n_out += corr.corr_dd_push_device(d, v, out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        corr.corr_dd_set_timing(d, True)
+        for _ in range(k):
+            corr.corr_dd_push_device(d, v, out, stream=stream)
+        st, cnt = corr.corr_dd_stage_times(d)
+        corr.corr_dd_set_timing(d, False)
+        st = [float(x) / max(cnt, 1) for x in st]
+        nb = n_push // keep                                 # blocks per push in the steady state
+        M = F * N_CHAN
+        traffic = {"ring_copy": 2 * n_push * N_CHAN * 16, "A": nb * 2 * M * 16, "B": nb * (2 * M * 16 + M * 8),
+                   "C": nb * (M * 16 + keep * (N_CHAN // 2) * 4), "D": nb * keep * (N_CHAN // 2) * 4}
+        names = ["ring_copy", "A", "B", "C", "D"]
+        stages = {}
+        for nme, t in zip(names, st):
+            gbs = traffic[nme] / (t * 1e-3) / 1e9
+            stages[nme] = {"ms": round(t, 4), "bytes": traffic[nme], "achieved_gbs": gbs,
+                           "frac_of_measured_hbm": gbs / pk["hbm_gbs"]}
+        dom = max(("A", "B", "C"), key=lambda q: stages[q]["ms"])
+        samples = n_push * N_CHAN
+        return {"workload": f"coherent dedispersion of one voltage beam: {N_CHAN} ch x 33.3 MHz at 610 MHz, DM {dm}, "
+                            f"{F}-frame blocks overlapping {O}, {n_push} frames per push, 1 output per frame",
+                "ms_per_push": ms, "outputs_per_push": n_out / k, "value": samples / (ms * 1e-3),
+                "unit": "beam samples/s (complex, both polarisations)",
+                "rtf": samples / (ms * 1e-3) / (bw * 1e6), "stages": stages,
+                "roofline": {"bound": "hbm", "kernel": f"pass {dom}", "achieved": stages[dom]["achieved_gbs"],
+                             "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": stages[dom]["frac_of_measured_hbm"]}}
+    finally:
+        corr.corr_dd_destroy(d)
 
 
 def run_blank_leg(corr, torch, s, xt, ld, coh, xmode, k, st_plain):
@@ -627,7 +691,8 @@ def run_ours(args, world, rank, local_rank):
     corr.load()
     pk = peaks()
     if args.leg != "all":                                 # one extra leg alone (profiling runs)
-        res = run_batch_leg(args, corr, torch, rank) if args.leg == "batched" else run_rfi_leg(corr, torch)
+        res = run_batch_leg(args, corr, torch, rank) if args.leg == "batched" else \
+            run_dedisp_leg(corr, torch, peaks()) if args.leg == "dedisp" else run_rfi_leg(corr, torch)
         emit({"leg": args.leg, **res}, rank)
         if dist:
             dist.destroy_process_group()
@@ -716,6 +781,10 @@ def run_ours(args, world, rank, local_rank):
     multibeam = None if args.no_extras else run_multibeam_leg(corr, torch, s, xt, ld, coh, all_forms[args.xmode],
                                                               max(10, min(K, 50)), st, pk)
 
+    # coherent dedispersion of one phased-array voltage beam (one integration per push)
+    dedisp = None if args.no_extras else run_dedisp_leg(corr, torch, pk)
+    torch.cuda.empty_cache()
+
     # end to end through the public API: pinned host samples in, visibilities + beams out
     e2e = None if args.no_extras else run_e2e(args, corr, torch, dist, s, coh, world, all_forms[args.xmode])
     e2e_4bit = None if args.no_extras else run_e2e(args, corr, torch, dist, s, coh, world, all_forms[args.xmode],
@@ -766,7 +835,7 @@ def run_ours(args, world, rank, local_rank):
             "batched_subarrays": batch, "learned_rfi": rfi,
             "e2e": e2e, "gpu_launches": 3 * K, "clocks": clocks, "cpu_baseline": cpu,
             "cpu_fft_baseline": cpu_fft, "voltage_blanker": blank, "multibeam": multibeam,
-            "e2e_4bit_adc": e2e_4bit,
+            "e2e_4bit_adc": e2e_4bit, "coherent_dedispersion": dedisp,
         }
     emit(line, rank)
     if dist:
@@ -783,7 +852,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--no-extras", action="store_true",
                     help="time only the FP32 step (no precision forms, no end-to-end leg); for profiling runs")
-    ap.add_argument("--leg", choices=("all", "batched", "rfi"), default="all",
+    ap.add_argument("--leg", choices=("all", "batched", "rfi", "dedisp"), default="all",
                     help="run only the batched sub-array leg or only the learned-RFI leg (profiling runs)")
     ap.add_argument("--xmode", choices=("fp32tc", "fp32"), default="fp32tc",
                     help="form of the timed step: FP32 on the tensor cores (default) or the plain CUDA-core FP32 form")

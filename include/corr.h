@@ -328,6 +328,11 @@ int corr_integrate_static(int n_ant, int n_pol, int n_fft, int n_int, const int8
  *   floats; CORR_E_INVAL when smaller), in time order, continuing where the previous push
  *   stopped; *n_out gets their count (known at return, no synchronisation).  The first output
  *   is the window starting at the first frame ever pushed (or pushed after corr_dd_reset).
+ * corr_dd_set_timing: on = 1 records CUDA events around the ring copy and the four passes of
+ *   every push that completes a block (each such push then waits for itself) and clears the sums;
+ *   corr_dd_stage_times: summed milliseconds per stage (ms5[5]: ring copy, A frames' DFTs,
+ *   B rows + chirp, C inverse + detection, D window means) over *n_timed pushes.
+ * corr_dd_reset: forget the frames pushed so far (the next push starts a new series).
  * corr_dd_smear_samples: samples by which the bottom of the band lags the top, -1 on bad input. */
 typedef struct corr_dd corr_dd_t;
 double corr_dd_smear_samples(double dm, double f_lo, double bw);
@@ -335,6 +340,8 @@ int corr_dd_create(corr_dd_t** out, int n_chan, int fft_frames, int overlap_fram
                    double f_lo, double bw, int avg);
 int corr_dd_push_device(corr_dd_t* d, const float* spec, int64_t n_frames, float* out, int64_t out_cap,
                         int64_t* n_out, void* stream);
+int corr_dd_set_timing(corr_dd_t* d, int on);
+int corr_dd_stage_times(corr_dd_t* d, float* ms5, int* n_timed);
 int corr_dd_reset(corr_dd_t* d);
 int corr_dd_destroy(corr_dd_t* d);
 

@@ -64,6 +64,8 @@ SIGNATURES = {
     "corr_dd_create": ([ctypes.POINTER(ctypes.c_void_p), _I, _I, _I, _I, ctypes.c_double, ctypes.c_double,
                         ctypes.c_double, _I], _I),
     "corr_dd_push_device": ([_P, _P, _L, _P, _L, ctypes.POINTER(ctypes.c_int64), _P], _I),
+    "corr_dd_set_timing": ([_P, _I], _I),
+    "corr_dd_stage_times": ([_P, _P, ctypes.POINTER(ctypes.c_int)], _I),
     "corr_dd_reset": ([_P], _I),
     "corr_dd_destroy": ([_P], _I),
     # include/rfi.h
@@ -464,6 +466,18 @@ def corr_dd_push_device(d, spec, out, stream=None) -> int:
     _ok(load().corr_dd_push_device(d, _ptr(spec), spec.shape[0], _ptr(out), out.numel(), ctypes.byref(n),
                                    _stream(stream)))
     return n.value
+
+
+def corr_dd_set_timing(d, on: bool):
+    return _ok(load().corr_dd_set_timing(d, 1 if on else 0))
+
+
+def corr_dd_stage_times(d):
+    """(ms[5] summed over the timed pushes: ring copy, A, B, C, D; number of timed pushes)"""
+    ms = np.zeros(5, np.float32)
+    n = ctypes.c_int(0)
+    _ok(load().corr_dd_stage_times(d, _ptr(ms), ctypes.byref(n)))
+    return ms, n.value
 
 
 def corr_dd_reset(d):

@@ -51,9 +51,12 @@ std::vector<float2> smem_fft_twiddles(int L) {
 namespace {
 
 constexpr double kDispConst = 4.148808e3;   // s MHz^2 pc^-1 cm^3: delay = D DM / nu^2
-constexpr int kColG = 2;                    // channels (A) / columns (C) per CTA
+// channels (A) / columns (C) per CTA: two, so that each frame's read or write is one whole
+// 32-byte sector (one channel per CTA measured slower at 4096 frames, despite two CTAs per SM)
+__host__ __device__ constexpr int col_g(int) { return 2; }
 
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
 
 // W_M^{p} = exp(-2 pi i p / M) for 0 <= p < M (M a power of two: 2p / M is exact)
 __device__ __forceinline__ float2 twiddle_m(int p, float inv_half_m) {
@@ -68,15 +71,16 @@ struct DdBlocks {
     int64_t start0;         // ring frame of block 0's first frame
     int step;               // frames between blocks (F - O)
     float2* work;           // [n_blocks][F][n_chan] float4 as pairs: pol X then pol Y per element
-    float* part;            // [n_blocks][n_chan / kColG][keep] detected column-group sums
+    float* part;            // [n_blocks][n_chan / col_g(F)][keep] detected column-group sums
     int keep;               // frames kept per block (F - O)
 };
 
 // A: per channel, the F-point DFT over the block's frames.  Groups g = 2 kk + pol.
 template <int F>
-__global__ void __launch_bounds__(2 * kColG * SmemFft<F>::T)
+__global__ void __launch_bounds__(2 * col_g(F) * SmemFft<F>::T, (2 * col_g(F) * SmemFft<F>::T <= 512) ? 2 : 1)
 dd_pass_a(DdBlocks d, int n_chan, const float2* __restrict__ tw) {
     using P = SmemFft<F>;
+    constexpr int kColG = col_g(F);
     extern __shared__ float2 sm[];
     const int g = threadIdx.x / P::T, t = threadIdx.x % P::T;
     const int k0 = blockIdx.x * kColG, blk = blockIdx.y;
@@ -110,6 +114,8 @@ dd_pass_b(float2* __restrict__ work, int F, const float2* __restrict__ chirp, co
           float inv_half_m) {
     using P = SmemFft<NC>;
     extern __shared__ float2 sm[];
+    float2* trow = sm + 2 * RB * P::PAD;             // [RB][NC] W_M^{m k1} of the CTA's rows
+    float2* crows = trow + RB * NC;                  // [RB][NC] the rows' chirp
     const int g = threadIdx.x / P::T, t = threadIdx.x % P::T;
     const int row0 = blockIdx.x * RB, blk = blockIdx.y;
     float4* rows = reinterpret_cast<float4*>(work) + (static_cast<int64_t>(blk) * F + row0) * NC;
@@ -118,17 +124,19 @@ dd_pass_b(float2* __restrict__ work, int F, const float2* __restrict__ chirp, co
         const float4 v = rows[static_cast<int64_t>(r) * NC + k];
         sm[(2 * r) * P::PAD + pad16(k)] = make_float2(v.x, -v.y);           // conj: inverse DFT
         sm[(2 * r + 1) * P::PAD + pad16(k)] = make_float2(v.z, -v.w);
+        trow[i] = twiddle_m(k * (row0 + r), inv_half_m);
+        crows[i] = __ldg(chirp + static_cast<int64_t>(row0) * NC + i);
     }
     __syncthreads();
-    const int k1 = row0 + g / 2;
     float2* buf = sm + g * P::PAD;
-    const float2* crow = chirp + static_cast<int64_t>(k1) * NC;
+    const float2* tr = trow + (g / 2) * NC;
+    const float2* crow = crows + (g / 2) * NC;
     // a = DFT(conj V) = conj(n_chan x~); next input n_chan x~ W^{m k1} = conj(a) W^{m k1}
-    smem_fft<NC>(buf, tw, t, g, [&](int m, float2 a) { return cmul(conjf2(a), twiddle_m(m * k1, inv_half_m)); });
+    smem_fft<NC>(buf, tw, t, g, [=](int m, float2 a) { return cmul(conjf2(a), tr[m]); });
     // X at k2; next input conj(X C)
-    smem_fft<NC>(buf, tw, t, g, [&](int k2, float2 x) { return conjf2(cmul(x, __ldg(crow + k2))); });
+    smem_fft<NC>(buf, tw, t, g, [=](int k2, float2 x) { return conjf2(cmul(x, crow[k2])); });
     // c = DFT(conj Y) = conj(inverse DFT of Y); keep conj(c) W^{-n k1} = conj(c W^{n k1})
-    smem_fft<NC>(buf, tw, t, g, [&](int n, float2 c) { return conjf2(cmul(c, twiddle_m(n * k1, inv_half_m))); });
+    smem_fft<NC>(buf, tw, t, g, [=](int n, float2 c) { return conjf2(cmul(c, tr[n])); });
     __syncthreads();
     for (int i = threadIdx.x; i < RB * NC; i += blockDim.x) {
         const int r = i / NC, n = i % NC;
@@ -140,9 +148,10 @@ dd_pass_b(float2* __restrict__ work, int F, const float2* __restrict__ chirp, co
 // C: per column n, the inverse F-point DFT over k1 (conj(DFT(conj))), then the detected power
 // of the kept frames summed over the CTA's columns and both polarisations.
 template <int F>
-__global__ void __launch_bounds__(2 * kColG * SmemFft<F>::T)
+__global__ void __launch_bounds__(2 * col_g(F) * SmemFft<F>::T, (2 * col_g(F) * SmemFft<F>::T <= 512) ? 2 : 1)
 dd_pass_c(DdBlocks d, int n_chan, const float2* __restrict__ tw, float scale) {
     using P = SmemFft<F>;
+    constexpr int kColG = col_g(F);
     extern __shared__ float2 sm[];
     const int g = threadIdx.x / P::T, t = threadIdx.x % P::T;
     const int n0 = blockIdx.x * kColG, blk = blockIdx.y;
@@ -169,41 +178,53 @@ dd_pass_c(DdBlocks d, int n_chan, const float2* __restrict__ tw, float scale) {
     }
 }
 
-// D: window means.  One thread per kept frame l of a block, reading the column-group sums
-// part[c][l] for c in order (consecutive threads, consecutive l).  avg <= n_chan: the frame's
-// n_chan / avg windows; avg > n_chan: the frame's total, summed over avg / n_chan frames by
-// shuffles (avg / n_chan <= 32).
-__global__ void dd_pass_d(const float* __restrict__ part, int n_blocks, int keep, int n_chan, int avg,
-                          float* __restrict__ out) {
-    const int n_cg = n_chan / kColG;
+// D: window means from the column-group sums part[blk][c][l] (G columns per group).
+// Windows inside a frame (avg < n_chan): one thread per (block, window, frame), consecutive
+// threads on consecutive frames (coalesced reads).  Whole-frame windows: a CTA takes 32 frames
+// (lanes) and its 8 warps split the column groups; the warps' partial sums are added in order
+// in shared memory, then over the avg / n_chan frames of a window by shuffles.
+__global__ void dd_pass_d_in_frame(const float* __restrict__ part, int n_blocks, int keep, int n_chan, int G,
+                                   int avg, float* __restrict__ out) {
+    const int n_cg = n_chan / G, nw = n_chan / avg, per = avg / G;
     const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    const bool live = i < static_cast<int64_t>(n_blocks) * keep;
-    const int blk = live ? static_cast<int>(i / keep) : 0, l = live ? static_cast<int>(i % keep) : 0;
-    const float* pp = part + static_cast<int64_t>(blk) * n_cg * keep + l;
-    const int64_t s0 = static_cast<int64_t>(blk) * keep * n_chan + static_cast<int64_t>(l) * n_chan;  // first sample
-    const float inv = 1.0f / static_cast<float>(avg);
-    if (avg <= n_chan) {
-        if (!live) return;
-        const int per = avg / kColG;
-        for (int w = 0; w < n_chan / avg; ++w) {
-            float s = 0.0f;
-            for (int c = 0; c < per; ++c) s += pp[static_cast<int64_t>(w * per + c) * keep];
-            out[s0 / avg + w] = s * inv;
-        }
-    } else {
-        float s = 0.0f;
-        if (live)
-            for (int c = 0; c < n_cg; ++c) s += pp[static_cast<int64_t>(c) * keep];
-        const int fr = avg / n_chan;             // frames per window: a power of two <= 32, divides keep
-        for (int o = fr / 2; o > 0; o /= 2) s += __shfl_down_sync(0xffffffffu, s, o, fr);
-        if (live && (l % fr) == 0) out[s0 / avg] = s * inv;
+    if (i >= static_cast<int64_t>(n_blocks) * nw * keep) return;
+    const int l = static_cast<int>(i % keep);
+    const int w = static_cast<int>((i / keep) % nw);
+    const int blk = static_cast<int>(i / (static_cast<int64_t>(keep) * nw));
+    const float* pp = part + (static_cast<int64_t>(blk) * n_cg + static_cast<int64_t>(w) * per) * keep + l;
+    float s = 0.0f;
+    for (int c = 0; c < per; ++c) s += pp[static_cast<int64_t>(c) * keep];
+    out[(static_cast<int64_t>(blk) * keep + l) * nw + w] = s * (1.0f / static_cast<float>(avg));
+}
+
+__global__ void __launch_bounds__(256) dd_pass_d_frames(const float* __restrict__ part, int keep, int n_chan, int G,
+                                                        int avg, float* __restrict__ out) {
+    __shared__ float red[8][32];
+    const int n_cg = n_chan / G, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int blk = blockIdx.y, l = blockIdx.x * 32 + lane;
+    const int c0 = w * (n_cg / 8), c1 = c0 + n_cg / 8;
+    float s = 0.0f;
+    if (l < keep) {
+        const float* pp = part + static_cast<int64_t>(blk) * n_cg * keep + l;
+        for (int c = c0; c < c1; ++c) s += pp[static_cast<int64_t>(c) * keep];
     }
+    red[w][lane] = s;
+    __syncthreads();
+    if (w != 0) return;
+    s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += red[q][lane];
+    const int fr = avg / n_chan;             // frames per window: a power of two <= 32, divides keep
+    for (int o = fr / 2; o > 0; o /= 2) s += __shfl_down_sync(0xffffffffu, s, o, fr);
+    if (l < keep && (l % fr) == 0)
+        out[(static_cast<int64_t>(blk) * keep + l) / fr] = s * (1.0f / static_cast<float>(avg));
 }
 
 template <int F>
 cudaError_t launch_ac(bool c_pass, const DdBlocks& d, int n_chan, int n_blocks, const float2* tw, float scale,
                       cudaStream_t s) {
     using P = SmemFft<F>;
+    constexpr int kColG = col_g(F);
     const size_t smem = static_cast<size_t>(2 * kColG) * P::PAD * sizeof(float2);
     const dim3 grid(n_chan / kColG, n_blocks), block(2 * kColG * P::T);
     if (!c_pass) {
@@ -235,7 +256,7 @@ cudaError_t launch_b(float2* work, int F, int n_blocks, const float2* chirp, con
                      cudaStream_t s) {
     using P = SmemFft<NC>;
     constexpr int RB = (2 * P::T >= 256) ? 1 : 256 / (2 * P::T);   // at least 256 threads a CTA
-    const size_t smem = static_cast<size_t>(2 * RB) * P::PAD * sizeof(float2);
+    const size_t smem = (static_cast<size_t>(2 * RB) * P::PAD + static_cast<size_t>(2 * RB) * NC) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(dd_pass_b<NC, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const dim3 grid(F / RB, n_blocks), block(2 * RB * P::T);
@@ -276,6 +297,11 @@ struct corr_dd {
     float2* chirp = nullptr;                // [F][n_chan]: C[k1 + F k2] at [k1][k2]
     float2* tw_f = nullptr;                 // smem_fft twiddles for F and n_chan points
     float2* tw_c = nullptr;
+    // stage timing (corr_dd_set_timing): events around the ring copy and passes A-D of a push
+    bool timing = false;
+    cudaEvent_t ev[6] = {};
+    double stage_ms[5] = {};
+    int timed = 0;
 };
 
 namespace {
@@ -289,6 +315,8 @@ void dd_free(corr_dd* d) {
     void* bufs[] = {d->ring, d->work, d->part, d->chirp, d->tw_f, d->tw_c};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    for (cudaEvent_t e : d->ev)
+        if (e) cudaEventDestroy(e);
     delete d;
 }
 }  // namespace
@@ -339,7 +367,8 @@ int corr_dd_create(corr_dd_t** out, int n_chan, int fft_frames, int overlap_fram
     if (cudaMalloc(&d->ring, d->cap * n_chan * sizeof(float4)) != cudaSuccess) return bad("cudaMalloc(ring)");
     if (cudaMalloc(&d->work, static_cast<size_t>(d->max_blocks) * M * sizeof(float4)) != cudaSuccess)
         return bad("cudaMalloc(work)");
-    if (cudaMalloc(&d->part, static_cast<size_t>(d->max_blocks) * (n_chan / kColG) * keep * sizeof(float)) != cudaSuccess)
+    if (cudaMalloc(&d->part, static_cast<size_t>(d->max_blocks) * (n_chan / col_g(fft_frames)) * keep * sizeof(float)) !=
+        cudaSuccess)
         return bad("cudaMalloc(part)");
     // the chirp, FP64 phase reduced to [0, 1) cycles before rounding, stored [k1][k2]
     std::vector<float2> ch(static_cast<size_t>(M));
@@ -382,6 +411,8 @@ int corr_dd_push_device(corr_dd_t* d, const float* spec, int64_t n_frames, float
     cudaSetDevice(d->dev);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t fb = static_cast<size_t>(d->n_chan) * sizeof(float4);
+    const bool tm = d->timing && n_blocks > 0;
+    if (tm) DDCU(cudaEventRecord(d->ev[0], s));
     // append to the ring (two pieces at the wrap)
     int64_t done = 0;
     while (done < n_frames) {
@@ -398,16 +429,53 @@ int corr_dd_push_device(corr_dd_t* d, const float* spec, int64_t n_frames, float
         const int64_t M = static_cast<int64_t>(d->F) * d->n_chan;
         const float inv_half_m = 2.0f / static_cast<float>(M);
         const float scale = static_cast<float>(1.0 / (static_cast<double>(d->n_chan) * static_cast<double>(M)));
+        if (tm) DDCU(cudaEventRecord(d->ev[1], s));
         DDCU(launch_ac_any(d->F, false, b, d->n_chan, n_blocks, d->tw_f, scale, s));
+        if (tm) DDCU(cudaEventRecord(d->ev[2], s));
         DDCU(launch_b_any(d->n_chan, d->work, d->F, n_blocks, d->chirp, d->tw_c, inv_half_m, s));
+        if (tm) DDCU(cudaEventRecord(d->ev[3], s));
         DDCU(launch_ac_any(d->F, true, b, d->n_chan, n_blocks, d->tw_f, scale, s));
-        const int64_t threads = static_cast<int64_t>(n_blocks) * keep;
-        dd_pass_d<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, s>>>(d->part, n_blocks, keep, d->n_chan,
-                                                                              d->avg, out);
+        if (tm) DDCU(cudaEventRecord(d->ev[4], s));
+        const int G = col_g(d->F);
+        if (d->avg < d->n_chan) {
+            const int64_t threads = static_cast<int64_t>(n_blocks) * (d->n_chan / d->avg) * keep;
+            dd_pass_d_in_frame<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, s>>>(d->part, n_blocks, keep,
+                                                                                           d->n_chan, G, d->avg, out);
+        } else {
+            dd_pass_d_frames<<<dim3((keep + 31) / 32, n_blocks), 256, 0, s>>>(d->part, keep, d->n_chan, G, d->avg, out);
+        }
         DDCU(cudaGetLastError());
+        if (tm) {   // timing mode waits for the push and adds up its stages
+            DDCU(cudaEventRecord(d->ev[5], s));
+            DDCU(cudaEventSynchronize(d->ev[5]));
+            for (int q = 0; q < 5; ++q) {
+                float ms = 0.0f;
+                DDCU(cudaEventElapsedTime(&ms, d->ev[q], d->ev[q + 1]));
+                d->stage_ms[q] += ms;
+            }
+            d->timed += 1;
+        }
     }
     d->have = have - static_cast<int64_t>(n_blocks) * keep;
     if (n_out) *n_out = static_cast<int64_t>(n_blocks) * per_block;
+    return CORR_OK;
+}
+
+int corr_dd_set_timing(corr_dd_t* d, int on) {
+    if (!d) return ddfail(CORR_E_INVAL, "null dedisperser");
+    cudaSetDevice(d->dev);
+    for (cudaEvent_t& e : d->ev)
+        if (!e) DDCU(cudaEventCreate(&e));
+    d->timing = on != 0;
+    std::memset(d->stage_ms, 0, sizeof d->stage_ms);
+    d->timed = 0;
+    return CORR_OK;
+}
+
+int corr_dd_stage_times(corr_dd_t* d, float* ms5, int* n_timed) {
+    if (!d || !ms5) return ddfail(CORR_E_INVAL, "null argument");
+    for (int q = 0; q < 5; ++q) ms5[q] = static_cast<float>(d->stage_ms[q]);
+    if (n_timed) *n_timed = d->timed;
     return CORR_OK;
 }
 

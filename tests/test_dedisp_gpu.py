@@ -78,15 +78,15 @@ def test_geometries_match_the_oracle(env, n_chan, F, O, dm):
 
 
 def test_bench_configuration_matches_the_oracle(env):
-    # the bench's workload: 2048 channels over 33.3 MHz at 610 MHz, DM 30, blocks of 2048 frames
-    # overlapping by 1024, one integration of 4096 frames per push, one output per frame
+    # the bench's workload: 1024 channels over 33.3 MHz at 610 MHz, DM 30, blocks of 4096 frames
+    # overlapping by 2048, one integration of 8192 frames per push, one output per frame
     torch, corr, dedisp = env
-    n_chan, F, O, dm, avg = 2048, 2048, 1024, 30.0, 2048
+    n_chan, F, O, dm, avg = 1024, 4096, 2048, 30.0, 1024
     assert corr.corr_dd_smear_samples(dm, F_LO, BW) < O * n_chan
-    v = _spectra(2 * 4096, n_chan, 13)
-    got = _run(torch, corr, v, [0, 4096, 8192], n_chan, F, O, dm, avg, max_push=4096)
+    v = _spectra(2 * 8192, n_chan, 13)
+    got = _run(torch, corr, v, [0, 8192, 16384], n_chan, F, O, dm, avg, max_push=8192)
     want = _oracle(dedisp, v, F, O, dm, avg)
-    assert got.shape == want.shape == (((8192 - F) // (F - O) + 1) * (F - O),)
+    assert got.shape == want.shape == (((16384 - F) // (F - O) + 1) * (F - O),)
     assert (np.abs(got - want) / want.mean()).max() < 2e-5
 
 
@@ -120,6 +120,14 @@ def test_arguments(env):
         assert ei.value.code == -1
     d = corr.corr_dd_create(256, 1024, 512, 1024, 2.0, F_LO, BW, 256)
     try:
+        corr.corr_dd_set_timing(d, True)               # stage timing of a push that completes blocks
+        v0 = torch.zeros((1024, 256, 4), dtype=torch.float32, device="cuda")
+        out0 = torch.empty(512, dtype=torch.float32, device="cuda")
+        assert corr.corr_dd_push_device(d, v0, out0) == 512
+        ms, cnt = corr.corr_dd_stage_times(d)
+        assert cnt == 1 and (ms >= 0).all() and ms[1:4].sum() > 0
+        corr.corr_dd_set_timing(d, False)
+        corr.corr_dd_reset(d)
         v = torch.zeros((1024, 256, 4), dtype=torch.float32, device="cuda")
         small = torch.empty(10, dtype=torch.float32, device="cuda")
         assert corr.corr_dd_push_device(d, v[:0], small) == 0          # nothing pushed
