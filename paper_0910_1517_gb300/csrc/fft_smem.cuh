@@ -13,6 +13,11 @@ namespace gbx {
 // one pad element per 16: every Stockham exchange of 8-byte points is free of bank conflicts
 __host__ __device__ constexpr int pad16(int i) { return i + (i >> 4); }
 
+// Packed FP32x2 arithmetic (sm_100 family): both components of a complex sum or difference in
+// one instruction, each rounded exactly as the scalar operation (a - b as fma(b, -1, a)).
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
 // cos / sin of 2 pi m / 16
 __device__ __forceinline__ constexpr float c16(int m) {
     return m == 0 ? 1.0f : m == 1 ? 0.92387953251128674f : m == 2 ? 0.70710678118654752f
@@ -65,8 +70,8 @@ struct Dft {
         if constexpr (K < R / 2) {
             const float2 e = out[K];
             const float2 t = twiddle_const<R, K>(out[K + R / 2]);
-            out[K] = cadd(e, t);
-            out[K + R / 2] = csub(e, t);
+            out[K] = padd(e, t);
+            out[K + R / 2] = psub(e, t);
             apply<K + 1>(out);
         }
     }
