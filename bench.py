@@ -440,13 +440,13 @@ def run_dedisp_leg(corr, torch, pk, k=20, dm=30.0, f_lo=1780.0 / 3.0, bw=100.0 /
     """Coherent dedispersion of the phased-array voltage beam (Sec. 5) at GMRT scale: one beam's
     voltage spectra (1024 channels over 33.3 MHz at 610 MHz, both polarisations), one
     integration (8192 frames) per push, DM 30 pc/cc (1.22 M samples = 1192 frames of smear),
-    blocks of 4096 frames overlapping by 2048 (four blocks per push), one total-power sample per
-    frame.  Input
+    blocks of 4096 frames overlapping by 1200 (just above the smear: 2896 new frames per
+    block, 2.83 blocks per push on average), one total-power sample per frame.  Input
     spectra (seeded Gaussian) are resident in HBM; each push copies them into the frame ring.
     Reports the push time, per-stage times and each pass's HBM traffic of the design (A: read the
     frames, write the work block; B: read it and the chirp, write it back; C: read it, write the
     column sums) against the measured HBM peak, and the real-time factor."""
-    F, O, n_push = 4096, 2048, N_INT
+    F, O, n_push = 4096, 1200, N_INT
     d = corr.corr_dd_create(N_CHAN, F, O, n_push, dm, f_lo, bw, N_CHAN)
     try:
         g = torch.Generator(device="cuda").manual_seed(555)
@@ -471,10 +471,11 @@ def run_dedisp_leg(corr, torch, pk, k=20, dm=30.0, f_lo=1780.0 / 3.0, bw=100.0 /
         st, cnt = corr.corr_dd_stage_times(d)
         corr.corr_dd_set_timing(d, False)
         st = [float(x) / max(cnt, 1) for x in st]
-        nb = n_push // keep                                 # blocks per push in the steady state
+        nb = n_out / k / keep                               # blocks per push, averaged (one output per frame)
         M = F * N_CHAN
         traffic = {"ring_copy": 2 * n_push * N_CHAN * 16, "A": nb * 2 * M * 16, "B": nb * (2 * M * 16 + M * 8),
                    "C": nb * (M * 16 + keep * (N_CHAN // 2) * 4), "D": nb * keep * (N_CHAN // 2) * 4}
+        traffic = {q: int(b) for q, b in traffic.items()}
         names = ["ring_copy", "A", "B", "C", "D"]
         stages = {}
         for nme, t in zip(names, st):

@@ -79,9 +79,10 @@ def test_geometries_match_the_oracle(env, n_chan, F, O, dm):
 
 def test_bench_configuration_matches_the_oracle(env):
     # the bench's workload: 1024 channels over 33.3 MHz at 610 MHz, DM 30, blocks of 4096 frames
-    # overlapping by 2048, one integration of 8192 frames per push, one output per frame
+    # overlapping by 1200 (the smear is 1192 frames), one integration of 8192 frames per push,
+    # one output per frame
     torch, corr, dedisp = env
-    n_chan, F, O, dm, avg = 1024, 4096, 2048, 30.0, 1024
+    n_chan, F, O, dm, avg = 1024, 4096, 1200, 30.0, 1024
     assert corr.corr_dd_smear_samples(dm, F_LO, BW) < O * n_chan
     v = _spectra(2 * 8192, n_chan, 13)
     got = _run(torch, corr, v, [0, 8192, 16384], n_chan, F, O, dm, avg, max_push=8192)
