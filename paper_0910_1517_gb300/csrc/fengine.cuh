@@ -97,6 +97,15 @@ int multibeam_wstride(int n_beams, int n_ant);
 cudaError_t launch_multibeam(const float* spec, int n_ant, int n_pol, int n_chan, int n_int, const float2* w,
                              int n_beams, int products, int avg, float4* out, unsigned* err, cudaStream_t s);
 
+// The same phased beams on the tcgen05 tensor cores (multibeam_tc.cu): FP32 accuracy from an
+// on-chip fp16 hi/lo split of weights and spectra; n_ant <= 64, n_beams <= 64, n_int % 64 == 0.
+// launch_multibeam takes this form whenever it applies.  split_scale: power of two bringing the
+// spectra below the fp16 range (2^-(log2 n_fft - 8)).
+bool multibeam_tc_supported(int n_ant, int n_pol, int n_chan, int n_int);
+cudaError_t launch_multibeam_tc(const float* spec, int n_ant, int n_pol, int n_chan, int n_int, const float2* w,
+                                int wstride, int n_beams, int products, int avg, float split_scale, float4* out,
+                                unsigned* err, cudaStream_t s);
+
 // ADC-format 4-bit ingest (ingest4.cu): card rows packed[c][0..2n) (stride ld, even) -> int8 rows
 // rows[4c + j][0..n) (stride ldr), the 4 interleaved inputs of each card demultiplexed and sign-extended.
 cudaError_t launch_unpack4(const uint8_t* packed, int64_t ld, int n_cards, int64_t n, int8_t* rows, int64_t ldr,

@@ -15,6 +15,7 @@
 // by shuffles across its lanes (avg <= 32) and then across 32-frame passes in order.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 
 #include "common.cuh"
@@ -185,8 +186,14 @@ cudaError_t launch_multibeam(const float* spec, int n_ant, int n_pol, int n_chan
     // hide the copies; fewer CTAs per channel leave enough of them)
     int span = avg > 64 ? avg : 64;
     while (span < 512 && n_int % (2 * span) == 0) span *= 2;
-    const size_t smem = multibeam_smem(n_ant * n_pol, n_chan, n_beams, n_ant);
     const int wstride = multibeam_wstride(n_beams, n_ant);
+    if (multibeam_tc_supported(n_ant, n_pol, n_chan, n_int)) {   // the tensor-core form
+        int e = -8;
+        for (int n = 2 * n_chan; n > 1; n >>= 1) ++e;
+        return launch_multibeam_tc(spec, n_ant, n_pol, n_chan, n_int, w, wstride, n_beams, products, avg,
+                                   ldexpf(1.0f, -e), out, err, s);
+    }
+    const size_t smem = multibeam_smem(n_ant * n_pol, n_chan, n_beams, n_ant);
     const dim3 grid(n_chan, n_int / span);
     auto go = [&](auto kern) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));

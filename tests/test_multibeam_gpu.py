@@ -66,6 +66,24 @@ def test_multibeam_matches_oracle(env, n_beams, products, avg):
     assert e <= 1e-5
 
 
+@pytest.mark.parametrize("n_ant,n_pol,n_fft,n_beams,products,avg", [
+    (32, 2, 2048, 16, 0, 32),      # GMRT-scale antennas, 8-frame K-blocks (tensor-core form)
+    (32, 2, 4096, 64, 0, 128),     # 4-frame K-blocks, 64 beams, windows across stages
+    (5, 1, 1024, 7, 1, 1),         # one polarisation, K padded (tensor-core form), voltages
+    (72, 1, 512, 9, 0, 8)])        # K = 144 > 128: the CUDA-core form
+def test_multibeam_shapes_match_oracle(env, n_ant, n_pol, n_fft, n_beams, products, avg):
+    torch, corr, orc = env
+    s = make_config(2, n_ant=n_ant, n_pol=n_pol, n_fft=n_fft, n_int=256, seed=7300 + n_ant + n_fft)
+    W = _weights(n_beams, s.n_ant, s.n_fft // 2, 73 + n_beams)
+    B, _ = _run(env, s, W, products, avg)
+    chans = [0, 1, 77, s.n_fft // 2 - 1]
+    Y = orc.fengine(s.x, s.n_ant, s.n_pol, s.n_fft, s.n_int, s.delay, s.phi0, s.rate, chans=chans)
+    Bo = orc.multibeam(Y, s.n_ant, s.n_pol, W[:, :, chans].astype(np.complex64).astype(np.complex128), products, avg)
+    e = _err(B[:, :, chans], Bo, products)
+    print(f"multibeam {n_ant}x{n_pol} N {n_fft} beams {n_beams} products {products} avg {avg}: {e:.2e}")
+    assert e <= 1e-5
+
+
 def test_multibeam_coherent_weights_reproduce_the_coherent_beam_and_fp32tc(env):
     torch, corr, orc = env
     s = make_config(2, n_ant=8, n_fft=512, n_int=128, seed=7100)
