@@ -99,7 +99,7 @@ cudaError_t launch_multibeam(const float* spec, int n_ant, int n_pol, int n_chan
 
 // The same phased beams on the tcgen05 tensor cores (multibeam_tc.cu): FP32 accuracy from an
 // on-chip fp16 hi/lo split of weights and spectra; n_ant <= 64, n_beams <= 64, n_int % 64 == 0.
-// launch_multibeam takes this form whenever it applies.  split_scale: power of two bringing the
+// launch_multibeam takes this form for more than 24 beams where it applies.  split_scale: power of two bringing the
 // spectra below the fp16 range (2^-(log2 n_fft - 8)).
 bool multibeam_tc_supported(int n_ant, int n_pol, int n_chan, int n_int);
 cudaError_t launch_multibeam_tc(const float* spec, int n_ant, int n_pol, int n_chan, int n_int, const float2* w,

@@ -29,6 +29,7 @@ constexpr int kMbWarps = kMbThreads / 32;
 constexpr int kMbMaxBeams = 64;                 // beams per launch (kMbMaxBeams / kMbWarps per thread)
 constexpr int kMbFrames = 64;                   // frames per shared-memory stage (a lane takes 2)
 constexpr int kMbMaxIn = 128;
+constexpr int kMbTcMinBeams = 24;               // more beams than this: the tensor-core form
 
 struct MbShared {
     uint64_t bar[2];
@@ -187,7 +188,10 @@ cudaError_t launch_multibeam(const float* spec, int n_ant, int n_pol, int n_chan
     int span = avg > 64 ? avg : 64;
     while (span < 512 && n_int % (2 * span) == 0) span *= 2;
     const int wstride = multibeam_wstride(n_beams, n_ant);
-    if (multibeam_tc_supported(n_ant, n_pol, n_chan, n_int)) {   // the tensor-core form
+    // the tensor-core form for many beams: its time hardly depends on the beam count (5.0 ms for
+    // 16 and 5.1 ms for 64 beams at GMRT scale), the CUDA-core kernel's grows with it (3.4 ms for
+    // 16, 13.0 ms for 64); they cross near 24 beams
+    if (n_beams > kMbTcMinBeams && multibeam_tc_supported(n_ant, n_pol, n_chan, n_int)) {
         int e = -8;
         for (int n = 2 * n_chan; n > 1; n >>= 1) ++e;
         return launch_multibeam_tc(spec, n_ant, n_pol, n_chan, n_int, w, wstride, n_beams, products, avg,

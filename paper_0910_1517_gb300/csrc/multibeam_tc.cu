@@ -242,7 +242,10 @@ multibeam_tc_kernel(const float* __restrict__ spec, int n_ant, int n_pol, int n_
                     }
                 }
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
+                for (int e1 = 0; e1 < 4; ++e1) {
+                    // frame f0 + e, rotated by tq so that the warp's 16-byte stores spread over
+                    // the bank groups (lanes are 64 bytes apart)
+                    const int e = (e1 + tq) & 3;
                     float x[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
@@ -286,35 +289,45 @@ multibeam_tc_kernel(const float* __restrict__ spec, int n_ant, int n_pol, int n_
                     tc_fence_before();
                     mbar_arrive(&sh.acce[s]);                   // every column of this accumulator is read
                 }
+                const int f32 = st * kFrames + h * 32;          // first frame of these 32 in the CTA's span
+                if (products == 1) {                            // voltages (avg 1)
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float u0 = __uint_as_float(r0[j]);
+                        const float u1 = n_pol == 2 ? __uint_as_float(r1[j]) : 0.0f;
+                        const float p0 = __shfl_xor_sync(0xffffffffu, u0, 1);
+                        const float p1 = __shfl_xor_sync(0xffffffffu, u1, 1);
+                        if (c == 0 && b < n_beams)
+                            out[(static_cast<int64_t>(b) * n_out + t0 + f32 + j) * n_chan + k] =
+                                make_float4(u0 * ds, p0 * ds, u1 * ds, p1 * ds);
+                    }
+                    continue;
+                }
+                // window complete after frame j when (j + 1) is a multiple of avg (avg <= 32: j is a
+                // compile-time index, avg a power of two), or after the 32 when avg > 32
+                auto flush = [&](int f_last) {                 // add the partner lane's half and write
+                    const float a00 = s00 + __shfl_xor_sync(0xffffffffu, s00, 1);
+                    const float a11 = s11 + __shfl_xor_sync(0xffffffffu, s11, 1);
+                    const float a01 = s01 + __shfl_xor_sync(0xffffffffu, s01, 1);
+                    const float ax = sx + __shfl_xor_sync(0xffffffffu, sx, 1);
+                    if (c == 0 && b < n_beams)
+                        out[(static_cast<int64_t>(b) * n_out + (t0 + f_last) / avg) * n_chan + k] =
+                            make_float4(a00 * sc, a11 * sc, a01 * sc, ax * sc);
+                    s00 = s11 = s01 = sx = 0.f;
+                };
+                const int wmask = avg - 1;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const float u0 = __uint_as_float(r0[j]);
                     const float u1 = n_pol == 2 ? __uint_as_float(r1[j]) : 0.0f;
-                    const int f = st * kFrames + h * 32 + j;   // frame within the CTA's span
-                    if (products == 1) {                       // voltages (avg 1)
-                        const float p0 = __shfl_xor_sync(0xffffffffu, u0, 1);
-                        const float p1 = __shfl_xor_sync(0xffffffffu, u1, 1);
-                        if (c == 0 && b < n_beams)
-                            out[(static_cast<int64_t>(b) * n_out + t0 + f) * n_chan + k] =
-                                make_float4(u0 * ds, p0 * ds, u1 * ds, p1 * ds);
-                        continue;
-                    }
                     const float p1 = __shfl_xor_sync(0xffffffffu, u1, 1);
                     s00 = fmaf(u0, u0, s00);
                     s11 = fmaf(u1, u1, s11);
                     s01 = fmaf(u0, u1, s01);
                     sx = fmaf(c == 0 ? -u0 : u0, p1, sx);      // re: -re0 im1, im: im0 re1
-                    if ((f + 1) % avg == 0) {                  // window complete: add the partner's half
-                        const float a00 = s00 + __shfl_xor_sync(0xffffffffu, s00, 1);
-                        const float a11 = s11 + __shfl_xor_sync(0xffffffffu, s11, 1);
-                        const float a01 = s01 + __shfl_xor_sync(0xffffffffu, s01, 1);
-                        const float ax = sx + __shfl_xor_sync(0xffffffffu, sx, 1);
-                        if (c == 0 && b < n_beams)
-                            out[(static_cast<int64_t>(b) * n_out + (t0 + f) / avg) * n_chan + k] =
-                                make_float4(a00 * sc, a11 * sc, a01 * sc, ax * sc);
-                        s00 = s11 = s01 = sx = 0.f;
-                    }
+                    if (avg <= 32 && ((j + 1) & wmask) == 0) flush(f32 + j);
                 }
+                if (avg > 32 && ((f32 + 32) & wmask) == 0) flush(f32 + 31);
             }
         }
     }

@@ -53,7 +53,7 @@ def _err(B, Bo, products):
 
 
 @pytest.mark.parametrize("n_beams,products,avg", [
-    (12, 0, 1), (12, 0, 4), (3, 0, 64), (1, 0, 128), (64, 0, 32), (12, 1, 1)])
+    (12, 0, 1), (12, 0, 4), (3, 0, 64), (1, 0, 128), (64, 0, 32), (12, 1, 1), (48, 0, 1), (33, 1, 1)])
 def test_multibeam_matches_oracle(env, n_beams, products, avg):
     torch, corr, orc = env
     s = make_config(2, n_ant=8, n_fft=512, n_int=128, seed=7000 + n_beams + avg)
@@ -67,10 +67,11 @@ def test_multibeam_matches_oracle(env, n_beams, products, avg):
 
 
 @pytest.mark.parametrize("n_ant,n_pol,n_fft,n_beams,products,avg", [
-    (32, 2, 2048, 16, 0, 32),      # GMRT-scale antennas, 8-frame K-blocks (tensor-core form)
-    (32, 2, 4096, 64, 0, 128),     # 4-frame K-blocks, 64 beams, windows across stages
-    (5, 1, 1024, 7, 1, 1),         # one polarisation, K padded (tensor-core form), voltages
-    (72, 1, 512, 9, 0, 8)])        # K = 144 > 128: the CUDA-core form
+    (32, 2, 2048, 16, 0, 32),      # GMRT-scale antennas, 16 beams: the CUDA-core form
+    (32, 2, 2048, 40, 0, 32),      # the same with 40 beams: the tensor-core form, 8-frame K-blocks
+    (32, 2, 4096, 64, 0, 128),     # 4-frame K-blocks, 64 beams, windows across stages (tensor cores)
+    (5, 1, 1024, 30, 1, 1),        # one polarisation, K padded, voltages (tensor cores)
+    (72, 1, 512, 30, 0, 8)])       # K = 144 > 128: the CUDA-core form even with 30 beams
 def test_multibeam_shapes_match_oracle(env, n_ant, n_pol, n_fft, n_beams, products, avg):
     torch, corr, orc = env
     s = make_config(2, n_ant=n_ant, n_pol=n_pol, n_fft=n_fft, n_int=256, seed=7300 + n_ant + n_fft)
