@@ -71,3 +71,31 @@ def test_null_handle_is_rejected(lib):
     from paper_0910_1517_gb300 import corr
     with pytest.raises(corr.CorrError):
         corr.corr_set_mode(None, 0, 0, 1)
+
+
+def test_dedisperser_smear_matches_the_oracle_on_the_host(lib):
+    # corr_dd_smear_samples is host arithmetic: the cold-plasma smear across the band
+    from oracle import dedisp
+    from paper_0910_1517_gb300 import corr
+    for dm, f_lo, bw in ((30.0, 1780.0 / 3.0, 100.0 / 3.0), (71.0398, 316.67, 16.66), (0.0, 600.0, 10.0)):
+        assert corr.corr_dd_smear_samples(dm, f_lo, bw) == pytest.approx(dedisp.smear_samples(dm, f_lo, bw),
+                                                                          rel=1e-12, abs=1e-9)
+    assert corr.corr_dd_smear_samples(1.0, 600.0, -1.0) == -1.0
+
+
+@pytest.mark.parametrize("args,code", [
+    ((100, 1024, 512, 1024, 2.0, 593.3, 33.3, 256), -1),     # n_chan not a power of two
+    ((256, 8192, 512, 1024, 2.0, 593.3, 33.3, 256), -1),     # fft_frames above 4096
+    ((256, 1024, 1024, 1024, 2.0, 593.3, 33.3, 256), -1),    # overlap = fft_frames
+    ((256, 1024, 512, 0, 2.0, 593.3, 33.3, 256), -1),        # no push room
+    ((256, 1024, 512, 1024, 2.0, 593.3, -33.3, 256), -1),    # lower sideband
+    ((256, 1024, 512, 1024, -1.0, 593.3, 33.3, 256), -1),    # negative DM
+    ((256, 1024, 512, 1024, 2.0, 593.3, 33.3, 3), -1),       # avg not a power of two
+    ((256, 1024, 511, 1024, 2.0, 593.3, 33.3, 512), -1),     # avg does not divide the block step (513 x 256)
+    ((256, 1024, 64, 1024, 2.0, 593.3, 33.3, 256), -2),      # overlap below the smear
+])
+def test_dedisperser_create_rejects_bad_arguments_before_any_cuda_call(lib, args, code):
+    from paper_0910_1517_gb300 import corr
+    with pytest.raises(corr.CorrError) as ei:
+        corr.corr_dd_create(*args)
+    assert ei.value.code == code
