@@ -97,3 +97,17 @@ def test_block_geometry_does_not_change_the_result():
     assert n >= 4096
     err = np.abs(Ia[:n] - Ib[:n]) / Ia[:n].mean()
     assert np.sqrt((err ** 2).mean()) < 1e-3 and err.max() < 3e-2
+
+
+def test_channel_smear_of_the_papers_b1937_example():
+    # the dispersion law the oracle uses reproduces the paper's printed worked example:
+    # arrival-time difference across one 65.1 kHz channel at 325 MHz for DM 71.0398
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "dispersion_smear_b1937.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    for dm, nu, dnu, want_ms, tol_ms in ((float(x) for x in r) for r in rows):
+        got = (dedisp.dispersion_delay(dm, nu - dnu / 2) - dedisp.dispersion_delay(dm, nu + dnu / 2)) * 1e3
+        assert abs(got - want_ms) <= tol_ms, got
+        # and the per-channel smear in samples of that channel's complex rate, the quantity the
+        # block overlap must cover when a single channel is dedispersed
+        assert dedisp.smear_samples(dm, nu - dnu / 2, dnu) == pytest.approx(got * 1e-3 * dnu * 1e6, rel=1e-9)
