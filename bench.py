@@ -695,8 +695,17 @@ def run_ours(args, world, rank, local_rank):
     corr.load()
     pk = peaks()
     if args.leg != "all":                                 # one extra leg alone (profiling runs)
-        res = run_batch_leg(args, corr, torch, rank) if args.leg == "batched" else \
-            run_dedisp_leg(corr, torch, peaks()) if args.leg == "dedisp" else run_rfi_leg(corr, torch)
+        if args.leg == "multibeam":                      # the phased-beam kernels alone (16 and 64 beams)
+            sm = make_config(2, seed=slice_seed(rank), n_int=N_INT)
+            ldm = ((sm.x.shape[1] + 15) // 16) * 16 + 16
+            xm = torch.zeros((N_IN, ldm), dtype=torch.int8, device="cuda")
+            xm[:, :sm.x.shape[1]] = torch.from_numpy(sm.x).cuda()
+            cm = (np.arange(N_ANT) < COH_ANTENNAS).astype(np.uint8)
+            res = {f"beams_{nb}": run_multibeam_leg(corr, torch, sm, xm, ldm, cm, corr.CORR_FP32TC, 10, None,
+                                                    peaks(), n_beams=nb) for nb in (16, 64)}
+        else:
+            res = run_batch_leg(args, corr, torch, rank) if args.leg == "batched" else \
+                run_dedisp_leg(corr, torch, peaks()) if args.leg == "dedisp" else run_rfi_leg(corr, torch)
         emit({"leg": args.leg, **res}, rank)
         if dist:
             dist.destroy_process_group()
@@ -859,8 +868,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--no-extras", action="store_true",
                     help="time only the FP32 step (no precision forms, no end-to-end leg); for profiling runs")
-    ap.add_argument("--leg", choices=("all", "batched", "rfi", "dedisp"), default="all",
-                    help="run only the batched sub-array leg or only the learned-RFI leg (profiling runs)")
+    ap.add_argument("--leg", choices=("all", "batched", "rfi", "dedisp", "multibeam"), default="all",
+                    help="run one extra leg alone: batched sub-arrays, learned RFI, dedispersion or phased beams (profiling runs)")
     ap.add_argument("--xmode", choices=("fp32tc", "fp32"), default="fp32tc",
                     help="form of the timed step: FP32 on the tensor cores (default) or the plain CUDA-core FP32 form")
     ap.add_argument("--n-int", type=int, default=N_INT,
