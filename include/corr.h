@@ -345,6 +345,14 @@ int corr_dd_stage_times(corr_dd_t* d, float* ms5, int* n_timed);
 int corr_dd_reset(corr_dd_t* d);
 int corr_dd_destroy(corr_dd_t* d);
 
+/* Failure detection, exercised without a GPU fault: one kernel waits on a barrier that nothing
+ * completes; every pipeline wait of this library is bounded by the same clock budget (~2 s at the
+ * maximum SM clock), after which it records an error bit in a device word and returns.
+ * corr_wait_selftest returns CORR_OK when the wait gave up and reported its bit as designed
+ * (*cycles_out, if given: the clock cycles it waited), CORR_E_STATE if it did not, CORR_E_CUDA on
+ * a CUDA error.  Runs on the current device's legacy default stream and synchronises it. */
+int corr_wait_selftest(long long* cycles_out);
+
 #if defined(__GNUC__)
 #pragma GCC visibility pop
 #endif

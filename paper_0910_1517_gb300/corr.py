@@ -60,6 +60,7 @@ SIGNATURES = {
     "corr_integrate_4bit_device": ([_P, _P, _L, _L, _L, _P], _I),
     "corr_read_multibeam": ([_P, _P, _I], _I),
     "corr_read_blank_stats": ([_P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], _I),
+    "corr_wait_selftest": ([ctypes.POINTER(ctypes.c_longlong)], _I),
     "corr_dd_smear_samples": ([ctypes.c_double, ctypes.c_double, ctypes.c_double], ctypes.c_double),
     "corr_dd_create": ([ctypes.POINTER(ctypes.c_void_p), _I, _I, _I, _I, ctypes.c_double, ctypes.c_double,
                         ctypes.c_double, _I], _I),
@@ -486,3 +487,10 @@ def corr_dd_reset(d):
 
 def corr_dd_destroy(d):
     return _ok(load().corr_dd_destroy(d))
+
+
+def corr_wait_selftest() -> int:
+    """Run the bounded-wait self-test; returns the clock cycles the wait took before giving up."""
+    c = ctypes.c_longlong(0)
+    _ok(load().corr_wait_selftest(ctypes.byref(c)))
+    return c.value
