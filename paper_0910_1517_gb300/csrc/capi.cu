@@ -478,11 +478,9 @@ int corr_create(corr_t** out, int n_ant, int n_pol, int n_fft, int n_int) {
     CUB(cudaMemset(h->d_vis, 0, nvis * sizeof(float2)));
     CUB(cudaMemset(h->d_vis_int, 0, nvis * sizeof(int2)));
     CUB(cudaMemset(h->d_scale, 0, ni * nch * sizeof(float)));
-    {
-        const std::vector<float2> tw = fengine_twiddles(n_fft);
-        CUB(dalloc(&h->d_tw, tw.size()));
-        CUB(cudaMemcpy(h->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
-    }
+    CUB(dalloc(&h->d_tw, static_cast<size_t>(fengine_tw_count(n_fft))));
+    CUB(launch_fengine_twiddles(n_fft, h->d_tw, h->stream));
+    CUB(cudaStreamSynchronize(h->stream));
 #undef CUB
     if (xengine_tc_supported(h->n_in)) {
         const int rb = 2 * h->n_in > 128 ? 2 : 1;

@@ -4,7 +4,7 @@
 #include <cmath>
 #include <vector>
 
-#include "fengine_impl.cuh"
+#include "fengine_wfft.cuh"
 
 namespace gbx {
 namespace {
@@ -19,23 +19,24 @@ __global__ void phasor_setup_kernel(int n_ant, int n_chan, int n_fft, int n_int,
          q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         if (q < n1) {
             const int a = static_cast<int>(q / n_chan), k = static_cast<int>(q % n_chan);
-            const double Da = floor(tau[a] + 0.5), tf = tau[a] - Da;
-            double sn, cs;
-            sincospi(2.0 * k * tf / n_fft, &sn, &cs);   // exp(+2 pi i k tau_f / N)
-            pf[q] = make_float2(static_cast<float>(cs), static_cast<float>(sn));
+            pf[q] = model_fstc_phasor(tau[a], k, n_fft);
         } else if (q < n1 + n2) {
             const int64_t r = q - n1;
             const int a = static_cast<int>(r / n_int), t = static_cast<int>(r % n_int);
-            const double twopi = 6.283185307179586476925286766559;
-            double ph = phi0[a] + rate[a] * static_cast<double>(g0 + t);   // FP64 over the global frame counter
-            ph -= twopi * rint(ph / twopi);
-            double sn, cs;
-            sincos(ph, &sn, &cs);
-            ff[r] = make_float2(static_cast<float>(cs), static_cast<float>(-sn));  // exp(-i phi)
+            ff[r] = model_fringe_phasor(phi0[a], rate[a], g0 + t);
         } else {
             const int a = static_cast<int>(q - n1 - n2);
-            D[a] = static_cast<int>(floor(tau[a] + 0.5));
+            D[a] = model_int_delay(tau[a]);
         }
+    }
+}
+
+__global__ void twiddle_kernel(int n_fft, int count, float2* __restrict__ tw) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+        double num, den, sn, cs;
+        fengine_tw_angle(n_fft, e, num, den);
+        sincospi(2.0 * num / den, &sn, &cs);
+        tw[e] = make_float2(static_cast<float>(cs), static_cast<float>(-sn));
     }
 }
 
@@ -94,23 +95,10 @@ size_t fengine_smem_bytes(int n_fft) {
     }
 }
 
-std::vector<float2> fengine_twiddles(int n_fft) {
-    // [R2][16] pass-2, [R3][16 R2] pass-3 and [M/2 + 1] real-split twiddles, from FP64
-    const int M = n_fft / 2;
-    const int R2 = (M / 16 >= 16) ? 16 : M / 16, R3 = M / (16 * R2), Ns3 = 16 * R2;
-    const double two_pi = 6.283185307179586476925286766559;
-    std::vector<float2> tw;
-    auto w = [&](double num, double den) {
-        return make_float2(static_cast<float>(std::cos(two_pi * num / den)),
-                           static_cast<float>(-std::sin(two_pi * num / den)));
-    };
-    for (int r = 0; r < R2; ++r)
-        for (int j = 0; j < 16; ++j) tw.push_back(w(static_cast<double>(j) * r, 16.0 * R2));
-    if (R3 > 1)
-        for (int r = 0; r < R3; ++r)
-            for (int j = 0; j < Ns3; ++j) tw.push_back(w(static_cast<double>(j) * r, static_cast<double>(M)));
-    for (int k = 0; k <= M / 2; ++k) tw.push_back(w(k, n_fft));
-    return tw;
+cudaError_t launch_fengine_twiddles(int n_fft, float2* tw, cudaStream_t s) {
+    const int count = fengine_tw_count(n_fft);
+    twiddle_kernel<<<(count + 255) / 256, 256, 0, s>>>(n_fft, count, tw);
+    return cudaGetLastError();
 }
 
 int fengine_frames_per_cta(int n_fft) { return kChanFrames / (n_fft / 2); }
@@ -118,9 +106,9 @@ int fengine_frames_per_cta(int n_fft) { return kChanFrames / (n_fft / 2); }
 cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s) {
     if (p.n_chan * 2 != p.n_fft) return cudaErrorInvalidValue;
     switch (mode) {
-        case OUT_FP32: return launch_mode<OUT_FP32>(p, s);
-        case OUT_I8: return launch_mode<OUT_I8>(p, s);
-        case OUT_F16: return launch_mode<OUT_F16>(p, s);
+        case OUT_FP32: return launch_w_mode<OUT_FP32>(p, s);
+        case OUT_I8: return launch_w_mode<OUT_I8>(p, s);
+        case OUT_F16: return launch_w_mode<OUT_F16>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cmath>
 #include <vector>
 
 namespace gbx {
@@ -46,7 +47,7 @@ struct FeParams {
     const float* scale;    // [n_in][n_chan] requantisation scales (I8 / F16)
     void* spec;            // spectra in the K-block layout
     float* beams;          // [2][n_int][n_chan] raw-resolution beams (0 inc, 1 coh)
-    const float2* tw;      // FFT twiddles laid out by fengine_twiddles()
+    const float2* tw;      // FFT twiddles laid out as fengine_tw_angle() describes
     unsigned* err;
 };
 
@@ -64,8 +65,75 @@ cudaError_t launch_fengine_batched(const FeBatch* dtab, int total_blocks, size_t
 // Dynamic shared memory needed by the F-engine for a given FFT size.
 size_t fengine_smem_bytes(int n_fft);
 int fengine_frames_per_cta(int n_fft);
-// Twiddle tables of the F-engine's FFT plan for n_fft, computed in FP64 and rounded once.
-std::vector<float2> fengine_twiddles(int n_fft);
+
+// Twiddle table of the F-engines for n_fft (M = n_fft / 2); entry e holds exp(-2 pi i num / den)
+// (fengine_tw_angle), evaluated in FP64 on the device and rounded once (launch_fengine_twiddles).
+//   part A, read by the kernel of fengine_impl.cuh (n_fft = 4096, batched launches): [R2][16]
+//     pass-2 twiddles W_{16 R2}^(j r), [R3][16 R2] pass-3 twiddles W_M^(j r) when R3 > 1, then
+//     [M/2 + 1] real-split twiddles W_N^k;
+//   part B (M <= 1024), read by the warp-FFT kernel of fengine_wfft.cuh: [P = M/32][32]
+//     inter-pass twiddles W_M^(l k1), then [M/2 + 1] W_N^k.
+__host__ __device__ constexpr int fengine_tw_r2(int M) { return (M / 16 >= 16) ? 16 : M / 16; }
+__host__ __device__ constexpr int fengine_tw_r3(int M) { return M / (16 * fengine_tw_r2(M)); }
+__host__ __device__ constexpr int fengine_tw_a_count(int n_fft) {
+    return fengine_tw_r2(n_fft / 2) * 16 +
+           (fengine_tw_r3(n_fft / 2) > 1 ? fengine_tw_r3(n_fft / 2) * 16 * fengine_tw_r2(n_fft / 2) : 0) + n_fft / 4 + 1;
+}
+__host__ __device__ constexpr int fengine_tw_wfft_offset(int n_fft) { return fengine_tw_a_count(n_fft); }
+__host__ __device__ constexpr int fengine_tw_count(int n_fft) {
+    return fengine_tw_a_count(n_fft) + (n_fft / 2 <= 1024 ? (n_fft / 64) * 32 + n_fft / 4 + 1 : 0);
+}
+__host__ __device__ inline void fengine_tw_angle(int n_fft, int e, double& num, double& den) {
+    const int M = n_fft / 2, R2 = fengine_tw_r2(M), R3 = fengine_tw_r3(M), Ns3 = 16 * R2;
+    const int A = fengine_tw_a_count(n_fft);
+    if (e < A) {
+        if (e < R2 * 16) {                                   // pass 2: W_{16 R2}^(j r), [r][j]
+            num = static_cast<double>(e % 16) * (e / 16);
+            den = 16.0 * R2;
+            return;
+        }
+        e -= R2 * 16;
+        if (R3 > 1 && e < R3 * Ns3) {                        // pass 3: W_M^(j r), [r][j]
+            num = static_cast<double>(e % Ns3) * (e / Ns3);
+            den = M;
+            return;
+        }
+        e -= (R3 > 1 ? R3 * Ns3 : 0);                        // real split: W_N^k
+        num = e;
+        den = n_fft;
+        return;
+    }
+    e -= A;
+    if (e < (M / 32) * 32) {                                 // inter-pass: W_M^(l k1), [k1][l]
+        num = static_cast<double>(e % 32) * (e / 32);
+        den = M;
+        return;
+    }
+    num = e - (M / 32) * 32;                                 // real split: W_N^k
+    den = n_fft;
+}
+cudaError_t launch_fengine_twiddles(int n_fft, float2* tw, cudaStream_t s);
+
+// The per-antenna delay model (Sec. 2.1, Eq. 2), shared by every table set-up:
+// integer delay D = floor(tau + 1/2), fractional-delay (FSTC) phasor exp(+2 pi i k tau_f / N)
+// with tau_f = tau - D, fringe phasor exp(-i phi) with phi = phi0 + rate g over the global frame
+// count g, reduced mod 2 pi in FP64.
+__host__ __device__ inline int model_int_delay(double tau) { return static_cast<int>(floor(tau + 0.5)); }
+__device__ inline float2 model_fstc_phasor(double tau, int k, int n_fft) {
+    const double tf = tau - floor(tau + 0.5);
+    double sn, cs;
+    sincospi(2.0 * k * tf / n_fft, &sn, &cs);
+    return make_float2(static_cast<float>(cs), static_cast<float>(sn));
+}
+__device__ inline float2 model_fringe_phasor(double phi0, double rate, int64_t g) {
+    const double twopi = 6.283185307179586476925286766559;
+    double ph = phi0 + rate * static_cast<double>(g);
+    ph -= twopi * rint(ph / twopi);
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    return make_float2(static_cast<float>(cs), static_cast<float>(-sn));
+}
+
 cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s);
 
 // pf, ff and D for one integration from the FP64 delay / fringe model.

@@ -1,0 +1,445 @@
+// fengine_wfft.cuh -- the F-engine for n_chan <= 1024 (n_fft <= 2048): warp-specialised, one
+// warp per FFT group, two radix-32 passes; included by fengine.cu after fengine_impl.cuh.
+//
+// Same work and outputs as the kernel of fengine_impl.cuh (Sec. 2.1 FX chain, Eq. 2 phasor,
+// Sec. 2.2 beams), organised to cut instructions and shared-memory traffic and to keep both
+// halves of the work in flight at once:
+//   * a CTA owns F = 8192 / M consecutive frames and walks over every input (the beams need
+//     every antenna of a frame in one CTA);
+//   * warps 0-7 (the FFT group, 96 registers a thread) transform the frames of input it:
+//     the M-point complex FFT of a frame (z[n] = x[2n] + i x[2n+1], M = 32 P) is a four-step
+//     FFT inside one warp -- lane l takes column n = l + 32 m of each of the warp's G = 32 / P
+//     frames, P-point DFTs in registers straight from the int8 staging buffer, the twiddle
+//     W_M^(l k1), one transpose through the warp's own shared-memory region (__syncwarp), then
+//     lane (g, k1) a 32-point DFT in registers: Z[k1 + P k2] -- and leave the results in the
+//     region in natural order;
+//   * warps 8-15 (the epilogue group, 160 registers a thread) meanwhile take input it - 1: each
+//     thread owns 8 frames of two channel pairs (k, M - k) for the real split, the Eq. 2 phasor,
+//     the beams (accumulated in its registers over all inputs) and the K-block stores;
+//   * the regions, the antenna tables and the staging buffer are double-buffered; mbarriers
+//     hand a region set from the FFT group to the epilogue group (full) and back (empty).
+//     Every wait is bounded: on a timeout the error word is set, the CTA's abort flag stops
+//     both groups, and the copies still in flight are waited for before the CTA exits.
+#pragma once
+
+#include "fengine_impl.cuh"
+
+namespace gbx {
+namespace {
+
+constexpr int kWThreads = 512;
+constexpr int kWFftWarps = 8;                  // warps 0-7: FFT group (warpgroups 0, 1)
+constexpr int kWEpiThreads = 256;              // warps 8-15: epilogue group (warpgroups 2, 3)
+constexpr int kWRegFft = 96, kWRegEpi = 160;   // 256 x 96 + 256 x 160 = 512 x 128 registers
+
+template <int M>
+struct WPlan {
+    static_assert(M >= 32 && M <= 1024 && (M & (M - 1)) == 0, "32 <= M <= 1024, a power of two");
+    static constexpr int P = M / 32;               // pass-1 points per lane and frame
+    static constexpr int G = 32 / P;               // frames per FFT warp
+    static constexpr int F = kWFftWarps * G;       // frames per CTA (8192 / M)
+    static constexpr int N = 2 * M;                // real FFT size
+    static constexpr int S = 33 * P;               // float2 stride of a frame in a warp region
+    static constexpr int REG = 32 * 33;            // float2 per warp region (rows padded to 33)
+    static constexpr int STAGE = F * N + 32;       // staging bytes per buffer
+    static constexpr int L = 8;                    // frames per epilogue thread
+    static constexpr int SLOTS = M / 4;            // pair slots per frame group (two pairs each)
+    static constexpr int NFG = kWEpiThreads / SLOTS;   // frame groups
+    static_assert(NFG * L == F && G * S <= REG && STAGE % 16 == 0, "plan");
+};
+
+template <int M>
+struct WSmem {
+    using P = WPlan<M>;
+    static constexpr int kTw1 = P::P * 32;         // inter-pass twiddles [k1][l]
+    static constexpr int kTwN = M / 2 + 1;         // real-split twiddles
+    static constexpr int kTab = 2 * M + P::F;      // [pf M | wcoh M | ff F] of one antenna
+    static constexpr size_t stage = 0;
+    static constexpr size_t X = stage + 2 * static_cast<size_t>(P::STAGE);
+    static constexpr size_t tw = X + 2 * sizeof(float2) * kWFftWarps * P::REG;
+    static constexpr size_t tab = ((tw + sizeof(float2) * (kTw1 + kTwN) + 127) / 128) * 128;
+    static constexpr size_t total = tab + 2 * sizeof(float2) * kTab;
+    static_assert(total <= 232448 - 1024, "F-engine shared memory exceeds 227 KB");
+    static_assert(X % 16 == 0 && tab % 16 == 0 && (sizeof(float2) * kTab) % 16 == 0, "bulk-copy targets");
+};
+
+struct WCtl {
+    uint64_t bar[2];           // staging buffer b landed
+    uint64_t tbar[2];          // antenna tables b landed
+    uint64_t full[2];          // region set b transformed (FFT warps -> epilogue)
+    uint64_t empty[2];         // region set b and tables b consumed (epilogue warps -> FFT group)
+    int abort_flag;
+    int Ds[kMaxAnt];
+};
+
+// int8 pair (x[2n], x[2n+1]) as the complex sample z[n]
+__device__ __forceinline__ float2 pair_u16(uint32_t w) {
+    return make_float2(static_cast<float>(static_cast<signed char>(w & 0xffu)),
+                       static_cast<float>(static_cast<signed char>((w >> 8) & 0xffu)));
+}
+
+template <int N_REG>
+__device__ __forceinline__ void reg_dealloc() { asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N_REG)); }
+template <int N_REG>
+__device__ __forceinline__ void reg_alloc() { asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N_REG)); }
+
+template <int M, int MODE>
+__global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams p) {
+    using P = WPlan<M>;
+    using S = WSmem<M>;
+    constexpr int PP = P::P, G = P::G, F = P::F, N = P::N, L = P::L;
+    constexpr int TB = (MODE == OUT_FP32) ? tb_fp32(M) : kTbHalf;
+    static_assert(TB == 8, "8-frame K-block runs");
+    __shared__ __align__(8) WCtl ctl;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* stage0 = smem + S::stage;
+    float2* Xbuf = reinterpret_cast<float2*>(smem + S::X);          // [2][8 warps][REG]
+    float2* tw1 = reinterpret_cast<float2*>(smem + S::tw);         // [P][32]
+    float2* twN = tw1 + S::kTw1;                                    // [M/2 + 1]
+    float2* tab = reinterpret_cast<float2*>(smem + S::tab);        // 2 x [pf | wcoh | ff]
+    volatile int* abort_flag = &ctl.abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int t0 = blockIdx.x * F;
+    const int n_fr = min(F, p.n_int - t0);
+    const int n_iter = p.n_in;                // polarisation-major: it = pol * n_ant + a
+
+    const float2* twsrc = p.tw + fengine_tw_wfft_offset(N);
+    for (int m = tid; m < S::kTw1 + S::kTwN; m += kWThreads) tw1[m] = twsrc[m];
+    for (int m = tid; m < p.n_ant; m += kWThreads) ctl.Ds[m] = p.D[m];
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&ctl.bar[b], 1);
+            mbar_init(&ctl.tbar[b], 1);
+            mbar_init(&ctl.full[b], kWFftWarps);
+            mbar_init(&ctl.empty[b], kWEpiThreads / 32);
+        }
+        fence_mbar_init();
+        ctl.abort_flag = 0;
+    }
+    __syncthreads();
+
+    if (warp < kWFftWarps) {
+        // ================================================================ FFT group
+        reg_dealloc<kWRegFft>();
+        // lane 0 of warp 0 issues the bulk copy of the F frames of input `it` (offset by its
+        // integer delay); bytes past the last 16-byte boundary are copied by the lanes only when
+        // rounding the copy up would read past the row's readable samples
+        auto issue = [&](int it) {
+            const int pol = it / p.n_ant, a = it % p.n_ant;
+            const int i = a * p.n_pol + pol;
+            unsigned char* dst = stage0 + (it & 1) * P::STAGE;
+            const int64_t s0 = static_cast<int64_t>(t0) * N + ctl.Ds[a];
+            const int64_t aligned = s0 & ~static_cast<int64_t>(15);
+            const int64_t end = s0 + static_cast<int64_t>(n_fr) * N;
+            const int64_t up = (end + 15) & ~static_cast<int64_t>(15);
+            const int64_t bulk_end = up <= p.n_avail ? up : (end & ~static_cast<int64_t>(15));
+            const uint32_t bulk = static_cast<uint32_t>(bulk_end - aligned);
+            const int8_t* row = p.x + static_cast<int64_t>(i) * p.ld;
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&ctl.bar[it & 1], bulk);
+                bulk_g2s(dst, row + aligned, bulk, &ctl.bar[it & 1]);
+            }
+            const int64_t q = bulk_end + lane;
+            if (q < end) dst[q - aligned] = static_cast<unsigned char>(row[q]);
+        };
+        // phasor, beam-weight and fringe rows of the antenna of input `it` (n_fr * 8 bytes of
+        // fringe phasors: a multiple of 16 since n_fr is a multiple of 16 or F)
+        auto issue_tab = [&](int it) {
+            const int a = it % p.n_ant;
+            float2* dst = tab + (it & 1) * S::kTab;
+            uint64_t* tb = &ctl.tbar[it & 1];
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(tb, (2 * M + n_fr) * sizeof(float2));
+            bulk_g2s(dst, p.pf + static_cast<int64_t>(a) * M, M * sizeof(float2), tb);
+            bulk_g2s(dst + M, p.wcoh + static_cast<int64_t>(a) * M, M * sizeof(float2), tb);
+            bulk_g2s(dst + 2 * M, p.ff + static_cast<int64_t>(a) * p.n_int + t0, n_fr * sizeof(float2), tb);
+        };
+        if (warp == 0) issue(0);
+        int staged = 1, tabbed = 0;           // copies issued so far (staging buffers, tables)
+        for (int it = 0; it < n_iter; ++it) {
+            const int b = it & 1;
+            // every FFT warp is done with input it - 1: its staging buffer takes input it + 1.  The
+            // barrier also takes the decision to stop (the OR of every FFT thread's view of the abort
+            // flag), so that the whole group leaves together.
+            if (named_bar_or(1, kWFftWarps * 32, *abort_flag != 0)) break;
+            if (warp == 0 && it + 1 < n_iter) {
+                issue(it + 1);
+                staged = it + 2;
+            }
+            // region set b and tables b: the epilogue has finished input it - 2
+            bool ok = it < 2 || mbar_wait(&ctl.empty[b], ((it - 2) >> 1) & 1, p.err, ERR_WAIT_EPI);
+            if (ok && tid == 0) {
+                issue_tab(it);
+                tabbed = it + 1;
+            }
+            ok = ok && mbar_wait(&ctl.bar[b], (it >> 1) & 1, p.err, ERR_WAIT_STAGE);
+            // a timed-out wait stops the CTA at the next barrier; this pass runs on whatever the
+            // buffers hold (every address is data-independent), so no thread leaves the group alone
+            if (!ok) *abort_flag = 1;
+            const int a = it % p.n_ant;
+            const int64_t s0 = static_cast<int64_t>(t0) * N + ctl.Ds[a];
+            float2* Rw = Xbuf + b * (kWFftWarps * P::REG) + warp * P::REG;   // this warp's region
+            // ---- pass 1: lane = column l of each of the warp's G frames, P-point DFTs
+            const unsigned char* st = stage0 + b * P::STAGE + (s0 & 15) + warp * G * N;
+            float2 v[32];
+            if ((s0 & 1) == 0) {               // pairs are 2-byte aligned: one load each
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const uint16_t* s16 = reinterpret_cast<const uint16_t*>(st + g * N);
+#pragma unroll
+                    for (int m = 0; m < PP; ++m) v[g * PP + m] = pair_u16(s16[lane + 32 * m]);
+                }
+            } else {
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+#pragma unroll
+                    for (int m = 0; m < PP; ++m) {
+                        const unsigned char* q = st + g * N + 2 * (lane + 32 * m);
+                        v[g * PP + m] = make_float2(static_cast<float>(static_cast<signed char>(q[0])),
+                                                    static_cast<float>(static_cast<signed char>(q[1])));
+                    }
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g) Dft<PP>::template run<1>(v + g * PP);
+            // twiddle W_M^(l k1)
+#pragma unroll
+            for (int k1 = 1; k1 < PP; ++k1) {
+                const float2 w = tw1[k1 * 32 + lane];
+#pragma unroll
+                for (int g = 0; g < G; ++g) v[g * PP + k1] = cmul(w, v[g * PP + k1]);
+            }
+            // ---- transpose through the warp's region: row r = g P + k1, column l
+#pragma unroll
+            for (int r = 0; r < 32; ++r) Rw[r * 33 + lane] = v[r];
+            __syncwarp();
+#pragma unroll
+            for (int n = 0; n < 32; ++n) v[n] = Rw[lane * 33 + n];
+            __syncwarp();
+            // ---- pass 2: lane = (g, k1), 32-point DFT over the columns: Z_g[k1 + P k2]
+            Dft<32>::template run<1>(v);
+            float2* o = Rw + (lane / PP) * P::S + (lane % PP);
+#pragma unroll
+            for (int k2 = 0; k2 < 32; ++k2) o[PP * k2] = v[k2];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl.full[b]);
+        }
+        if (*abort_flag && tid == 0) {
+            // copies issued and not yet seen to land must land before the CTA exits
+            for (int q = max(0, staged - 2); q < staged; ++q) mbar_wait(&ctl.bar[q & 1], (q >> 1) & 1, nullptr, 0);
+            for (int q = max(0, tabbed - 2); q < tabbed; ++q) mbar_wait(&ctl.tbar[q & 1], (q >> 1) & 1, nullptr, 0);
+        }
+    } else {
+        // ================================================================ epilogue group
+        reg_alloc<kWRegEpi>();
+        const int e = tid - kWFftWarps * 32;
+        const int fg = e / P::SLOTS, ps = e % P::SLOTS;
+        const bool live = fg * L < n_fr;      // n_fr is a multiple of 8: whole frame groups
+        const int R = 2 * p.n_in;
+        const int64_t ntb = p.n_int / TB;
+        const int kb_run = (t0 + fg * L) / TB;
+        const int64_t blk_elems = static_cast<int64_t>((MODE == OUT_FP32) ? rows_fp32(p.n_in) : R) * TB;
+        // channels of this thread: pairs (ps, M - ps) (pair 0 = (0, M/2)) and (ps + M/4, M - ps - M/4)
+        int chs[4];
+        chs[0] = ps;
+        chs[1] = (ps == 0) ? M / 2 : M - ps;
+        chs[2] = ps + M / 4;
+        chs[3] = M - ps - M / 4;
+        // -i W_N^k of the two pairs (the real split below works on 2 X)
+        float2 wn[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float2 w = twN[chs[2 * q]];
+            wn[q] = make_float2(w.y, -w.x);
+        }
+        float incr[L][4];
+        float2 cohr[L][4];
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                incr[l][c] = 0.0f;
+                cohr[l][c] = make_float2(0.0f, 0.0f);
+            }
+        for (int it = 0; it < n_iter; ++it) {
+            const int b = it & 1;
+            const int pol = it / p.n_ant, a = it % p.n_ant;
+            const int i = a * p.n_pol + pol;
+            const float g2 = p.ginc[a];
+            float scv[4];                      // requantisation scales of this thread's channels
+            if constexpr (MODE != OUT_FP32) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) scv[c] = p.scale[static_cast<int64_t>(i) * M + chs[c]];
+            }
+            // every lane waits; the warp goes on only if all of them saw both copies land and no
+            // abort (a warp-uniform decision: the stores below trade values between lanes)
+            bool ok = *abort_flag == 0 && mbar_wait(&ctl.full[b], (it >> 1) & 1, p.err, ERR_WAIT_EPI) &&
+                      mbar_wait(&ctl.tbar[b], (it >> 1) & 1, p.err, ERR_WAIT_STAGE);
+            if (!__all_sync(0xffffffffu, ok)) {
+                *abort_flag = 1;
+                break;
+            }
+            const float2* Xi = Xbuf + b * (kWFftWarps * P::REG);
+            const float2* pfa = tab + b * S::kTab;
+            const float2* wa = pfa + M;
+            const float2* fra = pfa + 2 * M;   // fringe phasors of the CTA's frames
+            // every lane computes (the FP32 stores trade values between lanes, and `live` is not
+            // warp-uniform when a warp spans several frame groups); only live lanes write
+            constexpr int PG = TB / 2;
+            const int Gr = (2 * i) >> 3, sgr = Gr & 7;
+            const int pstart = Gr * 8 * TB + ((((i & 3) ^ (sgr / PG)) * PG) << 2);   // floats from the block start
+            auto emit = [&](int c, const float2 (&yc)[L]) {
+                const float2 w = wa[chs[c]];
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    incr[l][c] += g2 * (yc[l].x * yc[l].x + yc[l].y * yc[l].y);
+                    const float2 prev = (a == 0) ? make_float2(0.0f, 0.0f) : cohr[l][c];
+                    cohr[l][c] = cadd(prev, cmul(w, yc[l]));
+                    if (live && a == p.n_ant - 1) {   // this polarisation's coherent sum is complete: detect
+                        float* bc = p.beams + (static_cast<int64_t>(p.n_int) + t0 + fg * L + l) * M + chs[c];
+                        const float pw = cohr[l][c].x * cohr[l][c].x + cohr[l][c].y * cohr[l][c].y;
+                        *bc = (pol == 0) ? pw : *bc + pw;
+                    }
+                }
+                if constexpr (MODE == OUT_FP32) {
+                    // 64-byte piece of (channel, input): granule slot (2 comp + half) ^ (sgr & 3); each lane
+                    // pair writes one piece per instruction, trading the component each needs by a shuffle
+                    float* spec = static_cast<float*>(p.spec);
+                    const bool odd = ps & 1;
+                    const int cA = (sgr >> 1) & 1;
+                    const bool hswap = sgr & 1;
+                    const int chp = __shfl_xor_sync(0xffffffffu, chs[c], 1);
+                    const int csend = odd ? cA : 1 - cA;
+                    float mine[8], recv[8];
+#pragma unroll
+                    for (int l = 0; l < 8; ++l) {
+                        const float own_keep = (odd ? 1 - cA : cA) ? yc[l].y : yc[l].x;
+                        const float own_send = csend ? yc[l].y : yc[l].x;
+                        mine[l] = own_keep;
+                        recv[l] = __shfl_xor_sync(0xffffffffu, own_send, 1);
+                    }
+                    auto put = [&](int ch, const float (&v)[8]) {
+                        uint32_t u[8];
+#pragma unroll
+                        for (int l = 0; l < 4; ++l) {
+                            u[l] = __float_as_uint(hswap ? v[4 + l] : v[l]);
+                            u[4 + l] = __float_as_uint(hswap ? v[l] : v[4 + l]);
+                        }
+                        if (live)
+                            st_global_v8(spec + (static_cast<int64_t>(ch) * ntb + kb_run) * blk_elems + pstart + (odd ? 8 : 0), u);
+                    };
+                    float d0[8], d1[8];
+#pragma unroll
+                    for (int l = 0; l < 8; ++l) {
+                        d0[l] = odd ? recv[l] : mine[l];
+                        d1[l] = odd ? mine[l] : recv[l];
+                    }
+                    put(odd ? chp : chs[c], d0);
+                    put(odd ? chs[c] : chp, d1);
+                } else {
+                    __half hr[L], hi[L];
+#pragma unroll
+                    for (int l = 0; l < L; ++l) {
+                        const float xr = yc[l].x * scv[c], xi = yc[l].y * scv[c];
+                        if constexpr (MODE == OUT_I8) {
+                            hr[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xr))));
+                            hi[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xi))));
+                        } else {
+                            hr[l] = __float2half_rn(xr);
+                            hi[l] = __float2half_rn(xi);
+                        }
+                    }
+                    __half* o = static_cast<__half*>(p.spec) + (static_cast<int64_t>(chs[c]) * ntb + kb_run) * blk_elems +
+                                2 * i * TB;
+                    uint32_t u[8];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        u[m] = pack_half2(hr[2 * m], hr[2 * m + 1]);
+                        u[4 + m] = pack_half2(hi[2 * m], hi[2 * m + 1]);
+                    }
+                    if (live) st_global_v8(o, u);
+                }
+            };
+            // ---- real split and Eq. 2 phasor.  With zk = Z[k], zm = Z[M - k]:
+            //   2 X[k] = E + Q, 2 X[M - k] = conj(E - Q), E = zk + conj(zm), Q = (-i W_N^k)(zk - conj(zm));
+            //   Y = X pf fr = (2 X) (pf / 2) fr.  Pair 0: 2 X[0] = 2 (Re + Im of Z[0]), 2 X[M/2] = 2 conj(Z[M/2]).
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int k = chs[2 * q], kc = chs[2 * q + 1];
+                const float2 hk = pfa[k], hm = pfa[kc];
+                const float2 pk = make_float2(0.5f * hk.x, 0.5f * hk.y), pm = make_float2(0.5f * hm.x, 0.5f * hm.y);
+                float2 yk[L], ym[L];
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    const int fl = fg * L + l;
+                    const float2* Xl = Xi + (fl / G) * P::REG + (fl % G) * P::S;
+                    const float2 zk = Xl[k];
+                    const float2 zm = Xl[kc];
+                    float2 xk, xmk;
+                    if (q == 0 && k == 0) {
+                        xk = make_float2(2.0f * (zk.x + zk.y), 0.0f);       // DC
+                        xmk = make_float2(2.0f * zm.x, -2.0f * zm.y);       // channel M/2 (zm = Z[M/2])
+                    } else {
+                        const float2 E = make_float2(zk.x + zm.x, zk.y - zm.y);
+                        const float2 D = make_float2(zk.x - zm.x, zk.y + zm.y);
+                        const float2 Q = cmul(wn[q], D);
+                        xk = make_float2(E.x + Q.x, E.y + Q.y);
+                        xmk = make_float2(E.x - Q.x, Q.y - E.y);
+                    }
+                    const float2 fr = fra[fl];
+                    yk[l] = cmul(xk, cmul(pk, fr));
+                    ym[l] = cmul(xmk, cmul(pm, fr));
+                }
+                emit(2 * q, yk);
+                emit(2 * q + 1, ym);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl.empty[b]);   // region set b and tables b may be reused
+        }
+        // incoherent beam of this thread's points
+        if (!*abort_flag && live) {
+#pragma unroll
+            for (int l = 0; l < L; ++l)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    p.beams[static_cast<int64_t>(t0 + fg * L + l) * M + chs[c]] = incr[l][c];
+        }
+    }
+}
+
+template <int M, int MODE>
+cudaError_t launch_w(const FeParams& p, cudaStream_t s) {
+    using P = WPlan<M>;
+    const size_t smem = WSmem<M>::total;
+    // the register split (setmaxnreg) hands the FFT group's registers to the epilogue group: it
+    // needs exactly the 512 x 128 registers of the launch, or the epilogue warps would wait for
+    // registers that never come -- refuse to launch otherwise
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, fengine_w_kernel<M, MODE>);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs * kWThreads != kWRegFft * kWFftWarps * 32 + kWRegEpi * kWEpiThreads) return cudaErrorInvalidConfiguration;
+    e = cudaFuncSetAttribute(fengine_w_kernel<M, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int grid = (p.n_int + P::F - 1) / P::F;
+    fengine_w_kernel<M, MODE><<<grid, kWThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_w_mode(const FeParams& p, cudaStream_t s) {
+    switch (p.n_chan) {
+        case 32: return launch_w<32, MODE>(p, s);
+        case 64: return launch_w<64, MODE>(p, s);
+        case 128: return launch_w<128, MODE>(p, s);
+        case 256: return launch_w<256, MODE>(p, s);
+        case 512: return launch_w<512, MODE>(p, s);
+        case 1024: return launch_w<1024, MODE>(p, s);
+        case 2048: return launch_t<2048, MODE>(p, s);   // 4-frame CTAs: the kernel of fengine_impl.cuh
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+}  // namespace gbx

@@ -18,30 +18,32 @@ __host__ __device__ constexpr int pad16(int i) { return i + (i >> 4); }
 __device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
 
-// cos / sin of 2 pi m / 16
-__device__ __forceinline__ constexpr float c16(int m) {
-    return m == 0 ? 1.0f : m == 1 ? 0.92387953251128674f : m == 2 ? 0.70710678118654752f
-         : m == 3 ? 0.38268343236508977f : m == 4 ? 0.0f : m == 5 ? -0.38268343236508977f
-         : m == 6 ? -0.70710678118654752f : m == 7 ? -0.92387953251128674f : -1.0f;
+// cos(2 pi m / 32), m = 0..16
+__device__ __forceinline__ constexpr float c32(int m) {
+    return m == 0 ? 1.0f : m == 1 ? 0.98078528040323044913f : m == 2 ? 0.92387953251128675613f
+         : m == 3 ? 0.83146961230254523708f : m == 4 ? 0.70710678118654752440f
+         : m == 5 ? 0.55557023301960222474f : m == 6 ? 0.38268343236508977173f
+         : m == 7 ? 0.19509032201612826785f : m == 8 ? 0.0f : -c32(16 - m);
 }
 
-// o * exp(-2 pi i k / R) with the trivial cases spelled out
+// o * exp(-2 pi i K / R) (R <= 32) with the trivial cases spelled out
 template <int R, int K>
 __device__ __forceinline__ float2 twiddle_const(float2 o) {
-    constexpr int m = K * (16 / R);              // position on the 16-point circle, 0..7
+    static_assert(R <= 32 && K < R / 2, "constant twiddles of radix <= 32");
+    constexpr int m = K * (32 / R);              // position on the 32-point circle, 0..15
     if constexpr (m == 0) {
         return o;
-    } else if constexpr (m == 4) {               // -i
+    } else if constexpr (m == 8) {               // -i
         return make_float2(o.y, -o.x);
-    } else if constexpr (m == 2) {               // (1 - i) / sqrt2
+    } else if constexpr (m == 4) {               // (1 - i) / sqrt2
         constexpr float h = 0.70710678118654752f;
         return make_float2(h * (o.x + o.y), h * (o.y - o.x));
-    } else if constexpr (m == 6) {               // (-1 - i) / sqrt2
+    } else if constexpr (m == 12) {              // (-1 - i) / sqrt2
         constexpr float h = 0.70710678118654752f;
         return make_float2(h * (o.y - o.x), -h * (o.x + o.y));
     } else {
-        constexpr float c = c16(m);
-        constexpr float s = (m <= 4) ? c16(4 - m) : c16(m - 4);  // sin(2 pi m / 16), m = 1..7
+        constexpr float c = c32(m);
+        constexpr float s = (m <= 8) ? c32(8 - m) : c32(m - 8);  // sin(2 pi m / 32), m = 1..15
         // w = c - i s
         return make_float2(c * o.x + s * o.y, c * o.y - s * o.x);
     }

@@ -53,12 +53,6 @@ struct Layout {
     size_t err, D, ginc, pf, wcoh, ff, tw, spec, total;
 };
 
-int twiddle_count(int n_fft) {
-    const int M = n_fft / 2;
-    const int R2 = (M / 16 >= 16) ? 16 : M / 16, R3 = M / (16 * R2);
-    return R2 * 16 + (R3 > 1 ? R3 * 16 * R2 : 0) + M / 2 + 1;
-}
-
 Layout layout(int n_ant, int n_pol, int n_fft, int n_int) {
     const size_t nch = n_fft / 2;
     Layout L{};
@@ -76,7 +70,7 @@ Layout layout(int n_ant, int n_pol, int n_fft, int n_int) {
     L.ff = o;
     o = align256(o + sizeof(float2) * n_ant * static_cast<size_t>(n_int));
     L.tw = o;
-    o = align256(o + sizeof(float2) * twiddle_count(n_fft));
+    o = align256(o + sizeof(float2) * gbx::fengine_tw_count(n_fft));
     L.spec = o;
     o = align256(o + sizeof(float) * nch * static_cast<size_t>(n_int) * gbx::rows_fp32(n_ant * n_pol));
     L.total = o;
@@ -84,60 +78,31 @@ Layout layout(int n_ant, int n_pol, int n_fft, int n_int) {
 }
 
 // Fill the per-integration tables of the F-engine: integer delays, FSTC and fringe phasors
-// (FP64 phase, as in the handle path), unit beam weights over all antennas, and the FFT
-// twiddles in the layout the F-engine reads.
+// (the delay-model helpers of fengine.cuh, as in the handle path) and unit beam weights over
+// all antennas.  The twiddles come from launch_fengine_twiddles, as in the handle path.
 __global__ void static_tables_kernel(Model m, int n_ant, int n_fft, int n_int, int64_t g0, unsigned char* base,
                                      Layout L) {
     const int M = n_fft / 2;
-    const int R2 = (M / 16 >= 16) ? 16 : M / 16, R3 = M / (16 * R2), Ns3 = 16 * R2;
-    const int n_tw = R2 * 16 + (R3 > 1 ? R3 * Ns3 : 0) + M / 2 + 1;
     int* D = reinterpret_cast<int*>(base + L.D);
     float* ginc = reinterpret_cast<float*>(base + L.ginc);
     float2* pf = reinterpret_cast<float2*>(base + L.pf);
     float2* wcoh = reinterpret_cast<float2*>(base + L.wcoh);
     float2* ff = reinterpret_cast<float2*>(base + L.ff);
-    float2* tw = reinterpret_cast<float2*>(base + L.tw);
     const int64_t n_pf = static_cast<int64_t>(n_ant) * M, n_ff = static_cast<int64_t>(n_ant) * n_int;
-    const int64_t total = n_pf + n_ff + n_tw + n_ant;
-    const double two_pi = 6.283185307179586476925286766559;
+    const int64_t total = n_pf + n_ff + n_ant;
     for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
          q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         if (q < n_pf) {
             const int a = static_cast<int>(q / M), k = static_cast<int>(q % M);
-            const double Da = floor(m.tau[a] + 0.5), tf = m.tau[a] - Da;
-            double sn, cs;
-            sincospi(2.0 * k * tf / n_fft, &sn, &cs);
-            pf[q] = make_float2(static_cast<float>(cs), static_cast<float>(sn));
+            pf[q] = gbx::model_fstc_phasor(m.tau[a], k, n_fft);
             wcoh[q] = make_float2(1.0f, 0.0f);
         } else if (q < n_pf + n_ff) {
             const int64_t r = q - n_pf;
             const int a = static_cast<int>(r / n_int), t = static_cast<int>(r % n_int);
-            double ph = m.phi0[a] + m.rate[a] * static_cast<double>(g0 + t);
-            ph -= two_pi * rint(ph / two_pi);
-            double sn, cs;
-            sincos(ph, &sn, &cs);
-            ff[r] = make_float2(static_cast<float>(cs), static_cast<float>(-sn));
-        } else if (q < n_pf + n_ff + n_tw) {
-            int e = static_cast<int>(q - n_pf - n_ff);
-            double num, den;
-            if (e < R2 * 16) {                                   // pass 2: W_{16 R2}^{j r}, [r][j]
-                num = static_cast<double>(e % 16) * (e / 16);
-                den = 16.0 * R2;
-            } else if (R3 > 1 && e < R2 * 16 + R3 * Ns3) {       // pass 3: W_M^{j r}, [r][j]
-                e -= R2 * 16;
-                num = static_cast<double>(e % Ns3) * (e / Ns3);
-                den = M;
-            } else {                                             // real split: W_N^k
-                e -= R2 * 16 + (R3 > 1 ? R3 * Ns3 : 0);
-                num = e;
-                den = n_fft;
-            }
-            double sn, cs;
-            sincospi(2.0 * num / den, &sn, &cs);
-            tw[q - n_pf - n_ff] = make_float2(static_cast<float>(cs), static_cast<float>(-sn));
+            ff[r] = gbx::model_fringe_phasor(m.phi0[a], m.rate[a], g0 + t);
         } else {
-            const int a = static_cast<int>(q - n_pf - n_ff - n_tw);
-            D[a] = static_cast<int>(floor(m.tau[a] + 0.5));
+            const int a = static_cast<int>(q - n_pf - n_ff);
+            D[a] = gbx::model_int_delay(m.tau[a]);
             ginc[a] = 1.0f;
         }
     }
@@ -196,11 +161,12 @@ extern "C" int corr_integrate_static(int n_ant, int n_pol, int n_fft, int n_int,
     // the error word keeps the previous call's value: clear it
     if (cudaMemsetAsync(base + L.err, 0, sizeof(unsigned), s) != cudaSuccess)
         return fail(CORR_E_CUDA, "corr_integrate_static: memset failed");
-    const int n_tw = twiddle_count(n_fft);
-    const int64_t work = static_cast<int64_t>(n_ant) * (n_fft / 2 + n_int) + n_tw + n_ant;
+    const int64_t work = static_cast<int64_t>(n_ant) * (n_fft / 2 + n_int) + n_ant;
     static_tables_kernel<<<static_cast<int>(std::min<int64_t>((work + 255) / 256, 4096)), 256, 0, s>>>(
         m, n_ant, n_fft, n_int, g0, base, L);
-    if (cudaGetLastError() != cudaSuccess) return fail(CORR_E_CUDA, "corr_integrate_static: table kernel");
+    if (cudaGetLastError() != cudaSuccess ||
+        gbx::launch_fengine_twiddles(n_fft, reinterpret_cast<float2*>(base + L.tw), s) != cudaSuccess)
+        return fail(CORR_E_CUDA, "corr_integrate_static: table kernel");
 
     gbx::FeParams fp{};
     fp.x = x;

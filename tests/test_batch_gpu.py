@@ -1,6 +1,6 @@
 """Several uneven sub-arrays in one graph-captured launch (corr_batch_*): every sub-array's
 integer visibilities equal the oracle's int64 MAC on its own requantised spectra, the batch
-agrees with the single-handle path, the graph replays correctly with new samples and frame
+agrees with the single-handle path (to rare +-1 requantisation flips), the graph replays correctly with new samples and frame
 counters, and the autotuner's stage choice leaves the results unchanged."""
 import numpy as np
 import pytest
@@ -71,10 +71,18 @@ def test_batch_int8_exact_matches_oracle_and_single_handle(env):
     try:
         corr.corr_batch_integrate_device(b, [x for x, _ in xs], n_avail=[n for _, n in xs], stream=st)
         batch_vi = [_check_exact(corr, orc, h, s) for h, s in zip(hs, streams)]
-        # the same integrations one handle at a time give the same integers
-        for h, (xt, n), vb in zip(hs, xs, batch_vi):
+        batch_q = [corr.corr_read_requant(h, 0, s.n_fft // 2, s.n_int)[0] for h, s in zip(hs, streams)]
+        # the same integrations one handle at a time: exact against the oracle on their own int8
+        # spectra, and those spectra equal the batch's but for rare +-1 flips where the two
+        # F-engine kernels (the batched launch and the single-handle warp-FFT kernel) round a
+        # requantised value that sits within an FP32 ulp of a rounding tie differently
+        for h, s, (xt, n), qb in zip(hs, streams, xs, batch_q):
             corr.corr_integrate_device(h, xt, n_avail=n, stream=st)
-            assert np.array_equal(corr.corr_read_vis_int(h), vb)
+            _check_exact(corr, orc, h, s)
+            qs = corr.corr_read_requant(h, 0, s.n_fft // 2, s.n_int)[0]
+            d = np.abs(qs.astype(np.int16) - qb.astype(np.int16))
+            print(f"batch vs single {s.n_ant} ant {s.n_fft}-pt: {int((d > 0).sum())} of {d.size} int8 values differ")
+            assert d.max() <= 1 and (d > 0).mean() <= 1e-4
         # replay the graph with other samples and a later frame counter
         for s_old, h, (xt, n) in zip(streams, hs, xs):
             s2 = make_config(2, n_ant=s_old.n_ant, n_pol=s_old.n_pol, n_fft=s_old.n_fft, n_int=s_old.n_int,
