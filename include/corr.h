@@ -289,10 +289,18 @@ int corr_batch_tune(corr_batch_t* b, int* ks_out, float* ms_out);
  *   vis                  device out [n_fft/2][n_bl][n_pol^2] complex64
  *   beams                device out [2][n_int][n_fft/2] float32 (raw resolution)
  *   stream               cudaStream_t to run on (NULL = legacy default stream)
- *   blocking             1: wait for completion and report kernel wait timeouts
- * Limits: n_ant <= 64 and the tables plus the FP32 spectra must fit the 32 MiB
- * (e.g. 4 ant x 2 pol x 512-pt FFT x 64 spectra uses ~1.1 MiB); larger
- * problems return CORR_E_RANGE.  The first call on a device looks up the
+ *   blocking             1: wait for completion, then report kernel wait timeouts
+ *                        (CORR_E_TIMEOUT); 0: return once queued.  Timeouts are
+ *                        recorded in a sticky error word in the static array that
+ *                        only a blocking call reads and clears, so a caller that
+ *                        queues with blocking = 0 learns of a timeout in any of
+ *                        those calls from its next blocking call.
+ * Errors before any CUDA call: CORR_E_INVAL for n_ant outside 1..64, n_pol not 1 or
+ * 2, bad n_fft / n_int, null or misaligned buffers, or a non-finite phi0 / rate;
+ * CORR_E_RANGE for a delay that is negative, not finite or rounds to more than
+ * 2e9 samples, for n_avail < n_int n_fft + max integer delay, and for problems
+ * whose tables plus FP32 spectra exceed the 32 MiB (e.g. 4 ant x 2 pol x 512-pt
+ * FFT x 64 spectra uses ~1.1 MiB).  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress, with that device current);
  * make that first call before any stream capture.  All calls share the one
  * array, so calls whose work overlaps on the GPU race with each other:

@@ -127,14 +127,21 @@ extern "C" int corr_integrate_static(int n_ant, int n_pol, int n_fft, int n_int,
     const Layout L = layout(n_ant, n_pol, n_fft, n_int);
     if (L.total > kScratchBytes)
         return fail(CORR_E_RANGE, "corr_integrate_static: problem needs more than the 32 MiB static scratch");
+    // the same delay-model checks as corr_set_delays, before any CUDA call: an integer delay
+    // D = floor(tau + 1/2) must be a non-negative int no larger than 2e9 (the F-engine offsets
+    // its sample reads by D), and the fringe model finite
     Model m{};
-    int dmax = 0;
+    int64_t dmax = 0;
     for (int a = 0; a < n_ant; ++a) {
-        if (!std::isfinite(delay[a]) || delay[a] < 0.0) return fail(CORR_E_RANGE, "corr_integrate_static: bad delay");
-        m.tau[a] = delay[a];
+        const double t = delay[a];
+        if (!std::isfinite(t) || t < 0.0 || std::floor(t + 0.5) > 2.0e9)
+            return fail(CORR_E_RANGE, "corr_integrate_static: delays must be finite, >= 0 and round to <= 2e9 samples");
+        if ((phi0 && !std::isfinite(phi0[a])) || (rate && !std::isfinite(rate[a])))
+            return fail(CORR_E_INVAL, "corr_integrate_static: fringe model is not finite");
+        m.tau[a] = t;
         m.phi0[a] = phi0 ? phi0[a] : 0.0;
         m.rate[a] = rate ? rate[a] : 0.0;
-        dmax = std::max(dmax, static_cast<int>(std::floor(delay[a] + 0.5)));
+        dmax = std::max(dmax, static_cast<int64_t>(std::floor(t + 0.5)));
     }
     if (n_avail < static_cast<int64_t>(n_int) * n_fft + dmax)
         return fail(CORR_E_RANGE, "corr_integrate_static: n_avail < n_int * n_fft + max delay");
@@ -158,9 +165,6 @@ extern "C" int corr_integrate_static(int n_ant, int n_pol, int n_fft, int n_int,
         return fail(CORR_E_CUDA, "corr_integrate_static: device query failed");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* base = static_cast<unsigned char*>(scratch);
-    // the error word keeps the previous call's value: clear it
-    if (cudaMemsetAsync(base + L.err, 0, sizeof(unsigned), s) != cudaSuccess)
-        return fail(CORR_E_CUDA, "corr_integrate_static: memset failed");
     const int64_t work = static_cast<int64_t>(n_ant) * (n_fft / 2 + n_int) + n_ant;
     static_tables_kernel<<<static_cast<int>(std::min<int64_t>((work + 255) / 256, 4096)), 256, 0, s>>>(
         m, n_ant, n_fft, n_int, g0, base, L);
@@ -202,11 +206,14 @@ extern "C" int corr_integrate_static(int n_ant, int n_pol, int n_fft, int n_int,
     if (gbx::launch_xengine_fp32(xp, n_sm, s) != cudaSuccess)
         return fail(CORR_E_CUDA, "corr_integrate_static: X-engine launch");
     if (blocking) {
+        // the error word is sticky: it collects the wait timeouts of this call and of every
+        // non-blocking call since the last blocking one; read it, then clear it
         unsigned err = 0;
         if (cudaStreamSynchronize(s) != cudaSuccess ||
-            cudaMemcpy(&err, base + L.err, sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess)
+            cudaMemcpy(&err, base + L.err, sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemset(base + L.err, 0, sizeof err) != cudaSuccess)
             return fail(CORR_E_CUDA, "corr_integrate_static: synchronisation failed");
-        if (err) return fail(CORR_E_TIMEOUT, "corr_integrate_static: a kernel wait timed out");
+        if (err) return fail(CORR_E_TIMEOUT, "corr_integrate_static: a kernel wait timed out (this call or an earlier non-blocking one)");
     }
     return CORR_OK;
 }

@@ -99,3 +99,36 @@ def test_dedisperser_create_rejects_bad_arguments_before_any_cuda_call(lib, args
     with pytest.raises(corr.CorrError) as ei:
         corr.corr_dd_create(*args)
     assert ei.value.code == code
+
+
+def _static_call(lib, n_ant=4, n_pol=2, n_fft=512, n_int=64, delay=None, phi0=None, rate=None, n_avail=None):
+    """corr_integrate_static with fake, never dereferenced device addresses: every case below is
+    refused by the host-side checks that run before the first CUDA call."""
+    import ctypes
+
+    import numpy as np
+    d = np.zeros(n_ant) if delay is None else np.asarray(delay, dtype=np.float64)
+    f = None if phi0 is None else np.asarray(phi0, dtype=np.float64)
+    w = None if rate is None else np.asarray(rate, dtype=np.float64)
+    ptr = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+    fake = ctypes.c_void_p(4096)
+    n_avail = n_int * n_fft + 4096 if n_avail is None else n_avail
+    ld = ((n_avail + 15) // 16) * 16
+    return lib.corr_integrate_static(n_ant, n_pol, n_fft, n_int, fake, ld, n_avail, 0, ptr(d), ptr(f), ptr(w),
+                                     fake, fake, None, 1)
+
+
+@pytest.mark.parametrize("kw,code", [
+    ({"delay": [0.0, 0.0, 3e9, 0.0]}, -2),                       # rounds beyond 2e9 samples
+    ({"delay": [0.0, -1.0, 0.0, 0.0]}, -2),                      # negative
+    ({"delay": [0.0, float("nan"), 0.0, 0.0]}, -2),              # not finite
+    ({"rate": [0.0, float("nan"), 0.0, 0.0]}, -1),               # fringe rate not finite
+    ({"phi0": [float("inf"), 0.0, 0.0, 0.0]}, -1),               # fringe phase not finite
+    ({"n_ant": 65, "delay": [0.0] * 65}, -1),                    # more antennas than the static tables hold
+    ({"n_ant": 64, "n_fft": 2048, "n_int": 8192, "delay": [0.0] * 64}, -2),   # beyond the 32 MiB scratch
+    ({"delay": [0.0, 0.0, 5000.0, 0.0], "n_avail": 64 * 512 + 100}, -2),     # samples short of the delay
+])
+def test_static_entry_refuses_bad_arguments_before_any_cuda_call(lib, kw, code):
+    from paper_0910_1517_gb300 import corr
+    assert _static_call(lib, **kw) == code
+    assert corr.corr_last_error()
