@@ -10,6 +10,8 @@ dedispersion stage, whose steps are FFTs, is numpy in ``dedisp.py``).
 Functions and the passage each follows (Roy et al., arXiv:0910.1517):
   fengine   -- integer delay, real DFT, FSTC + fringe phasor (Sec. 2.1, Eq. 2)
   xengine   -- MAC over N(N+1)/2 baselines x n_pol^2 products (Sec. 2.1)
+  xengine_self, xint_self -- the self-polar (total-intensity) MAC: products RR*, LL* only
+            (Sec. 2.1, 2.3.2), in FP64 and exactly on requantised spectra
   beams     -- incoherent and coherent array beams (Sec. 2.2, 4.3)
   multibeam -- several phased beams with full-polar products or voltages (Sec. 2.2, 5)
   requant   -- 8-bit requantisation of spectra (precision form; Sec. 4.1 analogue)
@@ -68,6 +70,8 @@ def lib():
         L.oracle_beams.argtypes = [i32, i32, i32, i32, i32, P, P, P, P, P, P, i32, P]
         L.oracle_requant.argtypes = [i32, i32, i32, P, P, P]
         L.oracle_xint.argtypes = [i32, i32, i32, i32, P, P, P, P]
+        L.oracle_xengine_self.argtypes = [i32, i32, i32, i32, P, P]
+        L.oracle_xint_self.argtypes = [i32, i32, i32, i32, P, P]
         L.oracle_mad_flag.argtypes = [i32, P, f64, P, P, P]
         L.oracle_threads.argtypes = []
         L.oracle_n_baselines.argtypes = [i32]
@@ -159,6 +163,26 @@ def xengine(Y, n_ant, n_pol):
     V = np.zeros((nch, n_baselines(n_ant), n_pol * n_pol, 2), dtype=np.float64)
     _check(lib().oracle_xengine(n_ant, n_pol, nch, n_frames, _p(Yr), _p(V)), "xengine")
     return V[..., 0] + 1j * V[..., 1]
+
+
+def xengine_self(Y, n_ant, n_pol):
+    """Self-polar visibilities V[c][b][p] (complex128): products Y_ap conj(Y_a'p) only."""
+    n_in, n_frames, nch = Y.shape
+    assert n_in == n_ant * n_pol
+    Yr = _as_ri(Y)
+    V = np.zeros((nch, n_baselines(n_ant), n_pol, 2), dtype=np.float64)
+    _check(lib().oracle_xengine_self(n_ant, n_pol, nch, n_frames, _p(Yr), _p(V)), "xengine_self")
+    return V[..., 0] + 1j * V[..., 1]
+
+
+def xint_self(q, n_ant, n_pol):
+    """Exact int64 self-polar MAC on int8 spectra q [n_in][n_frames][n_ch][2]: [c][b][p][2]."""
+    q = np.ascontiguousarray(q, dtype=np.int8)
+    n_in, n_frames, nch, _ = q.shape
+    assert n_in == n_ant * n_pol
+    Vi = np.zeros((nch, n_baselines(n_ant), n_pol, 2), dtype=np.int64)
+    _check(lib().oracle_xint_self(n_ant, n_pol, nch, n_frames, _p(q), _p(Vi)), "xint_self")
+    return Vi
 
 
 def beams(Y, n_ant, n_pol, n_fft, gain=None, theta=None, inc_mask=None, coh_mask=None,

@@ -153,6 +153,62 @@ int oracle_xengine(int n_ant, int n_pol, int n_chans, int n_frames,
 }
 
 /*
+ * Self-polar (total-intensity) MAC (Sec. 2.1 sizes the MAC for these two products,
+ * Sec. 2.3.2 names the self-polar mode): only the same-polarisation products
+ *   V[c][b][p] = sum_t Y_{a,p}[t][c] * conj(Y_{a',p}[t][c]),  a <= a',  p = 0 (RR*), 1 (LL*).
+ */
+int oracle_xengine_self(int n_ant, int n_pol, int n_chans, int n_frames,
+                        const double* Y, double* V) {
+    if (n_ant < 1 || (n_pol != 1 && n_pol != 2) || n_chans < 0 || n_frames < 0)
+        return OR_EINVAL;
+    const int n_bl = oracle_n_baselines(n_ant);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < n_chans; ++c) {
+        for (int a = 0; a < n_ant; ++a)
+            for (int a2 = a; a2 < n_ant; ++a2)
+                for (int p = 0; p < n_pol; ++p) {
+                    const int i = a * n_pol + p, j = a2 * n_pol + p;
+                    double sr = 0.0, si = 0.0;
+                    for (int t = 0; t < n_frames; ++t) {
+                        const double* u = Y + (((size_t)i * n_frames + t) * n_chans + c) * 2;
+                        const double* v = Y + (((size_t)j * n_frames + t) * n_chans + c) * 2;
+                        sr += u[0] * v[0] + u[1] * v[1];
+                        si += u[1] * v[0] - u[0] * v[1];
+                    }
+                    double* o = V + (((size_t)c * n_bl + bl_index(n_ant, a, a2)) * n_pol + p) * 2;
+                    o[0] = sr;
+                    o[1] = si;
+                }
+    }
+    return OR_OK;
+}
+
+/* The exact integer self-polar MAC on requantised spectra (as oracle_xint, products pp only). */
+int oracle_xint_self(int n_ant, int n_pol, int n_chans, int n_frames, const int8_t* q, int64_t* Vint) {
+    if (n_ant < 1 || (n_pol != 1 && n_pol != 2) || n_chans < 0 || n_frames < 0)
+        return OR_EINVAL;
+    const int n_bl = oracle_n_baselines(n_ant);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < n_chans; ++c)
+        for (int a = 0; a < n_ant; ++a)
+            for (int a2 = a; a2 < n_ant; ++a2)
+                for (int p = 0; p < n_pol; ++p) {
+                    const int i = a * n_pol + p, j = a2 * n_pol + p;
+                    int64_t sr = 0, si = 0;
+                    for (int t = 0; t < n_frames; ++t) {
+                        const int8_t* u = q + (((size_t)i * n_frames + t) * n_chans + c) * 2;
+                        const int8_t* v = q + (((size_t)j * n_frames + t) * n_chans + c) * 2;
+                        sr += (int64_t)u[0] * v[0] + (int64_t)u[1] * v[1];
+                        si += (int64_t)u[1] * v[0] - (int64_t)u[0] * v[1];
+                    }
+                    const size_t o = (((size_t)c * n_bl + bl_index(n_ant, a, a2)) * n_pol + p) * 2;
+                    Vint[o] = sr;
+                    Vint[o + 1] = si;
+                }
+    return OR_OK;
+}
+
+/*
  * Incoherent and coherent array beams (Sec. 2.2, 4.3), detected and summed
  * over polarisations, averaged over beam_avg consecutive frames.
  * gain   [n_ant] g_a;  theta [n_ant][n_fft/2] phase-calibration radians or NULL (=0)

@@ -419,6 +419,31 @@ def test_xint_descaled_equals_xengine_on_dequantised(orc):
     assert np.abs(V - V2).max() <= 1e-12 * np.abs(V2).max()
 
 
+def test_self_polar_mac_is_the_same_polarisation_products(orc):
+    # the self-polar (total-intensity) MAC keeps exactly the pp products of the full-polar one
+    # (itself pinned above), and a hand-written nested sum on a tiny input fixes one of them
+    rng = np.random.default_rng(12)
+    na, npol, nf, nch = 3, 2, 17, 4
+    Y = rng.standard_normal((na * npol, nf, nch)) + 1j * rng.standard_normal((na * npol, nf, nch))
+    Vf = orc.xengine(Y, na, npol)
+    Vs = orc.xengine_self(Y, na, npol)
+    assert Vs.shape == (nch, na * (na + 1) // 2, npol)
+    for p in range(npol):
+        assert np.array_equal(Vs[:, :, p], Vf[:, :, p * npol + p])
+    a, a2, p, c = 1, 2, 1, 3
+    ref = sum(Y[a * npol + p, t, c] * np.conj(Y[a2 * npol + p, t, c]) for t in range(nf))
+    b = na + (a2 - a)                      # baselines (0,0) (0,1) (0,2) (1,1) (1,2) ...
+    assert abs(Vs[c, b, p] - ref) <= 1e-12 * abs(ref)
+    # one polarisation: self-polar is the full-polar MAC
+    assert np.array_equal(orc.xengine_self(Y[:na], na, 1)[:, :, 0], orc.xengine(Y[:na], na, 1)[:, :, 0])
+    # the integer form equals the full integer MAC's pp entries
+    q = rng.integers(-127, 128, size=(na * npol, nf, nch, 2), dtype=np.int8)
+    Vi, _ = orc.xint(q, np.ones((na * npol, nch)), na, npol)
+    Vis = orc.xint_self(q, na, npol)
+    for p in range(npol):
+        assert np.array_equal(Vis[:, :, p], Vi[:, :, p * npol + p])
+
+
 # -------------------------------------------------------------- MAD (Eq. 3-4)
 
 def test_mad_flag_tiny_and_gaussian(orc):
