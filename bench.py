@@ -64,6 +64,8 @@ FORMS = {
               "H H^T in 128-frame FP32 chunks, H L^T + L H^T in a separate accumulator; FP32 accuracy bound",
     "i8": "per-channel scaled int8 requantisation, exact integer X-engine on tcgen05",
     "f16": "per-channel scaled FP16 requantisation, X-engine on tcgen05 with FP32 accumulation",
+    "fp32_self": "self-polar (total-intensity) mode of the plain FP32 form: products RR*, LL* only "
+                 "(528 baselines x 2 products), half the CUDA-core multiply-adds",
 }
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -747,8 +749,8 @@ def run_ours(args, world, rank, local_rank):
         for j in range(n):
             corr.corr_integrate_device(h, xt, n_avail=ld, g0=(g_start + j) * N_INT, stream=stream)
 
-    def timed(mode, k, w, sample_clocks=False):
-        corr.corr_set_mode(h, mode, 0, 1)
+    def timed(mode, k, w, sample_clocks=False, polmode=0):
+        corr.corr_set_mode(h, mode, polmode, 1)
         steps(w, mode, 0)
         torch.cuda.synchronize()
         corr.corr_set_timing(h, 1)
@@ -775,7 +777,8 @@ def run_ours(args, world, rank, local_rank):
         return ms, st / max(n, 1), clocks
 
     K, W = args.steps, args.warmup
-    all_forms = {"fp32": corr.CORR_FP32, "fp32tc": corr.CORR_FP32TC, "i8": corr.CORR_I8, "f16": corr.CORR_F16}
+    all_forms = {"fp32": corr.CORR_FP32, "fp32tc": corr.CORR_FP32TC, "i8": corr.CORR_I8, "f16": corr.CORR_F16,
+                 "fp32_self": corr.CORR_FP32}
     ms, st, clocks = timed(all_forms[args.xmode], K, W, sample_clocks=True)
     value = job_rate(world, K * step_samples(), ms * 1e-3)
     stage_names = ["phasor_setup", "fengine", "xengine", "beam_average"]
@@ -788,7 +791,7 @@ def run_ours(args, world, rank, local_rank):
         if name in runs:
             continue
         k2 = max(10, min(K, 100))
-        ms2, st2, _ = timed(m, k2, 3)
+        ms2, st2, _ = timed(m, k2, 3, polmode=corr.CORR_POL_SELF if name.endswith("_self") else 0)
         runs[name] = (ms2 / k2, st2)
     modes = {}
     for name, (step_ms, st2) in runs.items():
@@ -797,14 +800,26 @@ def run_ours(args, world, rank, local_rank):
         if "fp32" in runs and name != "fp32":
             d["xengine_speedup_vs_fp32"] = runs["fp32"][1][2] / st2[2]
             d["step_speedup_vs_fp32"] = runs["fp32"][0] / step_ms
-        if name != "fp32":
+        if name not in ("fp32", "fp32_self"):
             d["xengine_tensor_frac_of_sustained_peak"] = tensor_fraction(st2[2], pk, 3 if name == "fp32tc" else 1)
+        if name == "fp32_self":
+            # useful self-polar work: n_ant (n_ant + 1) / 2 baselines x 2 products, complex MAC (8 flop)
+            alg = 8.0 * N_CHAN * N_INT * N_BL * N_POL
+            d["xengine_useful_tflops"] = alg / (st2[2] * 1e-3) / 1e12
+            d["xengine_roofline"] = {"bound": "alu", "achieved": d["xengine_useful_tflops"],
+                                     "peak": fp32_peak_tflops(pk), "unit": "TFLOP/s",
+                                     "frac": d["xengine_useful_tflops"] / fp32_peak_tflops(pk)}
+            d["form"] = FORMS[name]
+            modes[name] = d
+            continue
         d["xengine_useful_tflops"] = useful_tflops(st2[2])
         bound, ach, peak, unit, _ = stage_roofline("xengine", name, st2[2], pk)
         d["xengine_roofline"] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak}
         d["form"] = FORMS[name]
         modes[name] = d
     corr.corr_set_mode(h, all_forms[args.xmode], 0, 1)
+    if "fp32_self" in modes and "fp32" in runs:
+        modes["fp32_self"]["xengine_speedup_vs_full_polar_fp32"] = runs["fp32"][1][2] / runs["fp32_self"][1][2]
 
     # the time-domain voltage blanker on an RFI-hit copy of the same samples
     blank = None if args.no_extras else run_blank_leg(corr, torch, s, xt, ld, coh, all_forms[args.xmode],

@@ -65,6 +65,7 @@ enum {
 };
 
 enum { CORR_FP32 = 0, CORR_I8 = 1, CORR_F16 = 2, CORR_FP32TC = 3 };  /* X-engine precision */
+enum { CORR_POL_FULL = 0, CORR_POL_SELF = 1 };                         /* polarisation products */
 
 /* Create a correlator for n_ant antennas x n_pol (1 or 2) polarisations
  * (n_in = n_ant * n_pol <= 128), an n_fft-point real FFT (power of two,
@@ -80,8 +81,14 @@ const char* corr_last_error(void);
 
 /* Precision mode, polarisation products and beam time averaging.
  * xmode: CORR_FP32 | CORR_I8 | CORR_F16 | CORR_FP32TC (the last three need
- * n_in <= 128; CORR_FP32TC is not available in batches).  polmode must be 0 (all n_pol^2
- * products are produced).  beam_avg >= 1 must divide n_int. */
+ * n_in <= 128; CORR_FP32TC is not available in batches).
+ * polmode (Sec. 2.3.2: self-polar and full-polar correlation): CORR_POL_FULL (0) produces
+ * all n_pol^2 products per baseline, RR*, RL*, LR*, LL*; CORR_POL_SELF (1) only the n_pol
+ * products RR*, LL* (total intensity; Sec. 2.1 sizes the MAC for these two), so the
+ * visibilities become [n_fft/2][n_bl][n_pol] -- half the multiply-adds on the CUDA-core
+ * X-engine (CORR_FP32); the tensor-core forms, bound by their operand read, compute the
+ * same Gram and write only the pp products.  Neither polmode nor beam_avg may change while
+ * an output ring is set (they size it).  beam_avg >= 1 must divide n_int. */
 int corr_set_mode(corr_t* h, int xmode, int polmode, int beam_avg);
 
 /* Largest integer delay (samples) the streaming ring supports; only before the
@@ -110,7 +117,9 @@ int corr_set_xengine_stage(corr_t* h, int ks);
 
 /* Requantisation scales s [n_in][n_fft/2] for CORR_I8 / CORR_F16.  NULL
  * derives them from the last completed integration's autocorrelations as
- * s = 127 / (4 sigma), sigma^2 = V_ii[k] / (2 n_int). */
+ * s = 127 / (4 sigma), sigma^2 = V_ii[k] / (2 n_int) -- one component's share of
+ * the power -- except at DC, sigma^2 = V_ii[0] / n_int: the DC bin of a real
+ * stream is real before the Eq. 2 rotation, so one component can carry it all. */
 int corr_set_scales(corr_t* h, const float* scale);
 
 /* Streaming ingest of host samples x [n_in][n] (planar int8, row i holds n

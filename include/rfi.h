@@ -41,6 +41,11 @@ int rfi_n_params(void);
 
 /* A network with buffers for batches of up to max_batch patches; parameters zero. */
 int rfi_create(rfi_net_t** out, int max_batch);
+/* The same network built with FP32 weights and activations (FP32 accumulation and gradients
+ * as in rfi_create, FP16 patches in): the build whose forward pass and gradients are checked
+ * against the FP64 oracle to 1e-5, which proves the kernels' arithmetic apart from FP16
+ * rounding.  Every other call works on it unchanged. */
+int rfi_create_fp32(rfi_net_t** out, int max_batch);
 int rfi_destroy(rfi_net_t* net);
 
 /* Host FP32 parameter vector in / out (set also resets the Adam moments). */

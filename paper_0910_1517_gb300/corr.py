@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgb300corr.so")
 
 CORR_FP32, CORR_I8, CORR_F16, CORR_FP32TC = 0, 1, 2, 3
+CORR_POL_FULL, CORR_POL_SELF = 0, 1
 CODES = {0: "CORR_OK", -1: "CORR_E_INVAL", -2: "CORR_E_RANGE", -3: "CORR_E_AGAIN", -4: "CORR_E_DATALOSS",
          -5: "CORR_E_CUDA", -6: "CORR_E_NOMEM", -7: "CORR_E_STATE", -8: "CORR_E_TIMEOUT"}
 
@@ -72,6 +73,7 @@ SIGNATURES = {
     # include/rfi.h
     "rfi_n_params": ([], _I),
     "rfi_create": ([ctypes.POINTER(ctypes.c_void_p), _I], _I),
+    "rfi_create_fp32": ([ctypes.POINTER(ctypes.c_void_p), _I], _I),
     "rfi_destroy": ([_P], _I),
     "rfi_set_params": ([_P, _P], _I),
     "rfi_get_params": ([_P, _P], _I),
@@ -371,6 +373,12 @@ def rfi_n_params() -> int:
 def rfi_create(max_batch: int):
     n = ctypes.c_void_p()
     _ok(load().rfi_create(ctypes.byref(n), max_batch))
+    return n
+
+
+def rfi_create_fp32(max_batch: int):
+    n = ctypes.c_void_p()
+    _ok(load().rfi_create_fp32(ctypes.byref(n), max_batch))
     return n
 
 

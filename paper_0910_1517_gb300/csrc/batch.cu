@@ -140,6 +140,7 @@ int capture(corr_batch* b) {
             xp.err = h->d_err;
             xp.vis_part = h->d_vis_part;
             xp.max_split = corr::kVisSplit;
+            xp.self = h->polmode == CORR_POL_SELF ? 1 : 0;
             ok = launch_xengine_fp32(xp, b->n_sm, s) == cudaSuccess;
         }
     }

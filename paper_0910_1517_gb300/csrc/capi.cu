@@ -203,6 +203,7 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
     xp.exact = h->xmode == CORR_I8 ? 1 : 0;
     xp.vis_part = h->d_vis_part;
     xp.max_split = corr::kVisSplit;
+    xp.self = h->polmode == CORR_POL_SELF ? 1 : 0;
     if (h->xmode == CORR_FP32)
         CU(launch_xengine_fp32(xp, h->n_sm, s));
     else
@@ -237,6 +238,7 @@ gbx::XtSub gbx::xt_sub_of(const corr* h) {
     x.vis = h->d_vis;
     x.vis_int = h->xmode == CORR_I8 ? h->d_vis_int : nullptr;
     x.exact = h->xmode == CORR_I8 ? 1 : 0;
+    x.self = h->polmode == CORR_POL_SELF ? 1 : 0;
     if (h->xmode == CORR_FP32TC) {
         const int max_ks = std::min(xengine_tc_ks_fp32(h->n_in), kSplitChunk);
         x.ks = h->ks > 0 ? std::min(h->ks, max_ks) : max_ks;
@@ -563,7 +565,10 @@ int corr_set_mode(corr_t* h, int xmode, int polmode, int beam_avg) {
         return fail(CORR_E_INVAL, "unknown xmode");
     if (xmode == CORR_FP32TC && h->batch_refs > 0)
         return fail(CORR_E_STATE, "CORR_FP32TC is not available to batch members");
-    if (polmode != 0) return fail(CORR_E_INVAL, "only polmode 0 (all products) is supported");
+    if (polmode != CORR_POL_FULL && polmode != CORR_POL_SELF)
+        return fail(CORR_E_INVAL, "polmode must be CORR_POL_FULL or CORR_POL_SELF");
+    if (h->out_vis && polmode != h->polmode)
+        return fail(CORR_E_STATE, "polmode sizes the output ring and its buffers: remove the ring first");
     if (beam_avg < 1 || h->n_int % beam_avg) return fail(CORR_E_INVAL, "beam_avg must divide n_int");
     if (h->out_vis && beam_avg != h->beam_avg)
         return fail(CORR_E_STATE, "beam_avg sizes the output ring and its buffers: remove the ring first");
@@ -578,13 +583,15 @@ int corr_set_mode(corr_t* h, int xmode, int polmode, int beam_avg) {
         h->d_beams = h->d_beams_raw;
         if (beam_avg > 1) CU(dalloc(&h->d_beams, 2 * static_cast<size_t>(h->n_int / beam_avg) * h->n_chan));
     }
-    const bool changed = h->xmode != xmode;
-    if (changed && xmode == CORR_FP32) {   // the FP32 layout's padding rows must read as zero again
+    const bool changed = h->xmode != xmode || h->polmode != polmode;
+    if (h->xmode != xmode && xmode == CORR_FP32) {   // the FP32 layout's padding rows must read as zero again
         const size_t spec_bytes = static_cast<size_t>(h->n_chan) * h->n_int * rows_fp32(h->n_in) * sizeof(float);
         CU(cudaMemset(h->d_spec, 0, spec_bytes));
     }
     h->xmode = xmode;
     h->beam_avg = beam_avg;
+    h->polmode = polmode;
+    h->npp = polmode == CORR_POL_SELF ? h->n_pol : h->n_pol * h->n_pol;
     return changed ? upload_xtab(h) : CORR_OK;
 }
 
@@ -647,8 +654,12 @@ int corr_set_scales(corr_t* h, const float* scale) {
             const int a = i / h->n_pol, p = i % h->n_pol;
             const int bl = a * h->n_ant - a * (a - 1) / 2;
             for (int k = 0; k < h->n_chan; ++k) {
-                const double auto_p = v[(static_cast<size_t>(k) * h->n_bl + bl) * h->npp + p * h->n_pol + p].x;
-                const double sigma = std::sqrt(std::max(auto_p, 0.0) / (2.0 * h->n_int));
+                const double auto_p =
+                    v[(static_cast<size_t>(k) * h->n_bl + bl) * h->npp + vis_prod(h->polmode == CORR_POL_SELF, h->n_pol, p, p)].x;
+                // sigma of one component: half the channel's power for the circular statistics of
+                // k > 0; at DC the spectrum of a real stream is real before the Eq. 2 rotation, so a
+                // frame's whole power can sit in one component -- take the full power there
+                const double sigma = std::sqrt(std::max(auto_p, 0.0) / ((k == 0 ? 1.0 : 2.0) * h->n_int));
                 s[static_cast<size_t>(i) * h->n_chan + k] = sigma > 0 ? static_cast<float>(127.0 / (4.0 * sigma)) : 1.0f;
             }
         }

@@ -2,7 +2,9 @@
 // flags (Sec. 5, Eq. 3-4), and a small convolutional flagger trained and run by
 // hand-written kernels (direct 3x3 convolutions over 16x16 output tiles, FP16
 // weights and activations, FP32 accumulation, FP32 gradients, Adam on FP32
-// master weights).
+// master weights).  Every network kernel is templated on the type TA its weights
+// and activations are kept in: __half for the flagger, float for the FP32 build
+// (rfi_create_fp32) that checks the kernels' arithmetic against the FP64 oracle.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -21,6 +23,11 @@ void set_last_error(const char* msg);
 
 namespace {
 
+__device__ __forceinline__ float ldf(const __half* p) { return __half2float(*p); }
+__device__ __forceinline__ float ldf(const float* p) { return *p; }
+__device__ __forceinline__ void stf(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void stf(float* p, float v) { *p = v; }
+
 constexpr int PH = 64, PW = 64, PHW = PH * PW;   // patch: 64 dumps x 64 channels
 constexpr int T = 16, TH = T + 2;                 // output tile and tile with halo
 constexpr int kTiles = (PH / T) * (PW / T);       // 16 tiles per patch
@@ -32,9 +39,10 @@ constexpr int OW1 = 0, OB1 = 144, OW2 = 160, OB2 = 4768, OW3 = 4800, OB3 = 9408,
 // MODE 0 (forward):       out[o] = relu(b[o] + sum_c sum_tap w[c][tap][o] in[c][pixel + tap])   (fp16 -> fp16)
 // MODE 1 (backward data): the same correlation without bias / ReLU on dZ = dA * (act > 0)        (fp32 -> fp32)
 // w is laid out [CI][9][CO] so that one (c, tap) reads CO consecutive weights (a broadcast).
-template <int CI, int CO, int MODE>
-__global__ void __launch_bounds__(256) conv3x3_kernel(const void* __restrict__ in, const __half* __restrict__ act,
-                                                      const __half* __restrict__ w, const __half* __restrict__ bias,
+// TIN: type of the forward input (the FP16 patches for layer 1, TA after it); TA: weights and activations.
+template <int CI, int CO, int MODE, typename TIN, typename TA>
+__global__ void __launch_bounds__(256) conv3x3_kernel(const void* __restrict__ in, const TA* __restrict__ act,
+                                                      const TA* __restrict__ w, const TA* __restrict__ bias,
                                                       void* __restrict__ out) {
     extern __shared__ __align__(16) float sm[];
     float* wsm = sm;                                   // CI * 9 * CO
@@ -42,7 +50,7 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(const void* __restrict__ i
     const int b = blockIdx.x / kTiles, tl = blockIdx.x % kTiles;
     const int ty0 = (tl / (PW / T)) * T, tx0 = (tl % (PW / T)) * T;
     const int tid = threadIdx.x, py = tid / T, px = tid % T;
-    for (int q = tid; q < CI * 9 * CO; q += 256) wsm[q] = __half2float(w[q]);
+    for (int q = tid; q < CI * 9 * CO; q += 256) wsm[q] = ldf(w + q);
     for (int q = tid; q < CI * TH * TH; q += 256) {
         const int c = q / (TH * TH), r = q % (TH * TH), yy = r / TH, xx = r % TH;
         const int gy = ty0 + yy - 1, gx = tx0 + xx - 1;
@@ -50,10 +58,10 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(const void* __restrict__ i
         if (gy >= 0 && gy < PH && gx >= 0 && gx < PW) {
             const size_t gi = (static_cast<size_t>(b) * CI + c) * PHW + gy * PW + gx;
             if constexpr (MODE == 0) {
-                v = __half2float(static_cast<const __half*>(in)[gi]);
+                v = ldf(static_cast<const TIN*>(in) + gi);
             } else {
                 v = static_cast<const float*>(in)[gi];
-                if (!(__half2float(act[gi]) > 0.0f)) v = 0.0f;    // ReLU gradient
+                if (!(ldf(act + gi) > 0.0f)) v = 0.0f;             // ReLU gradient
             }
         }
         tile[q] = v;
@@ -61,7 +69,7 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(const void* __restrict__ i
     __syncthreads();
     float acc[CO];
 #pragma unroll
-    for (int o = 0; o < CO; ++o) acc[o] = (MODE == 0) ? __half2float(bias[o]) : 0.0f;
+    for (int o = 0; o < CO; ++o) acc[o] = (MODE == 0) ? ldf(bias + o) : 0.0f;
     for (int c = 0; c < CI; ++c) {
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
@@ -81,13 +89,13 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(const void* __restrict__ i
 #pragma unroll
     for (int o = 0; o < CO; ++o) {
         if constexpr (MODE == 0)
-            static_cast<__half*>(out)[base + static_cast<size_t>(o) * PHW] = __float2half_rn(fmaxf(acc[o], 0.0f));
+            stf(static_cast<TA*>(out) + base + static_cast<size_t>(o) * PHW, fmaxf(acc[o], 0.0f));
         else
             static_cast<float*>(out)[base + static_cast<size_t>(o) * PHW] = acc[o];
     }
 }
 
-template <int CI, int CO, int MODE>
+template <int CI, int CO>
 size_t conv_smem() {
     return sizeof(float) * (CI * 9 * CO + CI * TH * TH);
 }
@@ -96,9 +104,9 @@ size_t conv_smem() {
 // dW[o][c][tap] += sum_pixels dZ[o][p] A[c][p + tap],  db[o] += sum_pixels dZ[o][p],
 // dZ = dA * (act > 0).  A CTA loops over tiles; each thread owns one input channel c,
 // NO output channels and a pixel subset, and adds its partial sums atomically at the end.
-template <int CI, int CO>
-__global__ void __launch_bounds__(256) wgrad_kernel(const __half* __restrict__ A, const float* __restrict__ dA,
-                                                    const __half* __restrict__ act, float* __restrict__ dW,
+template <int CI, int CO, typename TIN, typename TA>
+__global__ void __launch_bounds__(256) wgrad_kernel(const TIN* __restrict__ A, const float* __restrict__ dA,
+                                                    const TA* __restrict__ act, float* __restrict__ dW,
                                                     float* __restrict__ db, int n_tiles) {
     constexpr int PAIRS = CI * CO;
     constexpr int G = PAIRS >= 256 ? 1 : 256 / PAIRS;          // pixel groups
@@ -136,13 +144,13 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const __half* __restrict__ A
             const int gy = ty0 + yy - 1, gx = tx0 + xx - 1;
             float v = 0.0f;
             if (gy >= 0 && gy < PH && gx >= 0 && gx < PW)
-                v = __half2float(A[(static_cast<size_t>(b) * CI + cc) * PHW + gy * PW + gx]);
+                v = ldf(A + (static_cast<size_t>(b) * CI + cc) * PHW + gy * PW + gx);
             at[q] = v;
         }
         for (int q = tid; q < CO * T * T; q += 256) {
             const int oo = q / (T * T), r = q % (T * T);
             const size_t gi = (static_cast<size_t>(b) * CO + oo) * PHW + (ty0 + r / T) * PW + tx0 + r % T;
-            dz[q] = __half2float(act[gi]) > 0.0f ? dA[gi] : 0.0f;
+            dz[q] = ldf(act + gi) > 0.0f ? dA[gi] : 0.0f;
         }
         __syncthreads();
         for (int p = g; p < T * T; p += G) {
@@ -176,8 +184,9 @@ size_t wgrad_smem() {
 // ------------------------------------------------------------------- head
 // logit = b4 + sum_c W4[c] A3[c][p].  Training: loss += BCE, dlogit = (sigmoid - m) / N,
 // dA3[c][p] = W4[c] dlogit, dW4[c] += dlogit A3[c][p], db4 += dlogit.  Inference: prob.
-__global__ void __launch_bounds__(256) head_kernel(const __half* __restrict__ A3, const uint8_t* __restrict__ mask,
-                                                   const __half* __restrict__ pf16, int B, float inv_n,
+template <typename TA>
+__global__ void __launch_bounds__(256) head_kernel(const TA* __restrict__ A3, const uint8_t* __restrict__ mask,
+                                                   const TA* __restrict__ pf16, int B, float inv_n,
                                                    float* __restrict__ dA3, float* __restrict__ grad,
                                                    float* __restrict__ loss, float* __restrict__ prob) {
     __shared__ float red[8][18];
@@ -188,11 +197,11 @@ __global__ void __launch_bounds__(256) head_kernel(const __half* __restrict__ A3
     if (q < static_cast<int64_t>(B) * PHW) {
         const int64_t b = q / PHW, p = q % PHW;
         float a[16];
-        float s = __half2float(pf16[OB4]);
+        float s = ldf(pf16 + OB4);
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-            a[c] = __half2float(A3[(b * 16 + c) * PHW + p]);
-            s = fmaf(__half2float(pf16[OW4 + c]), a[c], s);
+            a[c] = ldf(A3 + (b * 16 + c) * PHW + p);
+            s = fmaf(ldf(pf16 + OW4 + c), a[c], s);
         }
         const float pr = 1.0f / (1.0f + expf(-s));
         if (prob) prob[q] = pr;
@@ -204,7 +213,7 @@ __global__ void __launch_bounds__(256) head_kernel(const __half* __restrict__ A3
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
                 part[c] = ds * a[c];
-                dA3[(b * 16 + c) * PHW + p] = ds * __half2float(pf16[OW4 + c]);
+                dA3[(b * 16 + c) * PHW + p] = ds * ldf(pf16 + OW4 + c);
             }
         }
     }
@@ -228,20 +237,24 @@ __global__ void __launch_bounds__(256) head_kernel(const __half* __restrict__ A3
 }
 
 // ------------------------------------------------------- optimiser / weights
-// fp16 copies of every parameter and the transposed / flipped layouts the convolutions read.
+// TA copies of every parameter (rounded once from the FP32 masters) and the transposed /
+// flipped layouts the convolutions read.
+template <typename TA>
 struct Wts {
-    __half* pf16;               // [NPAR] flat
-    __half *wf1, *wf2, *wf3;    // forward  [CI][9][CO]
-    __half *wb3, *wb2;          // backward [CO_fwd][9][CI_fwd], taps flipped
+    TA* pf16;                   // [NPAR] flat
+    TA *wf1, *wf2, *wf3;        // forward  [CI][9][CO]
+    TA *wb3, *wb2;              // backward [CO_fwd][9][CI_fwd], taps flipped
 };
 
-__global__ void transform_kernel(const float* __restrict__ p, Wts w) {
+template <typename TA>
+__global__ void transform_kernel(const float* __restrict__ p, Wts<TA> w) {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < NPAR; q += gridDim.x * blockDim.x) {
-        const __half h = __float2half_rn(p[q]);
+        TA h;
+        stf(&h, p[q]);
         w.pf16[q] = h;
         int o, c, tap, ci, co;
-        __half* fwd = nullptr;
-        __half* bwd = nullptr;
+        TA* fwd = nullptr;
+        TA* bwd = nullptr;
         int off;
         if (q < OB1) {
             off = q - OW1; ci = 1; co = 16; fwd = w.wf1;
@@ -339,9 +352,10 @@ __global__ void __launch_bounds__(1024) patch_kernel(const float* __restrict__ P
 struct rfi_net {
     int max_batch = 0;
     int step = 0;
+    int fp32 = 0;                        // weights and activations in FP32 (rfi_create_fp32), else FP16
     float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr, *loss = nullptr;
-    Wts w{};
-    __half *A1 = nullptr, *A2 = nullptr, *A3 = nullptr;
+    void* w[6] = {};                     // Wts<TA>: pf16, wf1, wf2, wf3, wb3, wb2
+    void *A1 = nullptr, *A2 = nullptr, *A3 = nullptr;   // TA activations
     float *dA1 = nullptr, *dA2 = nullptr, *dA3 = nullptr;
     int n_sm = 0;
 };
@@ -361,56 +375,97 @@ int rfail(int code, const char* what, cudaError_t e = cudaSuccess) {
         if (e_ != cudaSuccess) return rfail(CORR_E_CUDA, #call, e_);  \
     } while (0)
 
-template <int CI, int CO, int MODE>
-cudaError_t conv(const void* in, const __half* act, const __half* w, const __half* bias, void* out, int B,
-                 cudaStream_t s) {
-    const size_t smem = conv_smem<CI, CO, MODE>();
-    cudaError_t e = cudaFuncSetAttribute(conv3x3_kernel<CI, CO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+template <typename TA>
+Wts<TA> wts(rfi_net* n) {
+    Wts<TA> w;
+    w.pf16 = static_cast<TA*>(n->w[0]);
+    w.wf1 = static_cast<TA*>(n->w[1]);
+    w.wf2 = static_cast<TA*>(n->w[2]);
+    w.wf3 = static_cast<TA*>(n->w[3]);
+    w.wb3 = static_cast<TA*>(n->w[4]);
+    w.wb2 = static_cast<TA*>(n->w[5]);
+    return w;
+}
+
+template <int CI, int CO, int MODE, typename TIN, typename TA>
+cudaError_t conv(const void* in, const TA* act, const TA* w, const TA* bias, void* out, int B, cudaStream_t s) {
+    const size_t smem = conv_smem<CI, CO>();
+    auto kern = conv3x3_kernel<CI, CO, MODE, TIN, TA>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    conv3x3_kernel<CI, CO, MODE><<<B * kTiles, 256, smem, s>>>(in, act, w, bias, out);
+    kern<<<B * kTiles, 256, smem, s>>>(in, act, w, bias, out);
     return cudaGetLastError();
 }
 
-template <int CI, int CO>
-cudaError_t wgrad(const __half* A, const float* dA, const __half* act, float* dW, float* db, int B, int n_sm,
+template <int CI, int CO, typename TIN, typename TA>
+cudaError_t wgrad(const TIN* A, const float* dA, const TA* act, float* dW, float* db, int B, int n_sm,
                   cudaStream_t s) {
     const size_t smem = wgrad_smem<CI, CO>();
-    cudaError_t e = cudaFuncSetAttribute(wgrad_kernel<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    auto kern = wgrad_kernel<CI, CO, TIN, TA>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const int n_tiles = B * kTiles;
     const int grid = std::max(1, std::min(n_tiles, 4 * n_sm));
-    wgrad_kernel<CI, CO><<<grid, 256, smem, s>>>(A, dA, act, dW, db, n_tiles);
+    kern<<<grid, 256, smem, s>>>(A, dA, act, dW, db, n_tiles);
     return cudaGetLastError();
 }
 
-int forward(rfi_net* n, const uint16_t* x, int B, cudaStream_t s) {
-    const __half* xh = reinterpret_cast<const __half*>(x);
-    RCU((conv<1, 16, 0>(xh, nullptr, n->w.wf1, n->w.pf16 + OB1, n->A1, B, s)));
-    RCU((conv<16, 32, 0>(n->A1, nullptr, n->w.wf2, n->w.pf16 + OB2, n->A2, B, s)));
-    RCU((conv<32, 16, 0>(n->A2, nullptr, n->w.wf3, n->w.pf16 + OB3, n->A3, B, s)));
+template <typename TA>
+int forward_t(rfi_net* n, const uint16_t* x, int B, cudaStream_t s) {
+    const Wts<TA> w = wts<TA>(n);
+    TA *A1 = static_cast<TA*>(n->A1), *A2 = static_cast<TA*>(n->A2), *A3 = static_cast<TA*>(n->A3);
+    RCU((conv<1, 16, 0, __half, TA>(x, nullptr, w.wf1, w.pf16 + OB1, A1, B, s)));
+    RCU((conv<16, 32, 0, TA, TA>(A1, nullptr, w.wf2, w.pf16 + OB2, A2, B, s)));
+    RCU((conv<32, 16, 0, TA, TA>(A2, nullptr, w.wf3, w.pf16 + OB3, A3, B, s)));
     return CORR_OK;
+}
+
+template <typename TA>
+int forward_backward_t(rfi_net* n, const uint16_t* x, const uint8_t* mask, int B, cudaStream_t s) {
+    RCU(cudaMemsetAsync(n->g, 0, sizeof(float) * NPAR, s));
+    RCU(cudaMemsetAsync(n->loss, 0, sizeof(float), s));
+    if (int rc = forward_t<TA>(n, x, B, s)) return rc;
+    const Wts<TA> w = wts<TA>(n);
+    TA *A1 = static_cast<TA*>(n->A1), *A2 = static_cast<TA*>(n->A2), *A3 = static_cast<TA*>(n->A3);
+    const int64_t npx = static_cast<int64_t>(B) * PHW;
+    head_kernel<TA><<<static_cast<int>((npx + 255) / 256), 256, 0, s>>>(A3, mask, w.pf16, B, 1.0f / npx, n->dA3,
+                                                                         n->g, n->loss, nullptr);
+    RCU(cudaGetLastError());
+    RCU((wgrad<32, 16, TA, TA>(A2, n->dA3, A3, n->g + OW3, n->g + OB3, B, n->n_sm, s)));
+    RCU((conv<16, 32, 1, TA, TA>(n->dA3, A3, w.wb3, nullptr, n->dA2, B, s)));
+    RCU((wgrad<16, 32, TA, TA>(A1, n->dA2, A2, n->g + OW2, n->g + OB2, B, n->n_sm, s)));
+    RCU((conv<32, 16, 1, TA, TA>(n->dA2, A2, w.wb2, nullptr, n->dA1, B, s)));
+    RCU((wgrad<1, 16, __half, TA>(reinterpret_cast<const __half*>(x), n->dA1, A1, n->g + OW1, n->g + OB1, B,
+                                  n->n_sm, s)));
+    return CORR_OK;
+}
+
+int forward(rfi_net* n, const uint16_t* x, int B, cudaStream_t s) {
+    return n->fp32 ? forward_t<float>(n, x, B, s) : forward_t<__half>(n, x, B, s);
 }
 
 int forward_backward(rfi_net* n, const uint16_t* x, const uint8_t* mask, int B, cudaStream_t s) {
-    RCU(cudaMemsetAsync(n->g, 0, sizeof(float) * NPAR, s));
-    RCU(cudaMemsetAsync(n->loss, 0, sizeof(float), s));
-    if (int rc = forward(n, x, B, s)) return rc;
-    const int64_t npx = static_cast<int64_t>(B) * PHW;
-    head_kernel<<<static_cast<int>((npx + 255) / 256), 256, 0, s>>>(n->A3, mask, n->w.pf16, B, 1.0f / npx, n->dA3,
-                                                                     n->g, n->loss, nullptr);
-    RCU(cudaGetLastError());
-    RCU((wgrad<32, 16>(n->A2, n->dA3, n->A3, n->g + OW3, n->g + OB3, B, n->n_sm, s)));
-    RCU((conv<16, 32, 1>(n->dA3, n->A3, n->w.wb3, nullptr, n->dA2, B, s)));
-    RCU((wgrad<16, 32>(n->A1, n->dA2, n->A2, n->g + OW2, n->g + OB2, B, n->n_sm, s)));
-    RCU((conv<32, 16, 1>(n->dA2, n->A2, n->w.wb2, nullptr, n->dA1, B, s)));
-    RCU((wgrad<1, 16>(reinterpret_cast<const __half*>(x), n->dA1, n->A1, n->g + OW1, n->g + OB1, B, n->n_sm, s)));
-    return CORR_OK;
+    return n->fp32 ? forward_backward_t<float>(n, x, mask, B, s) : forward_backward_t<__half>(n, x, mask, B, s);
 }
 
 int transform(rfi_net* n, cudaStream_t s) {
-    transform_kernel<<<(NPAR + 255) / 256, 256, 0, s>>>(n->p, n->w);
+    if (n->fp32)
+        transform_kernel<float><<<(NPAR + 255) / 256, 256, 0, s>>>(n->p, wts<float>(n));
+    else
+        transform_kernel<__half><<<(NPAR + 255) / 256, 256, 0, s>>>(n->p, wts<__half>(n));
+    RCU(cudaGetLastError());
+    return CORR_OK;
+}
+
+int head_infer(rfi_net* n, int B, float* prob, cudaStream_t s) {
+    const int64_t npx = static_cast<int64_t>(B) * PHW;
+    const int grid = static_cast<int>((npx + 255) / 256);
+    if (n->fp32)
+        head_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float*>(n->A3), nullptr, wts<float>(n).pf16, B, 0.0f,
+                                                nullptr, nullptr, nullptr, prob);
+    else
+        head_kernel<__half><<<grid, 256, 0, s>>>(static_cast<const __half*>(n->A3), nullptr, wts<__half>(n).pf16, B,
+                                                 0.0f, nullptr, nullptr, nullptr, prob);
     RCU(cudaGetLastError());
     return CORR_OK;
 }
@@ -421,17 +476,12 @@ int check_batch(rfi_net* n, const void* x, int B) {
     return CORR_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int rfi_n_params(void) { return NPAR; }
-
-int rfi_create(rfi_net_t** out, int max_batch) {
+int create(rfi_net_t** out, int max_batch, int fp32) {
     if (!out || max_batch < 1) return rfail(CORR_E_INVAL, "rfi_create: bad arguments");
     *out = nullptr;
     rfi_net* n = new rfi_net();
     n->max_batch = max_batch;
+    n->fp32 = fp32;
     auto bail = [&](cudaError_t e) {
         rfi_destroy(n);
         return rfail(CORR_E_NOMEM, "rfi_create: allocation", e);
@@ -440,20 +490,18 @@ int rfi_create(rfi_net_t** out, int max_batch) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n->n_sm, cudaDevAttrMultiProcessorCount, dev);
     const size_t px = static_cast<size_t>(max_batch) * PHW;
+    const size_t ta = fp32 ? sizeof(float) : sizeof(__half);
     void** f32[] = {reinterpret_cast<void**>(&n->p), reinterpret_cast<void**>(&n->m), reinterpret_cast<void**>(&n->v),
                     reinterpret_cast<void**>(&n->g)};
     for (void** q : f32)
         if (e == cudaSuccess) e = cudaMalloc(q, sizeof(float) * NPAR);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->loss), sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->w.pf16), sizeof(__half) * NPAR);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->w.wf1), sizeof(__half) * 144);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->w.wf2), sizeof(__half) * 4608);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->w.wf3), sizeof(__half) * 4608);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->w.wb2), sizeof(__half) * 4608);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->w.wb3), sizeof(__half) * 4608);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->A1), sizeof(__half) * px * 16);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->A2), sizeof(__half) * px * 32);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->A3), sizeof(__half) * px * 16);
+    const size_t wn[6] = {NPAR, 144, 4608, 4608, 4608, 4608};
+    for (int q = 0; q < 6; ++q)
+        if (e == cudaSuccess) e = cudaMalloc(&n->w[q], ta * wn[q]);
+    if (e == cudaSuccess) e = cudaMalloc(&n->A1, ta * px * 16);
+    if (e == cudaSuccess) e = cudaMalloc(&n->A2, ta * px * 32);
+    if (e == cudaSuccess) e = cudaMalloc(&n->A3, ta * px * 16);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->dA1), sizeof(float) * px * 16);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->dA2), sizeof(float) * px * 32);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->dA3), sizeof(float) * px * 16);
@@ -466,10 +514,20 @@ int rfi_create(rfi_net_t** out, int max_batch) {
     return CORR_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int rfi_n_params(void) { return NPAR; }
+
+int rfi_create(rfi_net_t** out, int max_batch) { return create(out, max_batch, 0); }
+
+int rfi_create_fp32(rfi_net_t** out, int max_batch) { return create(out, max_batch, 1); }
+
 int rfi_destroy(rfi_net_t* n) {
     if (!n) return CORR_OK;
-    void* bufs[] = {n->p, n->m, n->v, n->g, n->loss, n->w.pf16, n->w.wf1, n->w.wf2, n->w.wf3, n->w.wb2,
-                    n->w.wb3, n->A1, n->A2, n->A3, n->dA1, n->dA2, n->dA3};
+    void* bufs[] = {n->p, n->m, n->v, n->g, n->loss, n->w[0], n->w[1], n->w[2], n->w[3], n->w[4],
+                    n->w[5], n->A1, n->A2, n->A3, n->dA1, n->dA2, n->dA3};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete n;
@@ -533,11 +591,7 @@ int rfi_infer(rfi_net_t* n, const uint16_t* x, int B, float* prob, void* stream)
     if (!prob) return rfail(CORR_E_INVAL, "rfi_infer: prob is null");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (int rc = forward(n, x, B, s)) return rc;
-    const int64_t npx = static_cast<int64_t>(B) * PHW;
-    head_kernel<<<static_cast<int>((npx + 255) / 256), 256, 0, s>>>(n->A3, nullptr, n->w.pf16, B, 0.0f, nullptr,
-                                                                     nullptr, nullptr, prob);
-    RCU(cudaGetLastError());
-    return CORR_OK;
+    return head_infer(n, B, prob, s);
 }
 
 int rfi_patches(const float* power, int n_in, int n_dump, int n_chan, float M, uint16_t* x, uint8_t* mad_flags,

@@ -17,7 +17,12 @@ struct XParams {
     int exact;             // tensor-core engine: 1 = int8-valued operands, integer flush
     float2* vis_part;      // CUDA-core engine: room for max_split partial visibility sets, or nullptr
     int max_split;
+    int self;              // 1: self-polar (total-intensity) mode, only products pp, vis [n_chan][n_bl][n_pol]
 };
+
+// Index of product (p, q) within a baseline's products: full-polar p n_pol + q (RR*, RL*, LR*, LL*),
+// self-polar p (RR*, LL*; only p = q exists)
+__host__ __device__ constexpr int vis_prod(int self, int n_pol, int p, int q) { return self ? p : p * n_pol + q; }
 
 // Plain FP32 X-engine on CUDA cores: register-tiled upper-triangular complex MAC.
 cudaError_t launch_xengine_fp32(const XParams& p, int n_sm, cudaStream_t s);
@@ -43,6 +48,7 @@ struct XtSub {
     const float* spec32;
     float split_scale, descale;
     int chunk;             // frames per TMEM accumulation chunk: power of two, multiple of ks
+    int self;              // self-polar mode: only products pp are written, vis [n_chan][n_bl][n_pol]
 };
 struct XtBatch {          // (the FP32 form, spec32 set, runs alone: launch with fp32_in)
     int n_sub;

@@ -9,7 +9,9 @@
 // memory as the F-engine's FP32 K-blocks (TB frames x Rp rows in 16-byte granules)
 // by TMA-engine bulk copies into a ring of stages.  Sums are kept per 256-frame
 // chunk and added into running sums in shared memory, which bounds the rounding
-// error of long integrations.
+// error of long integrations.  In the self-polar (total-intensity) mode with two
+// polarisations the tiles are 4x4 antenna blocks of one polarisation (products RR*
+// or LL* only): half the tiles, half the multiply-adds (Sec. 2.1 sizes the MAC so).
 #include "common.cuh"
 #include "fengine.cuh"
 #include "xengine.cuh"
@@ -33,7 +35,8 @@ __device__ __forceinline__ void decode_tri(int idx, int nb, int& I, int& J) {
 
 // TB: frames per K-block of the FP32 layout (4 or 8); a K-block is TB/4 slices of 4 frames,
 // each slice one 16-byte granule per row
-template <int MAXT, int TB>
+// SELF: self-polar mode with n_pol = 2 (tiles of one polarisation's antennas)
+template <int MAXT, int TB, bool SELF>
 __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p, int n_split) {
     constexpr int TQ = TB / 4, KBS = kStageFrames / TB;   // slices per K-block, K-blocks per stage
     extern __shared__ __align__(128) unsigned char smem[];
@@ -42,12 +45,21 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p, int
     const int R = rows_fp32(p.n_in);             // rows per K-block, a multiple of 8
     const int stage_bytes = kStageFrames * R * 4;
     float* part = reinterpret_cast<float*>(smem + kStages * stage_bytes);   // [32][blockDim] chunk sums
-    const int nb = (p.n_in + 3) / 4;
-    const int n_work = nb * (nb + 1) / 2;
+    // full: 4x4 blocks of inputs; self: 4x4 blocks of antennas of polarisation pol
+    const int nb = SELF ? (p.n_ant + 3) / 4 : (p.n_in + 3) / 4;
+    const int n_tri = nb * (nb + 1) / 2;
+    const int n_work = SELF ? 2 * n_tri : n_tri;
     const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
     const bool active = tid < n_work;
     int I = 0, J = 0;
-    if (active) decode_tri(tid, nb, I, J);
+    const int pol = SELF && tid >= n_tri ? 1 : 0;
+    if (active) decode_tri(tid - pol * n_tri, nb, I, J);
+    // self: antenna 4I + ii of polarisation pol is input 8I + 2 ii + pol: row group 2I + (ii >> 1),
+    // position 2 (ii & 1) + pol in it; groups past the last row (antennas beyond n_ant, never
+    // written out) read group 0 instead of running off the K-block
+    const int n_grp = R / 8;
+    const int gi0 = SELF ? min(2 * I, n_grp - 1) : I, gi1 = SELF ? min(2 * I + 1, n_grp - 1) : I;
+    const int gj0 = SELF ? min(2 * J, n_grp - 1) : J, gj1 = SELF ? min(2 * J + 1, n_grp - 1) : J;
     const int ntb = p.n_int / TB;
     const int nkb_u = ntb / n_split;                                 // K-blocks per work unit
     const int n_stage_ch = (nkb_u + KBS - 1) / KBS;                  // stages per unit
@@ -113,19 +125,37 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p, int
                 // G at position g ^ (G & 7), so a warp's loads of one granule spread over the banks
                 const int h = sl % TQ;
                 const float4* blk = st + (sl / TQ) * R * TQ;
-                const float4* li = blk + 8 * TQ * I;
-                const float4* lj = blk + 8 * TQ * J;
-                const int si = I & 7, sj = J & 7;
                 float4 ar[4], ai[4];
+                if constexpr (!SELF) {
+                    const float4* li = blk + 8 * TQ * I;
+                    const int si = I & 7;
 #pragma unroll
-                for (int ii = 0; ii < 4; ++ii) {
-                    ar[ii] = li[(2 * ii * TQ + h) ^ si];
-                    ai[ii] = li[((2 * ii + 1) * TQ + h) ^ si];
+                    for (int ii = 0; ii < 4; ++ii) {
+                        ar[ii] = li[(2 * ii * TQ + h) ^ si];
+                        ai[ii] = li[((2 * ii + 1) * TQ + h) ^ si];
+                    }
+                } else {
+#pragma unroll
+                    for (int ii = 0; ii < 4; ++ii) {
+                        const int G = (ii >> 1) ? gi1 : gi0, pos = 2 * (ii & 1) + pol;
+                        const float4* li = blk + 8 * TQ * G;
+                        ar[ii] = li[(2 * pos * TQ + h) ^ (G & 7)];
+                        ai[ii] = li[((2 * pos + 1) * TQ + h) ^ (G & 7)];
+                    }
                 }
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) {
-                    const float4 br = lj[(2 * jj * TQ + h) ^ sj];
-                    const float4 bi = lj[((2 * jj + 1) * TQ + h) ^ sj];
+                    float4 br, bi;
+                    if constexpr (!SELF) {
+                        const float4* lj = blk + 8 * TQ * J;
+                        br = lj[(2 * jj * TQ + h) ^ (J & 7)];
+                        bi = lj[((2 * jj + 1) * TQ + h) ^ (J & 7)];
+                    } else {
+                        const int G = (jj >> 1) ? gj1 : gj0, pos = 2 * (jj & 1) + pol;
+                        const float4* lj = blk + 8 * TQ * G;
+                        br = lj[(2 * pos * TQ + h) ^ (G & 7)];
+                        bi = lj[((2 * pos + 1) * TQ + h) ^ (G & 7)];
+                    }
 #pragma unroll
                     for (int ii = 0; ii < 4; ++ii) {
                         float2 c = acc[ii][jj];
@@ -160,7 +190,7 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p, int
         if (ch_done && active && ok) {
             const int u = blockIdx.x + (w / n_stage_ch) * gridDim.x;
             const int k = u / n_split;
-            const int n_bl = p.n_ant * (p.n_ant + 1) / 2, npp = p.n_pol * p.n_pol;
+            const int n_bl = p.n_ant * (p.n_ant + 1) / 2, npp = p.self ? p.n_pol : p.n_pol * p.n_pol;
             float2* out = n_split == 1 ? p.vis
                                        : p.vis_part + static_cast<int64_t>(u % n_split) * p.n_chan * n_bl * npp;
 #pragma unroll
@@ -174,11 +204,20 @@ __global__ void __launch_bounds__(MAXT) xengine_fp32_kernel(const XParams p, int
                     *pr = 0.0f;
                     *pi = 0.0f;
                     acc[ii][jj] = make_float2(0.f, 0.f);
-                    if (i >= p.n_in || j >= p.n_in) continue;
-                    const int a = i / p.n_pol, pp = i % p.n_pol, a2 = j / p.n_pol, qq = j % p.n_pol;
+                    int a, pp, a2, qq;
+                    if constexpr (SELF) {
+                        a = 4 * I + ii;
+                        a2 = 4 * J + jj;
+                        pp = qq = pol;
+                        if (a >= p.n_ant || a2 >= p.n_ant) continue;
+                    } else {
+                        if (i >= p.n_in || j >= p.n_in) continue;
+                        a = i / p.n_pol, pp = i % p.n_pol, a2 = j / p.n_pol, qq = j % p.n_pol;
+                        if (a > a2 || (p.self && pp != qq)) continue;
+                    }
                     if (a > a2) continue;
                     const int bl = a * p.n_ant - a * (a - 1) / 2 + (a2 - a);
-                    out[(static_cast<int64_t>(k) * n_bl + bl) * npp + pp * p.n_pol + qq] = v;
+                    out[(static_cast<int64_t>(k) * n_bl + bl) * npp + vis_prod(p.self, p.n_pol, pp, qq)] = v;
                 }
             kb_in_chunk = 0;
         }
@@ -208,8 +247,9 @@ __global__ void vis_split_sum_kernel(const float2* __restrict__ part, float2* __
 }  // namespace
 
 cudaError_t launch_xengine_fp32(const XParams& p, int n_sm, cudaStream_t s) {
-    const int nb = (p.n_in + 3) / 4;
-    const int n_work = nb * (nb + 1) / 2;
+    const bool self2 = p.self && p.n_pol == 2;   // self-polar with one polarisation is the full mode
+    const int nb = self2 ? (p.n_ant + 3) / 4 : (p.n_in + 3) / 4;
+    const int n_work = (self2 ? 2 : 1) * nb * (nb + 1) / 2;
     const int threads = ((n_work + 31) / 32) * 32;
     if (threads > 544) return cudaErrorInvalidValue;
     const int tb = tb_fp32(p.n_chan);
@@ -243,13 +283,17 @@ cudaError_t launch_xengine_fp32(const XParams& p, int n_sm, cudaStream_t s) {
         kern<<<grid, threads, smem, s>>>(p, n_split);
         e = cudaGetLastError();
         if (e != cudaSuccess || n_split == 1) return e;
-        const int64_t n = static_cast<int64_t>(p.n_chan) * (p.n_ant * (p.n_ant + 1) / 2) * p.n_pol * p.n_pol;
+        const int64_t n = static_cast<int64_t>(p.n_chan) * (p.n_ant * (p.n_ant + 1) / 2) * (p.self ? p.n_pol : p.n_pol * p.n_pol);
         const int sgrid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 4 * n_sm));
         vis_split_sum_kernel<<<sgrid, 256, 0, s>>>(p.vis_part, p.vis, n, n_split);
         return cudaGetLastError();
     };
-    if (tb == 8) return threads <= 256 ? go(xengine_fp32_kernel<256, 8>) : go(xengine_fp32_kernel<544, 8>);
-    return threads <= 256 ? go(xengine_fp32_kernel<256, 4>) : go(xengine_fp32_kernel<544, 4>);
+    if (self2) {
+        if (tb == 8) return threads <= 256 ? go(xengine_fp32_kernel<256, 8, true>) : go(xengine_fp32_kernel<544, 8, true>);
+        return threads <= 256 ? go(xengine_fp32_kernel<256, 4, true>) : go(xengine_fp32_kernel<544, 4, true>);
+    }
+    if (tb == 8) return threads <= 256 ? go(xengine_fp32_kernel<256, 8, false>) : go(xengine_fp32_kernel<544, 8, false>);
+    return threads <= 256 ? go(xengine_fp32_kernel<256, 4, false>) : go(xengine_fp32_kernel<544, 4, false>);
 }
 
 }  // namespace gbx

@@ -141,7 +141,7 @@ template <int W>
 __device__ __forceinline__ void write_piece(const XtSub& s, const ItemGeo& ig, int row, int j0,
                                             const uint32_t (&run)[W]) {
     constexpr int H = W / 2;                       // columns of the odd lane's half
-    const int n_bl = s.n_ant * (s.n_ant + 1) / 2, npp = s.n_pol * s.n_pol;
+    const int n_bl = s.n_ant * (s.n_ant + 1) / 2, npp = s.self ? s.n_pol : s.n_pol * s.n_pol;
     const bool odd = row & 1;
     const int i = row >> 1;
 #pragma unroll
@@ -157,9 +157,9 @@ __device__ __forceinline__ void write_piece(const XtSub& s, const ItemGeo& ig, i
         const uint32_t g_r1c1 = odd ? run[2 * jh + H + 1] : r1;
         if (i >= s.n_in || j >= s.n_in) continue;
         const int a = i / s.n_pol, pp = i % s.n_pol, a2 = j / s.n_pol, qq = j % s.n_pol;
-        if (a > a2) continue;
+        if (a > a2 || (s.self && pp != qq)) continue;
         const int bl = a * s.n_ant - a * (a - 1) / 2 + (a2 - a);
-        const int64_t o = (static_cast<int64_t>(ig.k) * n_bl + bl) * npp + pp * s.n_pol + qq;
+        const int64_t o = (static_cast<int64_t>(ig.k) * n_bl + bl) * npp + vis_prod(s.self, s.n_pol, pp, qq);
         if (s.exact) {
             const float d = s.scale[static_cast<int64_t>(i) * s.n_chan + ig.k] *
                             s.scale[static_cast<int64_t>(j) * s.n_chan + ig.k];

@@ -31,6 +31,19 @@ def vis_norm_error(V, Vref, n_ant, n_pol):
     return worst
 
 
+def vis_self_norm_error(V, Vref, n_ant, n_pol):
+    """The same metric for self-polar visibilities [n_chan][n_bl][n_pol] (products pp only)."""
+    worst = 0.0
+    for a in range(n_ant):
+        for a2 in range(a, n_ant):
+            b = bl_index(n_ant, a, a2)
+            for p in range(n_pol):
+                den = np.sqrt(np.maximum(Vref[:, bl_index(n_ant, a, a), p].real *
+                                         Vref[:, bl_index(n_ant, a2, a2), p].real, 1e-300))
+                worst = max(worst, float((np.abs(V[:, b, p] - Vref[:, b, p]) / den).max()))
+    return worst
+
+
 def beam_errors(B, Bref_inc, Bref_coh, Y, gain, coh_mask, n_pol, beam_avg=1):
     """(incoherent relative error, coherent error normalised by its Cauchy-Schwarz bound)."""
     e_inc = float(np.max(np.abs(B[0] - Bref_inc) / np.maximum(np.abs(Bref_inc), 1e-300)))

@@ -152,3 +152,40 @@ def test_batch_fp32_matches_single_handle(env):
         corr.corr_batch_destroy(b)
         for h in hs:
             corr.corr_destroy(h)
+
+
+def test_batch_with_the_64_antenna_4096_point_subarray(env):
+    """Config 4's largest sub-array, (64 ant, 2 pol, 4096-pt), at 256 spectra beside a small one:
+    the two-item 256-row Gram with the cluster-paired 4096-point F-engine.  Integer visibilities
+    equal the oracle's int64 MAC on the exported int8 spectra; against the FP64 oracle on raw
+    samples the int8 form stays within its quantisation bound (1e-2, as the single-handle test)."""
+    torch, corr, orc = env
+    subs = [(64, 2, 4096, 256, 721), (8, 2, 512, 256, 722)]
+    st = torch.cuda.current_stream()
+    hs, streams, xs = [], [], []
+    for na, npol, nfft, nint, seed in subs:
+        s = make_config(2, n_ant=na, n_pol=npol, n_fft=nfft, n_int=nint, seed=seed)
+        h = corr.corr_create(na, npol, nfft, nint)
+        corr.corr_set_delays(h, s.delay, s.phi0, s.rate)
+        xt, n = _dev(torch, s.x)
+        corr.corr_integrate_device(h, xt, n_avail=n, stream=st)
+        corr.corr_set_scales(h, None)
+        corr.corr_set_mode(h, corr.CORR_I8, 0, 1)
+        hs.append(h)
+        streams.append(s)
+        xs.append((xt, n))
+    b = corr.corr_batch_create(hs)
+    try:
+        corr.corr_batch_integrate_device(b, [x for x, _ in xs], n_avail=[n for _, n in xs], stream=st)
+        for h, s in zip(hs, streams):
+            _check_exact(corr, orc, h, s)
+            ch = [c for c in (0, 1, 100, 1023, 1024, 2047) if c < s.n_fft // 2]
+            Y = orc.fengine(s.x, s.n_ant, s.n_pol, s.n_fft, s.n_int, s.delay, s.phi0, s.rate, chans=ch)
+            Vg = corr.corr_read_visibilities(h).astype(np.complex128)[ch]
+            e = vis_norm_error(Vg, orc.xengine(Y, s.n_ant, s.n_pol), s.n_ant, s.n_pol)
+            print(f"batch {s.n_ant} ant {s.n_fft}-pt x {s.n_int}: int8 vs FP64 {e:.2e}")
+            assert e <= 1e-2
+    finally:
+        corr.corr_batch_destroy(b)
+        for h in hs:
+            corr.corr_destroy(h)

@@ -3,8 +3,11 @@
 Tolerances: power dumps are FP32 sums of FP32 spectra (relative 1e-5); patch medians and
 MADs are selections (exact up to the FP32 midpoint, relative 1e-6), flags agree except for
 values within 1e-5 of the threshold; the network runs with FP16 weights and activations,
-so its probabilities are compared to 1e-2 and its gradients to 3e-2 in norm per layer,
-against the oracle evaluated on the same FP16-rounded parameters and inputs.
+so its probabilities are compared to 2e-3 and its gradients element by element to 1e-2 in
+units of their layer's largest gradient (and each layer's norm to 1e-2), against the oracle on
+the same FP16-rounded parameters and inputs; the FP32 build of the same kernels meets 1e-5
+element by element (relative on entries of at least a tenth of their layer's largest, and in
+units of that largest everywhere).
 """
 import numpy as np
 import pytest
@@ -89,16 +92,30 @@ def test_patch_statistics_and_mad_flags_match_oracle(env):
     assert np.max(np.abs(zg - z) / np.maximum(1.0, np.abs(z))) <= 2e-3
 
 
-def test_network_forward_and_gradients_match_oracle(env):
+def _grad_errors(grad_g, grad_r, floor=0.1):
+    """Per layer: the largest relative error over the entries at least `floor` of the layer's
+    largest magnitude, the largest absolute error over every entry in units of that magnitude
+    (a wrong sign or a swapped index on any entry that matters fails it), and the relative norm
+    error of the layer."""
+    out = {}
+    for name, (o, n) in OFFS.items():
+        gr, gg = grad_r[o:o + n], grad_g[o:o + n].astype(np.float64)
+        big = float(np.abs(gr).max())
+        sel = np.abs(gr) >= floor * big
+        out[name] = (float((np.abs(gg - gr)[sel] / np.abs(gr[sel])).max()), float(np.abs(gg - gr).max() / big),
+                     float(np.linalg.norm(gg - gr) / np.linalg.norm(gr)))
+    return out
+
+
+def _network_vs_oracle(env, create, p_gpu):
     torch, corr, orc = env
     B = 2
     rng = np.random.default_rng(11)
     p = he_init(3)
-    p16 = p.astype(np.float16).astype(np.float64)           # the GPU runs on FP16 parameters
     x = rng.normal(size=(B, 64, 64)).astype(np.float16)
     m = (rng.random((B, 64, 64)) < 0.1).astype(np.uint8)
     m[0, 10:30, 20] = 1
-    net = corr.rfi_create(8)
+    net = create(8)
     try:
         corr.rfi_set_params(net, p)
         xt = torch.from_numpy(x).cuda()
@@ -110,18 +127,38 @@ def test_network_forward_and_gradients_match_oracle(env):
         loss_g, grad_g = corr.rfi_loss_grad(net, xt, mt, B, stream=torch.cuda.current_stream())
     finally:
         corr.rfi_destroy(net)
-    logits = orc.rfi_forward(p16, x.astype(np.float64))
+    pr_ = p_gpu(p)                                            # the parameters the GPU computes with
+    logits = orc.rfi_forward(pr_, x.astype(np.float64))
     pr = 1.0 / (1.0 + np.exp(-logits))
     e_p = float(np.max(np.abs(pg - pr)))
-    loss_r, grad_r = orc.rfi_loss_grad(p16, x.astype(np.float64), m)
+    loss_r, grad_r = orc.rfi_loss_grad(pr_, x.astype(np.float64), m)
     e_loss = abs(loss_g - loss_r) / loss_r
-    errs = {}
-    for name, (o, n) in OFFS.items():
-        gr, gg = grad_r[o:o + n], grad_g[o:o + n].astype(np.float64)
-        errs[name] = float(np.linalg.norm(gg - gr) / max(np.linalg.norm(gr), 1e-30))
-    print(f"network: prob {e_p:.2e} loss {e_loss:.2e} grads " + " ".join(f"{k}:{v:.1e}" for k, v in errs.items()))
-    assert e_p <= 1e-2 and e_loss <= 1e-2
-    assert max(errs.values()) <= 3e-2
+    return e_p, e_loss, _grad_errors(grad_g, grad_r)
+
+
+def test_network_forward_and_gradients_match_oracle(env):
+    # FP16 weights and activations (the flagger): against the oracle on the same FP16-rounded
+    # parameters and inputs.  Every stored activation is rounded to 2^-11 relative and a rounding
+    # can flip a ReLU mask, so an entry that is a sum over 8192 pixels with cancellation has no
+    # useful relative bound; the bound is per entry in units of its layer's largest gradient
+    # (measured <= 2.7e-3) and on each layer's norm (measured <= 4e-3), both <= 1e-2
+    torch, corr, orc = env
+    e_p, e_loss, errs = _network_vs_oracle(env, corr.rfi_create, lambda p: p.astype(np.float16).astype(np.float64))
+    print(f"network fp16: prob {e_p:.2e} loss {e_loss:.2e} grads (rel >= 10% of max, abs, norm) " +
+          " ".join(f"{k}:{v[0]:.1e},{v[1]:.1e},{v[2]:.1e}" for k, v in errs.items()))
+    assert e_p <= 2e-3 and e_loss <= 2e-3
+    assert max(v[1] for v in errs.values()) <= 1e-2 and max(v[2] for v in errs.values()) <= 1e-2
+
+
+def test_network_fp32_build_matches_oracle_to_1e5(env):
+    # the same kernels with FP32 weights and activations: only FP32 accumulation remains
+    torch, corr, orc = env
+    e_p, e_loss, errs = _network_vs_oracle(env, corr.rfi_create_fp32,
+                                           lambda p: p.astype(np.float32).astype(np.float64))
+    print(f"network fp32: prob {e_p:.2e} loss {e_loss:.2e} grads (rel >= 10% of max, abs, norm) " +
+          " ".join(f"{k}:{v[0]:.1e},{v[1]:.1e},{v[2]:.1e}" for k, v in errs.items()))
+    assert e_p <= 1e-5 and e_loss <= 1e-5
+    assert max(v[0] for v in errs.values()) <= 1e-5 and max(v[1] for v in errs.values()) <= 1e-5
 
 
 def _dataset(torch, corr, n_integrations, seed, n_fft=2048, n_int=2048, n_in=16):
