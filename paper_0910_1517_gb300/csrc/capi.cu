@@ -104,12 +104,16 @@ int upload_beam_weights(corr* h, const float* gain, const float* theta, const ui
     return CORR_OK;
 }
 
-// F-engine output mode of an X-engine precision mode (CORR_FP32TC reads the FP32 spectra)
-int fe_mode(int xmode) {
-    switch (xmode) {
+// CORR_FP32TC hands its FP32 spectra over in the channel-quad layout (f32q_piece) where the
+// warp-FFT F-engine runs (n_chan <= 1024) and no phased-beam kernel reads them
+bool spec_quad(const corr* h) { return h->xmode == CORR_FP32TC && h->n_chan <= 1024 && h->n_mb == 0; }
+
+// F-engine output mode of a handle's X-engine precision mode
+int fe_mode(const corr* h) {
+    switch (h->xmode) {
         case CORR_I8: return OUT_I8;
         case CORR_F16: return OUT_F16;
-        default: return OUT_FP32;
+        default: return spec_quad(h) ? OUT_F32Q : OUT_FP32;
     }
 }
 
@@ -173,7 +177,12 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
     fp.beams = h->d_beams_raw;
     fp.tw = h->d_tw;
     fp.err = h->d_err;
-    const int fmode = fe_mode(h->xmode);
+    const int fmode = fe_mode(h);
+    if (fmode == OUT_FP32 && h->last_quad) {   // back from the channel-quad layout: padding rows read as zero
+        CU(cudaMemsetAsync(h->d_spec, 0,
+                           static_cast<size_t>(h->n_chan) * h->n_int * rows_fp32(h->n_in) * sizeof(float), s));
+    }
+    h->last_quad = fmode == OUT_F32Q;
     if (int rc = mark(h, 1, s)) return rc;
     if (h->blank_M > 0.0) {   // voltage blanker: per-block statistics of every sample the F-engine reads
         const int64_t need = static_cast<int64_t>(h->n_int) * h->n_fft + max_int_delay(h);
@@ -211,7 +220,7 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
                                    h->xmode == CORR_FP32TC));
     if (h->dump > 0) {
         CU(launch_power_dumps(static_cast<const float*>(h->d_spec), h->n_in, h->n_chan, h->n_int, h->dump,
-                              h->d_power, s));
+                              h->d_power, s, fmode == OUT_F32Q));
     }
     if (int rc = mark(h, 3, s)) return rc;
     if (h->beam_avg > 1) CU(launch_beam_average(h->d_beams_raw, h->d_beams, h->n_int, h->n_chan, h->beam_avg, s));
@@ -246,6 +255,7 @@ gbx::XtSub gbx::xt_sub_of(const corr* h) {
         x.split_scale = std::ldexp(1.0f, -split_exp(h));
         x.descale = std::ldexp(1.0f, 2 * split_exp(h));
         x.chunk = kSplitChunk;
+        x.quad = spec_quad(h) ? 1 : 0;
     } else {
         const int max_ks = xengine_tc_max_ks(h->n_in);
         x.ks = h->ks > 0 ? std::min(h->ks, max_ks) : max_ks;
@@ -267,6 +277,8 @@ int upload_xtab(corr* h) {
     t.n_items = h->n_items;
     t.items = h->d_items;
     t.err = h->d_err;
+    if (t.sub[0].quad && !xengine_tc_encode_quad(t.sub[0]))
+        return fail(CORR_E_CUDA, "the driver refused the tensor map of the FP32 spectra");
     CU(cudaDeviceSynchronize());
     if (h->xtab_b1) {                    // double-buffered outputs: one table per buffer
         t.sub[0].vis = h->vis_b[0];
@@ -914,6 +926,23 @@ int corr_read_spectra(corr_t* h, int k0, int nk, float* out) {
     if (!out || k0 < 0 || nk < 0 || k0 + nk > h->n_chan) return fail(CORR_E_INVAL, "channel range");
     const int tb = tb_fp32(h->n_chan);
     const int R = 2 * h->n_in, Rp = rows_fp32(h->n_in), ntb = h->n_int / tb;
+    if (h->last_quad) {   // channel-quad layout: the quads covering channels k0 .. k0 + nk - 1
+        const int q0 = k0 / 4, q1 = (k0 + nk + 3) / 4;
+        const size_t per_q = static_cast<size_t>(ntb) * h->n_in * 64;
+        std::vector<float> buf(per_q * (q1 - q0));
+        CU(cudaMemcpy(buf.data(), static_cast<const float*>(h->d_spec) + per_q * q0, buf.size() * sizeof(float),
+                      cudaMemcpyDeviceToHost));
+        for (int c = 0; c < nk; ++c)
+            for (int kb = 0; kb < ntb; ++kb)
+                for (int i = 0; i < h->n_in; ++i)
+                    for (int cc = 0; cc < 2; ++cc)
+                        for (int e = 0; e < tb; ++e) {
+                            const int k = k0 + c, t = kb * tb + e;
+                            out[((static_cast<size_t>(i) * h->n_int + t) * nk + c) * 2 + cc] =
+                                buf[f32q_piece(k, kb, i, ntb, h->n_in) - static_cast<int64_t>(per_q) * q0 + cc * 8 + e];
+                        }
+        return CORR_OK;
+    }
     const size_t per_ch = static_cast<size_t>(ntb) * Rp * tb;
     std::vector<float> buf(per_ch * nk);
     CU(cudaMemcpy(buf.data(), static_cast<const float*>(h->d_spec) + per_ch * k0, buf.size() * sizeof(float),
@@ -1002,7 +1031,8 @@ int corr_set_multibeam(corr_t* h, int n_beams, const float* weights, int product
     h->d_mbw = nullptr;
     h->d_mb = nullptr;
     h->n_mb = 0;
-    if (n_beams == 0) return CORR_OK;
+    // the layout of the CORR_FP32TC hand-off depends on whether phased beams read it
+    if (n_beams == 0) return upload_xtab(h);
     // weights [beam][antenna][channel] -> [channel][beam * n_ant + antenna] (padded to even)
     const int ws = multibeam_wstride(n_beams, h->n_ant);
     std::vector<float2> w(static_cast<size_t>(h->n_chan) * ws, make_float2(0.0f, 0.0f));
@@ -1020,7 +1050,7 @@ int corr_set_multibeam(corr_t* h, int n_beams, const float* weights, int product
     h->n_mb = n_beams;
     h->mb_products = products;
     h->mb_avg = avg;
-    return CORR_OK;
+    return upload_xtab(h);
 }
 
 int corr_read_multibeam(corr_t* h, float* out, int blocking) {

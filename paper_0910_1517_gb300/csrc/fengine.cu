@@ -42,7 +42,7 @@ __global__ void twiddle_kernel(int n_fft, int count, float2* __restrict__ tw) {
 
 // grid.x: dumps, grid.y: 32-channel groups; lane = channel, warp rows step over inputs
 __global__ void power_dump_kernel(const float* __restrict__ spec, int n_in, int n_chan, int n_int, int dump,
-                                  float* __restrict__ P) {
+                                  float* __restrict__ P, bool quad) {
     const int d = blockIdx.x, k = blockIdx.y * 32 + threadIdx.x;
     if (k >= n_chan) return;
     const int tb = tb_fp32(n_chan);
@@ -51,6 +51,15 @@ __global__ void power_dump_kernel(const float* __restrict__ spec, int n_in, int 
     for (int i = threadIdx.y; i < n_in; i += blockDim.y) {
         float acc = 0.0f;
         for (int kb = kb0; kb < kb0 + nkb; ++kb) {
+            if (quad) {   // one 64-byte piece: 8 re then 8 im values, summed in the order of the other layout
+                const float4* pc = reinterpret_cast<const float4*>(spec + f32q_piece(k, kb, i, ntb, n_in));
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const float4 v = pc[(m >> 1) + 2 * (m & 1)];   // re 0-3, im 0-3, re 4-7, im 4-7
+                    acc += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+                }
+                continue;
+            }
             const float* blk = spec + (static_cast<int64_t>(k) * ntb + kb) * Rp * tb;
             for (int e = 0; e < tb; e += 4) {            // one 4-frame granule of each row at a time
                 const float4 re = *reinterpret_cast<const float4*>(blk + fp32_off(2 * i, e, tb));
@@ -109,6 +118,7 @@ cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s) {
         case OUT_FP32: return launch_w_mode<OUT_FP32>(p, s);
         case OUT_I8: return launch_w_mode<OUT_I8>(p, s);
         case OUT_F16: return launch_w_mode<OUT_F16>(p, s);
+        case OUT_F32Q: return launch_w_mode<OUT_F32Q>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -156,11 +166,11 @@ cudaError_t launch_phasor_setup(int n_ant, int n_chan, int n_fft, int n_int, int
 }
 
 cudaError_t launch_power_dumps(const float* spec, int n_in, int n_chan, int n_int, int dump, float* P,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool quad) {
     const int tb = tb_fp32(n_chan);
     if (dump < tb || dump % tb || n_int % dump) return cudaErrorInvalidValue;
     const dim3 grid(n_int / dump, (n_chan + 31) / 32), block(32, 8);
-    power_dump_kernel<<<grid, block, 0, s>>>(spec, n_in, n_chan, n_int, dump, P);
+    power_dump_kernel<<<grid, block, 0, s>>>(spec, n_in, n_chan, n_int, dump, P, quad);
     return cudaGetLastError();
 }
 

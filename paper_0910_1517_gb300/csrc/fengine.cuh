@@ -8,7 +8,7 @@
 
 namespace gbx {
 
-enum OutMode : int { OUT_FP32 = 0, OUT_I8 = 1, OUT_F16 = 2 };
+enum OutMode : int { OUT_FP32 = 0, OUT_I8 = 1, OUT_F16 = 2, OUT_F32Q = 3 };
 
 // Spectra hand-off layout ("K-block layout"), shared by every X-engine:
 //   S[k][kb][r][TB]   k channel, kb = t / TB, r = 2*i + c (c = 0 re, 1 im), TB = t % TB
@@ -32,6 +32,18 @@ __host__ __device__ constexpr int rows_fp32(int n_in) { return ((2 * n_in + 7) /
 __host__ __device__ constexpr int fp32_off(int r, int e, int tb) {
     const int G = r >> 3, g = (r & 7) * (tb >> 2) + (e >> 2);
     return G * 8 * tb + ((g ^ (G & 7)) << 2) + (e & 3);
+}
+
+// FP32 spectra in the channel-quad layout (OUT_F32Q, the F-to-X hand-off of CORR_FP32TC for
+// n_chan <= 1024): the piece of channel k, 8-frame K-block kb and input i -- 8 re then 8 im FP32
+// values, 64 bytes -- at float offset
+//   (((k / 4) * ntb + kb) * n_in + i) * 64 + (k % 4) * 16
+// i.e. [k / 4][kb][i][k % 4][16]: the F-engine, which holds one input of 8 frames for every
+// channel, writes 256 contiguous bytes per channel quad (instead of 64-byte pieces 4 MB apart,
+// which leave its stores at a third of the HBM bandwidth), and a channel's stage is a strided
+// gather that one 5-D TMA tensor copy performs ([kb][i][16] = [kb][row 2i + c][8 frames]).
+__host__ __device__ constexpr int64_t f32q_piece(int k, int64_t kb, int i, int64_t ntb, int n_in) {
+    return (((static_cast<int64_t>(k) >> 2) * ntb + kb) * n_in + i) * 64 + (k & 3) * 16;
 }
 
 struct FeParams {
@@ -142,10 +154,10 @@ cudaError_t launch_phasor_setup(int n_ant, int n_chan, int n_fft, int n_int, int
                                 const double* phi0, const double* rate, float2* pf, float2* ff, int* D,
                                 cudaStream_t s, const int64_t* g0_dev = nullptr);
 
-// Auto-power dumps from the FP32 K-block spectra: P[i][d][k] = sum of |Y_i[t][k]|^2 over the
-// `dump` frames of dump d (dump a multiple of tb_fp32(n_chan) dividing n_int).
+// Auto-power dumps from the FP32 K-block spectra (quad: the channel-quad layout): P[i][d][k] = sum
+// of |Y_i[t][k]|^2 over the `dump` frames of dump d (dump a multiple of tb_fp32(n_chan) dividing n_int).
 cudaError_t launch_power_dumps(const float* spec, int n_in, int n_chan, int n_int, int dump, float* P,
-                               cudaStream_t s);
+                               cudaStream_t s, bool quad = false);
 
 // Time-domain voltage blanker (blank.cu, Sec. 5, Eq. 3-4) on rows x[i][0..n) cut into blocks of
 // `block` samples (a multiple of 16): per block, stats [n_in][ceil(n / block)][4] = 2 med, 4 MAD,

@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
     constexpr int PP = P::P, G = P::G, F = P::F, N = P::N, L = P::L;
     constexpr int TB = (MODE == OUT_FP32) ? tb_fp32(M) : kTbHalf;
     static_assert(TB == 8, "8-frame K-block runs");
+    static_assert(MODE != OUT_F32Q || M >= 32, "channel quads");
     __shared__ __align__(8) WCtl ctl;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* stage0 = smem + S::stage;
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
             const int i = a * p.n_pol + pol;
             const float g2 = p.ginc[a];
             float scv[4];                      // requantisation scales of this thread's channels
-            if constexpr (MODE != OUT_FP32) {
+            if constexpr (MODE == OUT_I8 || MODE == OUT_F16) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) scv[c] = p.scale[static_cast<int64_t>(i) * M + chs[c]];
             }
@@ -302,7 +303,18 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
                         *bc = (pol == 0) ? pw : *bc + pw;
                     }
                 }
-                if constexpr (MODE == OUT_FP32) {
+                if constexpr (MODE == OUT_F32Q) {
+                    // the channel-quad layout: this lane's own 64-byte piece, two 32-byte stores; the lanes
+                    // of consecutive channels fill whole 256-byte quads
+                    float* o = static_cast<float*>(p.spec) + f32q_piece(chs[c], kb_run, i, ntb, p.n_in);
+                    uint32_t u[8];
+#pragma unroll
+                    for (int l = 0; l < 8; ++l) u[l] = __float_as_uint(yc[l].x);
+                    if (live) st_global_v8(o, u);
+#pragma unroll
+                    for (int l = 0; l < 8; ++l) u[l] = __float_as_uint(yc[l].y);
+                    if (live) st_global_v8(o + 8, u);
+                } else if constexpr (MODE == OUT_FP32) {
                     // 64-byte piece of (channel, input): granule slot (2 comp + half) ^ (sgr & 3); each lane
                     // pair writes one piece per instruction, trading the component each needs by a shuffle
                     float* spec = static_cast<float*>(p.spec);
@@ -429,6 +441,17 @@ cudaError_t launch_w(const FeParams& p, cudaStream_t s) {
 
 template <int MODE>
 cudaError_t launch_w_mode(const FeParams& p, cudaStream_t s) {
+    if constexpr (MODE == OUT_F32Q) {   // the channel-quad layout: n_chan 32 .. 1024 only
+        switch (p.n_chan) {
+            case 32: return launch_w<32, MODE>(p, s);
+            case 64: return launch_w<64, MODE>(p, s);
+            case 128: return launch_w<128, MODE>(p, s);
+            case 256: return launch_w<256, MODE>(p, s);
+            case 512: return launch_w<512, MODE>(p, s);
+            case 1024: return launch_w<1024, MODE>(p, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (p.n_chan) {
         case 32: return launch_w<32, MODE>(p, s);
         case 64: return launch_w<64, MODE>(p, s);

@@ -13,6 +13,7 @@ struct corr {
     int n_ant = 0, n_pol = 0, n_in = 0, n_fft = 0, n_chan = 0, n_int = 0, n_bl = 0, npp = 0;
     int xmode = CORR_FP32, beam_avg = 1, max_delay = 2048;
     int polmode = CORR_POL_FULL;         // CORR_POL_SELF: only the n_pol products pp (npp = n_pol)
+    bool last_quad = false;              // the last integration's FP32 spectra are in the channel-quad layout
     int dev = 0, n_sm = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_done = nullptr, ev_aux = nullptr;

@@ -1,6 +1,7 @@
 // xengine.cuh -- launch interface of the X-engines (MAC over all N(N+1)/2
 // baselines x n_pol^2 products, Sec. 2.1).
 #pragma once
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -32,7 +33,12 @@ cudaError_t launch_xengine_fp32(const XParams& p, int n_sm, cudaStream_t s);
 constexpr int kMaxSubX = 8;
 constexpr int kStageMaxBytes = 32768;        // bytes of one operand stage (ks/8 K-blocks x 2 n_in rows x 16 B)
 constexpr int kStage2Bytes = 32768;          // FP32 form: bytes of one FP32 stage (ks x rows_fp32(n_in) x 4 B)
-struct XtSub {
+struct alignas(64) XtSub {
+    // FP32 form with quad = 1: the spectra are in the channel-quad layout (f32q_piece) and each
+    // stage is one TMA copy through this 5-D tensor map over (16 floats, channel in quad, input,
+    // K-block, quad), box (16, 1, n_in, ks / 8, 1); it lands [kb][2 n_in rows][8 frames]
+    CUtensorMap tmap;
+    int quad;
     const __half* spec;    // [k][kb][2 n_in][8] fp16 K-block layout
     int n_ant, n_pol, n_in, n_chan, n_int;
     const float* scale;    // [n_in][n_chan]
@@ -57,6 +63,9 @@ struct XtBatch {          // (the FP32 form, spec32 set, runs alone: launch with
     const int4* items;     // (sub, channel, row block, 0)
     unsigned* err;
 };
+// Encode the tensor map of sub-array x's quad-layout FP32 spectra (x.spec32, x.n_in, x.n_chan,
+// x.n_int, x.ks); false if the driver refuses it
+bool xengine_tc_encode_quad(XtSub& x);
 bool xengine_tc_supported(int n_in);                 // 2 n_in <= 256
 int xengine_tc_max_ks(int n_in);                      // largest fp16 stage for the row count
 int xengine_tc_ks_fp32(int n_in);                     // largest FP32-form stage (FP32 slot <= kStage2Bytes)

@@ -45,6 +45,8 @@
 // the whole integration: narrow items then alternate two chunk accumulators
 // (columns 0-255), keep the cross terms in columns 256-383 and the running sums
 // in columns 384-511.
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 #include "fengine.cuh"
 #include "xengine.cuh"
@@ -320,6 +322,44 @@ __device__ __noinline__ void convert_stages(const XtBatch& t, Shared& sh, unsign
             const int frames = min(s.ks, s.n_int - st * s.ks);
             const float* src = reinterpret_cast<const float*>(smem + kOpStages2 * kSlot2 + fs * kStage2Bytes);
             unsigned char* dst = smem + os * kSlot2;
+            if (s.quad) {
+                // the stage is [kb][R rows][8 frames]: unit u = (j R + r) 2 + h takes frames 4h .. 4h + 3 of
+                // row r in K-block j (one 16-byte load; consecutive units, consecutive bytes) and writes
+                // their hi and lo halves (8 bytes each) into row r of K-block j of the two operand tiles
+                const int units = (frames / 8) * R * 2;
+#pragma unroll 4
+                for (int u = ct; u < units; u += kConvThreads) {
+                    const float4 q = *reinterpret_cast<const float4*>(src + 4 * u);
+                    const float v[4] = {q.x * sc, q.y * sc, q.z * sc, q.w * sc};
+                    uint32_t hw[2], lw[2];
+#pragma unroll
+                    for (int m = 0; m < 2; ++m) {
+                        float hv[2], lv[2];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {   // Veltkamp's split, explicit roundings
+                            const float x = v[2 * m + e];
+                            const float tt = __fmul_rn(x, 8193.0f);
+                            hv[e] = __fsub_rn(tt, __fsub_rn(tt, x));
+                            lv[e] = __fsub_rn(x, hv[e]);
+                        }
+                        const __half2 hh = __floats2half2_rn(hv[0], hv[1]);
+                        const __half2 ll = __floats2half2_rn(lv[0], lv[1]);
+                        hw[m] = *reinterpret_cast<const uint32_t*>(&hh);
+                        lw[m] = *reinterpret_cast<const uint32_t*>(&ll);
+                    }
+                    unsigned char* d = dst + u * 8;
+                    *reinterpret_cast<uint2*>(d) = make_uint2(hw[0], hw[1]);
+                    *reinterpret_cast<uint2*>(d + lo_off) = make_uint2(lw[0], lw[1]);
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    if (ct == 0) sh.consumed = g + 1;
+                    mbar_arrive(&sh.f32empty[fs]);
+                    mbar_arrive(&sh.full[os]);
+                }
+                continue;
+            }
             const int units = (frames / 8) * R;
             // unit u = j * R + r: thread ct takes u = ct, ct + kConvThreads, ... (r, j stepped incrementally)
             int r = ct % R, j = ct / R;
@@ -434,7 +474,14 @@ __global__ void __launch_bounds__((kF32 ? kWarps2 : kWarps1) * 32, 1) xengine_tc
                         break;
                     }
                     unsigned char* dst = slots + slot * pitch;
-                    if (f32) {
+                    if (f32 && s.quad) {
+                        // channel-quad layout: one 5-D tensor copy gathers the stage's pieces of channel k
+                        // (a last, shorter stage reads zeros past the end and counts the whole box)
+                        if (st == 0) tmap_acquire(&s.tmap);
+                        const int nkb = s.ks / kTbHalf;
+                        mbar_arrive_expect_tx(&fullb[slot], static_cast<uint32_t>(nkb) * s.n_in * 64);
+                        tma_load_5d(dst, &s.tmap, 0, ig.k & 3, 0, st * nkb, ig.k >> 2, &fullb[slot]);
+                    } else if (f32) {
                         // the stage's FP32 K-blocks of channel k are contiguous
                         const int frames = min(s.ks, s.n_int - st * s.ks);
                         const uint32_t bytes = static_cast<uint32_t>(frames) * ig.Rp * 4;
@@ -599,6 +646,26 @@ __global__ void __launch_bounds__((kF32 ? kWarps2 : kWarps1) * 32, 1) xengine_tc
 }
 
 }  // namespace
+
+bool xengine_tc_encode_quad(XtSub& x) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q{};
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t ntb = static_cast<cuuint64_t>(x.n_int / kTbHalf);
+    const cuuint64_t dim[5] = {16, 4, static_cast<cuuint64_t>(x.n_in), ntb, static_cast<cuuint64_t>(x.n_chan / 4)};
+    const cuuint64_t stride[4] = {64, 256, 256ull * x.n_in, 256ull * x.n_in * ntb};   // bytes, dims 1..4
+    const cuuint32_t box[5] = {16, 1, static_cast<cuuint32_t>(x.n_in), static_cast<cuuint32_t>(x.ks / kTbHalf), 1};
+    const cuuint32_t estride[5] = {1, 1, 1, 1, 1};
+    return encode(&x.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<float*>(x.spec32), dim, stride, box, estride,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 bool xengine_tc_supported(int n_in) { return n_in >= 1 && 2 * n_in <= 256; }
 

@@ -379,10 +379,10 @@ def test_rail_value_inputs(env):
     Y = Yall[:, :, chans]
     V = orc.xengine(Y, s.n_ant, s.n_pol)
     Bi_all, Bc_all = orc.beams(Yall, s.n_ant, s.n_pol, s.n_fft)
-    # a frame of constant samples has power only at DC, so per-channel relative beam errors are
-    # not defined there: beams are judged against the frame's mean power over all channels, the
-    # scale of an FP32 FFT's rounding (Parseval)
-    frame_scale = Bi_all.mean(axis=1, keepdims=True)
+    # a frame of constant samples has power only at DC, so a per-channel relative beam error is not
+    # defined in its other channels: beams are judged relative to the larger of their own value and
+    # the frame's mean power over all channels (the scale of an FP32 FFT's rounding, by Parseval)
+    frame_scale = np.maximum(Bi_all, Bi_all.mean(axis=1, keepdims=True))
     res = {}
     for mode, name in ((corr.CORR_FP32, "fp32"), (corr.CORR_FP32TC, "fp32tc")):
         r = run_gpu(env, s, mode=mode, want_spec=(0, s.n_fft // 2))
@@ -390,7 +390,7 @@ def test_rail_value_inputs(env):
         Yg = r["Y"][:, :, chans]
         e_y = max(float(np.abs(Yg[i] - Y[i]).max() / np.abs(Y[i]).max()) for i in range(s.n_in))
         e_bi = float(np.max(np.abs(r["B"][0] - Bi_all) / frame_scale))
-        e_bc = float(np.max(np.abs(r["B"][1] - Bc_all) / (s.n_ant * frame_scale)))
+        e_bc = float(np.max(np.abs(r["B"][1] - Bc_all) / np.maximum(Bc_all, s.n_ant * frame_scale)))
         print(f"rails {name}: vis {e_v:.2e} spectra {e_y:.2e} beams (per frame scale) {e_bi:.2e} {e_bc:.2e}")
         assert e_v <= FP32_TOL and e_y <= FP32_TOL and e_bi <= FP32_TOL and e_bc <= FP32_TOL
         res[name] = r
