@@ -83,8 +83,9 @@ int fengine_frames_per_cta(int n_fft);
 //   part A, read by the kernel of fengine_impl.cuh (n_fft = 4096, batched launches): [R2][16]
 //     pass-2 twiddles W_{16 R2}^(j r), [R3][16 R2] pass-3 twiddles W_M^(j r) when R3 > 1, then
 //     [M/2 + 1] real-split twiddles W_N^k;
-//   part B (M <= 1024), read by the warp-FFT kernel of fengine_wfft.cuh: [P = M/32][32]
-//     inter-pass twiddles W_M^(l k1), then [M/2 + 1] W_N^k.
+//   part B (M <= 1024), read by the warp-FFT kernel of fengine_wfft.cuh: [P/2][32][2] inter-pass
+//     twiddles W_M^(l k1) (k1 = 2 j + b at [j][l][b]; P = M/32; at P = 1 its 32 entries are
+//     unused), then [M/2 + 1] W_N^k.
 __host__ __device__ constexpr int fengine_tw_r2(int M) { return (M / 16 >= 16) ? 16 : M / 16; }
 __host__ __device__ constexpr int fengine_tw_r3(int M) { return M / (16 * fengine_tw_r2(M)); }
 __host__ __device__ constexpr int fengine_tw_a_count(int n_fft) {
@@ -116,8 +117,9 @@ __host__ __device__ inline void fengine_tw_angle(int n_fft, int e, double& num, 
         return;
     }
     e -= A;
-    if (e < (M / 32) * 32) {                                 // inter-pass: W_M^(l k1), [k1][l]
-        num = static_cast<double>(e % 32) * (e / 32);
+    if (e < (M / 32) * 32) {                                 // inter-pass: W_M^(l k1), [k1 / 2][l][k1 % 2]
+        const int l = (e >> 1) & 31, k1 = ((e >> 6) << 1) + (e & 1);
+        num = static_cast<double>(l) * k1;
         den = M;
         return;
     }

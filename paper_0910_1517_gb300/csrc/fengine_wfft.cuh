@@ -40,7 +40,8 @@ struct WPlan {
     static constexpr int F = kWFftWarps * G;       // frames per CTA (8192 / M)
     static constexpr int N = 2 * M;                // real FFT size
     static constexpr int S = 33 * P;               // float2 stride of a frame in a warp region
-    static constexpr int REG = 32 * 33;            // float2 per warp region (rows padded to 33)
+    static constexpr int RS = 34;                  // float2 per transpose row (16-byte aligned rows)
+    static constexpr int REG = 32 * RS;            // float2 per warp region
     static constexpr int STAGE = F * N + 32;       // staging bytes per buffer
     static constexpr int L = 8;                    // frames per epilogue thread
     static constexpr int SLOTS = M / 4;            // pair slots per frame group (two pairs each)
@@ -51,7 +52,7 @@ struct WPlan {
 template <int M>
 struct WSmem {
     using P = WPlan<M>;
-    static constexpr int kTw1 = P::P * 32;         // inter-pass twiddles [k1][l]
+    static constexpr int kTw1 = P::P * 32;         // inter-pass twiddles [k1 / 2][l][k1 % 2]
     static constexpr int kTwN = M / 2 + 1;         // real-split twiddles
     static constexpr int kTab = 2 * M + P::F;      // [pf M | wcoh M | ff F] of one antenna
     static constexpr size_t stage = 0;
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* stage0 = smem + S::stage;
     float2* Xbuf = reinterpret_cast<float2*>(smem + S::X);          // [2][8 warps][REG]
-    float2* tw1 = reinterpret_cast<float2*>(smem + S::tw);         // [P][32]
+    float2* tw1 = reinterpret_cast<float2*>(smem + S::tw);         // [P / 2][32][2]
     float2* twN = tw1 + S::kTw1;                                    // [M/2 + 1]
     float2* tab = reinterpret_cast<float2*>(smem + S::tab);        // 2 x [pf | wcoh | ff]
     volatile int* abort_flag = &ctl.abort_flag;
@@ -202,24 +203,38 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
                                                     static_cast<float>(static_cast<signed char>(q[1])));
                     }
             }
+            // the twiddle W_M^(l k1), k1 >= 1 (pairs of k1 in one 16-byte load), then the transpose
+            // through the warp's region (row r = g P + k1, column l; rows of 34 points, so a lane
+            // reads its row 16 bytes at a time without bank conflicts)
+            auto twiddle_transpose = [&]() {
 #pragma unroll
-            for (int g = 0; g < G; ++g) Dft<PP>::template run<1>(v + g * PP);
-            // twiddle W_M^(l k1)
+                for (int j = 0; 2 * j + 1 < PP; ++j) {   // (P = 1: no twiddle)
+                    const float4 w = reinterpret_cast<const float4*>(tw1)[j * 32 + lane];
 #pragma unroll
-            for (int k1 = 1; k1 < PP; ++k1) {
-                const float2 w = tw1[k1 * 32 + lane];
+                    for (int g = 0; g < G; ++g) {
+                        if (j > 0) v[g * PP + 2 * j] = cmul(make_float2(w.x, w.y), v[g * PP + 2 * j]);
+                        if (2 * j + 1 < PP) v[g * PP + 2 * j + 1] = cmul(make_float2(w.z, w.w), v[g * PP + 2 * j + 1]);
+                    }
+                }
 #pragma unroll
-                for (int g = 0; g < G; ++g) v[g * PP + k1] = cmul(w, v[g * PP + k1]);
+                for (int r = 0; r < 32; ++r) Rw[r * P::RS + lane] = v[r];
+                __syncwarp();
+                const float4* row = reinterpret_cast<const float4*>(Rw + lane * P::RS);
+#pragma unroll
+                for (int n = 0; n < 16; ++n) {
+                    const float4 q = row[n];
+                    v[2 * n] = make_float2(q.x, q.y);
+                    v[2 * n + 1] = make_float2(q.z, q.w);
+                }
+                __syncwarp();
+            };
+            {
+#pragma unroll
+                for (int g = 0; g < G; ++g) Dft<PP>::template run<1>(v + g * PP);
+                twiddle_transpose();
+                // ---- pass 2: lane = (g, k1), 32-point DFT over the columns: Z_g[k1 + P k2]
+                Dft<32>::template run<1>(v);
             }
-            // ---- transpose through the warp's region: row r = g P + k1, column l
-#pragma unroll
-            for (int r = 0; r < 32; ++r) Rw[r * 33 + lane] = v[r];
-            __syncwarp();
-#pragma unroll
-            for (int n = 0; n < 32; ++n) v[n] = Rw[lane * 33 + n];
-            __syncwarp();
-            // ---- pass 2: lane = (g, k1), 32-point DFT over the columns: Z_g[k1 + P k2]
-            Dft<32>::template run<1>(v);
             float2* o = Rw + (lane / PP) * P::S + (lane % PP);
 #pragma unroll
             for (int k2 = 0; k2 < 32; ++k2) o[PP * k2] = v[k2];
