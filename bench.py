@@ -396,10 +396,24 @@ def run_e2e(args, corr, torch, dist, s, coh, world, xmode, four_bit=False):
     corr.corr_wait_output(he, j + k3 - 1)
     dt = time.perf_counter() - t0
     dt = max_over_ranks(dt, dist, "cuda")
+    # the host link itself: one step's samples, pinned host to device, one copy, CUDA events
+    dev = torch.empty(hx.shape, dtype=hx.dtype, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        dev.copy_(hx, non_blocking=True)
+    e0.record()
+    for _ in range(5):
+        dev.copy_(hx, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    link_gbs = 5 * hx.numel() * hx.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del dev
     e2e = {"value": job_rate(world, k3 * step_samples(), dt), "unit": UNIT,
            "h2d_bytes_per_step": N_IN * body // (2 if four_bit else 1),
            "d2h_bytes_per_step": (hv.numel() + hb.numel()) * 4 // n_slots, "steps": k3,
            "ms_per_step": 1e3 * dt / k3,
+           "host_link_h2d_gbs": link_gbs,
+           "host_link_floor_ms_per_step": N_IN * body / (2 if four_bit else 1) / (link_gbs * 1e9) * 1e3,
            "path": ("corr_push_samples_4bit (pinned host ADC card rows, 4 bits per sample)" if four_bit else
                     "corr_push_samples (pinned host, two sample rings)") +
                    " + corr_wait_output (visibilities and beams of every integration in a ring of pinned host slots)"}
@@ -717,7 +731,11 @@ def run_ours(args, world, rank, local_rank):
     corr.load()
     pk = peaks()
     if args.leg != "all":                                 # one extra leg alone (profiling runs)
-        if args.leg == "multibeam":                      # the phased-beam kernels alone (16 and 64 beams)
+        if args.leg == "e2e4bit":                        # the 4-bit ADC streaming path alone
+            s4 = make_config(2, seed=slice_seed(rank), n_int=N_INT)
+            res = {"e2e_4bit_adc": run_e2e(args, corr, torch, dist, s4, (np.arange(N_ANT) < COH_ANTENNAS).astype(np.uint8),
+                                           world, corr.CORR_FP32TC, four_bit=True)}
+        elif args.leg == "multibeam":                    # the phased-beam kernels alone (16 and 64 beams)
             sm = make_config(2, seed=slice_seed(rank), n_int=N_INT)
             ldm = ((sm.x.shape[1] + 15) // 16) * 16 + 16
             xm = torch.zeros((N_IN, ldm), dtype=torch.int8, device="cuda")
@@ -725,6 +743,8 @@ def run_ours(args, world, rank, local_rank):
             cm = (np.arange(N_ANT) < COH_ANTENNAS).astype(np.uint8)
             res = {f"beams_{nb}": run_multibeam_leg(corr, torch, sm, xm, ldm, cm, corr.CORR_FP32TC, 10, None,
                                                     peaks(), n_beams=nb) for nb in (16, 64)}
+        if args.leg in ("e2e4bit", "multibeam"):
+            pass
         else:
             res = run_batch_leg(args, corr, torch, rank) if args.leg == "batched" else \
                 run_dedisp_leg(corr, torch, peaks()) if args.leg == "dedisp" else run_rfi_leg(corr, torch)
@@ -907,8 +927,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--no-extras", action="store_true",
                     help="time only the FP32 step (no precision forms, no end-to-end leg); for profiling runs")
-    ap.add_argument("--leg", choices=("all", "batched", "rfi", "dedisp", "multibeam"), default="all",
-                    help="run one extra leg alone: batched sub-arrays, learned RFI, dedispersion or phased beams (profiling runs)")
+    ap.add_argument("--leg", choices=("all", "batched", "rfi", "dedisp", "multibeam", "e2e4bit"), default="all",
+                    help="run one extra leg alone: batched sub-arrays, learned RFI, dedispersion, phased beams or the "
+                         "4-bit ADC streaming path (profiling runs)")
     ap.add_argument("--xmode", choices=("fp32tc", "fp32"), default="fp32tc",
                     help="form of the timed step: FP32 on the tensor cores (default) or the plain CUDA-core FP32 form")
     ap.add_argument("--n-int", type=int, default=N_INT,
