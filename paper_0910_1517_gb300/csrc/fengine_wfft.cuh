@@ -262,27 +262,34 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
         chs[1] = (ps == 0) ? M / 2 : M - ps;
         chs[2] = ps + M / 4;
         chs[3] = M - ps - M / 4;
-        // -i W_N^k of the two pairs (the real split below works on 2 X)
-        float2 wn[2];
+        // Frames go in pairs: a float2 holds one component (real or imaginary part) of frames
+        // 2j and 2j + 1, so one packed FP32x2 instruction does the arithmetic of both frames.
+        // -i W_N^k of the two pairs (the real split below works on 2 X), as broadcast pairs
+        float2 wnx[2], wny[2], nwny[2];        // -i W_N^k = (w.y, -w.x), w = W_N^k
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const float2 w = twN[chs[2 * q]];
-            wn[q] = make_float2(w.y, -w.x);
+            wnx[q] = make_float2(w.y, w.y);
+            wny[q] = make_float2(-w.x, -w.x);
+            nwny[q] = make_float2(w.x, w.x);
         }
-        float incr[L][4];
-        float2 cohr[L][4];
+        constexpr int LP = L / 2;              // frame pairs per thread
+        float2 incr[LP][4];                    // incoherent beam
+        float2 cre[LP][4], cim[LP][4];         // coherent sum of the current polarisation
 #pragma unroll
-        for (int l = 0; l < L; ++l)
+        for (int j = 0; j < LP; ++j)
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                incr[l][c] = 0.0f;
-                cohr[l][c] = make_float2(0.0f, 0.0f);
+                incr[j][c] = make_float2(0.0f, 0.0f);
+                cre[j][c] = make_float2(0.0f, 0.0f);
+                cim[j][c] = make_float2(0.0f, 0.0f);
             }
         for (int it = 0; it < n_iter; ++it) {
             const int b = it & 1;
             const int pol = it / p.n_ant, a = it % p.n_ant;
             const int i = a * p.n_pol + pol;
             const float g2 = p.ginc[a];
+            const float2 g22 = make_float2(g2, g2);
             float scv[4];                      // requantisation scales of this thread's channels
             if constexpr (MODE == OUT_I8 || MODE == OUT_F16) {
 #pragma unroll
@@ -300,22 +307,37 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
             const float2* pfa = tab + b * S::kTab;
             const float2* wa = pfa + M;
             const float2* fra = pfa + 2 * M;   // fringe phasors of the CTA's frames
+            const bool detect = a == p.n_ant - 1;   // this polarisation's coherent sums are complete
             // every lane computes (the FP32 stores trade values between lanes, and `live` is not
             // warp-uniform when a warp spans several frame groups); only live lanes write
             constexpr int PG = TB / 2;
             const int Gr = (2 * i) >> 3, sgr = Gr & 7;
             const int pstart = Gr * 8 * TB + ((((i & 3) ^ (sgr / PG)) * PG) << 2);   // floats from the block start
-            auto emit = [&](int c, const float2 (&yc)[L]) {
+            // y of frame l, channel slot: real / imaginary part
+            auto comp = [](const float2 (&v)[LP], int l) { return (l & 1) ? v[l >> 1].y : v[l >> 1].x; };
+            auto emit = [&](int c, const float2 (&yr)[LP], const float2 (&yi)[LP]) {
                 const float2 w = wa[chs[c]];
+                const float2 wx = make_float2(w.x, w.x), wy = make_float2(w.y, w.y), nwy = make_float2(-w.y, -w.y);
 #pragma unroll
-                for (int l = 0; l < L; ++l) {
-                    incr[l][c] += g2 * (yc[l].x * yc[l].x + yc[l].y * yc[l].y);
-                    const float2 prev = (a == 0) ? make_float2(0.0f, 0.0f) : cohr[l][c];
-                    cohr[l][c] = cadd(prev, cmul(w, yc[l]));
-                    if (live && a == p.n_ant - 1) {   // this polarisation's coherent sum is complete: detect
-                        float* bc = p.beams + (static_cast<int64_t>(p.n_int) + t0 + fg * L + l) * M + chs[c];
-                        const float pw = cohr[l][c].x * cohr[l][c].x + cohr[l][c].y * cohr[l][c].y;
-                        *bc = (pol == 0) ? pw : *bc + pw;
+                for (int j = 0; j < LP; ++j) {
+                    incr[j][c] = __ffma2_rn(g22, __ffma2_rn(yr[j], yr[j], __fmul2_rn(yi[j], yi[j])), incr[j][c]);
+                    cre[j][c] = __ffma2_rn(nwy, yi[j], __ffma2_rn(wx, yr[j], cre[j][c]));
+                    cim[j][c] = __ffma2_rn(wy, yr[j], __ffma2_rn(wx, yi[j], cim[j][c]));
+                }
+                if (detect) {                  // detect, add the polarisations, start the next sum
+#pragma unroll
+                    for (int j = 0; j < LP; ++j) {
+                        const float2 pw = __ffma2_rn(cim[j][c], cim[j][c], __fmul2_rn(cre[j][c], cre[j][c]));
+                        cre[j][c] = make_float2(0.0f, 0.0f);
+                        cim[j][c] = make_float2(0.0f, 0.0f);
+                        if (live) {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                float* bc = p.beams + (static_cast<int64_t>(p.n_int) + t0 + fg * L + 2 * j + h) * M + chs[c];
+                                const float v = h ? pw.y : pw.x;
+                                *bc = (pol == 0) ? v : *bc + v;
+                            }
+                        }
                     }
                 }
                 if constexpr (MODE == OUT_F32Q) {
@@ -324,10 +346,10 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
                     float* o = static_cast<float*>(p.spec) + f32q_piece(chs[c], kb_run, i, ntb, p.n_in);
                     uint32_t u[8];
 #pragma unroll
-                    for (int l = 0; l < 8; ++l) u[l] = __float_as_uint(yc[l].x);
+                    for (int l = 0; l < 8; ++l) u[l] = __float_as_uint(comp(yr, l));
                     if (live) st_global_v8(o, u);
 #pragma unroll
-                    for (int l = 0; l < 8; ++l) u[l] = __float_as_uint(yc[l].y);
+                    for (int l = 0; l < 8; ++l) u[l] = __float_as_uint(comp(yi, l));
                     if (live) st_global_v8(o + 8, u);
                 } else if constexpr (MODE == OUT_FP32) {
                     // 64-byte piece of (channel, input): granule slot (2 comp + half) ^ (sgr & 3); each lane
@@ -341,8 +363,8 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
                     float mine[8], recv[8];
 #pragma unroll
                     for (int l = 0; l < 8; ++l) {
-                        const float own_keep = (odd ? 1 - cA : cA) ? yc[l].y : yc[l].x;
-                        const float own_send = csend ? yc[l].y : yc[l].x;
+                        const float own_keep = (odd ? 1 - cA : cA) ? comp(yi, l) : comp(yr, l);
+                        const float own_send = csend ? comp(yi, l) : comp(yr, l);
                         mine[l] = own_keep;
                         recv[l] = __shfl_xor_sync(0xffffffffu, own_send, 1);
                     }
@@ -368,7 +390,7 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
                     __half hr[L], hi[L];
 #pragma unroll
                     for (int l = 0; l < L; ++l) {
-                        const float xr = yc[l].x * scv[c], xi = yc[l].y * scv[c];
+                        const float xr = comp(yr, l) * scv[c], xi = comp(yi, l) * scv[c];
                         if constexpr (MODE == OUT_I8) {
                             hr[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xr))));
                             hi[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xi))));
@@ -390,36 +412,55 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
             };
             // ---- real split and Eq. 2 phasor.  With zk = Z[k], zm = Z[M - k]:
             //   2 X[k] = E + Q, 2 X[M - k] = conj(E - Q), E = zk + conj(zm), Q = (-i W_N^k)(zk - conj(zm));
-            //   Y = X pf fr = (2 X) (pf / 2) fr.  Pair 0: 2 X[0] = 2 (Re + Im of Z[0]), 2 X[M/2] = 2 conj(Z[M/2]).
+            //   Y = X pf fr = ((2 X) (pf / 2)) fr.  Pair 0: 2 X[0] = 2 (Re + Im of Z[0]), 2 X[M/2] = 2 conj(Z[M/2]).
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int k = chs[2 * q], kc = chs[2 * q + 1];
                 const float2 hk = pfa[k], hm = pfa[kc];
-                const float2 pk = make_float2(0.5f * hk.x, 0.5f * hk.y), pm = make_float2(0.5f * hm.x, 0.5f * hm.y);
-                float2 yk[L], ym[L];
+                const float2 pkx = make_float2(0.5f * hk.x, 0.5f * hk.x), pky = make_float2(0.5f * hk.y, 0.5f * hk.y);
+                const float2 npky = make_float2(-0.5f * hk.y, -0.5f * hk.y);
+                const float2 pmx = make_float2(0.5f * hm.x, 0.5f * hm.x), pmy = make_float2(0.5f * hm.y, 0.5f * hm.y);
+                const float2 npmy = make_float2(-0.5f * hm.y, -0.5f * hm.y);
+                float2 ykr[LP], yki[LP], ymr[LP], ymi[LP];
 #pragma unroll
-                for (int l = 0; l < L; ++l) {
-                    const int fl = fg * L + l;
-                    const float2* Xl = Xi + (fl / G) * P::REG + (fl % G) * P::S;
-                    const float2 zk = Xl[k];
-                    const float2 zm = Xl[kc];
-                    float2 xk, xmk;
-                    if (q == 0 && k == 0) {
-                        xk = make_float2(2.0f * (zk.x + zk.y), 0.0f);       // DC
-                        xmk = make_float2(2.0f * zm.x, -2.0f * zm.y);       // channel M/2 (zm = Z[M/2])
+                for (int j = 0; j < LP; ++j) {
+                    const int f0 = fg * L + 2 * j, f1 = f0 + 1;
+                    const float2* X0 = Xi + (f0 / G) * P::REG + (f0 % G) * P::S;
+                    const float2* X1 = Xi + (f1 / G) * P::REG + (f1 % G) * P::S;
+                    const float2 a0 = X0[k], a1 = X1[k], b0 = X0[kc], b1 = X1[kc];
+                    const float2 zkr = make_float2(a0.x, a1.x), zki = make_float2(a0.y, a1.y);
+                    const float2 zmr = make_float2(b0.x, b1.x), zmi = make_float2(b0.y, b1.y);
+                    float2 xkr, xki, xmr, xmi;     // 2 X[k], 2 X[M - k]
+                    if (q == 0 && ps == 0) {
+                        xkr = __fmul2_rn(make_float2(2.0f, 2.0f), __fadd2_rn(zkr, zki));     // DC
+                        xki = make_float2(0.0f, 0.0f);
+                        xmr = __fmul2_rn(make_float2(2.0f, 2.0f), zmr);                     // channel M/2
+                        xmi = __fmul2_rn(make_float2(-2.0f, -2.0f), zmi);
                     } else {
-                        const float2 E = make_float2(zk.x + zm.x, zk.y - zm.y);
-                        const float2 D = make_float2(zk.x - zm.x, zk.y + zm.y);
-                        const float2 Q = cmul(wn[q], D);
-                        xk = make_float2(E.x + Q.x, E.y + Q.y);
-                        xmk = make_float2(E.x - Q.x, Q.y - E.y);
+                        const float2 er = __fadd2_rn(zkr, zmr), ei = psub(zki, zmi);
+                        const float2 dr = psub(zkr, zmr), di = __fadd2_rn(zki, zmi);
+                        const float2 qr = __ffma2_rn(nwny[q], di, __fmul2_rn(wnx[q], dr));
+                        const float2 qi = __ffma2_rn(wny[q], dr, __fmul2_rn(wnx[q], di));
+                        xkr = __fadd2_rn(er, qr);
+                        xki = __fadd2_rn(ei, qi);
+                        xmr = psub(er, qr);
+                        xmi = psub(qi, ei);
                     }
-                    const float2 fr = fra[fl];
-                    yk[l] = cmul(xk, cmul(pk, fr));
-                    ym[l] = cmul(xmk, cmul(pm, fr));
+                    // u = (2 X) (pf / 2), then y = u fr
+                    const float2 ukr = __ffma2_rn(npky, xki, __fmul2_rn(pkx, xkr));
+                    const float2 uki = __ffma2_rn(pky, xkr, __fmul2_rn(pkx, xki));
+                    const float2 umr = __ffma2_rn(npmy, xmi, __fmul2_rn(pmx, xmr));
+                    const float2 umi = __ffma2_rn(pmy, xmr, __fmul2_rn(pmx, xmi));
+                    const float2 r0 = fra[f0], r1 = fra[f1];
+                    const float2 frr = make_float2(r0.x, r1.x), fri = make_float2(r0.y, r1.y);
+                    const float2 nfri = make_float2(-r0.y, -r1.y);
+                    ykr[j] = __ffma2_rn(uki, nfri, __fmul2_rn(ukr, frr));
+                    yki[j] = __ffma2_rn(uki, frr, __fmul2_rn(ukr, fri));
+                    ymr[j] = __ffma2_rn(umi, nfri, __fmul2_rn(umr, frr));
+                    ymi[j] = __ffma2_rn(umi, frr, __fmul2_rn(umr, fri));
                 }
-                emit(2 * q, yk);
-                emit(2 * q + 1, ym);
+                emit(2 * q, ykr, yki);
+                emit(2 * q + 1, ymr, ymi);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl.empty[b]);   // region set b and tables b may be reused
@@ -430,7 +471,7 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
             for (int l = 0; l < L; ++l)
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                    p.beams[static_cast<int64_t>(t0 + fg * L + l) * M + chs[c]] = incr[l][c];
+                    p.beams[static_cast<int64_t>(t0 + fg * L + l) * M + chs[c]] = (l & 1) ? incr[l >> 1][c].y : incr[l >> 1][c].x;
         }
     }
 }
