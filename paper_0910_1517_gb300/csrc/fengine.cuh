@@ -128,6 +128,15 @@ __host__ __device__ inline void fengine_tw_angle(int n_fft, int e, double& num, 
 }
 cudaError_t launch_fengine_twiddles(int n_fft, float2* tw, cudaStream_t s);
 
+// int8 pair (x[2n], x[2n+1]) as the complex sample z[n], without the conversion unit: each byte
+// b, offset to b + 128 (sign bit flipped), becomes the low byte of the float 2^23 + b + 128
+// (exponent byte 0x4B), and one packed subtraction of 2^23 + 128 leaves b exactly
+__device__ __forceinline__ float2 pair_u16(uint32_t w) {
+    const uint32_t x = w ^ 0x8080u;
+    const uint32_t lo = __byte_perm(x, 0x4B000000u, 0x7440), hi = __byte_perm(x, 0x4B000000u, 0x7441);
+    return __fadd2_rn(make_float2(__uint_as_float(lo), __uint_as_float(hi)), make_float2(-8388736.0f, -8388736.0f));
+}
+
 // The per-antenna delay model (Sec. 2.1, Eq. 2), shared by every table set-up:
 // integer delay D = floor(tau + 1/2), fractional-delay (FSTC) phasor exp(+2 pi i k tau_f / N)
 // with tau_f = tau - D, fringe phasor exp(-i phi) with phi = phi0 + rate g over the global frame

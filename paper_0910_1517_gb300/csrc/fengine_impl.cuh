@@ -305,16 +305,13 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
                 const uint16_t* st16 = reinterpret_cast<const uint16_t*>(st);
 #pragma unroll
                 for (int r = 0; r < kE; ++r) {
-                    const uint16_t w = st16[t + r * NB];
-                    v[r] = make_float2(static_cast<float>(static_cast<signed char>(w & 0xff)),
-                                       static_cast<float>(static_cast<signed char>(w >> 8)));
+                    v[r] = pair_u16(st16[t + r * NB]);
                 }
             } else {
 #pragma unroll
                 for (int r = 0; r < kE; ++r) {
                     const int n = t + r * NB;
-                    v[r] = make_float2(static_cast<float>(static_cast<signed char>(st[2 * n])),
-                                       static_cast<float>(static_cast<signed char>(st[2 * n + 1])));
+                    v[r] = pair_u16(st[2 * n] | (static_cast<uint32_t>(st[2 * n + 1]) << 8));
                 }
             }
             Dft<16>::template run<1>(v);

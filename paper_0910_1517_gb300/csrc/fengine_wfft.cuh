@@ -6,14 +6,14 @@
 // halves of the work in flight at once:
 //   * a CTA owns F = 8192 / M consecutive frames and walks over every input (the beams need
 //     every antenna of a frame in one CTA);
-//   * warps 0-7 (the FFT group, 96 registers a thread) transform the frames of input it:
+//   * warps 0-7 (the FFT group, 104 registers a thread) transform the frames of input it:
 //     the M-point complex FFT of a frame (z[n] = x[2n] + i x[2n+1], M = 32 P) is a four-step
 //     FFT inside one warp -- lane l takes column n = l + 32 m of each of the warp's G = 32 / P
 //     frames, P-point DFTs in registers straight from the int8 staging buffer, the twiddle
 //     W_M^(l k1), one transpose through the warp's own shared-memory region (__syncwarp), then
 //     lane (g, k1) a 32-point DFT in registers: Z[k1 + P k2] -- and leave the results in the
 //     region in natural order;
-//   * warps 8-15 (the epilogue group, 160 registers a thread) meanwhile take input it - 1: each
+//   * warps 8-15 (the epilogue group, 152 registers a thread) meanwhile take input it - 1: each
 //     thread owns 8 frames of two channel pairs (k, M - k) for the real split, the Eq. 2 phasor,
 //     the beams (accumulated in its registers over all inputs) and the K-block stores;
 //   * the regions, the antenna tables and the staging buffer are double-buffered; mbarriers
@@ -30,7 +30,7 @@ namespace {
 constexpr int kWThreads = 512;
 constexpr int kWFftWarps = 8;                  // warps 0-7: FFT group (warpgroups 0, 1)
 constexpr int kWEpiThreads = 256;              // warps 8-15: epilogue group (warpgroups 2, 3)
-constexpr int kWRegFft = 96, kWRegEpi = 160;   // 256 x 96 + 256 x 160 = 512 x 128 registers
+constexpr int kWRegFft = 104, kWRegEpi = 152;  // 256 x 104 + 256 x 152 = 512 x 128 registers
 
 template <int M>
 struct WPlan {
@@ -72,12 +72,6 @@ struct WCtl {
     int abort_flag;
     int Ds[kMaxAnt];
 };
-
-// int8 pair (x[2n], x[2n+1]) as the complex sample z[n]
-__device__ __forceinline__ float2 pair_u16(uint32_t w) {
-    return make_float2(static_cast<float>(static_cast<signed char>(w & 0xffu)),
-                       static_cast<float>(static_cast<signed char>((w >> 8) & 0xffu)));
-}
 
 template <int N_REG>
 __device__ __forceinline__ void reg_dealloc() { asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N_REG)); }
@@ -199,8 +193,7 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
 #pragma unroll
                     for (int m = 0; m < PP; ++m) {
                         const unsigned char* q = st + g * N + 2 * (lane + 32 * m);
-                        v[g * PP + m] = make_float2(static_cast<float>(static_cast<signed char>(q[0])),
-                                                    static_cast<float>(static_cast<signed char>(q[1])));
+                        v[g * PP + m] = pair_u16(q[0] | (static_cast<uint32_t>(q[1]) << 8));
                     }
             }
             // the twiddle W_M^(l k1), k1 >= 1 (pairs of k1 in one 16-byte load), then the transpose

@@ -49,39 +49,51 @@ __device__ __forceinline__ float2 twiddle_const(float2 o) {
     }
 }
 
-// In-register forward DFT of R points (radix-2 recursion, natural-order output).
+// In-register forward DFT of R points, natural order in and out: radix-2 decimation in time,
+// written stage by stage (inputs in bit-reversed order, then log2 R stages of R/2 butterflies),
+// so that every stage offers R/2 independent butterflies to the instruction scheduler.  Stage H
+// joins the H-point DFTs of the even- and odd-indexed points into 2H-point ones:
+// out[j] = E[j] + W_2H^j O[j], out[j + H] = E[j] - W_2H^j O[j].
 template <int R>
 struct Dft {
+    static constexpr int brev(int i) {
+        int r = 0;
+        for (int b = 1; b < R; b <<= 1) {
+            r = (r << 1) | (i & 1);
+            i >>= 1;
+        }
+        return r;
+    }
     template <int S>
     __device__ __forceinline__ static void run(float2* v) {
         // v[0], v[S], v[2S], ... hold the R inputs; transform in place
-        Dft<R / 2>::template run<2 * S>(v);      // evens
-        Dft<R / 2>::template run<2 * S>(v + S);  // odds
-        float2 out[R];
+        float2 u[R];
 #pragma unroll
-        for (int k = 0; k < R / 2; ++k) {
-            out[k] = v[2 * S * k];
-            out[k + R / 2] = v[2 * S * k + S];
-        }
-        apply<0>(out);
+        for (int i = 0; i < R; ++i) u[i] = v[S * brev(i)];
+        stage<1>(u);
 #pragma unroll
-        for (int k = 0; k < R; ++k) v[S * k] = out[k];
+        for (int k = 0; k < R; ++k) v[S * k] = u[k];
     }
-    template <int K>
-    __device__ __forceinline__ static void apply(float2* out) {
-        if constexpr (K < R / 2) {
-            const float2 e = out[K];
-            const float2 t = twiddle_const<R, K>(out[K + R / 2]);
-            out[K] = padd(e, t);
-            out[K + R / 2] = psub(e, t);
-            apply<K + 1>(out);
+    template <int H>
+    __device__ __forceinline__ static void stage(float2* u) {
+        if constexpr (H < R) {
+            bfly<H, 0>(u);
+            stage<2 * H>(u);
         }
     }
-};
-template <>
-struct Dft<1> {
-    template <int S>
-    __device__ __forceinline__ static void run(float2*) {}
+    template <int H, int J>
+    __device__ __forceinline__ static void bfly(float2* u) {
+        if constexpr (J < H) {
+#pragma unroll
+            for (int blk = 0; blk < R; blk += 2 * H) {
+                const float2 e = u[blk + J];
+                const float2 t = twiddle_const<2 * H, J>(u[blk + J + H]);
+                u[blk + J] = padd(e, t);
+                u[blk + J + H] = psub(e, t);
+            }
+            bfly<H, J + 1>(u);
+        }
+    }
 };
 
 // barrier among the T threads of one FFT group (group g); a warp when T <= 32
