@@ -72,7 +72,10 @@ std::vector<int4> make_items(const corr_batch* b, int only_sub) {
 void fill_xt(corr_batch* b, XtBatch* t, const int4* items, int n_items) {
     std::memset(t, 0, sizeof *t);
     t->n_sub = b->n_sub;
-    for (int s = 0; s < b->n_sub; ++s) t->sub[s] = xt_sub_of(b->h[s]);
+    for (int s = 0; s < b->n_sub; ++s) {
+        t->sub[s] = xt_sub_of(b->h[s]);
+        t->sub[s].in8 = 0;   // the batched F-engine writes int8 values in the fp16 layout
+    }
     t->n_items = n_items;
     t->items = items;
     t->err = b->h[0]->d_err;
@@ -275,6 +278,8 @@ int corr_batch_integrate_device(corr_batch_t* b, const int8_t* const* x, const i
         BCU(cudaEventRecord(h->ev_done, s));
         h->launched += 1;
         h->last_mode = h->xmode;
+        h->last_quad = false;   // the batched F-engine writes the plain K-block layouts
+        h->last_i8b = false;
     }
     return CORR_OK;
 }

@@ -111,7 +111,7 @@ bool spec_quad(const corr* h) { return h->xmode == CORR_FP32TC && h->n_chan <= 1
 // F-engine output mode of a handle's X-engine precision mode
 int fe_mode(const corr* h) {
     switch (h->xmode) {
-        case CORR_I8: return OUT_I8;
+        case CORR_I8: return h->n_chan <= 1024 ? OUT_I8B : OUT_I8;   // int8 bytes where the warp-FFT kernel runs
         case CORR_F16: return OUT_F16;
         default: return spec_quad(h) ? OUT_F32Q : OUT_FP32;
     }
@@ -183,6 +183,7 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
                            static_cast<size_t>(h->n_chan) * h->n_int * rows_fp32(h->n_in) * sizeof(float), s));
     }
     h->last_quad = fmode == OUT_F32Q;
+    h->last_i8b = fmode == OUT_I8B;
     if (int rc = mark(h, 1, s)) return rc;
     if (h->blank_M > 0.0) {   // voltage blanker: per-block statistics of every sample the F-engine reads
         const int64_t need = static_cast<int64_t>(h->n_int) * h->n_fft + max_int_delay(h);
@@ -217,7 +218,7 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
         CU(launch_xengine_fp32(xp, h->n_sm, s));
     else
         CU(launch_xengine_tc_table(h->out_buf == 1 ? h->xtab_b1 : h->d_xtab, h->n_items, h->n_sm, s,
-                                   h->xmode == CORR_FP32TC));
+                                   h->xmode == CORR_FP32TC ? XT_FORM_F32 : fmode == OUT_I8B ? XT_FORM_I8 : XT_FORM_F16));
     if (h->dump > 0) {
         CU(launch_power_dumps(static_cast<const float*>(h->d_spec), h->n_in, h->n_chan, h->n_int, h->dump,
                               h->d_power, s, fmode == OUT_F32Q));
@@ -260,6 +261,7 @@ gbx::XtSub gbx::xt_sub_of(const corr* h) {
         const int max_ks = xengine_tc_max_ks(h->n_in);
         x.ks = h->ks > 0 ? std::min(h->ks, max_ks) : max_ks;
         x.chunk = 1024;
+        x.in8 = fe_mode(h) == OUT_I8B ? 1 : 0;
     }
     return x;
 }
@@ -277,8 +279,8 @@ int upload_xtab(corr* h) {
     t.n_items = h->n_items;
     t.items = h->d_items;
     t.err = h->d_err;
-    if (t.sub[0].quad && !xengine_tc_encode_quad(t.sub[0]))
-        return fail(CORR_E_CUDA, "the driver refused the tensor map of the FP32 spectra");
+    if ((t.sub[0].quad || t.sub[0].in8) && !xengine_tc_encode_quad(t.sub[0]))
+        return fail(CORR_E_CUDA, "the driver refused the tensor map of the spectra");
     CU(cudaDeviceSynchronize());
     if (h->xtab_b1) {                    // double-buffered outputs: one table per buffer
         t.sub[0].vis = h->vis_b[0];
@@ -901,18 +903,38 @@ int corr_read_requant(corr_t* h, int k0, int nk, int8_t* q, float* scale) {
         CU(cudaMemcpy(scale, h->d_scale, static_cast<size_t>(h->n_in) * h->n_chan * sizeof(float),
                       cudaMemcpyDeviceToHost));
     if (q && nk > 0) {
+        // int8 bytes in the channel-quad layout (OUT_I8B: i8q_piece), or int8 values in the fp16
+        // K-block layout [k][kb][r][8] (OUT_I8)
+        const bool bytes = h->last_i8b;
         const int R = 2 * h->n_in, ntb = h->n_int / kTbHalf;
         const size_t per_ch = static_cast<size_t>(ntb) * R * kTbHalf;
-        std::vector<__half> buf(per_ch * nk);
-        CU(cudaMemcpy(buf.data(), static_cast<const __half*>(h->d_spec) + per_ch * k0, buf.size() * sizeof(__half),
-                      cudaMemcpyDeviceToHost));
+        std::vector<__half> buf(bytes ? 0 : per_ch * nk);
+        std::vector<int8_t> buf8;
+        int q0 = 0;                                        // first channel quad copied
+        if (bytes) {
+            q0 = k0 / 4;
+            const int q1 = (k0 + nk + 3) / 4;
+            buf8.resize(per_ch * 4 * (q1 - q0));
+            CU(cudaMemcpy(buf8.data(), static_cast<const int8_t*>(h->d_spec) + per_ch * 4 * q0, buf8.size(),
+                          cudaMemcpyDeviceToHost));
+        } else {
+            CU(cudaMemcpy(buf.data(), static_cast<const __half*>(h->d_spec) + per_ch * k0, buf.size() * sizeof(__half),
+                          cudaMemcpyDeviceToHost));
+        }
         for (int c = 0; c < nk; ++c)
             for (int kb = 0; kb < ntb; ++kb)
                 for (int r = 0; r < R; ++r)
                     for (int e = 0; e < kTbHalf; ++e) {
-                        const float v = __half2float(buf[((static_cast<size_t>(c) * ntb + kb) * R + r) * kTbHalf + e]);
                         const int i = r / 2, cc = r % 2, t = kb * kTbHalf + e;
-                        q[((static_cast<size_t>(i) * h->n_int + t) * nk + c) * 2 + cc] = static_cast<int8_t>(v);
+                        int8_t v;
+                        if (bytes) {
+                            const int k = k0 + c;
+                            v = buf8[i8q_piece(k - 4 * q0, kb, i, ntb, h->n_in) + cc * kTbHalf + e];
+                        } else {
+                            v = static_cast<int8_t>(
+                                __half2float(buf[((static_cast<size_t>(c) * ntb + kb) * R + r) * kTbHalf + e]));
+                        }
+                        q[((static_cast<size_t>(i) * h->n_int + t) * nk + c) * 2 + cc] = v;
                     }
     }
     return CORR_OK;

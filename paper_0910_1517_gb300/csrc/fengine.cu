@@ -119,6 +119,7 @@ cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s) {
         case OUT_I8: return launch_w_mode<OUT_I8>(p, s);
         case OUT_F16: return launch_w_mode<OUT_F16>(p, s);
         case OUT_F32Q: return launch_w_mode<OUT_F32Q>(p, s);
+        case OUT_I8B: return launch_w_mode<OUT_I8B>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -8,13 +8,16 @@
 
 namespace gbx {
 
-enum OutMode : int { OUT_FP32 = 0, OUT_I8 = 1, OUT_F16 = 2, OUT_F32Q = 3 };
+enum OutMode : int { OUT_FP32 = 0, OUT_I8 = 1, OUT_F16 = 2, OUT_F32Q = 3, OUT_I8B = 4 };
 
 // Spectra hand-off layout ("K-block layout"), shared by every X-engine:
 //   S[k][kb][r][TB]   k channel, kb = t / TB, r = 2*i + c (c = 0 re, 1 im), TB = t % TB
 // One (k, kb) block holds every input's rows for TB consecutive frames.
 // fp16 (tensor-core X-engine): TB = 8, R = 2 n_in unswizzled rows of 16 bytes -- exactly
-// the no-swizzle K-major canonical layout of a tcgen05 operand tile.
+// the no-swizzle K-major canonical layout of a tcgen05 operand tile.  OUT_I8 writes the int8
+// requantised values in this fp16 layout; OUT_I8B (n_chan <= 1024) writes them as bytes in the
+// channel-quad arrangement (i8q_piece) that the X-engine gathers by TMA into [kb][r][8 bytes]
+// and widens to fp16 on chip.
 // FP32 (CUDA-core X-engine): TB = tb_fp32(n_chan) = 8 frames (4 when an F-engine CTA covers
 // only 4 frames, n_chan = 2048), rows padded to Rp = round_up(2 n_in, 8).  The block is cut
 // into 16-byte granules of 4 frames of one row, 8 rows (one input group of 4) per row group
@@ -44,6 +47,12 @@ __host__ __device__ constexpr int fp32_off(int r, int e, int tb) {
 // gather that one 5-D TMA tensor copy performs ([kb][i][16] = [kb][row 2i + c][8 frames]).
 __host__ __device__ constexpr int64_t f32q_piece(int k, int64_t kb, int i, int64_t ntb, int n_in) {
     return (((static_cast<int64_t>(k) >> 2) * ntb + kb) * n_in + i) * 64 + (k & 3) * 16;
+}
+// The same channel-quad arrangement for the int8 bytes of OUT_I8B: the piece of (k, kb, i) -- 8 re
+// then 8 im bytes, 16 bytes -- at byte offset (((k / 4) * ntb + kb) * n_in + i) * 64 + (k % 4) * 16,
+// so that four consecutive channels' pieces make whole 64-byte runs.
+__host__ __device__ constexpr int64_t i8q_piece(int k, int64_t kb, int i, int64_t ntb, int n_in) {
+    return f32q_piece(k, kb, i, ntb, n_in);
 }
 
 struct FeParams {

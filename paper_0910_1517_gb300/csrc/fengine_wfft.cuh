@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
             const float g2 = p.ginc[a];
             const float2 g22 = make_float2(g2, g2);
             float scv[4];                      // requantisation scales of this thread's channels
-            if constexpr (MODE == OUT_I8 || MODE == OUT_F16) {
+            if constexpr (MODE == OUT_I8 || MODE == OUT_F16 || MODE == OUT_I8B) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) scv[c] = p.scale[static_cast<int64_t>(i) * M + chs[c]];
             }
@@ -344,6 +344,24 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
 #pragma unroll
                     for (int l = 0; l < 8; ++l) u[l] = __float_as_uint(comp(yi, l));
                     if (live) st_global_v8(o + 8, u);
+                } else if constexpr (MODE == OUT_I8B) {
+                    // rows 2i (real) and 2i + 1 (imaginary) of the K-block, 8 int8 frames each: one
+                    // 16-byte piece of the channel-quad byte layout (the lanes of consecutive channels
+                    // fill whole 64-byte runs)
+                    uint32_t w[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {   // h = 2 comp + half: frames 4 (h & 1) .. + 3
+                        int qv[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int l = 4 * (h & 1) + e;
+                            const float x = ((h >> 1) ? comp(yi, l) : comp(yr, l)) * scv[c];
+                            qv[e] = max(-127, min(127, __float2int_rn(x)));
+                        }
+                        w[h] = __byte_perm(__byte_perm(qv[0], qv[1], 0x0040), __byte_perm(qv[2], qv[3], 0x0040), 0x5410);
+                    }
+                    int8_t* o = static_cast<int8_t*>(p.spec) + i8q_piece(chs[c], kb_run, i, ntb, p.n_in);
+                    if (live) *reinterpret_cast<uint4*>(o) = make_uint4(w[0], w[1], w[2], w[3]);
                 } else if constexpr (MODE == OUT_FP32) {
                     // 64-byte piece of (channel, input): granule slot (2 comp + half) ^ (sgr & 3); each lane
                     // pair writes one piece per instruction, trading the component each needs by a shuffle
@@ -490,7 +508,7 @@ cudaError_t launch_w(const FeParams& p, cudaStream_t s) {
 
 template <int MODE>
 cudaError_t launch_w_mode(const FeParams& p, cudaStream_t s) {
-    if constexpr (MODE == OUT_F32Q) {   // the channel-quad layout: n_chan 32 .. 1024 only
+    if constexpr (MODE == OUT_F32Q || MODE == OUT_I8B) {   // n_chan 32 .. 1024 only
         switch (p.n_chan) {
             case 32: return launch_w<32, MODE>(p, s);
             case 64: return launch_w<64, MODE>(p, s);

@@ -40,6 +40,9 @@ struct alignas(64) XtSub {
     CUtensorMap tmap;
     int quad;
     const __half* spec;    // [k][kb][2 n_in][8] fp16 K-block layout
+    // in8 = 1: spec holds the same layout in int8 bytes (rows of 8 bytes, the F-engine's OUT_I8B);
+    // each stage lands in an input slot and converter warps widen it to the fp16 operand tile
+    int in8;
     int n_ant, n_pol, n_in, n_chan, n_int;
     const float* scale;    // [n_in][n_chan]
     float2* vis;           // [n_chan][n_bl][n_pol^2]
@@ -56,7 +59,7 @@ struct alignas(64) XtSub {
     int chunk;             // frames per TMEM accumulation chunk: power of two, multiple of ks
     int self;              // self-polar mode: only products pp are written, vis [n_chan][n_bl][n_pol]
 };
-struct XtBatch {          // (the FP32 form, spec32 set, runs alone: launch with fp32_in)
+struct XtBatch {          // (the converted forms, spec32 or in8 set, run alone: launch with their form)
     int n_sub;
     XtSub sub[kMaxSubX];
     int n_items;
@@ -70,6 +73,9 @@ bool xengine_tc_supported(int n_in);                 // 2 n_in <= 256
 int xengine_tc_max_ks(int n_in);                      // largest fp16 stage for the row count
 int xengine_tc_ks_fp32(int n_in);                     // largest FP32-form stage (FP32 slot <= kStage2Bytes)
 size_t xengine_tc_smem();
-cudaError_t launch_xengine_tc_table(const XtBatch* dtab, int n_items, int n_sm, cudaStream_t s, bool fp32_in = false);
+// form of every sub-array of the table: one fp16 plane (XT_FORM_F16), FP32 split on chip (spec32,
+// XT_FORM_F32) or int8 bytes widened on chip (in8, XT_FORM_I8)
+enum XtForm : int { XT_FORM_F16 = 0, XT_FORM_F32 = 1, XT_FORM_I8 = 2 };
+cudaError_t launch_xengine_tc_table(const XtBatch* dtab, int n_items, int n_sm, cudaStream_t s, int form = XT_FORM_F16);
 
 }  // namespace gbx

@@ -19,8 +19,8 @@
 // tcgen05.mma from one thread.  One-plane forms (10 warps): warps 2-9 drain the
 // accumulators (warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. Gram rows, and
 // the column half (w - 2) / 4 of them; 168 registers a thread hold the running
-// sums).  FP32 form (16 warps, 128 registers): warps 2-5 drain (all columns of
-// their lanes, running sums in TMEM), warps 6-15 convert the FP32 stages.
+// sums).  Converted forms (FP32 split, int8 bytes; 16 warps, 128 registers): warps 2-5 drain
+// (all columns of their lanes, running sums in TMEM), warps 6-15 convert the input stages.
 // Accumulation is chunked: every `chunk` frames the FP32 accumulator is drained
 // and added into a running sum.  Items with N <= 128 rotate over four 128-column
 // accumulators (the MMAs run up to three chunks ahead of the drain) and keep the
@@ -30,6 +30,12 @@
 // integer of magnitude at most 127^2 = 16129 and a chunk sum at most 1024 * 16129 =
 // 16,516,096 < 2^24, so the FP32 accumulator is exact and the running sum is kept
 // as int32: the result equals the integer MAC.
+//
+// int8 form with byte operands (in8): the F-engine wrote the int8 values as bytes, so each stage
+// lands in an input slot at half the fp16 size and the converter warps of the FP32 form widen it
+// to the fp16 operand tile (exact: the fp16 bits 0x6400 | (b ^ 0x80) hold 1152 + b, one packed
+// subtraction leaves b); one MMA per 16-frame step, chunks of 1024 frames over three rotating
+// accumulators, int32 running sums in TMEM.
 //
 // FP32 form: the stages hold FP32 spectra in the CUDA-core engine's layout; ten
 // converter warps split each FP32 value v (scaled by a power of two) into fp16
@@ -69,8 +75,15 @@ constexpr int kTailSlack = 32768;
 // kStage2Bytes + (128 - 64) * 16 (R < 64 leaves more room).
 constexpr int kOpStages2 = 2;                 // operand slots ...
 constexpr int kF32Stages = 5;                 // ... and the FP32 slots after them
+// int8 form: four operand slots, then five input slots of kStage2Bytes / 2 (an int8 stage is half
+// the size of its fp16 operand tile)
+constexpr int kOpStagesI8 = 4;
+constexpr int kRawI8 = 5;
+constexpr int kRawPitch = kStage2Bytes / 2;
+constexpr int kInSlots = kRawI8 > kF32Stages ? kRawI8 : kF32Stages;
 constexpr int kSlot2 = kStage2Bytes + 1024;
 constexpr int kSmemBytes = kOpStages2 * kSlot2 + kF32Stages * kStage2Bytes;
+static_assert(kOpStagesI8 <= kStages && kOpStagesI8 * kSlot2 + kRawI8 * kRawPitch <= kSmemBytes, "int8-form slots");
 static_assert(kStages * kSlot + kTailSlack <= kSmemBytes && kSmemBytes <= 227 * 1024 - 1024, "shared memory");
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColRun = 256;             // running-sum columns of wide items
@@ -82,8 +95,8 @@ constexpr int kXBit = 4;                      // the cross-term accumulator's pa
 struct Shared {
     uint64_t full[kStages];       // operand slot ready (bulk copy landed, or converted)
     uint64_t empty[kStages];      // operand slot consumed by the MMAs
-    uint64_t f32full[kF32Stages];   // FP32 slot landed
-    uint64_t f32empty[kF32Stages];  // FP32 slot converted
+    uint64_t f32full[kInSlots];     // input slot (FP32 or int8) landed
+    uint64_t f32empty[kInSlots];    // input slot converted
     uint64_t accf[kAccBufs];
     uint64_t acce[kAccBufs];
     uint64_t xf;                  // cross-term accumulator complete (MMA -> epilogue)
@@ -97,7 +110,8 @@ struct ItemGeo {
     int sub, k, a0, b0, N, R, ntb, n_stage, n_chunk, nkb_stage;
     int Rp, tb32, ntb32;   // FP32 form: padded rows, frames per FP32 K-block, FP32 K-blocks per channel
     bool dbl;      // N <= 128: rotating 128-column accumulators
-    bool sep;      // dbl and FP32 form: cross terms in their own accumulator, TMEM running sums
+    bool sep;      // dbl and a converted form: rotating chunk accumulators, TMEM running sums
+    bool cross;    // sep and FP32 form: the cross terms in their own accumulator
     int nbuf;      // accumulators the item rotates over
 };
 
@@ -115,8 +129,9 @@ __device__ __forceinline__ ItemGeo item_geo(const XtBatch& t, int it) {
     g.tb32 = tb_fp32(s.n_chan);
     g.ntb32 = s.n_int / g.tb32;
     g.dbl = g.N <= 128;
-    g.sep = g.dbl && s.spec32 != nullptr;
-    g.nbuf = !g.dbl ? 1 : (g.sep ? 2 : kAccBufs);
+    g.sep = g.dbl && (s.spec32 != nullptr || s.in8);
+    g.cross = g.sep && s.spec32 != nullptr;
+    g.nbuf = !g.dbl ? 1 : (g.sep ? (g.cross ? 2 : 3) : kAccBufs);
     g.ntb = s.n_int / kTbHalf;
     g.nkb_stage = s.ks / kTbHalf;
     g.n_stage = (s.n_int + s.ks - 1) / s.ks;
@@ -212,8 +227,10 @@ __device__ __forceinline__ void drain_wide(const XtSub& s, const ItemGeo ig, uin
     if (!last) tmem_wait_st();
 }
 
-// One chunk of an FP32-form narrow item (chunk accumulator b, cross terms at kColX, running
-// sums at kColRun2): running sums += chunk, or after the last chunk + cross terms -> written.
+// One chunk of a converted-form narrow item (chunk accumulator b, running sums at kColRun2; the
+// FP32 form's cross terms at kColX): running sums += chunk, or after the last chunk (+ cross
+// terms) -> written.  kExact (int8 form): exact int32 running sums.
+template <int kExact>
 __device__ __forceinline__ void drain_split(const XtSub& s, const ItemGeo ig, uint32_t tm, int row, int b, int chunk) {
     const bool last = chunk == ig.n_chunk - 1;
     for (int j0 = 0; j0 < ig.N; j0 += 16) {        // 16-column pieces: few registers beside the converters
@@ -222,14 +239,16 @@ __device__ __forceinline__ void drain_split(const XtSub& s, const ItemGeo ig, ui
         if (chunk > 0) tmem_ld16(tm + kColRun2 + j0, rs);
         tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 16; ++e) rs[e] = chunk_add(0, chunk > 0, rs[e], v[e]);
+        for (int e = 0; e < 16; ++e) rs[e] = chunk_add(kExact, chunk > 0, rs[e], v[e]);
         if (!last) {
             tmem_st16(tm + kColRun2 + j0, rs);
         } else {
-            tmem_ld16(tm + kColX + j0, v);
-            tmem_wait_ld();
+            if (ig.cross) {
+                tmem_ld16(tm + kColX + j0, v);
+                tmem_wait_ld();
 #pragma unroll
-            for (int e = 0; e < 16; ++e) rs[e] = chunk_add(0, true, rs[e], v[e]);
+                for (int e = 0; e < 16; ++e) rs[e] = chunk_add(0, true, rs[e], v[e]);
+            }
             write_piece<16>(s, ig, row, j0, rs);
         }
     }
@@ -300,7 +319,10 @@ __device__ __forceinline__ uint32_t drain_narrow(Shared& sh, const XtSub& s, con
 // slot and the operand slot (the decision is shared by a shuffle), the warp converts, fences its
 // shared stores for the tensor core's (async) proxy, and lane 0 arrives on both slots' barriers,
 // which complete after all kConvWarps warps.  No barrier spans warps.
+template <bool kIn8>
 __device__ __noinline__ void convert_stages(const XtBatch& t, Shared& sh, unsigned char* smem, int ct) {
+    constexpr int nop = kIn8 ? kOpStagesI8 : kOpStages2;      // operand slots
+    constexpr int nin = kIn8 ? kRawI8 : kF32Stages, pin = kIn8 ? kRawPitch : kStage2Bytes;   // input slots
     volatile int* abort_flag = &sh.abort_flag;
     const int lane = ct & 31;
     int g = 0;
@@ -311,17 +333,45 @@ __device__ __noinline__ void convert_stages(const XtBatch& t, Shared& sh, unsign
         const float sc = s.split_scale;
         const int lo_off = ig.nkb_stage * R * 16;
         for (int st = 0; st < ig.n_stage; ++st, ++g) {
-            const int fs = g % kF32Stages, os = g % kOpStages2;
+            const int fs = g % nin, os = g % nop;
             int ok = 1;
             if (lane == 0) {
-                ok = !*abort_flag && mbar_wait(&sh.f32full[fs], (g / kF32Stages) & 1, t.err, ERR_WAIT_STAGE) &&
-                     mbar_wait(&sh.empty[os], ((g / kOpStages2) & 1) ^ 1, t.err, ERR_WAIT_MMA);
+                ok = !*abort_flag && mbar_wait(&sh.f32full[fs], (g / nin) & 1, t.err, ERR_WAIT_STAGE) &&
+                     mbar_wait(&sh.empty[os], ((g / nop) & 1) ^ 1, t.err, ERR_WAIT_MMA);
                 if (!ok) *abort_flag = 1;
             }
             if (!__shfl_sync(0xffffffffu, ok, 0)) return;   // the same decision in the whole warp
             const int frames = min(s.ks, s.n_int - st * s.ks);
-            const float* src = reinterpret_cast<const float*>(smem + kOpStages2 * kSlot2 + fs * kStage2Bytes);
+            const float* src = reinterpret_cast<const float*>(smem + nop * kSlot2 + fs * pin);
             unsigned char* dst = smem + os * kSlot2;
+            if constexpr (kIn8) {
+                // the stage is [kb][R rows][8 frames] of int8: unit u = j R + r (8 bytes) becomes the
+                // 16-byte row r of K-block j of the fp16 operand tile
+                const int units = (frames / 8) * R;
+                const unsigned char* src8 = reinterpret_cast<const unsigned char*>(src);
+                const __half2 bias = __float2half2_rn(1152.0f);
+#pragma unroll 4
+                for (int u = ct; u < units; u += kConvThreads) {
+                    const uint2 q = *reinterpret_cast<const uint2*>(src8 + 8 * u);
+                    const uint32_t x[2] = {q.x ^ 0x80808080u, q.y ^ 0x80808080u};
+                    uint32_t w[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {   // bytes 2m, 2m + 1 -> fp16 1152 + b -> b
+                        const uint32_t hb = __byte_perm(x[m >> 1], 0x64646464u, (m & 1) ? 0x4342 : 0x4140);
+                        const __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&hb), bias);
+                        w[m] = *reinterpret_cast<const uint32_t*>(&v);
+                    }
+                    *reinterpret_cast<uint4*>(dst + 16 * u) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    if (ct == 0) sh.consumed = g + 1;
+                    mbar_arrive(&sh.f32empty[fs]);
+                    mbar_arrive(&sh.full[os]);
+                }
+                continue;
+            }
             if (s.quad) {
                 // the stage is [kb][R rows][8 frames]: unit u = (j R + r) 2 + h takes frames 4h .. 4h + 3 of
                 // row r in K-block j (one 16-byte load; consecutive units, consecutive bytes) and writes
@@ -418,8 +468,13 @@ __device__ __noinline__ void convert_stages(const XtBatch& t, Shared& sh, unsign
     }
 }
 
-template <bool kF32>
-__global__ void __launch_bounds__((kF32 ? kWarps2 : kWarps1) * 32, 1) xengine_tc_kernel(const XtBatch* __restrict__ tab) {
+// kForm: XT_FORM_F16 (one plane, copied straight into the operand slots), XT_FORM_F32 (FP32 split),
+// XT_FORM_I8 (int8 bytes widened); one instantiation per form keeps every role's branches static
+template <int kForm>
+__global__ void __launch_bounds__((kForm != XT_FORM_F16 ? kWarps2 : kWarps1) * 32, 1)
+    xengine_tc_kernel(const XtBatch* __restrict__ tab) {
+    constexpr bool kF32 = kForm != XT_FORM_F16;   // a converted form
+    constexpr bool kIn8 = kForm == XT_FORM_I8;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ Shared sh;
     const XtBatch& t = *tab;
@@ -430,7 +485,7 @@ __global__ void __launch_bounds__((kF32 ? kWarps2 : kWarps1) * 32, 1) xengine_tc
             mbar_init(&sh.full[s], kF32 ? kConvWarps : 1);   // converted by every converter warp, or one copy
             mbar_init(&sh.empty[s], 1);
         }
-        for (int s = 0; s < kF32Stages; ++s) {
+        for (int s = 0; s < kInSlots; ++s) {
             mbar_init(&sh.f32full[s], 1);
             mbar_init(&sh.f32empty[s], kConvWarps);
         }
@@ -458,11 +513,12 @@ __global__ void __launch_bounds__((kF32 ? kWarps2 : kWarps1) * 32, 1) xengine_tc
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             constexpr bool f32 = kF32;
-            const int nsl = f32 ? kF32Stages : kStages;
+            constexpr bool in8 = kIn8;
+            const int nsl = f32 ? (in8 ? kRawI8 : kF32Stages) : kStages;
             uint64_t* fullb = f32 ? sh.f32full : sh.full;
             uint64_t* emptyb = f32 ? sh.f32empty : sh.empty;
-            unsigned char* slots = f32 ? smem + kOpStages2 * kSlot2 : smem;
-            const int pitch = f32 ? kStage2Bytes : kSlot;
+            unsigned char* slots = f32 ? smem + (in8 ? kOpStagesI8 : kOpStages2) * kSlot2 : smem;
+            const int pitch = f32 ? (in8 ? kRawPitch : kStage2Bytes) : kSlot;
             int g = 0;
             for (int it = blockIdx.x; it < t.n_items && !*abort_flag; it += gridDim.x) {
                 const ItemGeo ig = item_geo(t, it);
@@ -480,6 +536,13 @@ __global__ void __launch_bounds__((kF32 ? kWarps2 : kWarps1) * 32, 1) xengine_tc
                         if (st == 0) tmap_acquire(&s.tmap);
                         const int nkb = s.ks / kTbHalf;
                         mbar_arrive_expect_tx(&fullb[slot], static_cast<uint32_t>(nkb) * s.n_in * 64);
+                        tma_load_5d(dst, &s.tmap, 0, ig.k & 3, 0, st * nkb, ig.k >> 2, &fullb[slot]);
+                    } else if (f32 && in8) {
+                        // channel-quad int8 bytes: one 5-D tensor copy gathers the stage's 16-byte pieces
+                        // of channel k into [kb][2 n_in rows][8 bytes] (half the fp16 bytes)
+                        if (st == 0) tmap_acquire(&s.tmap);
+                        const int nkb = s.ks / kTbHalf;
+                        mbar_arrive_expect_tx(&fullb[slot], static_cast<uint32_t>(nkb) * s.n_in * 16);
                         tma_load_5d(dst, &s.tmap, 0, ig.k & 3, 0, st * nkb, ig.k >> 2, &fullb[slot]);
                     } else if (f32) {
                         // the stage's FP32 K-blocks of channel k are contiguous
@@ -509,7 +572,7 @@ __global__ void __launch_bounds__((kF32 ? kWarps2 : kWarps1) * 32, 1) xengine_tc
             int g = 0, cc = 0;
             uint32_t par = 0;                     // bit b: parity of accumulator b's uses so far
             int prev_nbuf = -1;
-            constexpr int nsl = kF32 ? kOpStages2 : kStages;
+            constexpr int nsl = kF32 ? (kIn8 ? kOpStagesI8 : kOpStages2) : kStages;
             for (int it = blockIdx.x; it < t.n_items && !*abort_flag; it += gridDim.x) {
                 const ItemGeo ig = item_geo(t, it);
                 const XtSub& s = t.sub[ig.sub];
@@ -519,7 +582,7 @@ __global__ void __launch_bounds__((kF32 ? kWarps2 : kWarps1) * 32, 1) xengine_tc
                 const bool two = s.spec32 != nullptr;
                 const uint32_t lo_off = static_cast<uint32_t>(ig.nkb_stage) * ig.R * 16;
                 bool xfirst = true;                   // next cross-term MMA starts the accumulator
-                if (ig.sep) {                         // the previous item's cross terms are drained
+                if (ig.cross) {                       // the previous item's cross terms are drained
                     if (!mbar_wait(&sh.xe, ((par >> kXBit) & 1) ^ 1, t.err, ERR_WAIT_EPI)) {
                         *abort_flag = 1;
                         break;
@@ -534,7 +597,7 @@ __global__ void __launch_bounds__((kF32 ? kWarps2 : kWarps1) * 32, 1) xengine_tc
                         for (int q = 0; q < kAccBufs && ok; ++q)
                             ok = mbar_wait(&sh.acce[q], ((par >> q) & 1) ^ 1, t.err, ERR_WAIT_EPI);
                         // (columns 256-383 may have held cross terms; a sep item already waited)
-                        if (ok && !ig.sep)
+                        if (ok && !ig.cross)
                             ok = mbar_wait(&sh.xe, ((par >> kXBit) & 1) ^ 1, t.err, ERR_WAIT_EPI);
                     } else {
                         ok = mbar_wait(&sh.acce[b], ((par >> b) & 1) ^ 1, t.err, ERR_WAIT_EPI);
@@ -581,12 +644,12 @@ __global__ void __launch_bounds__((kF32 ? kWarps2 : kWarps1) * 32, 1) xengine_tc
                     umma_commit(&sh.accf[b]);           // chunk complete
                 }
                 if (*abort_flag) break;
-                if (ig.sep) umma_commit(&sh.xf);        // cross terms complete
+                if (ig.cross) umma_commit(&sh.xf);      // cross terms complete
             }
         }
     } else if (kF32 && warp >= kConvWarp0) {
         // ------------------------------------------------------------ converters (FP32 form)
-        convert_stages(t, sh, smem, threadIdx.x - kConvWarp0 * 32);
+        convert_stages<kIn8>(t, sh, smem, threadIdx.x - kConvWarp0 * 32);
     } else {
         // ------------------------------------------------------------ epilogue (warps 2..9 or 2..5)
         const int q = warp & 3;                   // TMEM lane quarter this warp may access
@@ -599,23 +662,23 @@ __global__ void __launch_bounds__((kF32 ? kWarps2 : kWarps1) * 32, 1) xengine_tc
         for (int it = blockIdx.x; it < t.n_items && !*abort_flag; it += gridDim.x) {
             const ItemGeo ig = item_geo(t, it);
             const XtSub& s = t.sub[ig.sub];
-            if (kF32 && ig.sep) {           // (FP32 form: every narrow item)
+            if (kF32 && ig.sep) {           // (converted forms: every narrow item)
                 for (int chunk = 0; chunk < ig.n_chunk; ++chunk, ++cc) {
                     const int b = cc % ig.nbuf;
                     const bool last = chunk == ig.n_chunk - 1;
                     bool ok = mbar_wait(&sh.accf[b], (par >> b) & 1, t.err, ERR_WAIT_MMA);
-                    if (ok && last) ok = mbar_wait(&sh.xf, (par >> kXBit) & 1, t.err, ERR_WAIT_MMA);
+                    if (ok && last && ig.cross) ok = mbar_wait(&sh.xf, (par >> kXBit) & 1, t.err, ERR_WAIT_MMA);
                     if (!ok) {
                         sh.abort_flag = 1;
                         break;
                     }
                     par ^= 1u << b;
-                    if (last) par ^= 1u << kXBit;
+                    if (last && ig.cross) par ^= 1u << kXBit;
                     tc_fence_after();
-                    drain_split(s, ig, tmem + lane_off, ig.a0 + lrow, b, chunk);
+                    drain_split<kIn8 ? 1 : 0>(s, ig, tmem + lane_off, ig.a0 + lrow, b, chunk);
                     tc_fence_before();
                     mbar_arrive(&sh.acce[b]);
-                    if (last) mbar_arrive(&sh.xe);
+                    if (last && ig.cross) mbar_arrive(&sh.xe);
                 }
             } else if (!kF32 && ig.dbl) {
                 par = drain_narrow(sh, s, ig, tmem + lane_off, ig.a0 + lrow, half, cc, par, t.err);
@@ -648,6 +711,7 @@ __global__ void __launch_bounds__((kF32 ? kWarps2 : kWarps1) * 32, 1) xengine_tc
 }  // namespace
 
 bool xengine_tc_encode_quad(XtSub& x) {
+    const bool b8 = x.in8 != 0;                    // int8 bytes (16-byte pieces) or FP32 (64-byte pieces)
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q{};
@@ -659,10 +723,12 @@ bool xengine_tc_encode_quad(XtSub& x) {
     }
     const cuuint64_t ntb = static_cast<cuuint64_t>(x.n_int / kTbHalf);
     const cuuint64_t dim[5] = {16, 4, static_cast<cuuint64_t>(x.n_in), ntb, static_cast<cuuint64_t>(x.n_chan / 4)};
-    const cuuint64_t stride[4] = {64, 256, 256ull * x.n_in, 256ull * x.n_in * ntb};   // bytes, dims 1..4
+    const cuuint64_t piece = b8 ? 16 : 64;         // bytes of one (channel, K-block, input) piece
+    const cuuint64_t stride[4] = {piece, 4 * piece, 4 * piece * x.n_in, 4 * piece * x.n_in * ntb};   // bytes, dims 1..4
     const cuuint32_t box[5] = {16, 1, static_cast<cuuint32_t>(x.n_in), static_cast<cuuint32_t>(x.ks / kTbHalf), 1};
     const cuuint32_t estride[5] = {1, 1, 1, 1, 1};
-    return encode(&x.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<float*>(x.spec32), dim, stride, box, estride,
+    void* base = b8 ? static_cast<void*>(const_cast<__half*>(x.spec)) : static_cast<void*>(const_cast<float*>(x.spec32));
+    return encode(&x.tmap, b8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, base, dim, stride, box, estride,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -685,14 +751,17 @@ int xengine_tc_ks_fp32(int n_in) {
 
 size_t xengine_tc_smem() { return static_cast<size_t>(kSmemBytes); }
 
-cudaError_t launch_xengine_tc_table(const XtBatch* dtab, int n_items, int n_sm, cudaStream_t s, bool fp32_in) {
+cudaError_t launch_xengine_tc_table(const XtBatch* dtab, int n_items, int n_sm, cudaStream_t s, int form) {
     const size_t smem = xengine_tc_smem();
-    auto kern = fp32_in ? xengine_tc_kernel<true> : xengine_tc_kernel<false>;
+    auto kern = form == XT_FORM_F32 ? xengine_tc_kernel<XT_FORM_F32>
+              : form == XT_FORM_I8  ? xengine_tc_kernel<XT_FORM_I8>
+                                    : xengine_tc_kernel<XT_FORM_F16>;
+    const bool convert = form != XT_FORM_F16;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, std::min(n_items, n_sm));
-    kern<<<grid, (fp32_in ? kWarps2 : kWarps1) * 32, smem, s>>>(dtab);
+    kern<<<grid, (convert ? kWarps2 : kWarps1) * 32, smem, s>>>(dtab);
     return cudaGetLastError();
 }
 
