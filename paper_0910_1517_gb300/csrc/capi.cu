@@ -124,7 +124,10 @@ int split_exp(const corr* h) {
     return e;
 }
 
-constexpr int kSplitChunk = 128;   // frames per TMEM accumulation chunk of CORR_FP32TC
+// frames per TMEM accumulation chunk of CORR_FP32TC: 128, and 256 where the X-engine pairs the
+// hi and lo rows (64 inputs), whose drain then adds two accumulator halves per chunk
+constexpr int kSplitChunk = 128;
+constexpr int kSplitChunkPaired = 256;
 
 int max_int_delay(const corr* h) {
     int m = 0;
@@ -255,7 +258,7 @@ gbx::XtSub gbx::xt_sub_of(const corr* h) {
         x.spec32 = static_cast<const float*>(h->d_spec);
         x.split_scale = std::ldexp(1.0f, -split_exp(h));
         x.descale = std::ldexp(1.0f, 2 * split_exp(h));
-        x.chunk = kSplitChunk;
+        x.chunk = 2 * h->n_in == 128 ? kSplitChunkPaired : kSplitChunk;
         x.quad = spec_quad(h) ? 1 : 0;
     } else {
         const int max_ks = xengine_tc_max_ks(h->n_in);

@@ -47,9 +47,15 @@
 // tensor core's FP32 accumulation drops low bits of every partial sum, a
 // loss that grows with the accumulator's size and the number of steps.  So the
 // dominant H H^T term is accumulated in 128-frame chunks that the CUDA cores add
-// in FP32, while the cross terms, 2^-11 of it, go to a separate accumulator over
-// the whole integration: narrow items then alternate two chunk accumulators
-// (columns 0-255), keep the cross terms in columns 256-383 and the running sums
+// in FP32.  Items of 128 rows (64 inputs, the usual shape) are "paired": the
+// converters lay each K-block out as its 128 hi rows followed by its 128 lo rows, so
+// that one N = 256 MMA forms [H H^T | H L^T] = H [H; L]^T and a second, N = 128, adds
+// L H^T onto the right half -- two MMAs per step instead of three (the tensor core's
+// cost here is per instruction, nearly independent of N); two 256-column chunk
+// accumulators fill TMEM, and the CUDA cores add both halves of every chunk into FP32
+// running sums in shared memory.  Other narrow items keep three MMAs: the cross terms,
+// 2^-11 of H H^T, go to a separate accumulator over the whole integration (columns
+// 256-383), two chunk accumulators alternate in columns 0-255 and the running sums sit
 // in columns 384-511.
 #include <cudaTypedefs.h>
 
@@ -74,7 +80,8 @@ constexpr int kTailSlack = 32768;
 // 128-row MMA reads past R; ks * rows_fp32(n_in) * 4 <= kStage2Bytes bounds that by
 // kStage2Bytes + (128 - 64) * 16 (R < 64 leaves more room).
 constexpr int kOpStages2 = 2;                 // operand slots ...
-constexpr int kF32Stages = 5;                 // ... and the FP32 slots after them
+constexpr int kF32Stages = 3;                 // ... the FP32 slots after them ...
+constexpr int kRunBytes = 128 * 128 * 4;      // ... and the paired items' FP32 running sums, [column][row]
 // int8 form: four operand slots, then five input slots of kStage2Bytes / 2 (an int8 stage is half
 // the size of its fp16 operand tile)
 constexpr int kOpStagesI8 = 4;
@@ -82,7 +89,8 @@ constexpr int kRawI8 = 5;
 constexpr int kRawPitch = kStage2Bytes / 2;
 constexpr int kInSlots = kRawI8 > kF32Stages ? kRawI8 : kF32Stages;
 constexpr int kSlot2 = kStage2Bytes + 1024;
-constexpr int kSmemBytes = kOpStages2 * kSlot2 + kF32Stages * kStage2Bytes;
+constexpr int kRunOff = kOpStages2 * kSlot2 + kF32Stages * kStage2Bytes;
+constexpr int kSmemBytes = kRunOff + kRunBytes;
 static_assert(kOpStagesI8 <= kStages && kOpStagesI8 * kSlot2 + kRawI8 * kRawPitch <= kSmemBytes, "int8-form slots");
 static_assert(kStages * kSlot + kTailSlack <= kSmemBytes && kSmemBytes <= 227 * 1024 - 1024, "shared memory");
 constexpr uint32_t kTmemCols = 512;
@@ -111,7 +119,9 @@ struct ItemGeo {
     int Rp, tb32, ntb32;   // FP32 form: padded rows, frames per FP32 K-block, FP32 K-blocks per channel
     bool dbl;      // N <= 128: rotating 128-column accumulators
     bool sep;      // dbl and a converted form: rotating chunk accumulators, TMEM running sums
-    bool cross;    // sep and FP32 form: the cross terms in their own accumulator
+    bool pair;     // sep, FP32 form, 128 rows: hi and lo rows of a K-block side by side, one N = 256 MMA
+                   // H [H; L]^T and one L H^T per step into a 256-column chunk accumulator
+    bool cross;    // sep and FP32 form otherwise: the cross terms in their own accumulator
     int nbuf;      // accumulators the item rotates over
 };
 
@@ -130,8 +140,9 @@ __device__ __forceinline__ ItemGeo item_geo(const XtBatch& t, int it) {
     g.ntb32 = s.n_int / g.tb32;
     g.dbl = g.N <= 128;
     g.sep = g.dbl && (s.spec32 != nullptr || s.in8);
-    g.cross = g.sep && s.spec32 != nullptr;
-    g.nbuf = !g.dbl ? 1 : (g.sep ? (g.cross ? 2 : 3) : kAccBufs);
+    g.pair = g.sep && s.spec32 != nullptr && g.R == 128;
+    g.cross = g.sep && s.spec32 != nullptr && !g.pair;
+    g.nbuf = !g.dbl ? 1 : (g.sep ? (s.spec32 != nullptr ? 2 : 3) : kAccBufs);
     g.ntb = s.n_int / kTbHalf;
     g.nkb_stage = s.ks / kTbHalf;
     g.n_stage = (s.n_int + s.ks - 1) / s.ks;
@@ -255,6 +266,31 @@ __device__ __forceinline__ void drain_split(const XtSub& s, const ItemGeo ig, ui
     if (!last) tmem_wait_st();
 }
 
+// One chunk of a paired FP32-form item (chunk accumulator b: columns 256 b .. + 127 hold H H^T,
+// 256 b + 128 .. + 255 hold H L^T + L H^T): the FP32 running sums of row `row` (shared memory,
+// [column][row], so that a warp's rows are consecutive words) += the two halves, or after the
+// last chunk the sums are written.
+__device__ __forceinline__ void drain_pair(const XtSub& s, const ItemGeo ig, uint32_t tm, int row, int b, int chunk,
+                                           float* run) {
+    const bool last = chunk == ig.n_chunk - 1;
+    const int lr = row - ig.a0;
+    for (int j0 = 0; j0 < 128; j0 += 16) {
+        uint32_t h[16], x[16], rs[16];
+        tmem_ld16(tm + b * 256 + j0, h);
+        tmem_ld16(tm + b * 256 + 128 + j0, x);
+        tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            float v = __uint_as_float(h[e]) + __uint_as_float(x[e]);
+            float* r = run + (j0 + e) * 128 + lr;
+            if (chunk > 0) v = *r + v;
+            if (!last) *r = v;
+            rs[e] = __float_as_uint(v);
+        }
+        if (last) write_piece<16>(s, ig, row, j0, rs);
+    }
+}
+
 // run[0..63] (+)= this thread's 64 columns of the accumulator at TMEM address `col`
 __device__ __forceinline__ void drain64(uint32_t (&run)[64], uint32_t col, bool have, int exact) {
 #pragma unroll
@@ -307,6 +343,20 @@ __device__ __forceinline__ uint32_t drain_narrow(Shared& sh, const XtSub& s, con
         }
     }
     return par;
+}
+
+// Veltkamp's split of the pair v (both lanes at once; each packed operation rounds as its scalar
+// counterpart): hi = v rounded to 11 significant bits (2^13 + 1), lo = v - hi exactly; both as
+// fp16 pairs
+__device__ __forceinline__ void split_pair(float2 v, uint32_t& hw, uint32_t& lw) {
+    const float2 tt = __fmul2_rn(v, make_float2(8193.0f, 8193.0f));
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 hv = __ffma2_rn(__ffma2_rn(v, m1, tt), m1, tt);   // tt - (tt - v)
+    const float2 lv = __ffma2_rn(hv, m1, v);                        // v - hi
+    const __half2 hh = __floats2half2_rn(hv.x, hv.y);
+    const __half2 ll = __floats2half2_rn(lv.x, lv.y);
+    hw = *reinterpret_cast<const uint32_t*>(&hh);
+    lw = *reinterpret_cast<const uint32_t*>(&ll);
 }
 
 // FP32 form: stage g's FP32 slot g % kF32Stages (after the operand slots) becomes operand slot
@@ -380,26 +430,14 @@ __device__ __noinline__ void convert_stages(const XtBatch& t, Shared& sh, unsign
 #pragma unroll 4
                 for (int u = ct; u < units; u += kConvThreads) {
                     const float4 q = *reinterpret_cast<const float4*>(src + 4 * u);
-                    const float v[4] = {q.x * sc, q.y * sc, q.z * sc, q.w * sc};
+                    const float2 sc2 = make_float2(sc, sc);
                     uint32_t hw[2], lw[2];
-#pragma unroll
-                    for (int m = 0; m < 2; ++m) {
-                        float hv[2], lv[2];
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {   // Veltkamp's split, explicit roundings
-                            const float x = v[2 * m + e];
-                            const float tt = __fmul_rn(x, 8193.0f);
-                            hv[e] = __fsub_rn(tt, __fsub_rn(tt, x));
-                            lv[e] = __fsub_rn(x, hv[e]);
-                        }
-                        const __half2 hh = __floats2half2_rn(hv[0], hv[1]);
-                        const __half2 ll = __floats2half2_rn(lv[0], lv[1]);
-                        hw[m] = *reinterpret_cast<const uint32_t*>(&hh);
-                        lw[m] = *reinterpret_cast<const uint32_t*>(&ll);
-                    }
-                    unsigned char* d = dst + u * 8;
+                    split_pair(__fmul2_rn(make_float2(q.x, q.y), sc2), hw[0], lw[0]);
+                    split_pair(__fmul2_rn(make_float2(q.z, q.w), sc2), hw[1], lw[1]);
+                    // paired items (128 rows): K-block j holds 128 hi rows then 128 lo rows (4096 bytes)
+                    unsigned char* d = dst + u * 8 + (ig.pair ? (u >> 8) * 2048 : 0);
                     *reinterpret_cast<uint2*>(d) = make_uint2(hw[0], hw[1]);
-                    *reinterpret_cast<uint2*>(d + lo_off) = make_uint2(lw[0], lw[1]);
+                    *reinterpret_cast<uint2*>(d + (ig.pair ? 2048 : lo_off)) = make_uint2(lw[0], lw[1]);
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
@@ -423,33 +461,21 @@ __device__ __noinline__ void convert_stages(const XtBatch& t, Shared& sh, unsign
                 const int oa = fp32_off(r, sw ? 4 : 0, tb);
                 const int ob = tb == 8 ? fp32_off(r, sw ? 0 : 4, 8) : Rp * 4 + oa;
                 const float* p = src + j * 8 * Rp;
-                unsigned char* d = dst + u * 16;
+                unsigned char* d = dst + u * 16 + (ig.pair ? j * 2048 : 0);
                 const float4 qa = *reinterpret_cast<const float4*>(p + oa);
                 const float4 qb = *reinterpret_cast<const float4*>(p + ob);
                 const float4 q0 = sw ? qb : qa, q1 = sw ? qa : qb;
                 // hi: v rounded to 11 significant bits in FP32 (Veltkamp's split, 2^13 + 1), exact in fp16
                 // above 2^-14 (below, fp16 rounds it once more: under 2^-25 absolute, against values of
                 // order 2^6); lo = v - hi is exact.  Two packed conversions per pair of values.
-                const float v[8] = {q0.x * sc, q0.y * sc, q0.z * sc, q0.w * sc,
-                                    q1.x * sc, q1.y * sc, q1.z * sc, q1.w * sc};
+                const float2 sc2 = make_float2(sc, sc);
                 uint32_t hw[4], lw[4];
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    float hv[2], lv[2];
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {   // (explicit roundings: no contraction, no reassociation)
-                        const float x = v[2 * m + e];
-                        const float tt = __fmul_rn(x, 8193.0f);
-                        hv[e] = __fsub_rn(tt, __fsub_rn(tt, x));
-                        lv[e] = __fsub_rn(x, hv[e]);
-                    }
-                    const __half2 hh = __floats2half2_rn(hv[0], hv[1]);
-                    const __half2 ll = __floats2half2_rn(lv[0], lv[1]);
-                    hw[m] = *reinterpret_cast<const uint32_t*>(&hh);
-                    lw[m] = *reinterpret_cast<const uint32_t*>(&ll);
-                }
+                split_pair(__fmul2_rn(make_float2(q0.x, q0.y), sc2), hw[0], lw[0]);
+                split_pair(__fmul2_rn(make_float2(q0.z, q0.w), sc2), hw[1], lw[1]);
+                split_pair(__fmul2_rn(make_float2(q1.x, q1.y), sc2), hw[2], lw[2]);
+                split_pair(__fmul2_rn(make_float2(q1.z, q1.w), sc2), hw[3], lw[3]);
                 *reinterpret_cast<uint4*>(d) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                *reinterpret_cast<uint4*>(d + lo_off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                *reinterpret_cast<uint4*>(d + (ig.pair ? 2048 : lo_off)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                 r += dr;
                 j += dj;
                 if (r >= R) {
@@ -609,7 +635,7 @@ __global__ void __launch_bounds__((kForm != XT_FORM_F16 ? kWarps2 : kWarps1) * 3
                     }
                     par ^= 1u << b;
                     tc_fence_after();
-                    const uint32_t dcol = tmem + (ig.dbl ? b * 128 : 0);
+                    const uint32_t dcol = tmem + (ig.dbl ? b * (ig.pair ? 256 : 128) : 0);
                     const int st0 = chunk * stages_per_chunk;
                     const int st1 = min(ig.n_stage, st0 + stages_per_chunk);
                     bool first = true;
@@ -622,6 +648,24 @@ __global__ void __launch_bounds__((kForm != XT_FORM_F16 ? kWarps2 : kWarps1) * 3
                         tc_fence_after();
                         const int nkb = min(ig.nkb_stage, ig.ntb - st * ig.nkb_stage);
                         const uint32_t base = smem_u32(smem + slot * (kF32 ? kSlot2 : kSlot));
+                        if constexpr (kForm == XT_FORM_F32) {
+                            if (ig.pair) {
+                                // K-block: 128 hi rows then 128 lo rows (LBO 4096 bytes); per 16 frames
+                                // [H H^T | H L^T] = H [H; L]^T (N = 256), then L H^T onto the right half
+                                constexpr uint32_t lbo2 = 4096;
+                                const uint32_t idesc2 = idesc_f16_f32(128, 256);
+                                for (int kk = 0; kk < nkb / 2; ++kk) {
+                                    const uint32_t kbase = base + kk * 2 * lbo2;
+                                    const uint64_t dh = smem_desc_noswizzle(kbase, lbo2, sbo);
+                                    const uint64_t dl = smem_desc_noswizzle(kbase + 2048, lbo2, sbo);
+                                    umma_f16(dcol, dh, dh, idesc2, first ? 0u : 1u);
+                                    umma_f16(dcol + 128, dl, dh, idesc, 1u);
+                                    first = false;
+                                }
+                                umma_commit(&sh.empty[slot]);   // frees the stage once these MMAs finish
+                                continue;
+                            }
+                        }
                         for (int kk = 0; kk < nkb / 2; ++kk) {
                             const uint32_t kbase = base + kk * 2 * lbo;
                             const uint64_t da = smem_desc_noswizzle(kbase + ig.a0 * 16, lbo, sbo);
@@ -675,7 +719,14 @@ __global__ void __launch_bounds__((kForm != XT_FORM_F16 ? kWarps2 : kWarps1) * 3
                     par ^= 1u << b;
                     if (last && ig.cross) par ^= 1u << kXBit;
                     tc_fence_after();
-                    drain_split<kIn8 ? 1 : 0>(s, ig, tmem + lane_off, ig.a0 + lrow, b, chunk);
+                    if constexpr (kForm == XT_FORM_F32) {
+                        if (ig.pair)
+                            drain_pair(s, ig, tmem + lane_off, ig.a0 + lrow, b, chunk, reinterpret_cast<float*>(smem + kRunOff));
+                        else
+                            drain_split<0>(s, ig, tmem + lane_off, ig.a0 + lrow, b, chunk);
+                    } else {
+                        drain_split<kIn8 ? 1 : 0>(s, ig, tmem + lane_off, ig.a0 + lrow, b, chunk);
+                    }
                     tc_fence_before();
                     mbar_arrive(&sh.acce[b]);
                     if (last && ig.cross) mbar_arrive(&sh.xe);
