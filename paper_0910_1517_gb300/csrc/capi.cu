@@ -127,7 +127,7 @@ int split_exp(const corr* h) {
 // frames per TMEM accumulation chunk of CORR_FP32TC: 128, and 256 where the X-engine pairs the
 // hi and lo rows (64 inputs), whose drain then adds two accumulator halves per chunk
 constexpr int kSplitChunk = 128;
-constexpr int kSplitChunkPaired = 256;
+constexpr int kSplitChunkPaired = 512;
 
 int max_int_delay(const corr* h) {
     int m = 0;

@@ -278,13 +278,14 @@ __device__ __forceinline__ void drain_pair(const XtSub& s, const ItemGeo ig, uin
         uint32_t h[16], x[16], rs[16];
         tmem_ld16(tm + b * 256 + j0, h);
         tmem_ld16(tm + b * 256 + 128 + j0, x);
+        float p[16];                                // (all loads, then all stores: no dependent chains)
+#pragma unroll
+        for (int e = 0; e < 16; ++e) p[e] = chunk > 0 ? run[(j0 + e) * 128 + lr] : 0.0f;
         tmem_wait_ld();
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-            float v = __uint_as_float(h[e]) + __uint_as_float(x[e]);
-            float* r = run + (j0 + e) * 128 + lr;
-            if (chunk > 0) v = *r + v;
-            if (!last) *r = v;
+            const float v = p[e] + (__uint_as_float(h[e]) + __uint_as_float(x[e]));
+            if (!last) run[(j0 + e) * 128 + lr] = v;
             rs[e] = __float_as_uint(v);
         }
         if (last) write_piece<16>(s, ig, row, j0, rs);
