@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "common.cuh"
 #include "fengine.cuh"
@@ -67,26 +68,31 @@ __host__ __device__ inline TcGeo tc_geo(int n_ant, int n_pol, int n_in) {
     return g;
 }
 
-// Veltkamp split of 8 values into fp16 hi and lo words (explicit roundings, no contraction)
+// Veltkamp split of 8 values into fp16 hi and lo words, on packed FP32x2 pairs (each lane rounds
+// as the scalar operation: t = 8193 v, hi = t - (t - v), lo = v - hi)
 __device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
     uint32_t hw[4], lw[4];
+    const float2 m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        float hv[2], lv[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float v = x[2 * m + e];
-            const float t = __fmul_rn(v, 8193.0f);
-            hv[e] = __fsub_rn(t, __fsub_rn(t, v));
-            lv[e] = __fsub_rn(v, hv[e]);
-        }
-        const __half2 hh = __floats2half2_rn(hv[0], hv[1]);
-        const __half2 ll = __floats2half2_rn(lv[0], lv[1]);
+        const float2 v = make_float2(x[2 * m], x[2 * m + 1]);
+        const float2 t = __fmul2_rn(v, make_float2(8193.0f, 8193.0f));
+        const float2 hv = __ffma2_rn(__ffma2_rn(v, m1, t), m1, t);
+        const float2 lv = __ffma2_rn(hv, m1, v);
+        const __half2 hh = __floats2half2_rn(hv.x, hv.y);
+        const __half2 ll = __floats2half2_rn(lv.x, lv.y);
         hw[m] = *reinterpret_cast<const uint32_t*>(&hh);
         lw[m] = *reinterpret_cast<const uint32_t*>(&ll);
     }
     hi = make_uint4(hw[0], hw[1], hw[2], hw[3]);
     lo = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
+// (v.x, v.y, v.z, v.w) rotated left by r (0..3): two stages of selects
+__device__ __forceinline__ float4 rot4(float4 v, int r) {
+    if (r & 1) v = make_float4(v.y, v.z, v.w, v.x);
+    if (r & 2) v = make_float4(v.z, v.w, v.x, v.y);
+    return v;
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -242,14 +248,17 @@ multibeam_tc_kernel(const float* __restrict__ spec, int n_ant, int n_pol, int n_
                     }
                 }
 #pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = rot4(v[j], tq & 3);
+#pragma unroll
                 for (int e1 = 0; e1 < 4; ++e1) {
                     // frame f0 + e, rotated by tq so that the warp's 16-byte stores spread over
-                    // the bank groups (lanes are 64 bytes apart)
+                    // the bank groups (lanes are 64 bytes apart); v[j] is already rotated, so
+                    // component e1 is frame e
                     const int e = (e1 + tq) & 3;
                     float x[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
-                        x[j] = (e == 0 ? v[j].x : e == 1 ? v[j].y : e == 2 ? v[j].z : v[j].w) * split_scale;
+                        x[j] = (e1 == 0 ? v[j].x : e1 == 1 ? v[j].y : e1 == 2 ? v[j].z : v[j].w) * split_scale;
                     uint4 hi, lo;
                     split8(x, hi, lo);
                     const size_t off = (static_cast<size_t>(kc) * G.N + p * kFrames + f0 + e) * 16;
@@ -315,19 +324,36 @@ multibeam_tc_kernel(const float* __restrict__ spec, int n_ant, int n_pol, int n_
                             make_float4(a00 * sc, a11 * sc, a01 * sc, ax * sc);
                     s00 = s11 = s01 = sx = 0.f;
                 };
-                const int wmask = avg - 1;
+                // the 32 frames with the window length as a compile-time constant (A = 0: avg > 32,
+                // at most one flush after the 32), so the flushes sit at fixed frames
+                auto frames32 = [&](auto a_c) {
+                    constexpr int A = decltype(a_c)::value;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float u0 = __uint_as_float(r0[j]);
-                    const float u1 = n_pol == 2 ? __uint_as_float(r1[j]) : 0.0f;
-                    const float p1 = __shfl_xor_sync(0xffffffffu, u1, 1);
-                    s00 = fmaf(u0, u0, s00);
-                    s11 = fmaf(u1, u1, s11);
-                    s01 = fmaf(u0, u1, s01);
-                    sx = fmaf(c == 0 ? -u0 : u0, p1, sx);      // re: -re0 im1, im: im0 re1
-                    if (avg <= 32 && ((j + 1) & wmask) == 0) flush(f32 + j);
+                    for (int j = 0; j < 32; ++j) {
+                        const float u0 = __uint_as_float(r0[j]);
+                        const float u1 = n_pol == 2 ? __uint_as_float(r1[j]) : 0.0f;
+                        const float p1 = __shfl_xor_sync(0xffffffffu, u1, 1);
+                        s00 = fmaf(u0, u0, s00);
+                        s11 = fmaf(u1, u1, s11);
+                        s01 = fmaf(u0, u1, s01);
+                        sx = fmaf(c == 0 ? -u0 : u0, p1, sx);      // re: -re0 im1, im: im0 re1
+                        if constexpr (A > 0) {
+                            if ((j + 1) % A == 0) flush(f32 + j);
+                        }
+                    }
+                    if constexpr (A == 0) {
+                        if (((f32 + 32) & (avg - 1)) == 0) flush(f32 + 31);
+                    }
+                };
+                switch (avg) {
+                    case 1: frames32(std::integral_constant<int, 1>{}); break;
+                    case 2: frames32(std::integral_constant<int, 2>{}); break;
+                    case 4: frames32(std::integral_constant<int, 4>{}); break;
+                    case 8: frames32(std::integral_constant<int, 8>{}); break;
+                    case 16: frames32(std::integral_constant<int, 16>{}); break;
+                    case 32: frames32(std::integral_constant<int, 32>{}); break;
+                    default: frames32(std::integral_constant<int, 0>{}); break;
                 }
-                if (avg > 32 && ((f32 + 32) & wmask) == 0) flush(f32 + 31);
             }
         }
     }
