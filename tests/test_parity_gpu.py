@@ -142,12 +142,15 @@ def _calibrated_scales(env, s):
 
 
 # GMRT shape, and the 4096-point FFT whose 4-frame CTAs trade channel halves in cluster pairs
-# (channels 1023 / 1024 straddle the halves)
+# (channels 1023 / 1024 straddle the halves); the int8 form writes bytes in the channel-quad
+# layout up to 1024 channels (the 64-point case: 32 channels, 8 quads; 6 inputs per frame)
 TC_SHAPES = [dict(n_int=128), dict(n_ant=16, n_fft=4096, n_int=64)]
-TC_CHANS = {2048: [0, 1, 100, 333, 512, 777, 1023], 4096: [0, 1, 100, 1023, 1024, 1500, 2047]}
+I8_SHAPES = TC_SHAPES + [dict(n_ant=3, n_fft=64, n_int=48)]
+TC_CHANS = {2048: [0, 1, 100, 333, 512, 777, 1023], 4096: [0, 1, 100, 1023, 1024, 1500, 2047],
+            64: [0, 1, 3, 4, 16, 30, 31]}
 
 
-@pytest.mark.parametrize("shape", TC_SHAPES, ids=["gmrt", "fft4096"])
+@pytest.mark.parametrize("shape", I8_SHAPES, ids=["gmrt", "fft4096", "fft64"])
 def test_i8_bit_exact_on_requantised_spectra(env, shape):
     torch, corr, orc = env
     s = make_config(2, seed=3003, **shape)
@@ -202,7 +205,9 @@ def test_f16_mode_accuracy(env, shape):
 
 
 @pytest.mark.parametrize("n_ant,n_pol,n_fft,n_int", [
-    (32, 2, 2048, 512),    # GMRT shape, four 128-frame accumulation chunks
+    (32, 2, 2048, 512),    # GMRT shape (64 inputs: paired hi / lo rows), one 512-frame chunk
+    (32, 2, 256, 144),     # paired rows, one partial chunk of 9 K-block pairs
+    (32, 2, 512, 1040),    # paired rows, two 512-frame chunks and a 16-frame one
     (5, 2, 256, 48),       # ragged rows (R = 20), one short chunk, 3 F-engine tiles
     (3, 1, 64, 16),        # smallest FFT and integration, one polarisation
     (16, 2, 4096, 64),     # 4-frame F-engine CTAs: 8-byte half-row stores of both planes
