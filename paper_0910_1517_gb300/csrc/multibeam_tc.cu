@@ -221,7 +221,23 @@ multibeam_tc_kernel(const float* __restrict__ spec, int n_ant, int n_pol, int n_
     } else if (warp >= kConv0) {
         // ------------------------------------------------------------ converters
         const int ct = tid - kConv0 * 32;
-        const int units = G.KC * n_pol * (kFrames / 4);
+        const int units = G.KC * n_pol * (kFrames / 4);   // at most 2 kConvT (K <= 128)
+        // a thread's units are the same in every stage: their source offsets within an FP32 stage
+        // (-1 for padding antennas) and their (polarisation, K chunk, frame quad), once
+        constexpr int kMaxU = 2;
+        int soff[kMaxU][8], uq[kMaxU];
+#pragma unroll
+        for (int m = 0; m < kMaxU; ++m) {
+            const int u = ct + m * kConvT;
+            const int tq = u % (kFrames / 4), p = (u / (kFrames / 4)) % n_pol, kc = u / ((kFrames / 4) * n_pol);
+            const int f0 = 4 * tq, kb = f0 / tb, e0 = f0 % tb;
+            uq[m] = u;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int kk = 8 * kc + j, a = kk >> 1;
+                soff[m][j] = (u < units && a < n_ant) ? kb * Rp * tb + fp32_off(2 * (a * n_pol + p) + (kk & 1), e0, tb) : -1;
+            }
+        }
         for (int st = 0; st < n_stage; ++st) {
             const int fs = st % G.nf, s = st & 1;
             int ok = 1;
@@ -233,20 +249,17 @@ multibeam_tc_kernel(const float* __restrict__ spec, int n_ant, int n_pol, int n_
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             const float* src = reinterpret_cast<const float*>(f32_base + static_cast<size_t>(fs) * G.f32_bytes);
             unsigned char* bh = b_base + static_cast<size_t>(2 * s) * G.b_bytes;
-            for (int u = ct; u < units; u += kConvT) {
+#pragma unroll
+            for (int m = 0; m < kMaxU; ++m) {
+                const int u = uq[m];
+                if (u >= units) break;
                 // unit: K chunk kc (antennas 4 kc .. 4 kc + 3, re and im), polarisation p, frames 4 tq .. 4 tq + 3
                 const int tq = u % (kFrames / 4), p = (u / (kFrames / 4)) % n_pol, kc = u / ((kFrames / 4) * n_pol);
-                const int f0 = 4 * tq, kb = f0 / tb, e0 = f0 % tb;
+                const int f0 = 4 * tq;
                 float4 v[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int kk = 8 * kc + j, a = kk >> 1;
-                    v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (a < n_ant) {
-                        const int r = 2 * (a * n_pol + p) + (kk & 1);
-                        v[j] = *reinterpret_cast<const float4*>(src + kb * Rp * tb + fp32_off(r, e0, tb));
-                    }
-                }
+                for (int j = 0; j < 8; ++j)
+                    v[j] = soff[m][j] >= 0 ? *reinterpret_cast<const float4*>(src + soff[m][j]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) v[j] = rot4(v[j], tq & 3);
 #pragma unroll
