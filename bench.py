@@ -627,7 +627,8 @@ def run_batch_leg(args, corr, torch, rank):
                         f", {BATCH_N_INT} spectra each, int8 tensor-core X-engine, one CUDA graph per step",
             "value": samples / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": k,
             "tuned_frames_per_stage": [int(v) for v in ks], "tuned_xengine_ms": [float(v) for v in ms_x],
-            "launches_per_step": f"1 graph: {len(hs)} phasor set-ups + 1 F-engine + 1 X-engine kernel"}
+            "launches_per_step": f"1 graph of {len(hs)} concurrent branches (phasor set-up, F-engine, X-engine): "
+                                 f"{3 * len(hs)} kernels"}
 
 
 def run_rfi_leg(corr, torch, n_train_int=25, n_test_int=3):

@@ -1,13 +1,15 @@
 // batch.cu -- several sub-arrays of uneven sizes in one graph-captured launch, and
 // the autotuner that picks the tensor-core X-engine's stage size per sub-array.
 //
-// The graph holds, per sub-array, the upload of its delay model and its phasor
-// set-up, then ONE F-engine launch whose CTAs cover the frame blocks of every
-// sub-array (each CTA dispatches on its sub-array's FFT size) and ONE persistent
-// tensor-core X-engine launch whose CTAs walk a cost-ordered list of (sub-array,
-// channel, row block) items of all of them.  The per-launch parameters live in
-// device tables that memcpy nodes of the same graph refresh from pinned host
-// copies, so the graph is captured once and replayed for every integration.
+// The graph refreshes the batch's parameter tables from pinned host copies, then forks one
+// branch per sub-array: the upload of its delay model, its phasor set-up, its F-engine (the
+// kernel a single handle of that FFT size and mode runs, reading its parameters from the
+// device table) and its X-engine (the persistent tensor-core kernel over that sub-array's
+// (channel, row block) items, in the operand form its F-engine writes), then the optional
+// dumps and beam averages; the branches join at the end.  Independent branches let the
+// F-engine of one sub-array overlap the X-engine of another.  The graph is captured once and
+// replayed for every integration; new sample pointers and frame counters reach the kernels
+// through the refreshed tables.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,16 +27,18 @@ using namespace gbx;
 struct corr_batch {
     int n_sub = 0;
     corr* h[kMaxSub] = {};
+    int fmode[kMaxSub] = {};       // F-engine output layout of each sub-array
     int xmode = 0, n_sm = 0, dev = 0;
     cudaStream_t cap = nullptr;
+    cudaStream_t br[kMaxSub] = {};    // capture branches, one per sub-array
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kMaxSub] = {};
     FeBatch* h_fe = nullptr;     // pinned
     FeBatch* d_fe = nullptr;
-    XtBatch* h_xt = nullptr;     // pinned
+    XtBatch* h_xt = nullptr;     // pinned, one one-entry table per sub-array
     XtBatch* d_xt = nullptr;
-    int4* d_items = nullptr;
-    int n_items = 0;
-    int fe_blocks = 0;
-    size_t fe_smem = 0;
+    int4* d_items[kMaxSub] = {};
+    int n_items[kMaxSub] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t done = nullptr;  // the last launch: guards the pinned tables
@@ -52,34 +56,28 @@ int bfail(int code, const char* msg) { return fail_code(code, msg); }
 
 bool tc_mode(int xmode) { return xmode == CORR_I8 || xmode == CORR_F16; }
 
-// (sub, channel, row block) items ordered by decreasing cost: wide sub-arrays first.
-std::vector<int4> make_items(const corr_batch* b, int only_sub) {
+// (channel, row block) items of sub-array q, for its one-entry table (sub index 0): a 256-row
+// Gram has two row blocks per channel, the wider one first.
+std::vector<int4> make_items(const corr_batch* b, int q) {
     std::vector<int4> items;
-    for (int s = 0; s < b->n_sub; ++s) {
-        if (only_sub >= 0 && s != only_sub) continue;
-        const int R = 2 * b->h[s]->n_in, rbs = R > 128 ? 2 : 1;
-        for (int k = 0; k < b->h[s]->n_chan; ++k)
-            for (int r = 0; r < rbs; ++r) items.push_back(make_int4(s, k, r, 0));
-    }
-    auto cost = [&](const int4& e) {
-        const corr* h = b->h[e.x];
-        return static_cast<double>(h->n_int) * std::min(2 * h->n_in, 256);
-    };
-    std::stable_sort(items.begin(), items.end(), [&](const int4& a, const int4& c) { return cost(a) > cost(c); });
+    const int R = 2 * b->h[q]->n_in, rbs = R > 128 ? 2 : 1;
+    for (int k = 0; k < b->h[q]->n_chan; ++k)
+        for (int r = 0; r < rbs; ++r) items.push_back(make_int4(0, k, r, 0));
     return items;
 }
 
-void fill_xt(corr_batch* b, XtBatch* t, const int4* items, int n_items) {
+// sub-array q's one-entry X-engine table; false if the driver refuses its tensor map
+bool fill_xt(const corr_batch* b, int q, XtBatch* t, const int4* items, int n_items) {
     std::memset(t, 0, sizeof *t);
-    t->n_sub = b->n_sub;
-    for (int s = 0; s < b->n_sub; ++s) {
-        t->sub[s] = xt_sub_of(b->h[s]);
-        t->sub[s].in8 = 0;   // the batched F-engine writes int8 values in the fp16 layout
-    }
+    t->n_sub = 1;
+    t->sub[0] = xt_sub_of(b->h[q]);   // in8 where the F-engine writes int8 bytes (OUT_I8B)
     t->n_items = n_items;
     t->items = items;
-    t->err = b->h[0]->d_err;
+    t->err = b->h[q]->d_err;
+    return !t->sub[0].in8 || xengine_tc_encode_quad(t->sub[0]);
 }
+
+int xt_form(const corr_batch* b, int q) { return b->fmode[q] == OUT_I8B ? XT_FORM_I8 : XT_FORM_F16; }
 
 FeParams fe_params(corr* h, const int8_t* x, int64_t ld, int64_t n_avail) {
     FeParams fp{};
@@ -105,7 +103,43 @@ FeParams fe_params(corr* h, const int8_t* x, int64_t ld, int64_t n_avail) {
     return fp;
 }
 
-// Capture the integration of every sub-array into one graph on the batch's stream.
+// Branch q of the graph: sub-array q's whole integration on stream s.
+bool capture_branch(corr_batch* b, int q, cudaStream_t s) {
+    corr* h = b->h[q];
+    const int nd = h->n_ant;
+    bool ok = cudaMemcpyAsync(h->d_model, h->h_model, 3 * nd * sizeof(double), cudaMemcpyHostToDevice, s) ==
+                  cudaSuccess &&
+              launch_phasor_setup(h->n_ant, h->n_chan, h->n_fft, h->n_int, 0, h->d_model, h->d_model + nd,
+                                  h->d_model + 2 * nd, h->d_pf, h->d_ff, h->d_D, s, &b->d_fe->g0[q]) == cudaSuccess;
+    ok = ok && launch_fengine_sub(b->d_fe, q, h->n_chan, h->n_int, b->fmode[q], s) == cudaSuccess;
+    if (ok && tc_mode(b->xmode)) {
+        ok = launch_xengine_tc_table(b->d_xt + q, b->n_items[q], b->n_sm, s, xt_form(b, q)) == cudaSuccess;
+    } else if (ok) {
+        XParams xp{};
+        xp.spec = h->d_spec;
+        xp.n_ant = h->n_ant;
+        xp.n_pol = h->n_pol;
+        xp.n_in = h->n_in;
+        xp.n_chan = h->n_chan;
+        xp.n_int = h->n_int;
+        xp.scale = h->d_scale;
+        xp.vis = h->d_vis;
+        xp.err = h->d_err;
+        xp.vis_part = h->d_vis_part;
+        xp.max_split = corr::kVisSplit;
+        xp.self = h->polmode == CORR_POL_SELF ? 1 : 0;
+        ok = launch_xengine_fp32(xp, b->n_sm, s) == cudaSuccess;
+    }
+    if (ok && h->dump > 0 && b->xmode == CORR_FP32)
+        ok = launch_power_dumps(static_cast<const float*>(h->d_spec), h->n_in, h->n_chan, h->n_int, h->dump,
+                                h->d_power, s) == cudaSuccess;
+    if (ok && h->beam_avg > 1)
+        ok = launch_beam_average(h->d_beams_raw, h->d_beams, h->n_int, h->n_chan, h->beam_avg, s) == cudaSuccess;
+    return ok;
+}
+
+// Capture the integration of every sub-array into one graph: the table refresh on the batch's
+// stream, then one branch per sub-array, joined before the capture ends.
 int capture(corr_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
@@ -115,45 +149,18 @@ int capture(corr_batch* b) {
     BCU(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
     bool ok = cudaMemcpyAsync(b->d_fe, b->h_fe, sizeof(FeBatch), cudaMemcpyHostToDevice, s) == cudaSuccess;
     if (ok && tc_mode(b->xmode))
-        ok = cudaMemcpyAsync(b->d_xt, b->h_xt, sizeof(XtBatch), cudaMemcpyHostToDevice, s) == cudaSuccess;
+        ok = cudaMemcpyAsync(b->d_xt, b->h_xt, b->n_sub * sizeof(XtBatch), cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && cudaEventRecord(b->fork, s) == cudaSuccess;
     for (int q = 0; ok && q < b->n_sub; ++q) {
-        corr* h = b->h[q];
-        const int nd = h->n_ant;
-        ok = cudaMemcpyAsync(h->d_model, h->h_model, 3 * nd * sizeof(double), cudaMemcpyHostToDevice, s) ==
-                 cudaSuccess &&
-             launch_phasor_setup(h->n_ant, h->n_chan, h->n_fft, h->n_int, 0, h->d_model, h->d_model + nd,
-                                 h->d_model + 2 * nd, h->d_pf, h->d_ff, h->d_D, s, &b->d_fe->g0[q]) == cudaSuccess;
-    }
-    const int fmode = b->xmode == CORR_FP32 ? OUT_FP32 : (b->xmode == CORR_I8 ? OUT_I8 : OUT_F16);
-    if (ok) ok = launch_fengine_batched(b->d_fe, b->fe_blocks, b->fe_smem, fmode, s) == cudaSuccess;
-    if (ok && tc_mode(b->xmode)) {
-        ok = launch_xengine_tc_table(b->d_xt, b->n_items, b->n_sm, s) == cudaSuccess;
-    } else {
-        for (int q = 0; ok && q < b->n_sub; ++q) {
-            corr* h = b->h[q];
-            XParams xp{};
-            xp.spec = h->d_spec;
-            xp.n_ant = h->n_ant;
-            xp.n_pol = h->n_pol;
-            xp.n_in = h->n_in;
-            xp.n_chan = h->n_chan;
-            xp.n_int = h->n_int;
-            xp.scale = h->d_scale;
-            xp.vis = h->d_vis;
-            xp.err = h->d_err;
-            xp.vis_part = h->d_vis_part;
-            xp.max_split = corr::kVisSplit;
-            xp.self = h->polmode == CORR_POL_SELF ? 1 : 0;
-            ok = launch_xengine_fp32(xp, b->n_sm, s) == cudaSuccess;
+        if (cudaStreamWaitEvent(b->br[q], b->fork, 0) != cudaSuccess) {
+            ok = false;
+            break;
         }
-    }
-    for (int q = 0; ok && q < b->n_sub; ++q) {
-        corr* h = b->h[q];
-        if (h->dump > 0 && b->xmode == CORR_FP32)
-            ok = launch_power_dumps(static_cast<const float*>(h->d_spec), h->n_in, h->n_chan, h->n_int, h->dump,
-                                    h->d_power, s) == cudaSuccess;
-        if (ok && h->beam_avg > 1)
-            ok = launch_beam_average(h->d_beams_raw, h->d_beams, h->n_int, h->n_chan, h->beam_avg, s) == cudaSuccess;
+        ok = capture_branch(b, q, b->br[q]);
+        // join even a failed branch, so that the capture ends cleanly
+        const bool joined = cudaEventRecord(b->join[q], b->br[q]) == cudaSuccess &&
+                            cudaStreamWaitEvent(s, b->join[q], 0) == cudaSuccess;
+        ok = ok && joined;
     }
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(s, &g);
@@ -187,6 +194,7 @@ int corr_batch_create(corr_batch_t** out, int n_sub, corr_t* const* subs) {
     b->xmode = subs[0]->xmode;
     for (int s = 0; s < n_sub; ++s) {
         b->h[s] = subs[s];
+        b->fmode[s] = fe_out_mode(subs[s]);
         subs[s]->batch_refs += 1;
     }
     auto bail = [&](const char* m) {
@@ -197,25 +205,26 @@ int corr_batch_create(corr_batch_t** out, int n_sub, corr_t* const* subs) {
         cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->dev) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(reinterpret_cast<void**>(&b->h_fe), sizeof(FeBatch)) != cudaSuccess ||
-        cudaMallocHost(reinterpret_cast<void**>(&b->h_xt), sizeof(XtBatch)) != cudaSuccess ||
-        cudaMalloc(&b->d_fe, sizeof(FeBatch)) != cudaSuccess || cudaMalloc(&b->d_xt, sizeof(XtBatch)) != cudaSuccess)
+        cudaMallocHost(reinterpret_cast<void**>(&b->h_xt), n_sub * sizeof(XtBatch)) != cudaSuccess ||
+        cudaMalloc(&b->d_fe, sizeof(FeBatch)) != cudaSuccess || cudaMalloc(&b->d_xt, n_sub * sizeof(XtBatch)) != cudaSuccess)
         return bail("batch tables");
+    for (int s = 0; s < n_sub; ++s)
+        if (cudaStreamCreateWithFlags(&b->br[s], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join[s], cudaEventDisableTiming) != cudaSuccess)
+            return bail("batch streams");
     std::memset(b->h_fe, 0, sizeof(FeBatch));
-    b->fe_blocks = 0;
-    for (int s = 0; s < n_sub; ++s) {
-        b->h_fe->first[s] = b->fe_blocks;
-        b->fe_blocks += (fengine_blocks(subs[s]->n_fft, subs[s]->n_int) + 1) & ~1;   // even: cluster pairs
-        b->fe_smem = std::max(b->fe_smem, fengine_smem_bytes(subs[s]->n_fft));
-    }
-    b->h_fe->first[n_sub] = b->fe_blocks;
     b->h_fe->n_sub = n_sub;
     if (tc_mode(b->xmode)) {
-        const std::vector<int4> items = make_items(b, -1);
-        b->n_items = static_cast<int>(items.size());
-        if (cudaMalloc(&b->d_items, sizeof(int4) * items.size()) != cudaSuccess ||
-            cudaMemcpy(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-            return bail("batch items");
+        for (int s = 0; s < n_sub; ++s) {
+            const std::vector<int4> items = make_items(b, s);
+            b->n_items[s] = static_cast<int>(items.size());
+            if (cudaMalloc(&b->d_items[s], sizeof(int4) * items.size()) != cudaSuccess ||
+                cudaMemcpy(b->d_items[s], items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) !=
+                    cudaSuccess)
+                return bail("batch items");
+        }
     }
     *out = b;
     return CORR_OK;
@@ -229,10 +238,15 @@ int corr_batch_destroy(corr_batch_t* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->d_fe) cudaFree(b->d_fe);
     if (b->d_xt) cudaFree(b->d_xt);
-    if (b->d_items) cudaFree(b->d_items);
+    for (int q = 0; q < kMaxSub; ++q) {
+        if (b->d_items[q]) cudaFree(b->d_items[q]);
+        if (b->join[q]) cudaEventDestroy(b->join[q]);
+        if (b->br[q]) cudaStreamDestroy(b->br[q]);
+    }
     if (b->h_fe) cudaFreeHost(b->h_fe);
     if (b->h_xt) cudaFreeHost(b->h_xt);
     if (b->done) cudaEventDestroy(b->done);
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->cap) cudaStreamDestroy(b->cap);
     for (int q = 0; q < b->n_sub; ++q)   // the handles outlive their batches
         if (b->h[q]) b->h[q]->batch_refs -= 1;
@@ -265,11 +279,18 @@ int corr_batch_integrate_device(corr_batch_t* b, const int8_t* const* x, const i
         std::memcpy(h->h_model, h->tau.data(), nd * sizeof(double));
         std::memcpy(h->h_model + nd, h->phi0.data(), nd * sizeof(double));
         std::memcpy(h->h_model + 2 * nd, h->rate.data(), nd * sizeof(double));
+        if (tc_mode(b->xmode) && !fill_xt(b, s, b->h_xt + s, b->d_items[s], b->n_items[s]))
+            return bfail(CORR_E_CUDA, "the driver refused the tensor map of a sub-array's spectra");
     }
-    if (tc_mode(b->xmode)) fill_xt(b, b->h_xt, b->d_items, b->n_items);
     if (!b->exec)
         if (int rc = capture(b)) return rc;
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : b->cap;
+    for (int q = 0; q < b->n_sub; ++q) {   // back from the channel-quad layout: padding rows read as zero
+        corr* h = b->h[q];
+        if (b->fmode[q] == OUT_FP32 && h->last_quad)
+            BCU(cudaMemsetAsync(h->d_spec, 0,
+                                static_cast<size_t>(h->n_chan) * h->n_int * rows_fp32(h->n_in) * sizeof(float), s));
+    }
     BCU(cudaGraphLaunch(b->exec, s));
     BCU(cudaEventRecord(b->done, s));
     b->pending = true;
@@ -278,8 +299,8 @@ int corr_batch_integrate_device(corr_batch_t* b, const int8_t* const* x, const i
         BCU(cudaEventRecord(h->ev_done, s));
         h->launched += 1;
         h->last_mode = h->xmode;
-        h->last_quad = false;   // the batched F-engine writes the plain K-block layouts
-        h->last_i8b = false;
+        h->last_quad = false;
+        h->last_i8b = b->fmode[q] == OUT_I8B;
     }
     return CORR_OK;
 }
@@ -291,7 +312,6 @@ int corr_batch_tune(corr_batch_t* b, int* ks_out, float* ms_out) {
     BCU(cudaSetDevice(b->dev));
     BCU(cudaEventSynchronize(b->done));
     XtBatch* d_tmp = nullptr;
-    int4* d_it = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = CORR_OK;
     if (cudaMalloc(&d_tmp, sizeof(XtBatch)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
@@ -299,25 +319,25 @@ int corr_batch_tune(corr_batch_t* b, int* ks_out, float* ms_out) {
         rc = bfail(CORR_E_NOMEM, "tuning buffers");
     for (int s = 0; rc == CORR_OK && s < b->n_sub; ++s) {
         corr* h = b->h[s];
-        const std::vector<int4> items = make_items(b, s);
-        if (d_it) cudaFree(d_it);
-        d_it = nullptr;
-        if (cudaMalloc(&d_it, sizeof(int4) * items.size()) != cudaSuccess ||
-            cudaMemcpy(d_it, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-            rc = bfail(CORR_E_NOMEM, "tuning items");
-            break;
-        }
         int best = 0;
         float best_ms = 0.0f;
         for (int ks = 32; rc == CORR_OK && ks <= xengine_tc_max_ks(h->n_in); ks *= 2) {
             XtBatch t;
-            fill_xt(b, &t, d_it, static_cast<int>(items.size()));
-            t.sub[s].ks = ks;
+            if (!fill_xt(b, s, &t, b->d_items[s], b->n_items[s])) {
+                rc = bfail(CORR_E_CUDA, "the driver refused the tensor map of a sub-array's spectra");
+                break;
+            }
+            t.sub[0].ks = ks;
+            if (t.sub[0].in8 && !xengine_tc_encode_quad(t.sub[0])) {   // the map's box follows ks
+                rc = bfail(CORR_E_CUDA, "the driver refused the tensor map of a sub-array's spectra");
+                break;
+            }
             float ms = 0.0f;
             bool ok = cudaMemcpy(d_tmp, &t, sizeof t, cudaMemcpyHostToDevice) == cudaSuccess &&
-                      launch_xengine_tc_table(d_tmp, t.n_items, b->n_sm, b->cap) == cudaSuccess &&
+                      launch_xengine_tc_table(d_tmp, t.n_items, b->n_sm, b->cap, xt_form(b, s)) == cudaSuccess &&
                       cudaEventRecord(e0, b->cap) == cudaSuccess;
-            for (int r = 0; ok && r < 3; ++r) ok = launch_xengine_tc_table(d_tmp, t.n_items, b->n_sm, b->cap) == cudaSuccess;
+            for (int r = 0; ok && r < 3; ++r)
+                ok = launch_xengine_tc_table(d_tmp, t.n_items, b->n_sm, b->cap, xt_form(b, s)) == cudaSuccess;
             ok = ok && cudaEventRecord(e1, b->cap) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
                  cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
             if (!ok) {
@@ -336,7 +356,6 @@ int corr_batch_tune(corr_batch_t* b, int* ks_out, float* ms_out) {
             if (ms_out) ms_out[s] = best_ms;
         }
     }
-    if (d_it) cudaFree(d_it);
     if (d_tmp) cudaFree(d_tmp);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

@@ -239,6 +239,8 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
     return CORR_OK;
 }
 
+int gbx::fe_out_mode(const corr* h) { return fe_mode(h); }
+
 gbx::XtSub gbx::xt_sub_of(const corr* h) {
     XtSub x{};
     x.spec = static_cast<const __half*>(h->d_spec);

@@ -1,5 +1,5 @@
-// fengine.cu -- F-engine of the FX correlator for sm_103a: launches of the kernel in
-// fengine_impl.cuh (single integrations and the batched form), the per-integration phasor
+// fengine.cu -- F-engine of the FX correlator for sm_103a: launches of the kernels in
+// fengine_wfft.cuh and fengine_impl.cuh for single integrations, the per-integration phasor
 // set-up, the RFI stage's power dumps and the beam averaging.
 #include <cmath>
 #include <vector>
@@ -91,26 +91,11 @@ __global__ void beam_average_kernel(const float* __restrict__ raw, float* __rest
 
 }  // namespace
 
-size_t fengine_smem_bytes(int n_fft) {
-    switch (n_fft / 2) {
-        case 32: return Smem<32>::total;
-        case 64: return Smem<64>::total;
-        case 128: return Smem<128>::total;
-        case 256: return Smem<256>::total;
-        case 512: return Smem<512>::total;
-        case 1024: return Smem<1024>::total;
-        case 2048: return Smem<2048>::total;
-        default: return 0;
-    }
-}
-
 cudaError_t launch_fengine_twiddles(int n_fft, float2* tw, cudaStream_t s) {
     const int count = fengine_tw_count(n_fft);
     twiddle_kernel<<<(count + 255) / 256, 256, 0, s>>>(n_fft, count, tw);
     return cudaGetLastError();
 }
-
-int fengine_frames_per_cta(int n_fft) { return kChanFrames / (n_fft / 2); }
 
 cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s) {
     if (p.n_chan * 2 != p.n_fft) return cudaErrorInvalidValue;
@@ -120,39 +105,6 @@ cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s) {
         case OUT_F16: return launch_w_mode<OUT_F16>(p, s);
         case OUT_F32Q: return launch_w_mode<OUT_F32Q>(p, s);
         case OUT_I8B: return launch_w_mode<OUT_I8B>(p, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-int fengine_blocks(int n_fft, int n_int) { return (n_int + kChanFrames / (n_fft / 2) - 1) / (kChanFrames / (n_fft / 2)); }
-
-cudaError_t launch_fengine_batched(const FeBatch* dtab, int total_blocks, size_t smem, int mode, cudaStream_t s) {
-    // clusters of two: every sub-array's first block is even (batch code pads the block counts),
-    // so the 4096-point fp16 sub-arrays get their frame-block pairs
-    if (total_blocks % 2) return cudaErrorInvalidValue;
-    auto go = [&](auto kern) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(total_blocks);
-        cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, kern, dtab);
-        if (e != cudaSuccess) return e;
-        return cudaGetLastError();
-    };
-    switch (mode) {
-        case OUT_FP32: return go(fengine_batched_kernel<OUT_FP32>);
-        case OUT_I8: return go(fengine_batched_kernel<OUT_I8>);
-        case OUT_F16: return go(fengine_batched_kernel<OUT_F16>);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -72,24 +72,23 @@ struct FeParams {
     unsigned* err;
 };
 
-// Several integrations in one launch (sub-arrays of uneven sizes).
+// The integrations of a batch (sub-arrays of uneven sizes), in device memory that a captured
+// graph refreshes before each replay.
 constexpr int kMaxSub = 8;
 struct FeBatch {
     int n_sub;
-    int first[kMaxSub + 1];    // first CTA of each sub-array; first[n_sub] = total CTAs
     FeParams p[kMaxSub];
     int64_t g0[kMaxSub];       // global frame index of each sub-array's first frame
 };
-int fengine_blocks(int n_fft, int n_int);
-cudaError_t launch_fengine_batched(const FeBatch* dtab, int total_blocks, size_t smem, int mode, cudaStream_t s);
-
-// Dynamic shared memory needed by the F-engine for a given FFT size.
-size_t fengine_smem_bytes(int n_fft);
-int fengine_frames_per_cta(int n_fft);
+// F-engine of member `sub` of a batch on stream s: the kernel of launch_fengine for n_chan and
+// mode (n_chan <= 1024: OUT_FP32, OUT_F16, OUT_I8B; n_chan = 2048: OUT_FP32, OUT_F16, OUT_I8),
+// reading its parameters from tab->p[sub] when it runs; n_int sizes the grid and must equal
+// tab->p[sub].n_int at that time.
+cudaError_t launch_fengine_sub(const FeBatch* tab, int sub, int n_chan, int n_int, int mode, cudaStream_t s);
 
 // Twiddle table of the F-engines for n_fft (M = n_fft / 2); entry e holds exp(-2 pi i num / den)
 // (fengine_tw_angle), evaluated in FP64 on the device and rounded once (launch_fengine_twiddles).
-//   part A, read by the kernel of fengine_impl.cuh (n_fft = 4096, batched launches): [R2][16]
+//   part A, read by the kernel of fengine_impl.cuh (n_fft = 4096): [R2][16]
 //     pass-2 twiddles W_{16 R2}^(j r), [R3][16 R2] pass-3 twiddles W_M^(j r) when R3 > 1, then
 //     [M/2 + 1] real-split twiddles W_N^k;
 //   part B (M <= 1024), read by the warp-FFT kernel of fengine_wfft.cuh: [P/2][32][2] inter-pass

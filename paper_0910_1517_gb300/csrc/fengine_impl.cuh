@@ -176,7 +176,7 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
     const int fg = tid / TPG;         // frame group of the split: frames fg*L .. fg*L + L - 1
     const int kk = tid % TPG;         // channel pairs kk + q*TPG, q < NP
     const int t0 = block * F;
-    if (t0 >= p.n_int) return;        // padding CTA of a batched launch (never a cluster-paired one)
+    if (t0 >= p.n_int) return;        // no frames left (never in a cluster-paired launch)
     const int n_fr = min(F, p.n_int - t0);
     const bool live = fg * L < n_fr;  // n_fr is a multiple of L: whole frame groups are live or not
     constexpr bool kPair = E::kPair;
@@ -539,30 +539,12 @@ __global__ void __launch_bounds__(kThreads, 1) fengine_kernel(const FeParams p) 
     fengine_cta<M, MODE>(p, blockIdx.x, ctl);
 }
 
-// Several integrations (sub-arrays of any supported FFT size) in one launch: CTA b runs
-// frame block b - first[s] of sub-array s, first[s] <= b < first[s + 1].
-template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1) fengine_batched_kernel(const FeBatch* __restrict__ tab) {
+// One member of a batch: frame block blockIdx.x of the integration in tab->p[sub], the
+// parameters read from the batch's device table when the kernel runs.
+template <int M, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) fengine_tab_kernel(const FeBatch* __restrict__ tab, int sub) {
     __shared__ __align__(8) FeCtl ctl;
-    __shared__ int sub;
-    if (threadIdx.x == 0) {
-        int q = 0;
-        while (q + 1 < tab->n_sub && static_cast<int>(blockIdx.x) >= tab->first[q + 1]) ++q;
-        sub = q;
-    }
-    __syncthreads();
-    const FeParams& p = tab->p[sub];
-    const int block = blockIdx.x - tab->first[sub];
-    switch (p.n_chan) {
-        case 32: fengine_cta<32, MODE>(p, block, ctl); break;
-        case 64: fengine_cta<64, MODE>(p, block, ctl); break;
-        case 128: fengine_cta<128, MODE>(p, block, ctl); break;
-        case 256: fengine_cta<256, MODE>(p, block, ctl); break;
-        case 512: fengine_cta<512, MODE>(p, block, ctl); break;
-        case 1024: fengine_cta<1024, MODE>(p, block, ctl); break;
-        case 2048: fengine_cta<2048, MODE>(p, block, ctl); break;
-        default: break;
-    }
+    fengine_cta<M, MODE>(tab->p[sub], blockIdx.x, ctl);
 }
 
 template <int M, int MODE>

@@ -127,6 +127,8 @@ struct corr {
 namespace gbx {
 // Fill a one-entry tensor-core table describing handle h (its spectra, scales and outputs).
 XtSub xt_sub_of(const corr* h);
+// F-engine output layout (OutMode) of handle h's precision mode.
+int fe_out_mode(const corr* h);
 // Queue the integration's kernels of handle h (used by the C ABI and the batch code).
 int run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, int64_t g0, cudaStream_t s);
 void set_last_error(const char* msg);
