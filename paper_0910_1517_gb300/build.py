@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgb300corr.so")
-SOURCES = ["fengine.cu", "fengine_sub.cu", "xengine_fp32.cu", "xengine_tc.cu", "capi.cu", "noalloc.cu", "rfi.cu", "batch.cu", "blank.cu",
+SOURCES = ["fengine.cu", "xengine_fp32.cu", "xengine_tc.cu", "capi.cu", "noalloc.cu", "rfi.cu", "batch.cu", "blank.cu",
            "multibeam.cu", "multibeam_tc.cu", "ingest4.cu", "dedisp.cu", "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -1,15 +1,16 @@
 // batch.cu -- several sub-arrays of uneven sizes in one graph-captured launch, and
 // the autotuner that picks the tensor-core X-engine's stage size per sub-array.
 //
-// The graph refreshes the batch's parameter tables from pinned host copies, then forks one
-// branch per sub-array: the upload of its delay model, its phasor set-up, its F-engine (the
-// kernel a single handle of that FFT size and mode runs, reading its parameters from the
-// device table) and its X-engine (the persistent tensor-core kernel over that sub-array's
-// (channel, row block) items, in the operand form its F-engine writes), then the optional
-// dumps and beam averages; the branches join at the end.  Independent branches let the
-// F-engine of one sub-array overlap the X-engine of another.  The graph is captured once and
-// replayed for every integration; new sample pointers and frame counters reach the kernels
-// through the refreshed tables.
+// The graph refreshes the batch's small tables (frame counters, X-engine tables) from pinned
+// host copies, then forks one branch per sub-array: the upload of its delay model, its phasor
+// set-up, its F-engine (the kernel a single handle of that FFT size and mode runs) and its
+// X-engine (the persistent tensor-core kernel over that sub-array's (channel, row block) items,
+// in the operand form its F-engine writes), then the optional dumps and beam averages; the
+// branches join at the end.  Independent branches let the F-engine of one sub-array overlap
+// the X-engine of another.  The graph is captured once and replayed for every integration;
+// each replay first sets the F-engine nodes' parameters (new sample pointers) in the
+// executable graph -- except where the F-engine runs in 2-CTA clusters, whose parameters are
+// only ever those of a capture: new ones for such a node capture the graph again.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,8 +34,12 @@ struct corr_batch {
     cudaStream_t br[kMaxSub] = {};    // capture branches, one per sub-array
     cudaEvent_t fork = nullptr;
     cudaEvent_t join[kMaxSub] = {};
-    FeBatch* h_fe = nullptr;     // pinned
-    FeBatch* d_fe = nullptr;
+    int64_t* h_g0 = nullptr;     // pinned: global frame index of each sub-array's first frame
+    int64_t* d_g0 = nullptr;
+    FeParams fe_p[kMaxSub] = {};              // F-engine parameters of the next replay
+    FeParams cap_p[kMaxSub] = {};             // ... and those the graph was captured with
+    cudaGraphNode_t fe_node[kMaxSub] = {};    // the F-engine kernel node of each branch
+    cudaKernelNodeParams fe_kp[kMaxSub] = {};
     XtBatch* h_xt = nullptr;     // pinned, one one-entry table per sub-array
     XtBatch* d_xt = nullptr;
     int4* d_items[kMaxSub] = {};
@@ -110,8 +115,16 @@ bool capture_branch(corr_batch* b, int q, cudaStream_t s) {
     bool ok = cudaMemcpyAsync(h->d_model, h->h_model, 3 * nd * sizeof(double), cudaMemcpyHostToDevice, s) ==
                   cudaSuccess &&
               launch_phasor_setup(h->n_ant, h->n_chan, h->n_fft, h->n_int, 0, h->d_model, h->d_model + nd,
-                                  h->d_model + 2 * nd, h->d_pf, h->d_ff, h->d_D, s, &b->d_fe->g0[q]) == cudaSuccess;
-    ok = ok && launch_fengine_sub(b->d_fe, q, h->n_chan, h->n_int, b->fmode[q], s) == cudaSuccess;
+                                  h->d_model + 2 * nd, h->d_pf, h->d_ff, h->d_D, s, b->d_g0 + q) == cudaSuccess;
+    ok = ok && launch_fengine(b->fe_p[q], b->fmode[q], s) == cudaSuccess;
+    if (ok) {   // the node just captured: its parameters are set again before every replay
+        cudaStreamCaptureStatus st{};
+        const cudaGraphNode_t* deps = nullptr;
+        size_t n_deps = 0;
+        ok = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &n_deps) == cudaSuccess &&
+             st == cudaStreamCaptureStatusActive && n_deps == 1;
+        if (ok) b->fe_node[q] = deps[0];
+    }
     if (ok && tc_mode(b->xmode)) {
         ok = launch_xengine_tc_table(b->d_xt + q, b->n_items[q], b->n_sm, s, xt_form(b, q)) == cudaSuccess;
     } else if (ok) {
@@ -147,7 +160,7 @@ int capture(corr_batch* b) {
     b->graph = nullptr;
     cudaStream_t s = b->cap;
     BCU(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-    bool ok = cudaMemcpyAsync(b->d_fe, b->h_fe, sizeof(FeBatch), cudaMemcpyHostToDevice, s) == cudaSuccess;
+    bool ok = cudaMemcpyAsync(b->d_g0, b->h_g0, b->n_sub * sizeof(int64_t), cudaMemcpyHostToDevice, s) == cudaSuccess;
     if (ok && tc_mode(b->xmode))
         ok = cudaMemcpyAsync(b->d_xt, b->h_xt, b->n_sub * sizeof(XtBatch), cudaMemcpyHostToDevice, s) == cudaSuccess;
     ok = ok && cudaEventRecord(b->fork, s) == cudaSuccess;
@@ -170,6 +183,8 @@ int capture(corr_batch* b) {
     }
     b->graph = g;
     BCU(cudaGraphInstantiate(&b->exec, g, 0));
+    for (int q = 0; q < b->n_sub; ++q) b->cap_p[q] = b->fe_p[q];
+    for (int q = 0; q < b->n_sub; ++q) BCU(cudaGraphKernelNodeGetParams(b->fe_node[q], &b->fe_kp[q]));
     return CORR_OK;
 }
 
@@ -206,16 +221,16 @@ int corr_batch_create(corr_batch_t** out, int n_sub, corr_t* const* subs) {
         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost(reinterpret_cast<void**>(&b->h_fe), sizeof(FeBatch)) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&b->h_g0), kMaxSub * sizeof(int64_t)) != cudaSuccess ||
         cudaMallocHost(reinterpret_cast<void**>(&b->h_xt), n_sub * sizeof(XtBatch)) != cudaSuccess ||
-        cudaMalloc(&b->d_fe, sizeof(FeBatch)) != cudaSuccess || cudaMalloc(&b->d_xt, n_sub * sizeof(XtBatch)) != cudaSuccess)
+        cudaMalloc(&b->d_g0, kMaxSub * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&b->d_xt, n_sub * sizeof(XtBatch)) != cudaSuccess)
         return bail("batch tables");
     for (int s = 0; s < n_sub; ++s)
         if (cudaStreamCreateWithFlags(&b->br[s], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&b->join[s], cudaEventDisableTiming) != cudaSuccess)
             return bail("batch streams");
-    std::memset(b->h_fe, 0, sizeof(FeBatch));
-    b->h_fe->n_sub = n_sub;
+    std::memset(b->h_g0, 0, kMaxSub * sizeof(int64_t));
     if (tc_mode(b->xmode)) {
         for (int s = 0; s < n_sub; ++s) {
             const std::vector<int4> items = make_items(b, s);
@@ -236,14 +251,14 @@ int corr_batch_destroy(corr_batch_t* b) {
     if (b->done) cudaEventSynchronize(b->done);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    if (b->d_fe) cudaFree(b->d_fe);
+    if (b->d_g0) cudaFree(b->d_g0);
     if (b->d_xt) cudaFree(b->d_xt);
     for (int q = 0; q < kMaxSub; ++q) {
         if (b->d_items[q]) cudaFree(b->d_items[q]);
         if (b->join[q]) cudaEventDestroy(b->join[q]);
         if (b->br[q]) cudaStreamDestroy(b->br[q]);
     }
-    if (b->h_fe) cudaFreeHost(b->h_fe);
+    if (b->h_g0) cudaFreeHost(b->h_g0);
     if (b->h_xt) cudaFreeHost(b->h_xt);
     if (b->done) cudaEventDestroy(b->done);
     if (b->fork) cudaEventDestroy(b->fork);
@@ -273,8 +288,8 @@ int corr_batch_integrate_device(corr_batch_t* b, const int8_t* const* x, const i
     if (b->pending) BCU(cudaEventSynchronize(b->done));
     for (int s = 0; s < b->n_sub; ++s) {
         corr* h = b->h[s];
-        b->h_fe->p[s] = fe_params(h, x[s], ld[s], n_avail[s]);
-        b->h_fe->g0[s] = g0 ? g0[s] : 0;
+        b->fe_p[s] = fe_params(h, x[s], ld[s], n_avail[s]);
+        b->h_g0[s] = g0 ? g0[s] : 0;
         const int nd = h->n_ant;
         std::memcpy(h->h_model, h->tau.data(), nd * sizeof(double));
         std::memcpy(h->h_model + nd, h->phi0.data(), nd * sizeof(double));
@@ -282,8 +297,20 @@ int corr_batch_integrate_device(corr_batch_t* b, const int8_t* const* x, const i
         if (tc_mode(b->xmode) && !fill_xt(b, s, b->h_xt + s, b->d_items[s], b->n_items[s]))
             return bfail(CORR_E_CUDA, "the driver refused the tensor map of a sub-array's spectra");
     }
-    if (!b->exec)
+    bool recapture = !b->exec;
+    for (int q = 0; q < b->n_sub; ++q)
+        if (fengine_clustered(b->h[q]->n_chan, b->fmode[q]) && std::memcmp(&b->fe_p[q], &b->cap_p[q], sizeof(FeParams)))
+            recapture = true;
+    if (recapture)
         if (int rc = capture(b)) return rc;
+    for (int q = 0; q < b->n_sub; ++q) {   // this integration's sample pointers into the F-engine nodes
+        if (fengine_clustered(b->h[q]->n_chan, b->fmode[q])) continue;
+        cudaKernelNodeParams kp = b->fe_kp[q];
+        void* args[1] = {&b->fe_p[q]};
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        BCU(cudaGraphExecKernelNodeSetParams(b->exec, b->fe_node[q], &kp));
+    }
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : b->cap;
     for (int q = 0; q < b->n_sub; ++q) {   // back from the channel-quad layout: padding rows read as zero
         corr* h = b->h[q];

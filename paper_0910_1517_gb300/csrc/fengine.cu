@@ -109,6 +109,8 @@ cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s) {
     }
 }
 
+bool fengine_clustered(int n_chan, int mode) { return n_chan == 2048 && (mode == OUT_I8 || mode == OUT_F16); }
+
 cudaError_t launch_phasor_setup(int n_ant, int n_chan, int n_fft, int n_int, int64_t g0, const double* tau,
                                 const double* phi0, const double* rate, float2* pf, float2* ff, int* D,
                                 cudaStream_t s, const int64_t* g0_dev) {

@@ -72,19 +72,8 @@ struct FeParams {
     unsigned* err;
 };
 
-// The integrations of a batch (sub-arrays of uneven sizes), in device memory that a captured
-// graph refreshes before each replay.
+// Sub-arrays of one batch (corr_batch_*).
 constexpr int kMaxSub = 8;
-struct FeBatch {
-    int n_sub;
-    FeParams p[kMaxSub];
-    int64_t g0[kMaxSub];       // global frame index of each sub-array's first frame
-};
-// F-engine of member `sub` of a batch on stream s: the kernel of launch_fengine for n_chan and
-// mode (n_chan <= 1024: OUT_FP32, OUT_F16, OUT_I8B; n_chan = 2048: OUT_FP32, OUT_F16, OUT_I8),
-// reading its parameters from tab->p[sub] when it runs; n_int sizes the grid and must equal
-// tab->p[sub].n_int at that time.
-cudaError_t launch_fengine_sub(const FeBatch* tab, int sub, int n_chan, int n_int, int mode, cudaStream_t s);
 
 // Twiddle table of the F-engines for n_fft (M = n_fft / 2); entry e holds exp(-2 pi i num / den)
 // (fengine_tw_angle), evaluated in FP64 on the device and rounded once (launch_fengine_twiddles).
@@ -166,6 +155,8 @@ __device__ inline float2 model_fringe_phasor(double phi0, double rate, int64_t g
 }
 
 cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s);
+// true where launch_fengine launches 2-CTA clusters (n_chan 2048, fp16 K-block layouts)
+bool fengine_clustered(int n_chan, int mode);
 
 // pf, ff and D for one integration from the FP64 delay / fringe model.
 // g0_dev, when given, is read on the device instead of g0 (graph-captured launches).

@@ -539,14 +539,6 @@ __global__ void __launch_bounds__(kThreads, 1) fengine_kernel(const FeParams p) 
     fengine_cta<M, MODE>(p, blockIdx.x, ctl);
 }
 
-// One member of a batch: frame block blockIdx.x of the integration in tab->p[sub], the
-// parameters read from the batch's device table when the kernel runs.
-template <int M, int MODE>
-__global__ void __launch_bounds__(kThreads, 1) fengine_tab_kernel(const FeBatch* __restrict__ tab, int sub) {
-    __shared__ __align__(8) FeCtl ctl;
-    fengine_cta<M, MODE>(tab->p[sub], blockIdx.x, ctl);
-}
-
 template <int M, int MODE>
 cudaError_t launch_t(const FeParams& p, cudaStream_t s) {
     using P = Plan<M>;
