@@ -262,10 +262,11 @@ int corr_stage_times(corr_t* h, float* ms4, int* n);
 /* ---- Several sub-arrays in one launch ----------------------------------------
  * A batch runs one integration of each of up to 8 handles (sub-arrays of uneven
  * antenna counts and FFT sizes, all in the same precision mode) as a single CUDA
- * graph: one phasor set-up per sub-array, one F-engine launch whose CTAs cover
- * the frame blocks of every sub-array, and one persistent X-engine launch whose
- * CTAs walk the (sub-array, channel) work of all of them (tensor-core modes; in
- * CORR_FP32 the X stage is one launch per sub-array).  The paper runs its
+ * graph launch: one branch per sub-array -- its phasor set-up, the F-engine
+ * kernel a single handle of that size runs, and its X-engine (the persistent
+ * tensor-core kernel over its (channel, row block) items, or the CUDA-core
+ * kernel in CORR_FP32) -- with the branches running concurrently, so that one
+ * sub-array's X-engine overlaps another's F-engine.  The paper runs its
  * functional pipeline over several time slices concurrently (Sec. 2.3.2); here
  * the concurrency is across independent observations.  Results are read per
  * handle with the functions above.  The handles stay owned by the caller and
@@ -273,7 +274,10 @@ int corr_stage_times(corr_t* h, float* ms4, int* n);
  * cannot join one (CORR_E_STATE), nor can a batch member get a ring.
  * corr_batch_integrate_device takes per-sub-array
  * device sample pointers, row strides, readable samples and first global
- * frames (arrays of n_sub); the graph is captured on the first call.
+ * frames (arrays of n_sub); the graph is captured on the first call, later
+ * calls set the new pointers in its F-engine nodes (a sub-array whose F-engine
+ * runs in 2-CTA clusters -- 4096-point FFTs in CORR_I8 / CORR_F16 -- captures
+ * the graph again when its pointers change).
  * corr_batch_tune times every allowed X-engine stage size per sub-array on the
  * spectra of the last batch integration, keeps the fastest (ks_out, ms_out per
  * sub-array, either may be NULL) and rebuilds the graph. */
