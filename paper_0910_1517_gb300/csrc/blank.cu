@@ -8,9 +8,9 @@
 // sample is replaced iff d2 > T2 -- the same decision as the FP64 comparison -- by
 // rint(sigma g) clamped to +-127, sigma = MAD / 0.6745 rounded to FP32 and g the input's
 // table noise at the sample's position.  The same CTA then writes the block's blanked samples
-// (a second read of the block, from L1), which the F-engine reads instead of the raw rows.
-// (Fusing the replacement into the F-engine's sample conversion was measured first: +1.75 ms
-// on the GMRT-scale F-engine against +0.3 ms for this separate pass.)
+// (testing four samples at a time against integer bounds), which the F-engine reads instead of
+// the raw rows.  (Fusing the replacement into the F-engine's sample conversion was measured
+// first: +1.75 ms on the GMRT-scale F-engine, more than this separate pass.)
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -56,6 +56,11 @@ __device__ __forceinline__ int warp_select(const int* hist, int rank, int lane) 
     return __shfl_sync(0xffffffffu, bin, src);
 }
 
+// int4 pieces of the block a thread keeps in registers between the histogram and the copy;
+// the copy reads the others again (from L1 / L2).  One: at 48 registers (four pieces) the SM
+// holds 5 CTAs instead of 8, and the GMRT-scale pass ran 10 % slower.
+constexpr int kBlankCache = 1;
+
 __global__ void __launch_bounds__(kBlankThreads) blank_kernel(const int8_t* __restrict__ x, int64_t ld, int64_t n,
                                                                int block, double M, const float* __restrict__ noise,
                                                                int noise_mask, int32_t* __restrict__ stats,
@@ -71,17 +76,28 @@ __global__ void __launch_bounds__(kBlankThreads) blank_kernel(const int8_t* __re
     for (int q = threadIdx.x; q < kBlankWarps * 256; q += kBlankThreads) (&hw[0][0])[q] = 0;
     for (int q = threadIdx.x; q < 512; q += kBlankThreads) hd[q] = 0;
     __syncthreads();
-    // pass 1: histogram of x (16-byte loads: rows and blocks start on 16-byte boundaries)
+    // pass 1: histogram of x (16-byte loads: rows and blocks start on 16-byte boundaries).  The
+    // first kBlankCache pieces of each thread are loaded together and kept for pass 3; a byte
+    // b of w ^ 0x80808080 is x + 128.
     const int n16 = len / 16;
     int* h = hw[warp];
-    for (int q = threadIdx.x; q < n16; q += kBlankThreads) {
-        const int4 w = __ldg(reinterpret_cast<const int4*>(row) + q);
-        const uint32_t u[4] = {static_cast<uint32_t>(w.x), static_cast<uint32_t>(w.y), static_cast<uint32_t>(w.z),
-                               static_cast<uint32_t>(w.w)};
+    auto count = [&](const int4& w) {
+        const uint32_t u[4] = {static_cast<uint32_t>(w.x) ^ 0x80808080u, static_cast<uint32_t>(w.y) ^ 0x80808080u,
+                               static_cast<uint32_t>(w.z) ^ 0x80808080u, static_cast<uint32_t>(w.w) ^ 0x80808080u};
 #pragma unroll
-        for (int e = 0; e < 16; ++e)
-            atomicAdd(&h[static_cast<int>(static_cast<int8_t>((u[e >> 2] >> (8 * (e & 3))) & 0xff)) + 128], 1);
+        for (int e = 0; e < 16; ++e) atomicAdd(&h[(u[e >> 2] >> (8 * (e & 3))) & 0xff], 1);
+    };
+    int4 keep[kBlankCache];
+#pragma unroll
+    for (int k = 0; k < kBlankCache; ++k) {
+        const int q = threadIdx.x + k * kBlankThreads;
+        keep[k] = q < n16 ? __ldg(reinterpret_cast<const int4*>(row) + q) : make_int4(0, 0, 0, 0);
     }
+#pragma unroll
+    for (int k = 0; k < kBlankCache; ++k)
+        if (threadIdx.x + k * kBlankThreads < n16) count(keep[k]);
+    for (int q = threadIdx.x + kBlankCache * kBlankThreads; q < n16; q += kBlankThreads)
+        count(__ldg(reinterpret_cast<const int4*>(row) + q));
     for (int q = 16 * n16 + threadIdx.x; q < len; q += kBlankThreads) atomicAdd(&h[row[q] + 128], 1);
     __syncthreads();
     {   // merge the warp histograms into hw[0]
@@ -126,33 +142,48 @@ __global__ void __launch_bounds__(kBlankThreads) blank_kernel(const int8_t* __re
         }
     }
     __syncthreads();
-    // pass 3: the blanked block
+    // pass 3: the blanked block.  |2x - med2| > T2 holds exactly for x > hi_x or x < lo_x,
+    // hi_x = floor((med2 + T2) / 2), lo_x = ceil((med2 - T2) / 2) (integer x); clamped to the
+    // int8 range they compare four samples at a time, and only a word holding a flagged sample
+    // takes the per-byte replacement.
     const int T2 = t2_s;
     const float sg = sig_s;
+    const int hi_x = min(127, (med2 + T2) >> 1), lo_x = max(-128, (med2 - T2 + 1) >> 1);
+    const uint32_t hi4 = static_cast<uint32_t>(hi_x & 0xff) * 0x01010101u;
+    const uint32_t lo4 = static_cast<uint32_t>(lo_x & 0xff) * 0x01010101u;
     const float* g = noise + static_cast<int64_t>(i) * (noise_mask + 1);
     int8_t* out = y + static_cast<int64_t>(i) * ldy + p0;
-    auto fix = [&](int v, int64_t pos) {
-        if (abs(2 * v - med2) <= T2) return v;
+    auto repl = [&](int64_t pos) {
         const float r = rintf(__fmul_rn(sg, __ldg(g + (pos & noise_mask))));
         return static_cast<int>(fminf(127.0f, fmaxf(-127.0f, r)));
     };
-    for (int q = threadIdx.x; q < n16; q += kBlankThreads) {
-        const int4 w = __ldg(reinterpret_cast<const int4*>(row) + q);
-        uint32_t u[4] = {static_cast<uint32_t>(w.x), static_cast<uint32_t>(w.y), static_cast<uint32_t>(w.z),
-                         static_cast<uint32_t>(w.w)};
+    auto fix_word = [&](uint32_t w, int64_t pos) {   // 4 samples starting at block position pos
+        const uint32_t flag = __vcmpgts4(w, hi4) | __vcmplts4(w, lo4);
+        if (flag == 0u) return w;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int v = static_cast<int>(static_cast<int8_t>((u[e >> 2] >> (8 * (e & 3))) & 0xff));
-            const int nv = fix(v, p0 + 16 * q + e);
-            if (nv != v)
-                u[e >> 2] = (u[e >> 2] & ~(0xffu << (8 * (e & 3)))) |
-                            ((static_cast<uint32_t>(nv) & 0xffu) << (8 * (e & 3)));
-        }
-        reinterpret_cast<int4*>(out)[q] = make_int4(static_cast<int>(u[0]), static_cast<int>(u[1]),
-                                                    static_cast<int>(u[2]), static_cast<int>(u[3]));
+        for (int e = 0; e < 4; ++e)
+            if ((flag >> (8 * e)) & 0xffu)
+                w = (w & ~(0xffu << (8 * e))) | ((static_cast<uint32_t>(repl(pos + e)) & 0xffu) << (8 * e));
+        return w;
+    };
+    auto fix = [&](const int4& v, int q) {
+        const int64_t pos = p0 + 16 * static_cast<int64_t>(q);
+        reinterpret_cast<int4*>(out)[q] = make_int4(static_cast<int>(fix_word(static_cast<uint32_t>(v.x), pos)),
+                                                    static_cast<int>(fix_word(static_cast<uint32_t>(v.y), pos + 4)),
+                                                    static_cast<int>(fix_word(static_cast<uint32_t>(v.z), pos + 8)),
+                                                    static_cast<int>(fix_word(static_cast<uint32_t>(v.w), pos + 12)));
+    };
+#pragma unroll
+    for (int k = 0; k < kBlankCache; ++k) {
+        const int q = threadIdx.x + k * kBlankThreads;
+        if (q < n16) fix(keep[k], q);
     }
-    for (int q = 16 * n16 + threadIdx.x; q < len; q += kBlankThreads)
-        out[q] = static_cast<int8_t>(fix(row[q], p0 + q));
+    for (int q = threadIdx.x + kBlankCache * kBlankThreads; q < n16; q += kBlankThreads)
+        fix(__ldg(reinterpret_cast<const int4*>(row) + q), q);
+    for (int q = 16 * n16 + threadIdx.x; q < len; q += kBlankThreads) {
+        const int v = row[q];
+        out[q] = static_cast<int8_t>(v > hi_x || v < lo_x ? repl(p0 + q) : v);
+    }
 }
 
 }  // namespace

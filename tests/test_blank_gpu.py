@@ -39,12 +39,12 @@ def _stream(seed=6100):
     return s, clean, noise
 
 
-def _run(env, s, x, mode=0, blank=True, noise=None):
+def _run(env, s, x, mode=0, blank=True, noise=None, block=BLOCK):
     torch, corr, _ = env
     h = corr.corr_create(s.n_ant, s.n_pol, s.n_fft, s.n_int)
     corr.corr_set_delays(h, s.delay, s.phi0, s.rate)
     if blank:
-        corr.corr_set_blanker(h, M, BLOCK, noise)
+        corr.corr_set_blanker(h, M, block, noise)
     n = x.shape[1]
     xt = torch.zeros((s.n_in, ((n + 15) // 16) * 16 + 16), dtype=torch.int8, device="cuda")
     xt[:, :n] = torch.from_numpy(np.ascontiguousarray(x)).cuda()
@@ -61,13 +61,17 @@ def _run(env, s, x, mode=0, blank=True, noise=None):
     return out
 
 
-def test_blank_statistics_bit_exact_and_spectra_match_oracle(env):
+# 4096: one 16-byte piece a thread, kept in registers; 16384: four, all kept; 32768: the pieces
+# past the fourth read again for the copy; every size ends in a ragged block
+@pytest.mark.parametrize("block", [4096, 16384, 32768])
+def test_blank_statistics_bit_exact_and_spectra_match_oracle(env, block):
     torch, corr, orc = env
     s, _, noise = _stream()
-    r = _run(env, s, s.x, noise=noise)
+    r = _run(env, s, s.x, noise=noise, block=block)
     n = r["n"]
     assert n == s.n_int * s.n_fft + int(np.floor(s.delay + 0.5).max())
-    xb, st = orc.mad_blank(s.x[:, :n], BLOCK, M, noise)
+    assert n % block
+    xb, st = orc.mad_blank(s.x[:, :n], block, M, noise)
     assert r["stats"].shape == st.shape and np.array_equal(r["stats"], st)
     assert st[..., 3].sum() > 1000                   # the bursts are there and get replaced
     chans = [0, 1, 100, 255, 256, 333, 511]
