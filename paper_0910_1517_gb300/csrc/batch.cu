@@ -327,7 +327,6 @@ int corr_batch_integrate_device(corr_batch_t* b, const int8_t* const* x, const i
         h->launched += 1;
         h->last_mode = h->xmode;
         h->last_quad = false;
-        h->last_i8b = b->fmode[q] == OUT_I8B;
     }
     return CORR_OK;
 }

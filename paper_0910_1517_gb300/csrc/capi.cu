@@ -111,7 +111,7 @@ bool spec_quad(const corr* h) { return h->xmode == CORR_FP32TC && h->n_chan <= 1
 // F-engine output mode of a handle's X-engine precision mode
 int fe_mode(const corr* h) {
     switch (h->xmode) {
-        case CORR_I8: return h->n_chan <= 1024 ? OUT_I8B : OUT_I8;   // int8 bytes where the warp-FFT kernel runs
+        case CORR_I8: return OUT_I8B;                                  // int8 bytes, 1 B a sample
         case CORR_F16: return OUT_F16;
         default: return spec_quad(h) ? OUT_F32Q : OUT_FP32;
     }
@@ -186,7 +186,6 @@ int gbx::run_integration(corr* h, const int8_t* x, int64_t ld, int64_t n_avail, 
                            static_cast<size_t>(h->n_chan) * h->n_int * rows_fp32(h->n_in) * sizeof(float), s));
     }
     h->last_quad = fmode == OUT_F32Q;
-    h->last_i8b = fmode == OUT_I8B;
     if (int rc = mark(h, 1, s)) return rc;
     if (h->blank_M > 0.0) {   // voltage blanker: per-block statistics of every sample the F-engine reads
         const int64_t need = static_cast<int64_t>(h->n_int) * h->n_fft + max_int_delay(h);
@@ -908,38 +907,20 @@ int corr_read_requant(corr_t* h, int k0, int nk, int8_t* q, float* scale) {
         CU(cudaMemcpy(scale, h->d_scale, static_cast<size_t>(h->n_in) * h->n_chan * sizeof(float),
                       cudaMemcpyDeviceToHost));
     if (q && nk > 0) {
-        // int8 bytes in the channel-quad layout (OUT_I8B: i8q_piece), or int8 values in the fp16
-        // K-block layout [k][kb][r][8] (OUT_I8)
-        const bool bytes = h->last_i8b;
+        // int8 bytes in the channel-quad layout (OUT_I8B: i8q_piece): the quads covering k0 .. k0 + nk - 1
         const int R = 2 * h->n_in, ntb = h->n_int / kTbHalf;
         const size_t per_ch = static_cast<size_t>(ntb) * R * kTbHalf;
-        std::vector<__half> buf(bytes ? 0 : per_ch * nk);
-        std::vector<int8_t> buf8;
-        int q0 = 0;                                        // first channel quad copied
-        if (bytes) {
-            q0 = k0 / 4;
-            const int q1 = (k0 + nk + 3) / 4;
-            buf8.resize(per_ch * 4 * (q1 - q0));
-            CU(cudaMemcpy(buf8.data(), static_cast<const int8_t*>(h->d_spec) + per_ch * 4 * q0, buf8.size(),
-                          cudaMemcpyDeviceToHost));
-        } else {
-            CU(cudaMemcpy(buf.data(), static_cast<const __half*>(h->d_spec) + per_ch * k0, buf.size() * sizeof(__half),
-                          cudaMemcpyDeviceToHost));
-        }
+        const int q0 = k0 / 4, q1 = (k0 + nk + 3) / 4;
+        std::vector<int8_t> buf8(per_ch * 4 * (q1 - q0));
+        CU(cudaMemcpy(buf8.data(), static_cast<const int8_t*>(h->d_spec) + per_ch * 4 * q0, buf8.size(),
+                      cudaMemcpyDeviceToHost));
         for (int c = 0; c < nk; ++c)
             for (int kb = 0; kb < ntb; ++kb)
                 for (int r = 0; r < R; ++r)
                     for (int e = 0; e < kTbHalf; ++e) {
                         const int i = r / 2, cc = r % 2, t = kb * kTbHalf + e;
-                        int8_t v;
-                        if (bytes) {
-                            const int k = k0 + c;
-                            v = buf8[i8q_piece(k - 4 * q0, kb, i, ntb, h->n_in) + cc * kTbHalf + e];
-                        } else {
-                            v = static_cast<int8_t>(
-                                __half2float(buf[((static_cast<size_t>(c) * ntb + kb) * R + r) * kTbHalf + e]));
-                        }
-                        q[((static_cast<size_t>(i) * h->n_int + t) * nk + c) * 2 + cc] = v;
+                        q[((static_cast<size_t>(i) * h->n_int + t) * nk + c) * 2 + cc] =
+                            buf8[i8q_piece(k0 + c - 4 * q0, kb, i, ntb, h->n_in) + cc * kTbHalf + e];
                     }
     }
     return CORR_OK;

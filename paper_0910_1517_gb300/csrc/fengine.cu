@@ -101,7 +101,6 @@ cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s) {
     if (p.n_chan * 2 != p.n_fft) return cudaErrorInvalidValue;
     switch (mode) {
         case OUT_FP32: return launch_w_mode<OUT_FP32>(p, s);
-        case OUT_I8: return launch_w_mode<OUT_I8>(p, s);
         case OUT_F16: return launch_w_mode<OUT_F16>(p, s);
         case OUT_F32Q: return launch_w_mode<OUT_F32Q>(p, s);
         case OUT_I8B: return launch_w_mode<OUT_I8B>(p, s);
@@ -109,7 +108,9 @@ cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s) {
     }
 }
 
-bool fengine_clustered(int n_chan, int mode) { return n_chan == 2048 && (mode == OUT_I8 || mode == OUT_F16); }
+bool fengine_clustered(int n_chan, int mode) {
+    return n_chan == 2048 && (mode == OUT_F16 || mode == OUT_I8B);
+}
 
 cudaError_t launch_phasor_setup(int n_ant, int n_chan, int n_fft, int n_int, int64_t g0, const double* tau,
                                 const double* phi0, const double* rate, float2* pf, float2* ff, int* D,

@@ -8,16 +8,15 @@
 
 namespace gbx {
 
-enum OutMode : int { OUT_FP32 = 0, OUT_I8 = 1, OUT_F16 = 2, OUT_F32Q = 3, OUT_I8B = 4 };
+enum OutMode : int { OUT_FP32 = 0, OUT_F16 = 2, OUT_F32Q = 3, OUT_I8B = 4 };
 
 // Spectra hand-off layout ("K-block layout"), shared by every X-engine:
 //   S[k][kb][r][TB]   k channel, kb = t / TB, r = 2*i + c (c = 0 re, 1 im), TB = t % TB
 // One (k, kb) block holds every input's rows for TB consecutive frames.
 // fp16 (tensor-core X-engine): TB = 8, R = 2 n_in unswizzled rows of 16 bytes -- exactly
-// the no-swizzle K-major canonical layout of a tcgen05 operand tile.  OUT_I8 writes the int8
-// requantised values in this fp16 layout; OUT_I8B (n_chan <= 1024) writes them as bytes in the
-// channel-quad arrangement (i8q_piece) that the X-engine gathers by TMA into [kb][r][8 bytes]
-// and widens to fp16 on chip.
+// the no-swizzle K-major canonical layout of a tcgen05 operand tile (OUT_F16).  OUT_I8B writes
+// the int8 requantised values as bytes in the channel-quad arrangement (i8q_piece) that the
+// X-engine gathers by TMA into [kb][r][8 bytes] and widens to fp16 on chip.
 // FP32 (CUDA-core X-engine): TB = tb_fp32(n_chan) = 8 frames (4 when an F-engine CTA covers
 // only 4 frames, n_chan = 2048), rows padded to Rp = round_up(2 n_in, 8).  The block is cut
 // into 16-byte granules of 4 frames of one row, 8 rows (one input group of 4) per row group
@@ -155,7 +154,7 @@ __device__ inline float2 model_fringe_phasor(double phi0, double rate, int64_t g
 }
 
 cudaError_t launch_fengine(const FeParams& p, int mode, cudaStream_t s);
-// true where launch_fengine launches 2-CTA clusters (n_chan 2048, fp16 K-block layouts)
+// true where launch_fengine launches 2-CTA clusters (n_chan 2048, fp16 layouts and int8 bytes)
 bool fengine_clustered(int n_chan, int mode);
 
 // pf, ff and D for one integration from the FP64 delay / fringe model.

@@ -111,6 +111,8 @@ struct Epi {
     // frame blocks) trade halves of their channels through distributed shared memory, so that each
     // writes whole 32-byte pieces (8 frames x re, im) of its half of the channels
     static constexpr bool kPair = (M == 2048 && MODE != OUT_FP32);
+    static_assert(MODE != OUT_I8B || M == 2048, "int8 bytes from this kernel at n_chan 2048 only");
+    static_assert(MODE != OUT_F32Q, "the channel-quad FP32 layout comes from the warp-FFT kernel");
     static_assert(L % TB == 0 || L < TB, "whole K-block runs, or part of one when F < TB");
     static constexpr int NP = kE / (2 * L);                // channel pairs per thread
     static constexpr int TPG = L * P::T;                   // threads per frame group
@@ -229,7 +231,8 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
     // partner's buffer a CTA waits on xempty, which the partner's arrive completes once it has
     // read that buffer.  All waits are bounded; one cluster barrier at exit keeps both CTAs
     // resident while the other may still write into them.
-    constexpr uint32_t kXBytes = (M / 2) * 16;           // partner's re + im halves of our channels
+    // partner's re + im halves of our channels: 4 frames of fp16 (16 bytes), or of int8 (8 bytes)
+    constexpr uint32_t kXBytes = (M / 2) * (MODE == OUT_I8B ? 8 : 16);
     uint32_t peer_xfull = 0, peer_xempty = 0;
     if constexpr (kPair) {
         cluster_sync();                                  // both CTAs and their barriers exist
@@ -419,18 +422,36 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
                     put(odd ? chp : chs[c], d0);
                     put(odd ? chs[c] : chp, d1);
                 }
+            } else if constexpr (MODE == OUT_I8B) {
+                // int8 bytes (the channel-quad piece i8q_piece: 8 re then 8 im bytes): this CTA's
+                // 4 frames go, as one 8-byte word (re 4 | im 4), to slot `rank` of the exchange
+                // buffer of the pair's CTA that writes channel ch (rank 0: channels < M/2)
+                static_assert(L == 4 && kPair, "int8 bytes of 4-frame CTAs in cluster pairs");
+                uint32_t wv[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {   // h = 0 re, 1 im
+                    int qv[4];
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        const float xq = (h ? yc[l].y : yc[l].x) * scv[c];
+                        qv[l] = max(-127, min(127, __float2int_rn(xq)));
+                    }
+                    wv[h] = __byte_perm(__byte_perm(qv[0], qv[1], 0x0040), __byte_perm(qv[2], qv[3], 0x0040), 0x5410);
+                }
+                const int ch = chs[c];
+                const uint32_t owner = ch < M / 2 ? 0u : 1u;
+                unsigned char* d = xch + (static_cast<size_t>(rank) * (M / 2) + ch % (M / 2)) * 8;
+                if (owner == rank)
+                    *reinterpret_cast<uint2*>(d) = make_uint2(wv[0], wv[1]);
+                else
+                    st_async_v2(cluster_map(d, owner), wv[0], wv[1], peer_xfull);
             } else {
                 __half hr[L], hi[L];
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
                     const float xr = yc[l].x * scv[c], xi = yc[l].y * scv[c];
-                    if constexpr (MODE == OUT_I8) {
-                        hr[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xr))));
-                        hi[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xi))));
-                    } else {
-                        hr[l] = __float2half_rn(xr);
-                        hi[l] = __float2half_rn(xi);
-                    }
+                    hr[l] = __float2half_rn(xr);
+                    hi[l] = __float2half_rn(xi);
                 }
                 __half* o = static_cast<__half*>(p.spec) + blk + 2 * i * TB + (t0 + fg * L) % TB;
                 if constexpr (L == 8) {
@@ -501,13 +522,24 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
             __syncthreads();
             if (!mbar_wait_cluster(&ctl.xfull, it & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
             const int64_t kb8 = (t0 - 4 * static_cast<int>(rank)) / TB;
-            __half* spec = static_cast<__half*>(p.spec);
             const uint2* xw = reinterpret_cast<const uint2*>(xch);   // [slot][M/2]
-            for (int j = tid; j < M / 2; j += kThreads) {
-                const int ch = static_cast<int>(rank) * (M / 2) + j;
-                const uint2 r0 = xw[j], r1 = xw[M / 2 + j], i0 = xw[M + j], i1 = xw[3 * (M / 2) + j];
-                const uint32_t u[8] = {r0.x, r0.y, r1.x, r1.y, i0.x, i0.y, i1.x, i1.y};
-                st_global_v8(spec + (static_cast<int64_t>(ch) * ntb + kb8) * blk_elems + 2 * i * TB, u);
+            if constexpr (MODE == OUT_I8B) {
+                // slots 0, 1: (re 4 | im 4) of frames 0-3 and 4-7; one 16-byte piece per channel,
+                // consecutive channels' pieces contiguous within a channel quad
+                int8_t* spec = static_cast<int8_t*>(p.spec);
+                for (int j = tid; j < M / 2; j += kThreads) {
+                    const int ch = static_cast<int>(rank) * (M / 2) + j;
+                    const uint2 b0 = xw[j], b1 = xw[M / 2 + j];
+                    *reinterpret_cast<uint4*>(spec + i8q_piece(ch, kb8, i, ntb, p.n_in)) = make_uint4(b0.x, b1.x, b0.y, b1.y);
+                }
+            } else {
+                __half* spec = static_cast<__half*>(p.spec);
+                for (int j = tid; j < M / 2; j += kThreads) {
+                    const int ch = static_cast<int>(rank) * (M / 2) + j;
+                    const uint2 r0 = xw[j], r1 = xw[M / 2 + j], i0 = xw[M + j], i1 = xw[3 * (M / 2) + j];
+                    const uint32_t u[8] = {r0.x, r0.y, r1.x, r1.y, i0.x, i0.y, i1.x, i1.y};
+                    st_global_v8(spec + (static_cast<int64_t>(ch) * ntb + kb8) * blk_elems + 2 * i * TB, u);
+                }
             }
         }
     }
@@ -567,20 +599,6 @@ cudaError_t launch_t(const FeParams& p, cudaStream_t s) {
     }
     fengine_kernel<M, MODE><<<grid, kThreads, smem, s>>>(p);
     return cudaGetLastError();
-}
-
-template <int MODE>
-cudaError_t launch_mode(const FeParams& p, cudaStream_t s) {
-    switch (p.n_chan) {
-        case 32: return launch_t<32, MODE>(p, s);
-        case 64: return launch_t<64, MODE>(p, s);
-        case 128: return launch_t<128, MODE>(p, s);
-        case 256: return launch_t<256, MODE>(p, s);
-        case 512: return launch_t<512, MODE>(p, s);
-        case 1024: return launch_t<1024, MODE>(p, s);
-        case 2048: return launch_t<2048, MODE>(p, s);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 }  // namespace

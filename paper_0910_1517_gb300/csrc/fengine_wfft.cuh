@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
             const float g2 = p.ginc[a];
             const float2 g22 = make_float2(g2, g2);
             float scv[4];                      // requantisation scales of this thread's channels
-            if constexpr (MODE == OUT_I8 || MODE == OUT_F16 || MODE == OUT_I8B) {
+            if constexpr (MODE == OUT_F16 || MODE == OUT_I8B) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) scv[c] = p.scale[static_cast<int64_t>(i) * M + chs[c]];
             }
@@ -402,13 +402,8 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
 #pragma unroll
                     for (int l = 0; l < L; ++l) {
                         const float xr = comp(yr, l) * scv[c], xi = comp(yi, l) * scv[c];
-                        if constexpr (MODE == OUT_I8) {
-                            hr[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xr))));
-                            hi[l] = __int2half_rn(max(-127, min(127, __float2int_rn(xi))));
-                        } else {
-                            hr[l] = __float2half_rn(xr);
-                            hi[l] = __float2half_rn(xi);
-                        }
+                        hr[l] = __float2half_rn(xr);
+                        hi[l] = __float2half_rn(xi);
                     }
                     __half* o = static_cast<__half*>(p.spec) + (static_cast<int64_t>(chs[c]) * ntb + kb_run) * blk_elems +
                                 2 * i * TB;
@@ -508,7 +503,7 @@ cudaError_t launch_w(const FeParams& p, cudaStream_t s) {
 
 template <int MODE>
 cudaError_t launch_w_mode(const FeParams& p, cudaStream_t s) {
-    if constexpr (MODE == OUT_F32Q || MODE == OUT_I8B) {   // n_chan 32 .. 1024 only
+    if constexpr (MODE == OUT_F32Q || MODE == OUT_I8B) {   // n_chan 32 .. 1024 (int8 bytes: .. 2048)
         switch (p.n_chan) {
             case 32: return launch_w<32, MODE>(p, s);
             case 64: return launch_w<64, MODE>(p, s);
@@ -516,9 +511,12 @@ cudaError_t launch_w_mode(const FeParams& p, cudaStream_t s) {
             case 256: return launch_w<256, MODE>(p, s);
             case 512: return launch_w<512, MODE>(p, s);
             case 1024: return launch_w<1024, MODE>(p, s);
+            case 2048:   // 4-frame CTAs in cluster pairs: the kernel of fengine_impl.cuh
+                if constexpr (MODE == OUT_I8B) return launch_t<2048, MODE>(p, s);
+                return cudaErrorInvalidValue;
             default: return cudaErrorInvalidValue;
         }
-    }
+    } else {
     switch (p.n_chan) {
         case 32: return launch_w<32, MODE>(p, s);
         case 64: return launch_w<64, MODE>(p, s);
@@ -528,6 +526,7 @@ cudaError_t launch_w_mode(const FeParams& p, cudaStream_t s) {
         case 1024: return launch_w<1024, MODE>(p, s);
         case 2048: return launch_t<2048, MODE>(p, s);   // 4-frame CTAs: the kernel of fengine_impl.cuh
         default: return cudaErrorInvalidValue;
+    }
     }
 }
 

@@ -14,7 +14,6 @@ struct corr {
     int xmode = CORR_FP32, beam_avg = 1, max_delay = 2048;
     int polmode = CORR_POL_FULL;         // CORR_POL_SELF: only the n_pol products pp (npp = n_pol)
     bool last_quad = false;              // the last integration's FP32 spectra are in the channel-quad layout
-    bool last_i8b = false;               // the last integration's int8 spectra are bytes (OUT_I8B)
     int dev = 0, n_sm = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_done = nullptr, ev_aux = nullptr;
