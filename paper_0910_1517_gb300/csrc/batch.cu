@@ -62,12 +62,13 @@ int bfail(int code, const char* msg) { return fail_code(code, msg); }
 bool tc_mode(int xmode) { return xmode == CORR_I8 || xmode == CORR_F16; }
 
 // (channel, row block) items of sub-array q, for its one-entry table (sub index 0): a 256-row
-// Gram has two row blocks per channel, the wider one first.
+// Gram has two row blocks per channel; every channel's wide block first, as in the handle's own
+// list, so that the CTAs striding the list get both kinds.
 std::vector<int4> make_items(const corr_batch* b, int q) {
     std::vector<int4> items;
     const int R = 2 * b->h[q]->n_in, rbs = R > 128 ? 2 : 1;
-    for (int k = 0; k < b->h[q]->n_chan; ++k)
-        for (int r = 0; r < rbs; ++r) items.push_back(make_int4(0, k, r, 0));
+    for (int r = 0; r < rbs; ++r)
+        for (int k = 0; k < b->h[q]->n_chan; ++k) items.push_back(make_int4(0, k, r, 0));
     return items;
 }
 

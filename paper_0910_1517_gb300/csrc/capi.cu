@@ -504,9 +504,12 @@ int corr_create(corr_t** out, int n_ant, int n_pol, int n_fft, int n_int) {
 #undef CUB
     if (xengine_tc_supported(h->n_in)) {
         const int rb = 2 * h->n_in > 128 ? 2 : 1;
+        // row block outermost: the CTAs stride the list by the SM count, so interleaving a 256-row
+        // Gram's wide (rows 0-127 x 256 columns) and narrow items per channel would hand each CTA
+        // items of one kind only; wide ones first spreads both kinds over every CTA
         std::vector<int4> items;
-        for (int k = 0; k < h->n_chan; ++k)
-            for (int r = 0; r < rb; ++r) items.push_back(make_int4(0, k, r, 0));
+        for (int r = 0; r < rb; ++r)
+            for (int k = 0; k < h->n_chan; ++k) items.push_back(make_int4(0, k, r, 0));
         h->n_items = static_cast<int>(items.size());
         if (cudaMalloc(&h->d_xtab, sizeof(XtBatch)) != cudaSuccess ||
             cudaMalloc(&h->d_items, sizeof(int4) * items.size()) != cudaSuccess ||

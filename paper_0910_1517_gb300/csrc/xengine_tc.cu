@@ -397,12 +397,12 @@ __device__ __noinline__ void convert_stages(const XtBatch& t, Shared& sh, unsign
             unsigned char* dst = smem + os * kSlot2;
             if constexpr (kIn8) {
                 // the stage is [kb][R rows][8 frames] of int8: unit u = j R + r (8 bytes) becomes the
-                // 16-byte row r of K-block j of the fp16 operand tile
-                const int units = (frames / 8) * R;
+                // 16-byte row r of K-block j of the fp16 operand tile.  Only rows b0 .. R - 1 are
+                // converted: the second item of a 256-row Gram (rows and columns 128 .. R - 1)
+                // reads no others.
                 const unsigned char* src8 = reinterpret_cast<const unsigned char*>(src);
                 const __half2 bias = __float2half2_rn(1152.0f);
-#pragma unroll 4
-                for (int u = ct; u < units; u += kConvThreads) {
+                auto widen = [&](int u) {
                     const uint2 q = *reinterpret_cast<const uint2*>(src8 + 8 * u);
                     const uint32_t x[2] = {q.x ^ 0x80808080u, q.y ^ 0x80808080u};
                     uint32_t w[4];
@@ -413,6 +413,26 @@ __device__ __noinline__ void convert_stages(const XtBatch& t, Shared& sh, unsign
                         w[m] = *reinterpret_cast<const uint32_t*>(&v);
                     }
                     *reinterpret_cast<uint4*>(dst + 16 * u) = make_uint4(w[0], w[1], w[2], w[3]);
+                };
+                if (ig.b0 == 0) {
+                    const int units = (frames / 8) * R;
+#pragma unroll 4
+                    for (int u = ct; u < units; u += kConvThreads) widen(u);
+                } else {
+                    // rows b0 .. R - 1 of each K-block: index v = j (R - b0) + (r - b0), stepped incrementally
+                    const int Rs = R - ig.b0, units = (frames / 8) * Rs;
+                    int r = ct % Rs, j = ct / Rs;
+                    const int dr = kConvThreads % Rs, dj = kConvThreads / Rs;
+#pragma unroll 2
+                    for (int v = ct; v < units; v += kConvThreads) {
+                        widen(j * R + ig.b0 + r);
+                        r += dr;
+                        j += dj;
+                        if (r >= Rs) {
+                            r -= Rs;
+                            ++j;
+                        }
+                    }
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
