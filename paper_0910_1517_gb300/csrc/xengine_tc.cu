@@ -172,6 +172,9 @@ __device__ __forceinline__ void write_piece(const XtSub& s, const ItemGeo& ig, i
     const int n_bl = s.n_ant * (s.n_ant + 1) / 2, npp = s.self ? s.n_pol : s.n_pol * s.n_pol;
     const bool odd = row & 1;
     const int i = row >> 1;
+    // requantisation scales through the read-only path: the loads of every column pair can then
+    // issue together instead of one L2 round trip per output behind the previous stores
+    const float si = (!s.spec32 && i < s.n_in) ? __ldg(s.scale + static_cast<int64_t>(i) * s.n_chan + ig.k) : 1.0f;
 #pragma unroll
     for (int jh = 0; jh < W / 4; ++jh) {
         const uint32_t r0 = __shfl_xor_sync(0xffffffffu, odd ? run[2 * jh] : run[2 * jh + H], 1);
@@ -189,8 +192,7 @@ __device__ __forceinline__ void write_piece(const XtSub& s, const ItemGeo& ig, i
         const int bl = a * s.n_ant - a * (a - 1) / 2 + (a2 - a);
         const int64_t o = (static_cast<int64_t>(ig.k) * n_bl + bl) * npp + vis_prod(s.self, s.n_pol, pp, qq);
         if (s.exact) {
-            const float d = s.scale[static_cast<int64_t>(i) * s.n_chan + ig.k] *
-                            s.scale[static_cast<int64_t>(j) * s.n_chan + ig.k];
+            const float d = si * __ldg(s.scale + static_cast<int64_t>(j) * s.n_chan + ig.k);
             const int re = static_cast<int>(g_r0c0) + static_cast<int>(g_r1c1);
             const int im = static_cast<int>(g_r1c0) - static_cast<int>(g_r0c1);
             if (s.vis_int) s.vis_int[o] = make_int2(re, im);
@@ -201,8 +203,7 @@ __device__ __forceinline__ void write_piece(const XtSub& s, const ItemGeo& ig, i
             if (s.spec32) {
                 s.vis[o] = make_float2(re * s.descale, im * s.descale);
             } else {
-                const float d = s.scale[static_cast<int64_t>(i) * s.n_chan + ig.k] *
-                                s.scale[static_cast<int64_t>(j) * s.n_chan + ig.k];
+                const float d = si * __ldg(s.scale + static_cast<int64_t>(j) * s.n_chan + ig.k);
                 s.vis[o] = make_float2(re / d, im / d);
             }
         }
