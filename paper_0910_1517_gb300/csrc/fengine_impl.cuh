@@ -111,7 +111,7 @@ struct Epi {
     // frame blocks) trade halves of their channels through distributed shared memory, so that each
     // writes whole 32-byte pieces (8 frames x re, im) of its half of the channels
     static constexpr bool kPair = (M == 2048 && MODE != OUT_FP32);
-    static_assert(MODE != OUT_I8B || M == 2048, "int8 bytes from this kernel at n_chan 2048 only");
+    static_assert(M == 2048 && L == 4, "this kernel runs the 4096-point FFTs (4-frame CTAs); smaller ones run fengine_wfft.cuh's");
     static_assert(MODE != OUT_F32Q, "the channel-quad FP32 layout comes from the warp-FFT kernel");
     static_assert(L % TB == 0 || L < TB, "whole K-block runs, or part of one when F < TB");
     static constexpr int NP = kE / (2 * L);                // channel pairs per thread
@@ -200,15 +200,18 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
     const int64_t blk_elems = static_cast<int64_t>((MODE == OUT_FP32) ? rows_fp32(p.n_in) : R) * TB;
 
     // beam accumulators of this thread's L x 2 NP points: the incoherent sum over every input,
-    // and the coherent voltage sum of the current polarisation
-    float incr[L][2 * NP];
-    float2 cohr[L][2 * NP];
+    // and the coherent voltage sum of the current polarisation.  Frames go in pairs: a float2
+    // holds one component of frames 2j and 2j + 1, so one packed FP32x2 instruction does both.
+    constexpr int LP = L / 2;
+    float2 incr[LP][2 * NP];
+    float2 cre[LP][2 * NP], cim[LP][2 * NP];
 #pragma unroll
-    for (int l = 0; l < L; ++l)
+    for (int j = 0; j < LP; ++j)
 #pragma unroll
         for (int c = 0; c < 2 * NP; ++c) {
-            incr[l][c] = 0.0f;
-            cohr[l][c] = make_float2(0.0f, 0.0f);
+            incr[j][c] = make_float2(0.0f, 0.0f);
+            cre[j][c] = make_float2(0.0f, 0.0f);
+            cim[j][c] = make_float2(0.0f, 0.0f);
         }
 
     for (int m = tid; m < S::kTw; m += kThreads) tw2[m] = p.tw[m];
@@ -350,92 +353,57 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
             if (!mbar_wait_cluster(&ctl.xempty, it & 1, p.err, ERR_WAIT_STAGE)) abort_flag = 1;
         }
         if (live) {
-        // FP32 piece of input i in a K-block: granules m*PG .. m*PG + PG - 1 of row group G (PG = TB/2:
-        // the re row's TB/4 granules, then the im row's), XOR-placed by s = G & 7
-        constexpr int PG = TB / 2;
-        const int G = (2 * i) >> 3, s = G & 7;
-        const int pstart = G * 8 * TB + ((((i & 3) ^ (s / PG)) * PG) << 2);   // floats from the block start
-        // beams and the K-block store of channel c from its L frames
-        auto emit = [&](int c, const float2 (&yc)[L]) {
+        // component l of a frame-paired value: frame l (0 .. L - 1)
+        auto comp = [](const float2 (&v)[LP], int l) { return (l & 1) ? v[l >> 1].y : v[l >> 1].x; };
+        // beams and the K-block store of channel c from its L frames (yr, yi: frame pairs)
+        auto emit = [&](int c, const float2 (&yr)[LP], const float2 (&yi)[LP]) {
             const float2 w = wa[chs[c]];
+            const float2 wx = make_float2(w.x, w.x), wy = make_float2(w.y, w.y), nwy = make_float2(-w.y, -w.y);
+            const float2 g22 = make_float2(g2, g2);
 #pragma unroll
-            for (int l = 0; l < L; ++l) {
-                incr[l][c] += g2 * (yc[l].x * yc[l].x + yc[l].y * yc[l].y);
-                const float2 prev = (a == 0) ? make_float2(0.0f, 0.0f) : cohr[l][c];
-                cohr[l][c] = cadd(prev, cmul(w, yc[l]));
+            for (int j = 0; j < LP; ++j) {
+                incr[j][c] = __ffma2_rn(g22, __ffma2_rn(yr[j], yr[j], __fmul2_rn(yi[j], yi[j])), incr[j][c]);
+                if (a == 0) {
+                    cre[j][c] = make_float2(0.0f, 0.0f);
+                    cim[j][c] = make_float2(0.0f, 0.0f);
+                }
+                cre[j][c] = __ffma2_rn(nwy, yi[j], __ffma2_rn(wx, yr[j], cre[j][c]));
+                cim[j][c] = __ffma2_rn(wy, yr[j], __ffma2_rn(wx, yi[j], cim[j][c]));
                 if (a == p.n_ant - 1) {  // this polarisation's coherent sum is complete: detect
-                    float* bc = p.beams + (static_cast<int64_t>(p.n_int) + t0 + fg * L + l) * M + chs[c];
-                    const float pw = cohr[l][c].x * cohr[l][c].x + cohr[l][c].y * cohr[l][c].y;
-                    *bc = (pol == 0) ? pw : *bc + pw;
+                    const float2 pw = __ffma2_rn(cim[j][c], cim[j][c], __fmul2_rn(cre[j][c], cre[j][c]));
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        float* bc = p.beams + (static_cast<int64_t>(p.n_int) + t0 + fg * L + 2 * j + h) * M + chs[c];
+                        const float v = h ? pw.y : pw.x;
+                        *bc = (pol == 0) ? v : *bc + v;
+                    }
                 }
             }
-            // one 32-byte sector per (channel, input): rows 2i and 2i+1 over the L frames
             const int64_t blk = (static_cast<int64_t>(chs[c]) * ntb + kb_run) * blk_elems;
             if constexpr (MODE == OUT_FP32) {
-                float* spec = static_cast<float*>(p.spec);
-                if constexpr (TB == 4) {
-                    // 32-byte piece: granule slot j' = c ^ (s & 1) holds component c (0 re, 1 im)
-                    const bool flip = s & 1;
-                    uint32_t u[8];
+                // 4-frame K-blocks: one 32-byte piece per (channel, input), rows 2i and 2i + 1 as
+                // neighbouring granules, in the order the XOR placement of row group G gives them
+                const int G = (2 * i) >> 3;
+                const int pos = ((2 * i) & 7) ^ (G & 7);
+                const bool flip = pos & 1;
+                uint32_t u[8];
 #pragma unroll
-                    for (int l = 0; l < 4; ++l) {
-                        u[l] = __float_as_uint(flip ? yc[l].y : yc[l].x);
-                        u[4 + l] = __float_as_uint(flip ? yc[l].x : yc[l].y);
-                    }
-                    st_global_v8(spec + blk + pstart, u);
-                } else {
-                    // 64-byte piece: slot j' = (2 c + h) ^ (s & 3), h = frames 0-3 / 4-7.  Each lane pair
-                    // writes one piece per instruction (a full 64-byte request): the even lane slots 0-1
-                    // (component cA), the odd lane slots 2-3 (component 1 - cA); first the even lane's
-                    // channel, then the odd lane's, trading the component each needs by a shuffle.
-                    static_assert(TB == 8 && L == 8, "FP32 runs of 8 frames");
-                    const bool odd = kk & 1;
-                    const int cA = (s >> 1) & 1;
-                    const bool hswap = s & 1;
-                    const int chp = __shfl_xor_sync(0xffffffffu, chs[c], 1);
-                    const int csend = odd ? cA : 1 - cA;
-                    float mine[8], recv[8];
-#pragma unroll
-                    for (int l = 0; l < 8; ++l) {
-                        const float own_keep = (odd ? 1 - cA : cA) ? yc[l].y : yc[l].x;
-                        const float own_send = csend ? yc[l].y : yc[l].x;
-                        mine[l] = own_keep;
-                        recv[l] = __shfl_xor_sync(0xffffffffu, own_send, 1);
-                    }
-                    auto put = [&](int ch, const float (&v)[8]) {
-                        uint32_t u[8];
-#pragma unroll
-                        for (int l = 0; l < 4; ++l) {   // static indices: v stays in registers
-                            u[l] = __float_as_uint(hswap ? v[4 + l] : v[l]);
-                            u[4 + l] = __float_as_uint(hswap ? v[l] : v[4 + l]);
-                        }
-                        st_global_v8(spec + (static_cast<int64_t>(ch) * ntb + kb_run) * blk_elems + pstart + (odd ? 8 : 0), u);
-                    };
-                    // piece of the even lane's channel, then of the odd lane's: both lanes of a pair
-                    // issue the same two stores (selects, no divergence)
-                    float d0[8], d1[8];
-#pragma unroll
-                    for (int l = 0; l < 8; ++l) {
-                        d0[l] = odd ? recv[l] : mine[l];
-                        d1[l] = odd ? mine[l] : recv[l];
-                    }
-                    put(odd ? chp : chs[c], d0);
-                    put(odd ? chs[c] : chp, d1);
+                for (int l = 0; l < 4; ++l) {
+                    const uint32_t re = __float_as_uint(comp(yr, l)), im = __float_as_uint(comp(yi, l));
+                    u[l] = flip ? im : re;
+                    u[4 + l] = flip ? re : im;
                 }
+                st_global_v8(static_cast<float*>(p.spec) + blk + G * 32 + (pos & ~1) * 4, u);
             } else if constexpr (MODE == OUT_I8B) {
                 // int8 bytes (the channel-quad piece i8q_piece: 8 re then 8 im bytes): this CTA's
                 // 4 frames go, as one 8-byte word (re 4 | im 4), to slot `rank` of the exchange
                 // buffer of the pair's CTA that writes channel ch (rank 0: channels < M/2)
-                static_assert(L == 4 && kPair, "int8 bytes of 4-frame CTAs in cluster pairs");
                 uint32_t wv[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {   // h = 0 re, 1 im
                     int qv[4];
 #pragma unroll
-                    for (int l = 0; l < 4; ++l) {
-                        const float xq = (h ? yc[l].y : yc[l].x) * scv[c];
-                        qv[l] = max(-127, min(127, __float2int_rn(xq)));
-                    }
+                    for (int l = 0; l < 4; ++l) qv[l] = max(-127, min(127, __float2int_rn((h ? comp(yi, l) : comp(yr, l)) * scv[c])));
                     wv[h] = __byte_perm(__byte_perm(qv[0], qv[1], 0x0040), __byte_perm(qv[2], qv[3], 0x0040), 0x5410);
                 }
                 const int ch = chs[c];
@@ -446,74 +414,83 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
                 else
                     st_async_v2(cluster_map(d, owner), wv[0], wv[1], peer_xfull);
             } else {
-                __half hr[L], hi[L];
+                // fp16: the 4-frame halves of the 8-frame run go into the exchange buffer of the CTA
+                // of the pair that writes this channel (rank 0: channels < M/2): slot 2c + rank
+                // (c = 0 re, 1 im), word ch % (M/2)
+                __half hr[4], hi[4];
 #pragma unroll
-                for (int l = 0; l < L; ++l) {
-                    const float xr = yc[l].x * scv[c], xi = yc[l].y * scv[c];
-                    hr[l] = __float2half_rn(xr);
-                    hi[l] = __float2half_rn(xi);
+                for (int l = 0; l < 4; ++l) {
+                    hr[l] = __float2half_rn(comp(yr, l) * scv[c]);
+                    hi[l] = __float2half_rn(comp(yi, l) * scv[c]);
                 }
-                __half* o = static_cast<__half*>(p.spec) + blk + 2 * i * TB + (t0 + fg * L) % TB;
-                if constexpr (L == 8) {
-                    uint32_t u[8];
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        u[m] = pack_half2(hr[2 * m], hr[2 * m + 1]);
-                        u[4 + m] = pack_half2(hi[2 * m], hi[2 * m + 1]);
-                    }
-                    st_global_v8(o, u);
+                const int ch = chs[c];
+                const uint32_t owner = ch < M / 2 ? 0u : 1u;
+                unsigned char* dre = xch + (static_cast<size_t>(rank) * (M / 2) + ch % (M / 2)) * 8;
+                unsigned char* dim = dre + static_cast<size_t>(M) * 8;
+                const uint2 vr = make_uint2(pack_half2(hr[0], hr[1]), pack_half2(hr[2], hr[3]));
+                const uint2 vi = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
+                if (owner == rank) {
+                    *reinterpret_cast<uint2*>(dre) = vr;
+                    *reinterpret_cast<uint2*>(dim) = vi;
                 } else {
-                    // 4-frame halves of the 8-frame run: into the exchange buffer of the CTA of the
-                    // pair that writes this channel (rank 0: channels < M/2), at frame offset 4 rank
-                    static_assert(L == 4 && kPair, "fp16 runs of 4 frames only in cluster pairs");
-                    (void)o;
-                    const int ch = chs[c];
-                    const uint32_t owner = ch < M / 2 ? 0u : 1u;
-                    // slot 2c + rank (c = 0 re, 1 im), word ch % (M/2)
-                    unsigned char* dre = xch + (static_cast<size_t>(rank) * (M / 2) + ch % (M / 2)) * 8;
-                    unsigned char* dim = dre + static_cast<size_t>(M) * 8;
-                    const uint2 vr = make_uint2(pack_half2(hr[0], hr[1]), pack_half2(hr[2], hr[3]));
-                    const uint2 vi = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
-                    if (owner == rank) {
-                        *reinterpret_cast<uint2*>(dre) = vr;
-                        *reinterpret_cast<uint2*>(dim) = vi;
-                    } else {
-                        st_async_v2(cluster_map(dre, owner), vr.x, vr.y, peer_xfull);
-                        st_async_v2(cluster_map(dim, owner), vi.x, vi.y, peer_xfull);
-                    }
+                    st_async_v2(cluster_map(dre, owner), vr.x, vr.y, peer_xfull);
+                    st_async_v2(cluster_map(dim, owner), vi.x, vi.y, peer_xfull);
                 }
             }
         };
+        // ---- real split and Eq. 2 phasor.  With zk = Z[k], zm = Z[M - k]:
+        //   2 X[k] = E + Q, 2 X[M - k] = conj(E - Q), E = zk + conj(zm), Q = (-i W_N^k)(zk - conj(zm));
+        //   Y = X pf fr = ((2 X) (pf / 2)) fr.  Pair 0: 2 X[0] = 2 (Re + Im of Z[0]), 2 X[M/2] = 2 conj(Z[M/2]).
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             const int k = chs[2 * q], kc = chs[2 * q + 1];
-            const float2 wk = twN[k];
-            const float2 pk = pfa[k], pm = pfa[kc];
-            float2 yk[L], ym[L];
+            const float2 w = twN[k];
+            const float2 wnx = make_float2(w.y, w.y), wny = make_float2(-w.x, -w.x), nwny = make_float2(w.x, w.x);
+            const float2 hk = pfa[k], hm = pfa[kc];
+            const float2 pkx = make_float2(0.5f * hk.x, 0.5f * hk.x), pky = make_float2(0.5f * hk.y, 0.5f * hk.y);
+            const float2 npky = make_float2(-0.5f * hk.y, -0.5f * hk.y);
+            const float2 pmx = make_float2(0.5f * hm.x, 0.5f * hm.x), pmy = make_float2(0.5f * hm.y, 0.5f * hm.y);
+            const float2 npmy = make_float2(-0.5f * hm.y, -0.5f * hm.y);
+            float2 ykr[LP], yki[LP], ymr[LP], ymi[LP];
 #pragma unroll
-            for (int l = 0; l < L; ++l) {
-                const int fl = fg * L + l;
-                const float2* Xl = X + fl * P::PADM;
-                const float2 zk = Xl[pad16(k)];
-                const float2 zm = Xl[pad16(kc)];
-                float2 xk, xmk;
+            for (int j = 0; j < LP; ++j) {
+                const int f0 = fg * L + 2 * j;
+                const float2* X0 = X + f0 * P::PADM;
+                const float2* X1 = X0 + P::PADM;
+                const float2 a0 = X0[pad16(k)], a1 = X1[pad16(k)], b0 = X0[pad16(kc)], b1 = X1[pad16(kc)];
+                const float2 zkr = make_float2(a0.x, a1.x), zki = make_float2(a0.y, a1.y);
+                const float2 zmr = make_float2(b0.x, b1.x), zmi = make_float2(b0.y, b1.y);
+                float2 xkr, xki, xmr, xmi;     // 2 X[k], 2 X[M - k]
                 if (k == 0) {
-                    xk = make_float2(zk.x + zk.y, 0.0f);       // DC
-                    xmk = make_float2(zm.x, -zm.y);            // channel M/2 (zm = z[M/2])
+                    xkr = __fmul2_rn(make_float2(2.0f, 2.0f), __fadd2_rn(zkr, zki));     // DC
+                    xki = make_float2(0.0f, 0.0f);
+                    xmr = __fmul2_rn(make_float2(2.0f, 2.0f), zmr);                     // channel M/2
+                    xmi = __fmul2_rn(make_float2(-2.0f, -2.0f), zmi);
                 } else {
-                    const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-                    const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-                    const float2 wo = cmul(wk, o);
-                    xk = cadd(e, wo);
-                    const float2 d = csub(e, wo);
-                    xmk = make_float2(d.x, -d.y);
+                    const float2 er = __fadd2_rn(zkr, zmr), ei = psub(zki, zmi);
+                    const float2 dr = psub(zkr, zmr), di = __fadd2_rn(zki, zmi);
+                    const float2 qr = __ffma2_rn(nwny, di, __fmul2_rn(wnx, dr));
+                    const float2 qi = __ffma2_rn(wny, dr, __fmul2_rn(wnx, di));
+                    xkr = __fadd2_rn(er, qr);
+                    xki = __fadd2_rn(ei, qi);
+                    xmr = psub(er, qr);
+                    xmi = psub(qi, ei);
                 }
-                const float2 fr = fra[fl];
-                yk[l] = cmul(xk, cmul(pk, fr));
-                ym[l] = cmul(xmk, cmul(pm, fr));
+                // u = (2 X) (pf / 2), then y = u fr
+                const float2 ukr = __ffma2_rn(npky, xki, __fmul2_rn(pkx, xkr));
+                const float2 uki = __ffma2_rn(pky, xkr, __fmul2_rn(pkx, xki));
+                const float2 umr = __ffma2_rn(npmy, xmi, __fmul2_rn(pmx, xmr));
+                const float2 umi = __ffma2_rn(pmy, xmr, __fmul2_rn(pmx, xmi));
+                const float2 r0 = fra[f0], r1 = fra[f0 + 1];
+                const float2 frr = make_float2(r0.x, r1.x), fri = make_float2(r0.y, r1.y);
+                const float2 nfri = make_float2(-r0.y, -r1.y);
+                ykr[j] = __ffma2_rn(uki, nfri, __fmul2_rn(ukr, frr));
+                yki[j] = __ffma2_rn(uki, frr, __fmul2_rn(ukr, fri));
+                ymr[j] = __ffma2_rn(umi, nfri, __fmul2_rn(umr, frr));
+                ymi[j] = __ffma2_rn(umi, frr, __fmul2_rn(umr, fri));
             }
-            emit(2 * q, yk);
-            emit(2 * q + 1, ym);
+            emit(2 * q, ykr, yki);
+            emit(2 * q + 1, ymr, ymi);
         }
         }  // live
         if constexpr (kPair) {
@@ -552,7 +529,7 @@ __device__ __forceinline__ void fengine_cta(const FeParams& p, int block, FeCtl&
             for (int l = 0; l < L; ++l)
 #pragma unroll
                 for (int c = 0; c < 2 * NP; ++c)
-                    p.beams[static_cast<int64_t>(t0 + fg * L + l) * M + chs[c]] = incr[l][c];
+                    p.beams[static_cast<int64_t>(t0 + fg * L + l) * M + chs[c]] = (l & 1) ? incr[l >> 1][c].y : incr[l >> 1][c].x;
         }
     } else if (tid == 0) {
         // copies issued ahead of an aborted iteration must land before the CTA exits: the
