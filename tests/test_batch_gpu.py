@@ -114,6 +114,43 @@ def test_batch_int8_exact_matches_oracle_and_single_handle(env):
             corr.corr_destroy(h)
 
 
+def test_batch_replays_with_new_sample_buffers(env):
+    """Later calls may pass other sample buffers: the graph's F-engine nodes take the new pointers
+    (the 4096-point sub-array, whose F-engine runs in 2-CTA clusters, captures the graph again),
+    and switching back to the first buffers gives their results again."""
+    torch, corr, orc = env
+    hs, streams, xs = _handles(torch, corr, [711, 712, 713, 714, 715], corr.CORR_I8)
+    st = torch.cuda.current_stream()
+    b = corr.corr_batch_create(hs)
+    try:
+        corr.corr_batch_integrate_device(b, [x for x, _ in xs], n_avail=[n for _, n in xs], stream=st)
+        first = [corr.corr_read_vis_int(h) for h in hs]
+        news = [make_config(2, n_ant=s.n_ant, n_pol=s.n_pol, n_fft=s.n_fft, n_int=s.n_int, seed=s.recipe["seed"] + 60)
+                for s in streams]
+        xs2 = [_dev(torch, s2.x) for s2 in news]        # other allocations: other pointers
+        assert all(a.data_ptr() != c.data_ptr() for (a, _), (c, _) in zip(xs, xs2))
+        corr.corr_batch_integrate_device(b, [x for x, _ in xs2], n_avail=[n for _, n in xs2], stream=st)
+        for h, s, s2, v in zip(hs, streams, news, first):
+            _check_exact(corr, orc, h, s2)
+            assert not np.array_equal(corr.corr_read_vis_int(h), v)
+            # the new buffers were read: the FP64 spectra of the new samples (the handle's own delay
+            # model), requantised with the GPU's scales, give the same visibilities up to rare flips
+            ch = CHANS[:3]
+            Y = orc.fengine(s2.x, s.n_ant, s.n_pol, s.n_fft, s.n_int, s.delay, s.phi0, s.rate, chans=ch)
+            _, sc = corr.corr_read_requant(h, 0, 0, s.n_int)
+            sc64 = sc[:, ch].astype(np.float64)
+            _, Vq = orc.xint(orc.requant(Y, sc64), sc64, s.n_ant, s.n_pol)
+            Vg = corr.corr_read_visibilities(h).astype(np.complex128)[ch]
+            assert vis_norm_error(Vg, Vq, s.n_ant, s.n_pol) < 2e-3, (s.n_ant, s.n_fft)
+        corr.corr_batch_integrate_device(b, [x for x, _ in xs], n_avail=[n for _, n in xs], stream=st)
+        for h, v in zip(hs, first):
+            assert np.array_equal(corr.corr_read_vis_int(h), v)
+    finally:
+        corr.corr_batch_destroy(b)
+        for h in hs:
+            corr.corr_destroy(h)
+
+
 def test_batch_autotune_keeps_results(env):
     torch, corr, orc = env
     hs, streams, xs = _handles(torch, corr, [801, 802, 803, 804, 805], corr.CORR_I8)
