@@ -6,14 +6,14 @@
 // halves of the work in flight at once:
 //   * a CTA owns F = 8192 / M consecutive frames and walks over every input (the beams need
 //     every antenna of a frame in one CTA);
-//   * warps 0-7 (the FFT group, 104 registers a thread) transform the frames of input it:
+//   * warps 0-7 (the FFT group, 104 or 80 registers a thread, WRegs) transform the frames of input it:
 //     the M-point complex FFT of a frame (z[n] = x[2n] + i x[2n+1], M = 32 P) is a four-step
 //     FFT inside one warp -- lane l takes column n = l + 32 m of each of the warp's G = 32 / P
 //     frames, P-point DFTs in registers straight from the int8 staging buffer, the twiddle
 //     W_M^(l k1), one transpose through the warp's own shared-memory region (__syncwarp), then
 //     lane (g, k1) a 32-point DFT in registers: Z[k1 + P k2] -- and leave the results in the
 //     region in natural order;
-//   * warps 8-15 (the epilogue group, 152 registers a thread) meanwhile take input it - 1: each
+//   * warps 8-15 (the epilogue group, 152 or 176 registers a thread) meanwhile take input it - 1: each
 //     thread owns 8 frames of two channel pairs (k, M - k) for the real split, the Eq. 2 phasor,
 //     the beams (accumulated in its registers over all inputs) and the K-block stores;
 //   * the regions, the antenna tables and the staging buffer are double-buffered; mbarriers
@@ -30,7 +30,19 @@ namespace {
 constexpr int kWThreads = 512;
 constexpr int kWFftWarps = 8;                  // warps 0-7: FFT group (warpgroups 0, 1)
 constexpr int kWEpiThreads = 256;              // warps 8-15: epilogue group (warpgroups 2, 3)
-constexpr int kWRegFft = 104, kWRegEpi = 152;  // 256 x 104 + 256 x 152 = 512 x 128 registers
+constexpr int kWRegs = 128;                    // registers a thread at launch (512 x 128)
+
+// Registers a thread of each group after setmaxnreg, for 256 + 256 threads = 512 x kWRegs: the
+// 1024-point FFT group takes 104 (with 80 the int8 GMRT-scale kernel ran 15 % slower, though
+// spill-free); below that 80 / 176, which removes the 60-200 bytes a thread the smaller sizes'
+// epilogues spilled with 104 / 152 (measured 4-7 % faster at 256 and 512 points)
+template <int M, int MODE>
+struct WRegs {
+    static constexpr bool kWide = M == 1024;
+    static constexpr int FFT = kWide ? 104 : 80;
+    static constexpr int EPI = kWide ? 152 : 176;
+    static_assert(FFT * kWFftWarps * 32 + EPI * kWEpiThreads == kWRegs * kWThreads, "the launch's registers, split");
+};
 
 template <int M>
 struct WPlan {
@@ -117,7 +129,7 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
 
     if (warp < kWFftWarps) {
         // ================================================================ FFT group
-        reg_dealloc<kWRegFft>();
+        reg_dealloc<WRegs<M, MODE>::FFT>();
         // lane 0 of warp 0 issues the bulk copy of the F frames of input `it` (offset by its
         // integer delay); bytes past the last 16-byte boundary are copied by the lanes only when
         // rounding the copy up would read past the row's readable samples
@@ -241,7 +253,7 @@ __global__ void __launch_bounds__(kWThreads, 1) fengine_w_kernel(const FeParams 
         }
     } else {
         // ================================================================ epilogue group
-        reg_alloc<kWRegEpi>();
+        reg_alloc<WRegs<M, MODE>::EPI>();
         const int e = tid - kWFftWarps * 32;
         const int fg = e / P::SLOTS, ps = e % P::SLOTS;
         const bool live = fg * L < n_fr;      // n_fr is a multiple of 8: whole frame groups
@@ -492,7 +504,7 @@ cudaError_t launch_w(const FeParams& p, cudaStream_t s) {
     cudaFuncAttributes fa{};
     cudaError_t e = cudaFuncGetAttributes(&fa, fengine_w_kernel<M, MODE>);
     if (e != cudaSuccess) return e;
-    if (fa.numRegs * kWThreads != kWRegFft * kWFftWarps * 32 + kWRegEpi * kWEpiThreads) return cudaErrorInvalidConfiguration;
+    if (fa.numRegs != kWRegs) return cudaErrorInvalidConfiguration;
     e = cudaFuncSetAttribute(fengine_w_kernel<M, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem));
     if (e != cudaSuccess) return e;
