@@ -744,7 +744,31 @@ def run_ours(args, world, rank, local_rank):
             cm = (np.arange(N_ANT) < COH_ANTENNAS).astype(np.uint8)
             res = {f"beams_{nb}": run_multibeam_leg(corr, torch, sm, xm, ldm, cm, corr.CORR_FP32TC, 10, None,
                                                     peaks(), n_beams=nb) for nb in (16, 64)}
-        if args.leg in ("e2e4bit", "multibeam"):
+        elif args.leg == "blank":                        # the voltage blanker alone, on the GMRT-scale step
+            sb = make_config(2, seed=slice_seed(rank), n_int=N_INT)
+            ldb = ((sb.x.shape[1] + 15) // 16) * 16 + 16
+            xb = torch.zeros((N_IN, ldb), dtype=torch.int8, device="cuda")
+            xb[:, :sb.x.shape[1]] = torch.from_numpy(sb.x).cuda()
+            cb = (np.arange(N_ANT) < COH_ANTENNAS).astype(np.uint8)
+            hp = corr.corr_create(N_ANT, N_POL, N_FFT, N_INT)   # the same step unblanked, for its F-engine stage
+            try:
+                corr.corr_set_delays(hp, sb.delay, sb.phi0, sb.rate)
+                corr.corr_set_beam_weights(hp, None, None, None, cb)
+                corr.corr_set_mode(hp, corr.CORR_FP32TC, 0, 1)
+                st = torch.cuda.current_stream()
+                for j in range(3):
+                    corr.corr_integrate_device(hp, xb, n_avail=ldb, g0=j * N_INT, stream=st)
+                torch.cuda.synchronize()
+                corr.corr_set_timing(hp, 1)
+                for j in range(max(args.steps, 1)):
+                    corr.corr_integrate_device(hp, xb, n_avail=ldb, g0=(3 + j) * N_INT, stream=st)
+                torch.cuda.synchronize()
+                t_plain, n_plain = corr.corr_stage_times(hp)
+            finally:
+                corr.corr_destroy(hp)
+            res = {"voltage_blanker": run_blank_leg(corr, torch, sb, xb, ldb, cb, corr.CORR_FP32TC, max(args.steps, 1),
+                                                    t_plain / max(n_plain, 1))}
+        if args.leg in ("e2e4bit", "multibeam", "blank"):
             pass
         else:
             res = run_batch_leg(args, corr, torch, rank) if args.leg == "batched" else \
@@ -928,9 +952,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--no-extras", action="store_true",
                     help="time only the FP32 step (no precision forms, no end-to-end leg); for profiling runs")
-    ap.add_argument("--leg", choices=("all", "batched", "rfi", "dedisp", "multibeam", "e2e4bit"), default="all",
-                    help="run one extra leg alone: batched sub-arrays, learned RFI, dedispersion, phased beams or the "
-                         "4-bit ADC streaming path (profiling runs)")
+    ap.add_argument("--leg", choices=("all", "batched", "rfi", "dedisp", "multibeam", "e2e4bit", "blank"), default="all",
+                    help="run one extra leg alone: batched sub-arrays, learned RFI, dedispersion, phased beams, the "
+                         "4-bit ADC streaming path or the voltage blanker (profiling runs)")
     ap.add_argument("--xmode", choices=("fp32tc", "fp32"), default="fp32tc",
                     help="form of the timed step: FP32 on the tensor cores (default) or the plain CUDA-core FP32 form")
     ap.add_argument("--n-int", type=int, default=N_INT,
