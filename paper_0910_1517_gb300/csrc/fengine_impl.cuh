@@ -1,7 +1,7 @@
-// fengine_impl.cuh -- the F-engine kernel body (templates) and its launchers, included by
-// fengine.cu.
+// fengine_impl.cuh -- the F-engine kernel for 4096-point FFTs (n_chan 2048; smaller FFTs run
+// the warp-FFT kernel of fengine_wfft.cuh) and its launcher, included by fengine_wfft.cuh.
 //
-// One CTA owns a block of F consecutive frames (F * n_chan = 8192 complex
+// One CTA owns a block of F = 4 consecutive frames (F * n_chan = 8192 complex
 // channel-frames) and walks over every input (antenna x polarisation) in turn:
 //   1. the F frames of input i, offset by its integer delay D_a (Sec. 2.1,
 //      Sec. 2.3.2: the read pointer is moved, no data is shifted), arrive in
@@ -17,9 +17,10 @@
 //      (sum of g_a e^{i theta} Y, detected once per polarisation) accumulate in
 //      the registers of the thread that owns each (frame, channel) point, since
 //      this CTA sees every antenna of its frames (Sec. 2.2) -- no atomics;
-//   5. each thread writes its (channel, input) pieces of the K-block layout the
-//      X-engines read (FP32, or requantised int8-valued / FP16 values for the
-//      tensor-core X-engine) straight from registers.
+//   5. each thread writes its (channel, input) pieces of the layout the X-engines
+//      read: FP32 4-frame K-blocks straight from registers, or -- FP16 values or
+//      requantised int8 bytes, in 8-frame pieces -- through the 2-CTA cluster
+//      exchange with the CTA of the neighbouring 4 frames.
 #pragma once
 #include <cuda_fp16.h>
 
