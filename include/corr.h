@@ -279,8 +279,9 @@ int corr_stage_times(corr_t* h, float* ms4, int* n);
  * runs in 2-CTA clusters -- 4096-point FFTs in CORR_I8 / CORR_F16 -- captures
  * the graph again when its pointers change).
  * corr_batch_tune times every allowed X-engine stage size per sub-array on the
- * spectra of the last batch integration, keeps the fastest (ks_out, ms_out per
- * sub-array, either may be NULL) and rebuilds the graph. */
+ * spectra of the last batch integration and keeps the fastest in the handle
+ * (ks_out, ms_out per sub-array, either may be NULL); later batch integrations
+ * use it (the X-engine tables are refreshed on every call). */
 typedef struct corr_batch corr_batch_t;
 int corr_batch_create(corr_batch_t** out, int n_sub, corr_t* const* subs);
 int corr_batch_destroy(corr_batch_t* b);
