@@ -29,11 +29,12 @@ __host__ __device__ constexpr int vis_prod(int self, int n_pol, int p, int q) { 
 cudaError_t launch_xengine_fp32(const XParams& p, int n_sm, cudaStream_t s);
 
 // tcgen05 X-engine: G = A A^T per channel on the tensor cores, TMEM accumulators, over a
-// table of sub-arrays and a cost-ordered list of (sub-array, channel, row block) items.
+// table of sub-arrays and a list of (sub-array, channel, row block) items that the persistent
+// CTAs stride (every wide item before the narrow ones, so that both kinds reach every CTA).
 constexpr int kMaxSubX = 8;
 constexpr int kStageMaxBytes = 32768;        // bytes of one operand stage (ks/8 K-blocks x 2 n_in rows x 16 B)
 constexpr int kStage2Bytes = 32768;          // FP32 form: bytes of one FP32 stage (ks x rows_fp32(n_in) x 4 B)
-struct alignas(64) XtSub {
+struct alignas(128) XtSub {   // (the tensor map's own alignment)
     // FP32 form with quad = 1: the spectra are in the channel-quad layout (f32q_piece) and each
     // stage is one TMA copy through this 5-D tensor map over (16 floats, channel in quad, input,
     // K-block, quad), box (16, 1, n_in, ks / 8, 1); it lands [kb][2 n_in rows][8 frames]
